@@ -1,0 +1,342 @@
+"""Throughput of the fused ternary colour-gradient LBM step (D2Q9) on GB300.
+
+Workload: the 2048x2048 periodic compound double droplet (fluid-3 core radius
+200 inside a fluid-2 shell radius 400 in a fluid-1 matrix, tau = (0.6, 0.7,
+0.9) for viscosity ratio 1:2:4, sigma_12/13/23 = 0.01/0.012/0.005,
+beta^0 = 0.7), FP32 plain storage.  A "step" is one lattice time step of the
+whole grid (one launch of the fused kernel).  The metric is MLUPS (million
+lattice-node updates per second), reported with the HBM roofline fraction
+(216 algorithmic bytes per node update: 27 FP32 populations read and written).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun as independent replicas, one per GPU (the method
+has no exchange step on one grid per GPU; weak scaling).  --impl reference
+times the FP64 CPU oracle on the host cores on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_NODE = 216            # 27 pops x 4 B read + 27 x 4 B written
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD = ("compound double droplet 2048x2048 periodic, fluid-3 core r=200 in fluid-2 shell r=400, "
+            "tau=(0.6,0.7,0.9), sigma12/13/23=0.01/0.012/0.005, beta0=0.7, FP32 populations")
+STEP_KERNEL = "fused_step_kernel"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("lbm3_step.cu", "lbm3_internal.h"):
+        with open(os.path.join(ROOT, "paper_1808_08555_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "fused_step_compound_2048_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        if d.get("source_hash") == kernel_source_hash():
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def reduce_max(x: float, ws: int, device) -> float:
+    """Maximum of x over all ranks (the slowest rank's time)."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(ws: int, nodes: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: node updates of all ranks over the slowest time."""
+    return ws * nodes * steps / seconds / 1e6
+
+
+def make_case(size: int = 2048):
+    from paper_1808_08555_gb300 import workloads as W
+    return W.case_compound_2048() if size == 2048 else W.case_compound_scaled(size)
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    from paper_1808_08555_gb300 import build as B
+    if rank == 0 or ws == 1:
+        B.build()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    from paper_1808_08555_gb300 import lbm3 as L
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case = make_case(args.size)
+    p = L.Params(case.nx, case.ny, tau=case.tau, sigma=case.sigma, beta0=case.beta0)
+    nodes = case.nx * case.ny
+    sim = L.Simulation(p, device=dev)
+    stream = sim.stream
+    sim.init(case.rho)
+    sim.step(args.warmup)
+    sim.sync()
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def max_over_ranks(x: float) -> float:
+        return reduce_max(x, ws, dev)
+
+    # ---------------- device-resident throughput (inputs already in HBM)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    sim.sync()
+    barrier()
+    ms = max_over_ranks(ms)
+    m, mom = sim.mass()
+
+    # ---------------- end to end through the C ABI with host buffers
+    host_rho = torch.from_numpy(case.rho).pin_memory()
+    outs = {k: torch.empty(sh, dtype=torch.float64).pin_memory() for k, sh in
+            (("rho", (3, case.ny, case.nx)), ("ux", (case.ny, case.nx)), ("uy", (case.ny, case.nx)),
+             ("p", (case.ny, case.nx)))}
+    barrier()
+    t0 = time.perf_counter()
+    L.lbm3_init(sim.ctx, host_rho)
+    L.lbm3_step(sim.ctx, args.steps)
+    L.lbm3_fields(sim.ctx, outs["rho"], outs["ux"], outs["uy"], outs["p"])
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    e2e_s = max_over_ranks(e2e_s)
+    sim.close()
+
+    if rank != 0:
+        return None
+    total_updates = ws * nodes * args.steps
+    value = aggregate_mlups(ws, nodes, args.steps, ms / 1e3)
+    per_launch_s = ms / 1e3 / args.steps
+    achieved = BYTES_PER_NODE * nodes / per_launch_s / 1e9
+    peak, peak_kind = hbm_peak()
+    line = {
+        "metric": "ternary D2Q9 MLUPS (fused colour-gradient step, 2048^2 compound droplet)",
+        "value": round(value, 2),
+        "unit": "MLUPS",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seedless analytic droplet fields, Eq. 21 tanh edges)",
+        "config": {"workload": WORKLOAD, "nx": case.nx, "ny": case.ny, "nodes_per_step": nodes,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2: two 453 MB population buffers vs 129 MB L2"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": recorded_traffic(),
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                     else "fallback 6.8 TB/s", "bytes_per_node": BYTES_PER_NODE,
+                     "kernel": STEP_KERNEL},
+        "e2e": {"value": round(total_updates / e2e_s / 1e6, 2), "unit": "MLUPS",
+                "h2d_bytes_per_step": round(3 * nodes * 8 / args.steps, 1),
+                "d2h_bytes_per_step": round(6 * nodes * 8 / args.steps, 1),
+                "note": "lbm3_init from pinned host rho, K steps, lbm3_fields to pinned host; bytes amortised over K"},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "checks": {"mass": [float(x) for x in m], "momentum": [float(x) for x in mom]},
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(case, args.cpu_steps)
+    return line
+
+
+def cpu_baseline(case, steps: int):
+    """The FP64 oracle as it stands, single-threaded on a host core, on a
+    bounded sample of the same workload: `steps` steps of the full grid."""
+    import oracle as O
+    op = O.Params(case.nx, case.ny, tau=case.tau, sigma=case.sigma, beta0=case.beta0)
+    f = O.init(op, case.rho)
+    t0 = time.perf_counter()
+    O.step(op, f, steps)
+    dt = time.perf_counter() - t0
+    return {"value": round(case.nx * case.ny * steps / dt / 1e6, 4), "unit": "MLUPS", "cores": 1,
+            "kind": "oracle", "sample": f"{steps} steps of the full {case.nx}x{case.ny} grid ({dt:.1f} s)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    case = make_case(args.size)
+    import oracle as O
+    O.build()
+    op = O.Params(case.nx, case.ny, tau=case.tau, sigma=case.sigma, beta0=case.beta0)
+    f = O.init(op, case.rho)
+    sample = max(1, args.cpu_steps // 2)
+    for _ in range(min(args.warmup, 1)):
+        f = O.step(op, f, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        f = O.step(op, f, sample)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = case.nx * case.ny * sample * len(times) / total / 1e6
+    return {
+        "impl": "reference",
+        "metric": "ternary D2Q9 MLUPS (fused colour-gradient step, 2048^2 compound droplet)",
+        "value": round(value, 4), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": case.nx, "ny": case.ny},
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"each step = {sample} lattice step(s) of the full {case.nx}x{case.ny} grid"},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--size", type=int, default=2048,
+                    help="grid edge; other than 2048 scales the droplet radii (profiling only)")
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 3 if args.impl == "reference" else 5000
+    if args.warmup is None:
+        args.warmup = 3 if args.impl == "reference" else 50
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        if backend == "nccl":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    try:
+        line = run_reference(args, ws, rank) if args.impl == "reference" else run_ours(args, ws, rank, local)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+    finally:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * lbm3.h -- C ABI of the GB300 ternary colour-gradient lattice Boltzmann
+ * library (D2Q9).  The method is that of Yu, Liu, Liang & Zhang, "A versatile
+ * lattice Boltzmann model for immiscible ternary fluid flows" (arXiv
+ * 1808.08555), Sec. 2.  One call of lbm3_step advances every node of a
+ * periodic nx x ny grid by one time step: colour gradients (Eq. fd1), the
+ * N-phase interfacial force (Eq. 11) applied with Guo's forcing (Eq. 5)
+ * inside a BGK collision with harmonic-mean viscosity (Eqs. 1-3, uk1, vis_1,
+ * tau), recolouring with the segregation parameters of Eqs. 18-20 (Eq. 6),
+ * and streaming of the three colour populations (Eq. 30).
+ *
+ * Conventions shared by every call
+ *  - Colours k = 0, 1, 2 are the paper's r, g, b (fluids 1, 2, 3).
+ *    D2Q9 directions i = 0..8: e0 = (0,0), e1 = (1,0), e2 = (0,1),
+ *    e3 = (-1,0), e4 = (0,-1), e5 = (1,1), e6 = (-1,1), e7 = (-1,-1),
+ *    e8 = (1,-1).
+ *  - Node (x, y), 0 <= x < nx, 0 <= y < ny, x fastest; periodic in x and y.
+ *  - Host-side arrays are FP64, C order: colour densities rho[3][ny][nx],
+ *    populations f[3][9][ny][nx] (post-streaming, i.e. the f_{i,k}(x,t) from
+ *    which rho_k = sum_i f_{i,k}).  They always belong to the caller and are
+ *    copied.  Where a call takes `on_device`, a non-zero value means the
+ *    pointer is a CUDA device pointer of the same layout on the context's
+ *    device; the copy is then device-to-device.
+ *  - Every call returns an lbm3_status and never aborts the process.  On an
+ *    error the text is in lbm3_last_error(ctx).  A NULL context gives
+ *    LBM3_EINVAL.
+ *  - All device work is ordered on the CUDA stream given to lbm3_create.
+ *    lbm3_step is asynchronous; the calls that return host data
+ *    synchronise that stream.
+ */
+#ifndef LBM3_H
+#define LBM3_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm3_ctx lbm3_ctx;
+
+typedef enum {
+  LBM3_OK = 0,
+  LBM3_EINVAL = 1,   /* bad argument or parameter */
+  LBM3_ENOMEM = 2,   /* device allocation failed */
+  LBM3_ECUDA = 3,    /* a CUDA call failed; text in lbm3_last_error */
+  LBM3_ESTATE = 4,   /* call out of order (e.g. step before init) */
+  LBM3_ENUMERIC = 5, /* NaN or Inf found in the state */
+  LBM3_ETIMEOUT = 6  /* a bounded in-kernel wait gave up; results invalid */
+} lbm3_status;
+
+typedef enum {
+  LBM3_FP32 = 0 /* populations stored as FP32, FP32 arithmetic */
+} lbm3_storage;
+
+typedef enum {
+  LBM3_BETA_PAPER = 0,    /* Eqs. 18-20: beta^0 [1 + min(35 r g b / rho^3, 1) g(X_kl)] */
+  LBM3_BETA_FU = 1,       /* Eq. fu: beta_kl = beta^0 */
+  LBM3_BETA_SPENCER = 2,  /* Eq. 16 */
+  LBM3_BETA_LECLAIRE = 3  /* Eq. 17 */
+} lbm3_beta_form;
+
+typedef enum {
+  LBM3_RECOLOR_COSINE = 0, /* Eq. 6 with n_kl.e_i/|e_i| (matches the paper's xi = 1.5831, Sec. 3.1) */
+  LBM3_RECOLOR_LITERAL = 1 /* Eq. 6 with n_kl.e_i exactly as printed */
+} lbm3_recolor_form;
+
+/* Problem statement (Sec. 2).  Validation in lbm3_create:
+ * nx >= 4 and a multiple of 4, ny >= 1, nx*ny < 2^31; tau[k] > 0.5;
+ * rho0[k] > 0; sigma_kl > 0; 0 < beta0 <= 1; forms and storage in range. */
+typedef struct {
+  int32_t nx, ny;
+  double tau[3];      /* per-fluid relaxation time; nu_k = (tau_k - 1/2)/3 (Eq. tau) */
+  double rho0[3];     /* pure-fluid densities rho_k^0 of Eq. 15 */
+  double sigma12, sigma13, sigma23; /* interfacial tensions (Eq. 11) */
+  double beta0;       /* reference segregation parameter (0.7 in the paper) */
+  int32_t beta_form;  /* lbm3_beta_form */
+  int32_t recolor_form; /* lbm3_recolor_form */
+  int32_t storage;    /* lbm3_storage */
+  int32_t reserved;   /* must be 0 */
+} lbm3_params;
+
+/* Bytes of ONE population buffer for these parameters (27 * nx * ny * 4 for
+ * FP32).  Writes *bytes.  No device work. */
+lbm3_status lbm3_buffer_bytes(const lbm3_params* p, size_t* bytes);
+
+/* Validate p and create a context bound to the current CUDA device and to
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
+ * context allocates a small reduction scratch area (< 1 MiB).  It allocates
+ * the two population buffers itself unless lbm3_bind_buffers is called
+ * before the first lbm3_init / lbm3_set_populations.  *out receives the
+ * context (NULL on failure). */
+lbm3_status lbm3_create(const lbm3_params* p, void* cuda_stream, lbm3_ctx** out);
+
+/* Use caller-owned device memory for the two population buffers (each at
+ * least lbm3_buffer_bytes bytes, 256-byte aligned, distinct).  The caller keeps
+ * ownership and must keep both alive until lbm3_destroy.  Only allowed before
+ * the state is first set (else LBM3_ESTATE). */
+lbm3_status lbm3_bind_buffers(lbm3_ctx* ctx, void* dev_f0, void* dev_f1, size_t bytes_each);
+
+/* Set the state at t = 0 from colour densities rho[3][ny][nx] (FP64; every
+ * rho_k >= 0 and rho_r + rho_g + rho_b > 0, else LBM3_EINVAL -- checked on
+ * the host for host input, by a device check for device input): populations
+ * at rest, f_{i,k} = w_i rho_k (the paper does not state an initialisation;
+ * this is the per-colour equilibrium of Eq. 3 with u = 0). */
+lbm3_status lbm3_init(lbm3_ctx* ctx, const double* rho, int on_device);
+
+/* Set the state to given post-streaming populations f[3][9][ny][nx] (FP64,
+ * rounded to the storage precision).  Resets the step counter to 0.  Used
+ * for checkpoint restore and for tests from non-equilibrium states. */
+lbm3_status lbm3_set_populations(lbm3_ctx* ctx, const double* f, int on_device);
+
+/* Tuning: rows of the grid each CTA of the fused step kernel marches over
+ * (0 = automatic: about one full wave of CTAs over the GPU's SMs; otherwise
+ * 1..ny).  Results do not depend on it beyond FP32 rounding being identical
+ * (the arithmetic per node is the same); only speed does. */
+lbm3_status lbm3_set_rows_per_cta(lbm3_ctx* ctx, int32_t rows);
+
+/* Advance n >= 0 time steps (Sec. 2: collision, recolouring, streaming),
+ * asynchronously on the context's stream. */
+lbm3_status lbm3_step(lbm3_ctx* ctx, int64_t n);
+
+/* Macroscopic fields at the current time t: rho[3][ny][nx] = rho_k
+ * (after Eq. 30), ux/uy[ny][nx] from Eq. uk1 (including the F_s/2 term),
+ * p[ny][nx] = rho c_s^2 = rho/3 (the paper gives no pressure formula).
+ * Any output pointer may be NULL.  Synchronises the stream when on_device is
+ * 0.  Returns LBM3_ETIMEOUT if an earlier kernel reported a timed-out wait. */
+lbm3_status lbm3_fields(lbm3_ctx* ctx, double* rho, double* ux, double* uy, double* p, int on_device);
+
+/* Post-streaming populations f[3][9][ny][nx] at time t, widened to FP64. */
+lbm3_status lbm3_populations(lbm3_ctx* ctx, double* f, int on_device);
+
+/* FP64 reductions of the current state (synchronises): mass[k] = sum_x rho_k,
+ * mom[0..1] = sum_x sum_i f_i e_i (lattice momentum; the F_s/2 term of
+ * Eq. uk1 sums to zero on a periodic grid).  Either pointer may be NULL.
+ * Returns LBM3_ENUMERIC if a sum is NaN or Inf. */
+lbm3_status lbm3_mass(lbm3_ctx* ctx, double* mass, double* mom);
+
+/* Wait for the context's stream and report device-side errors (timed-out
+ * waits) recorded since the last check. */
+lbm3_status lbm3_sync(lbm3_ctx* ctx);
+
+/* Number of steps taken since the last init / set_populations. */
+int64_t lbm3_time(const lbm3_ctx* ctx);
+
+/* Free the context and everything it allocated (bound buffers are not
+ * freed).  Synchronises its stream first.  NULL is accepted. */
+lbm3_status lbm3_destroy(lbm3_ctx* ctx);
+
+/* Text of the last error on this context ("" if none); a static string for
+ * ctx == NULL.  Valid until the next call on the context. */
+const char* lbm3_last_error(const lbm3_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM3_H */

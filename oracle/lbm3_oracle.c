@@ -23,8 +23,16 @@
  *    interface-thickness result (Eq. 21 with k = 0.1504 from Eq. k, Sec. 3.1)
  *    belongs to the cosine form n_kl . e_i / |e_i|.  Both are provided
  *    (recolor_form 0 = cosine form, the default; 1 = as printed).
- *  - the unit normal n_kl = G_kl/|G_kl| is taken as zero where |G_kl| <= 1e-12,
- *    and so is the tension tensor term |G|(I - n n), which vanishes with |G|.
+ *  - n_kl = G_kl/|G_kl| is undefined where G_kl = 0, and the recolouring
+ *    term of Eq. 6 jumps there whenever rho_k rho_l/rho is not negligible
+ *    (e.g. at a droplet centre or at the saddle of phi between two nearby
+ *    droplets), where rounding noise in G then decides the direction.  The
+ *    recolouring uses n_kl = G_kl / max(|G_kl|, 0.1 phi_k phi_l), which
+ *    equals the paper's unit normal wherever a k-l interface exists (there
+ *    |G_kl| is about 1.26 phi_k phi_l across the whole tanh profile of Eq. 21)
+ *    and goes to zero continuously, with a bounded gain, where G_kl
+ *    vanishes.  The tension tensor
+ *    term |G|(I - n n) vanishes with |G| and is taken as 0 for |G| <= 1e-15.
  *  - the derivatives inside F_s (Eq. 11) are the isotropic stencil of
  *    Eq. fd1 applied to phi_k = rho_k/rho, and then again to each component
  *    of the tensor inside the divergence.
@@ -44,7 +52,8 @@ static const double WT[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
                              1.0 / 9.0,  1.0 / 9.0,  1.0 / 36.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 static const double CS2 = 1.0 / 3.0;
-static const double GEPS = 1e-12;
+static const double GEPS = 1e-15;   /* |G| below which the tension tensor term is 0 */
+static const double NDELTA = 1e-1;  /* recolouring normal: n = G / max(|G|, NDELTA phi_k phi_l) */
 
 typedef struct {
   int nx, ny;
@@ -334,8 +343,10 @@ static void orc_step_once(const orc_params* p, double* f, double* fn) {
             if (l == k) continue;
             double gx = G[((k * 3 + l) * 2 + 0) * N + n], gy = G[((k * 3 + l) * 2 + 1) * N + n];
             double mag = sqrt(gx * gx + gy * gy);
-            if (mag <= GEPS) continue;
-            double en = (gx * EX[i] + gy * EY[i]) / mag;
+            double den = NDELTA * (rloc[k] / r) * (rloc[l] / r);
+            if (mag > den) den = mag;
+            if (den <= 1e-30) continue;  /* both fluids absent: no recolouring term */
+            double en = (gx * EX[i] + gy * EY[i]) / den;
             if (p->recolor_form == 0 && i != 0) en /= sqrt((double)(EX[i] * EX[i] + EY[i] * EY[i]));
             int a = k < l ? k : l, b = k < l ? l : k;
             int q = (a == 0 && b == 1) ? 0 : (a == 0 ? 1 : 2);

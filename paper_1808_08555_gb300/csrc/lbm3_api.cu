@@ -1,0 +1,505 @@
+// Host side of liblbm3: the C ABI declared in include/lbm3.h.
+//
+// The context owns (or borrows) two FP32 population buffers used in
+// ping-pong: one holds the current state (post-collision populations stored
+// where they were produced, read by the next step's pull), the other is the
+// target of the next step and, between steps, doubles as staging memory for
+// host input/output, so no extra full-grid allocation is made.
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/lbm3.h"
+#include "lbm3_internal.h"
+
+using lbm3::StepArgs;
+
+struct lbm3_ctx {
+  lbm3_params p{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  int occ = 0;
+  float* buf[2] = {nullptr, nullptr};
+  bool owns_bufs = false;
+  int cur = 0;
+  bool state_set = false;
+  int64_t t = 0;
+  size_t buf_bytes = 0;
+  // small scratch: reduction partials, reduction output, error word, check flag
+  unsigned char* scratch = nullptr;
+  double* partial = nullptr;
+  double* red_out = nullptr;
+  unsigned int* err = nullptr;
+  unsigned int* bad = nullptr;
+  int red_blocks = 1;
+  int rows_override = 0;
+  StepArgs base{};
+  std::string msg;
+};
+
+namespace {
+
+const char* kNullCtxMsg = "lbm3: NULL context";
+
+lbm3_status fail(lbm3_ctx* c, lbm3_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->msg = buf;
+  return st;
+}
+
+lbm3_status cuda_fail(lbm3_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, LBM3_ECUDA, "lbm3: %s: %s", where, cudaGetErrorString(e));
+}
+
+#define LBM3_CUDA(ctx, call)                                 \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+size_t nodes(const lbm3_params& p) { return static_cast<size_t>(p.nx) * static_cast<size_t>(p.ny); }
+
+lbm3_status validate(const lbm3_params* p, std::string* why) {
+  char b[256];
+  if (!p) {
+    *why = "lbm3: NULL params";
+    return LBM3_EINVAL;
+  }
+  if (p->nx < 4 || p->nx % 4 != 0 || p->ny < 1) {
+    std::snprintf(b, sizeof b, "lbm3: grid %d x %d: nx must be a multiple of 4 and >= 4, ny >= 1", p->nx, p->ny);
+    *why = b;
+    return LBM3_EINVAL;
+  }
+  if (static_cast<double>(p->nx) * p->ny >= 2147483648.0) {
+    *why = "lbm3: nx*ny must be below 2^31";
+    return LBM3_EINVAL;
+  }
+  for (int k = 0; k < 3; ++k) {
+    if (!(p->tau[k] > 0.5) || !std::isfinite(p->tau[k])) {
+      std::snprintf(b, sizeof b, "lbm3: tau[%d] = %g must be > 0.5", k, p->tau[k]);
+      *why = b;
+      return LBM3_EINVAL;
+    }
+    if (!(p->rho0[k] > 0.0) || !std::isfinite(p->rho0[k])) {
+      std::snprintf(b, sizeof b, "lbm3: rho0[%d] = %g must be > 0", k, p->rho0[k]);
+      *why = b;
+      return LBM3_EINVAL;
+    }
+  }
+  const double s[3] = {p->sigma12, p->sigma13, p->sigma23};
+  for (int q = 0; q < 3; ++q)
+    if (!(s[q] > 0.0) || !std::isfinite(s[q])) {
+      *why = "lbm3: every sigma_kl must be > 0";
+      return LBM3_EINVAL;
+    }
+  if (!(p->beta0 > 0.0 && p->beta0 <= 1.0)) {
+    *why = "lbm3: beta0 must be in (0, 1]";
+    return LBM3_EINVAL;
+  }
+  if (p->beta_form < 0 || p->beta_form > 3 || p->recolor_form < 0 || p->recolor_form > 1 ||
+      p->storage != LBM3_FP32 || p->reserved != 0) {
+    *why = "lbm3: beta_form, recolor_form, storage or reserved out of range";
+    return LBM3_EINVAL;
+  }
+  return LBM3_OK;
+}
+
+// Eq. 20
+double g_of_X(double X) {
+  if (X < -1.0) return 1.0;
+  if (X < 0.0) return 1.0 - std::sqrt(1.0 - X * X);
+  if (X <= 1.0) return std::sqrt(1.0 - X * X) - 1.0;
+  return -1.0;
+}
+
+// Host-side constants of the step: 1/nu_k, the C_kl prefactor, sigmas, the
+// per-pair beta coefficients and the recolouring direction weights.
+void fill_constants(const lbm3_params& p, StepArgs* a) {
+  const double s[3] = {p.sigma12, p.sigma13, p.sigma23};
+  const int pk[3] = {0, 0, 1}, pl[3] = {1, 2, 2};
+  auto sig = [&](int k, int l) {
+    const int lo = k < l ? k : l, hi = k < l ? l : k;
+    return lo == 0 ? (hi == 1 ? s[0] : s[1]) : s[2];
+  };
+  double X[3], ang[3];
+  bool tri = true;
+  for (int q = 0; q < 3; ++q) {
+    const int k = pk[q], l = pl[q], m = 3 - k - l;
+    const double smk = sig(m, k), sml = sig(m, l), skl = sig(k, l);
+    X[q] = (smk * smk + sml * sml - skl * skl) / (2.0 * smk * sml);  // Eq. 18
+    tri = tri && std::fabs(X[q]) < 1.0;
+    ang[q] = std::acos(X[q] < -1.0 ? -1.0 : (X[q] > 1.0 ? 1.0 : X[q]));
+  }
+  double A = 0.0, h[3] = {0.0, 0.0, 0.0};
+  switch (p.beta_form) {
+    case LBM3_BETA_PAPER:  // Eqs. 19-20
+      A = 35.0;
+      for (int q = 0; q < 3; ++q) h[q] = g_of_X(X[q]);
+      break;
+    case LBM3_BETA_FU:  // Eq. fu
+      break;
+    case LBM3_BETA_SPENCER:  // Eq. 16; beta^0 everywhere without a Neumann triangle
+      if (tri) {
+        A = 27.0;
+        h[1] = std::sin(ang[2]) - 1.0;
+        h[2] = std::sin(ang[1]) - 1.0;
+      }
+      break;
+    case LBM3_BETA_LECLAIRE:  // Eq. 17; beta^0 everywhere without a Neumann triangle
+      if (tri) {
+        A = 35.0;
+        int qm = 0;
+        for (int q = 1; q < 3; ++q)
+          if (ang[q] > ang[qm]) qm = q;
+        const double pi = std::acos(-1.0);
+        for (int q = 0; q < 3; ++q) h[q] = q == qm ? 0.0 : std::sin(pi - ang[qm] - ang[q]) - 1.0;
+      }
+      break;
+  }
+  for (int k = 0; k < 3; ++k) a->inv_nu[k] = static_cast<float>(3.0 / (p.tau[k] - 0.5));
+  for (int q = 0; q < 3; ++q) {
+    a->cpair[q] = static_cast<float>(1e6 / (p.rho0[pk[q]] * p.rho0[pl[q]]));
+    a->sigma[q] = static_cast<float>(s[q]);
+    a->beta_h[q] = static_cast<float>(h[q]);
+  }
+  a->beta0 = static_cast<float>(p.beta0);
+  a->beta_A = static_cast<float>(A);
+  for (int i = 0; i < 9; ++i) {
+    const double w = lbm3::wt(i);
+    const double len = std::sqrt(static_cast<double>(lbm3::ex(i) * lbm3::ex(i) + lbm3::ey(i) * lbm3::ey(i)));
+    a->wrec[i] = static_cast<float>((p.recolor_form == LBM3_RECOLOR_COSINE && i != 0) ? w / len : w);
+  }
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int now = -1;
+    if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+  }
+};
+
+lbm3_status ensure_buffers(lbm3_ctx* c) {
+  if (c->buf[0]) return LBM3_OK;
+  void* a = nullptr;
+  void* b = nullptr;
+  if (cudaMalloc(&a, c->buf_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, LBM3_ENOMEM, "lbm3: cannot allocate %zu bytes for populations", c->buf_bytes);
+  }
+  if (cudaMalloc(&b, c->buf_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(a);
+    return fail(c, LBM3_ENOMEM, "lbm3: cannot allocate %zu bytes for populations", c->buf_bytes);
+  }
+  c->buf[0] = static_cast<float*>(a);
+  c->buf[1] = static_cast<float*>(b);
+  c->owns_bufs = true;
+  return LBM3_OK;
+}
+
+// Read and clear the device error word (synchronises the stream).
+lbm3_status check_device_errors(lbm3_ctx* c) {
+  LBM3_CUDA(c, cudaStreamSynchronize(c->stream));
+  unsigned int e = 0;
+  LBM3_CUDA(c, cudaMemcpy(&e, c->err, sizeof e, cudaMemcpyDeviceToHost));
+  if (e) {
+    LBM3_CUDA(c, cudaMemset(c->err, 0, sizeof e));
+    return fail(c, LBM3_ETIMEOUT, "lbm3: a bounded wait inside the step kernel timed out (error word %u)", e);
+  }
+  return LBM3_OK;
+}
+
+void tiling(const lbm3_ctx* c, int* rows, int* grid) {
+  const int nstrips = (c->p.nx + lbm3::kTX - 1) / lbm3::kTX;
+  int H = c->rows_override;
+  if (H <= 0) {
+    const int resident = (c->occ > 0 ? c->occ : 1) * (c->num_sms > 0 ? c->num_sms : 1);
+    int chunks = resident / nstrips;
+    if (chunks < 1) chunks = 1;
+    H = (c->p.ny + chunks - 1) / chunks;
+    if (H < 8) H = 8;
+  }
+  if (H > c->p.ny) H = c->p.ny;
+  const int chunks = (c->p.ny + H - 1) / H;
+  *rows = H;
+  *grid = nstrips * chunks;
+}
+
+StepArgs args_for(const lbm3_ctx* c, const float* fin, float* fout, int* grid) {
+  StepArgs a = c->base;
+  a.fin = fin;
+  a.fout = fout;
+  int rows = 0;
+  tiling(c, &rows, grid);
+  a.rows_per_cta = rows;
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm3_status lbm3_buffer_bytes(const lbm3_params* p, size_t* bytes) {
+  std::string why;
+  if (!bytes) return LBM3_EINVAL;
+  lbm3_status st = validate(p, &why);
+  if (st != LBM3_OK) return st;
+  *bytes = 27 * nodes(*p) * sizeof(float);
+  return LBM3_OK;
+}
+
+lbm3_status lbm3_create(const lbm3_params* p, void* cuda_stream, lbm3_ctx** out) {
+  if (!out) return LBM3_EINVAL;
+  *out = nullptr;
+  std::string why;
+  lbm3_status st = validate(p, &why);
+  if (st != LBM3_OK) {
+    std::fprintf(stderr, "%s\n", why.c_str());
+    return st;
+  }
+  lbm3_ctx* c = new (std::nothrow) lbm3_ctx();
+  if (!c) return LBM3_ENOMEM;
+  c->p = *p;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->buf_bytes = 27 * nodes(*p) * sizeof(float);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = lbm3::step_configure();
+  if (e == cudaSuccess) e = static_cast<cudaError_t>(lbm3::step_occupancy(&c->occ));
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "lbm3_create: %s\n", cudaGetErrorString(e));
+    delete c;
+    return LBM3_ECUDA;
+  }
+  c->red_blocks = lbm3::reduce_blocks(static_cast<int>(nodes(*p)));
+  const size_t scratch_bytes = static_cast<size_t>(c->red_blocks) * 5 * sizeof(double) + 8 * sizeof(double) + 256;
+  void* sp = nullptr;
+  if (cudaMalloc(&sp, scratch_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return LBM3_ENOMEM;
+  }
+  c->scratch = static_cast<unsigned char*>(sp);
+  c->partial = reinterpret_cast<double*>(c->scratch);
+  c->red_out = c->partial + static_cast<size_t>(c->red_blocks) * 5;
+  c->err = reinterpret_cast<unsigned int*>(c->red_out + 5);
+  c->bad = c->err + 1;
+  if (cudaMemset(c->scratch, 0, scratch_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(sp);
+    delete c;
+    return LBM3_ECUDA;
+  }
+  StepArgs& a = c->base;
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nstrips = (p->nx + lbm3::kTX - 1) / lbm3::kTX;
+  a.err = c->err;
+  fill_constants(*p, &a);
+  *out = c;
+  return LBM3_OK;
+}
+
+lbm3_status lbm3_bind_buffers(lbm3_ctx* c, void* f0, void* f1, size_t bytes_each) {
+  if (!c) return LBM3_EINVAL;
+  if (c->state_set || c->buf[0]) return fail(c, LBM3_ESTATE, "lbm3_bind_buffers: buffers already set");
+  if (!f0 || !f1 || f0 == f1) return fail(c, LBM3_EINVAL, "lbm3_bind_buffers: need two distinct buffers");
+  if (bytes_each < c->buf_bytes)
+    return fail(c, LBM3_EINVAL, "lbm3_bind_buffers: %zu bytes < required %zu", bytes_each, c->buf_bytes);
+  if ((reinterpret_cast<uintptr_t>(f0) | reinterpret_cast<uintptr_t>(f1)) & 255u)
+    return fail(c, LBM3_EINVAL, "lbm3_bind_buffers: buffers must be 256-byte aligned");
+  c->buf[0] = static_cast<float*>(f0);
+  c->buf[1] = static_cast<float*>(f1);
+  c->owns_bufs = false;
+  return LBM3_OK;
+}
+
+lbm3_status lbm3_init(lbm3_ctx* c, const double* rho, int on_device) {
+  if (!c) return LBM3_EINVAL;
+  if (!rho) return fail(c, LBM3_EINVAL, "lbm3_init: NULL rho");
+  DeviceGuard g(c->device);
+  lbm3_status st = ensure_buffers(c);
+  if (st != LBM3_OK) return st;
+  const size_t N = nodes(c->p);
+  const double* src = rho;
+  if (!on_device) {
+    for (size_t n = 0; n < N; ++n) {
+      const double a = rho[n], b = rho[N + n], d = rho[2 * N + n];
+      if (!(std::isfinite(a) && std::isfinite(b) && std::isfinite(d) && a >= 0.0 && b >= 0.0 && d >= 0.0 &&
+            a + b + d > 0.0))
+        return fail(c, LBM3_EINVAL, "lbm3_init: rho at node %zu is invalid (needs rho_k >= 0, sum > 0)", n);
+    }
+    double* staging = reinterpret_cast<double*>(c->buf[c->cur ^ 1]);
+    LBM3_CUDA(c, cudaMemcpyAsync(staging, rho, 3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    src = staging;
+  } else {
+    LBM3_CUDA(c, cudaMemsetAsync(c->bad, 0, sizeof(unsigned int), c->stream));
+    LBM3_CUDA(c, lbm3::launch_check_rho(rho, static_cast<int>(N), c->bad, c->stream));
+    unsigned int bad = 0;
+    LBM3_CUDA(c, cudaMemcpyAsync(&bad, c->bad, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+    LBM3_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (bad) return fail(c, LBM3_EINVAL, "lbm3_init: device rho has a node with rho_k < 0, NaN or sum 0");
+  }
+  LBM3_CUDA(c, lbm3::launch_init_from_rho(src, c->buf[c->cur], c->p.nx, c->p.ny, c->stream));
+  if (!on_device) LBM3_CUDA(c, cudaStreamSynchronize(c->stream));  // staging reused next
+  c->state_set = true;
+  c->t = 0;
+  return LBM3_OK;
+}
+
+lbm3_status lbm3_set_populations(lbm3_ctx* c, const double* f, int on_device) {
+  if (!c) return LBM3_EINVAL;
+  if (!f) return fail(c, LBM3_EINVAL, "lbm3_set_populations: NULL f");
+  DeviceGuard g(c->device);
+  lbm3_status st = ensure_buffers(c);
+  if (st != LBM3_OK) return st;
+  const size_t N = nodes(c->p);
+  if (on_device) {
+    LBM3_CUDA(c, lbm3::launch_set_planes(f, c->buf[c->cur], c->p.nx, c->p.ny, 0, 27, c->stream));
+  } else {
+    double* staging = reinterpret_cast<double*>(c->buf[c->cur ^ 1]);
+    for (int p0 = 0; p0 < 27; p0 += 13) {
+      const int np = p0 + 13 <= 27 ? 13 : 27 - p0;
+      LBM3_CUDA(c, cudaMemcpyAsync(staging, f + static_cast<size_t>(p0) * N, np * N * sizeof(double),
+                                   cudaMemcpyHostToDevice, c->stream));
+      LBM3_CUDA(c, lbm3::launch_set_planes(staging, c->buf[c->cur], c->p.nx, c->p.ny, p0, np, c->stream));
+      LBM3_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+  }
+  c->state_set = true;
+  c->t = 0;
+  return LBM3_OK;
+}
+
+lbm3_status lbm3_set_rows_per_cta(lbm3_ctx* c, int32_t rows) {
+  if (!c) return LBM3_EINVAL;
+  if (rows < 0 || rows > c->p.ny) return fail(c, LBM3_EINVAL, "lbm3_set_rows_per_cta: %d not in [0, ny]", rows);
+  c->rows_override = rows;
+  return LBM3_OK;
+}
+
+lbm3_status lbm3_step(lbm3_ctx* c, int64_t n) {
+  if (!c) return LBM3_EINVAL;
+  if (n < 0) return fail(c, LBM3_EINVAL, "lbm3_step: n = %lld < 0", static_cast<long long>(n));
+  if (!c->state_set) return fail(c, LBM3_ESTATE, "lbm3_step: state not initialised");
+  DeviceGuard g(c->device);
+  for (int64_t s = 0; s < n; ++s) {
+    int grid = 0;
+    StepArgs a = args_for(c, c->buf[c->cur], c->buf[c->cur ^ 1], &grid);
+    LBM3_CUDA(c, lbm3::launch_step(a, grid, lbm3::MODE_STEP, c->stream));
+    c->cur ^= 1;
+    c->t += 1;
+  }
+  return LBM3_OK;
+}
+
+lbm3_status lbm3_fields(lbm3_ctx* c, double* rho, double* ux, double* uy, double* pr, int on_device) {
+  if (!c) return LBM3_EINVAL;
+  if (!c->state_set) return fail(c, LBM3_ESTATE, "lbm3_fields: state not initialised");
+  DeviceGuard g(c->device);
+  const size_t N = nodes(c->p);
+  int grid = 0;
+  StepArgs a = args_for(c, c->buf[c->cur], nullptr, &grid);
+  double* staging = reinterpret_cast<double*>(c->buf[c->cur ^ 1]);
+  if (on_device) {
+    a.out_rho = rho;
+    a.out_ux = ux;
+    a.out_uy = uy;
+    a.out_p = pr;
+  } else {
+    a.out_rho = rho ? staging : nullptr;
+    a.out_ux = ux ? staging + 3 * N : nullptr;
+    a.out_uy = uy ? staging + 4 * N : nullptr;
+    a.out_p = pr ? staging + 5 * N : nullptr;
+  }
+  LBM3_CUDA(c, lbm3::launch_step(a, grid, lbm3::MODE_FIELDS, c->stream));
+  if (!on_device) {
+    if (rho) LBM3_CUDA(c, cudaMemcpyAsync(rho, staging, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (ux) LBM3_CUDA(c, cudaMemcpyAsync(ux, staging + 3 * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (uy) LBM3_CUDA(c, cudaMemcpyAsync(uy, staging + 4 * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (pr) LBM3_CUDA(c, cudaMemcpyAsync(pr, staging + 5 * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return check_device_errors(c);
+  }
+  return LBM3_OK;
+}
+
+lbm3_status lbm3_populations(lbm3_ctx* c, double* f, int on_device) {
+  if (!c) return LBM3_EINVAL;
+  if (!f) return fail(c, LBM3_EINVAL, "lbm3_populations: NULL f");
+  if (!c->state_set) return fail(c, LBM3_ESTATE, "lbm3_populations: state not initialised");
+  DeviceGuard g(c->device);
+  const size_t N = nodes(c->p);
+  if (on_device) {
+    LBM3_CUDA(c, lbm3::launch_get_planes(c->buf[c->cur], f, c->p.nx, c->p.ny, 0, 27, c->stream));
+    return LBM3_OK;
+  }
+  double* staging = reinterpret_cast<double*>(c->buf[c->cur ^ 1]);
+  for (int p0 = 0; p0 < 27; p0 += 13) {
+    const int np = p0 + 13 <= 27 ? 13 : 27 - p0;
+    LBM3_CUDA(c, lbm3::launch_get_planes(c->buf[c->cur], staging, c->p.nx, c->p.ny, p0, np, c->stream));
+    LBM3_CUDA(c, cudaMemcpyAsync(f + static_cast<size_t>(p0) * N, staging, np * N * sizeof(double),
+                                 cudaMemcpyDeviceToHost, c->stream));
+    LBM3_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return check_device_errors(c);
+}
+
+lbm3_status lbm3_mass(lbm3_ctx* c, double* mass, double* mom) {
+  if (!c) return LBM3_EINVAL;
+  if (!c->state_set) return fail(c, LBM3_ESTATE, "lbm3_mass: state not initialised");
+  DeviceGuard g(c->device);
+  LBM3_CUDA(c, lbm3::launch_reduce(c->buf[c->cur], static_cast<int>(nodes(c->p)), c->partial, c->red_blocks,
+                                   c->red_out, c->stream));
+  double h[5];
+  LBM3_CUDA(c, cudaMemcpyAsync(h, c->red_out, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  lbm3_status st = check_device_errors(c);
+  if (st != LBM3_OK) return st;
+  if (mass)
+    for (int k = 0; k < 3; ++k) mass[k] = h[k];
+  if (mom) {
+    mom[0] = h[3];
+    mom[1] = h[4];
+  }
+  for (int j = 0; j < 5; ++j)
+    if (!std::isfinite(h[j])) return fail(c, LBM3_ENUMERIC, "lbm3_mass: non-finite sum (NaN/Inf in the state)");
+  return LBM3_OK;
+}
+
+lbm3_status lbm3_sync(lbm3_ctx* c) {
+  if (!c) return LBM3_EINVAL;
+  DeviceGuard g(c->device);
+  return check_device_errors(c);
+}
+
+int64_t lbm3_time(const lbm3_ctx* c) { return c ? c->t : -1; }
+
+lbm3_status lbm3_destroy(lbm3_ctx* c) {
+  if (!c) return LBM3_OK;
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  if (c->owns_bufs) {
+    cudaFree(c->buf[0]);
+    cudaFree(c->buf[1]);
+  }
+  cudaFree(c->scratch);
+  cudaGetLastError();
+  delete c;
+  return LBM3_OK;
+}
+
+const char* lbm3_last_error(const lbm3_ctx* c) { return c ? c->msg.c_str() : kNullCtxMsg; }
+
+}  // extern "C"

@@ -1,0 +1,188 @@
+// Auxiliary kernels of liblbm3: state set-up and read-out in the pull layout,
+// and the FP64 mass/momentum reductions.
+//
+// The library stores, between steps, the post-collision populations
+// f^ddagger_{i,k}(x) at the node x where they were produced (before
+// streaming).  The post-streaming state the paper works with (Eq. 30) is then
+// f_{i,k}(x, t) = stored_{i,k}(x - e_i); these kernels translate between the
+// two.
+
+#include <cmath>
+#include <cstdint>
+
+#include "lbm3_internal.h"
+
+namespace lbm3 {
+namespace {
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ int dir_ex(int i) { return ex(i); }
+__device__ __forceinline__ int dir_ey(int i) { return ey(i); }
+
+// stored_{i,k}(x') = w_i rho_k(x' + e_i): the rest equilibrium w_i rho_k
+// after the pull of the next step.
+__global__ void init_from_rho_kernel(const double* __restrict__ rho, float* __restrict__ f, int nx, int ny) {
+  const int plane = blockIdx.y;  // k*9 + i
+  const int k = plane / 9, i = plane % 9;
+  const size_t N = static_cast<size_t>(nx) * ny;
+  const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < N;
+       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
+    const size_t src = static_cast<size_t>(wrapi(y + dir_ey(i), ny)) * nx + wrapi(x + dir_ex(i), nx);
+    f[plane * N + n] = static_cast<float>(w * rho[k * N + src]);
+  }
+}
+
+// stored(x') = fpost(x' + e_i) for planes plane0 .. plane0+nplanes-1.
+__global__ void set_planes_kernel(const double* __restrict__ fpost, float* __restrict__ f, int nx, int ny,
+                                  int plane0) {
+  const int pl = blockIdx.y;
+  const int plane = plane0 + pl, i = plane % 9;
+  const size_t N = static_cast<size_t>(nx) * ny;
+  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < N;
+       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
+    const size_t src = static_cast<size_t>(wrapi(y + dir_ey(i), ny)) * nx + wrapi(x + dir_ex(i), nx);
+    f[plane * N + n] = static_cast<float>(fpost[pl * N + src]);
+  }
+}
+
+// fpost(x) = stored(x - e_i).
+__global__ void get_planes_kernel(const float* __restrict__ f, double* __restrict__ fpost, int nx, int ny,
+                                  int plane0) {
+  const int pl = blockIdx.y;
+  const int plane = plane0 + pl, i = plane % 9;
+  const size_t N = static_cast<size_t>(nx) * ny;
+  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < N;
+       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
+    const size_t src = static_cast<size_t>(wrapi(y - dir_ey(i), ny)) * nx + wrapi(x - dir_ex(i), nx);
+    fpost[pl * N + n] = static_cast<double>(f[plane * N + src]);
+  }
+}
+
+__global__ void check_rho_kernel(const double* __restrict__ rho, int n, unsigned int* bad) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const double a = rho[j], b = rho[n + j], c = rho[2 * n + j];
+    const bool ok = std::isfinite(a) && std::isfinite(b) && std::isfinite(c) && a >= 0.0 && b >= 0.0 &&
+                    c >= 0.0 && (a + b + c) > 0.0;
+    if (!ok) atomicOr(bad, 1u);
+  }
+}
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-level FP64 sums of (mass_r, mass_g, mass_b, mom_x, mom_y) over nodes:
+// per thread in registers, then warp shuffles, then one shared-memory pass.
+__global__ void reduce_partial_kernel(const float* __restrict__ f, int N, double* __restrict__ partial) {
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const double v = static_cast<double>(f[static_cast<size_t>(k * 9 + i) * N + n]);
+        acc[k] += v;
+        acc[3] += v * ex(i);
+        acc[4] += v * ey(i);
+      }
+    }
+  }
+  __shared__ double red[kRedThreads / 32][5];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const double v = warp_sum(acc[j]);
+    if (lane == 0) red[warp][j] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      double v = lane < kRedThreads / 32 ? red[lane][j] : 0.0;
+      v = warp_sum(v);
+      if (lane == 0) partial[blockIdx.x * 5 + j] = v;
+    }
+  }
+}
+
+__global__ void reduce_final_kernel(const double* __restrict__ partial, int blocks, double* __restrict__ out) {
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < blocks; b += blockDim.x)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) acc[j] += partial[b * 5 + j];
+  __shared__ double red[kRedThreads / 32][5];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const double v = warp_sum(acc[j]);
+    if (lane == 0) red[warp][j] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      double v = lane < kRedThreads / 32 ? red[lane][j] : 0.0;
+      v = warp_sum(v);
+      if (lane == 0) out[j] = v;
+    }
+  }
+}
+
+int grid_for(size_t N) {
+  const size_t b = (N + 255) / 256;
+  return static_cast<int>(b < 65535 ? (b > 0 ? b : 1) : 65535);
+}
+
+}  // namespace
+
+cudaError_t launch_init_from_rho(const double* rho, float* f, int nx, int ny, cudaStream_t s) {
+  dim3 grid(grid_for(static_cast<size_t>(nx) * ny), 27);
+  init_from_rho_kernel<<<grid, 256, 0, s>>>(rho, f, nx, ny);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_planes(const double* fpost, float* f, int nx, int ny, int plane0, int nplanes,
+                              cudaStream_t s) {
+  dim3 grid(grid_for(static_cast<size_t>(nx) * ny), nplanes);
+  set_planes_kernel<<<grid, 256, 0, s>>>(fpost, f, nx, ny, plane0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_planes(const float* f, double* fpost, int nx, int ny, int plane0, int nplanes,
+                              cudaStream_t s) {
+  dim3 grid(grid_for(static_cast<size_t>(nx) * ny), nplanes);
+  get_planes_kernel<<<grid, 256, 0, s>>>(f, fpost, nx, ny, plane0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_rho(const double* rho, int n, unsigned int* bad, cudaStream_t s) {
+  check_rho_kernel<<<grid_for(static_cast<size_t>(n)), 256, 0, s>>>(rho, n, bad);
+  return cudaGetLastError();
+}
+
+int reduce_blocks(int N) {
+  int b = (N + kRedThreads * 8 - 1) / (kRedThreads * 8);
+  return b < 1 ? 1 : (b > 1024 ? 1024 : b);
+}
+
+cudaError_t launch_reduce(const float* f, int N, double* partial, int blocks, double* out, cudaStream_t s) {
+  reduce_partial_kernel<<<blocks, kRedThreads, 0, s>>>(f, N, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  reduce_final_kernel<<<1, kRedThreads, 0, s>>>(partial, blocks, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm3

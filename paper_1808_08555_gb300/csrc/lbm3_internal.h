@@ -1,0 +1,77 @@
+// Internal declarations shared by the CUDA translation units of liblbm3.
+// Nothing here is part of the public C ABI (see include/lbm3.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace lbm3 {
+
+// ---------------------------------------------------------------- lattice
+// D2Q9 (arXiv 1808.08555, Sec. 2 after Eq. 3): e0 = (0,0), e1 = (1,0),
+// e2 = (0,1), e3 = (-1,0), e4 = (0,-1), e5 = (1,1), e6 = (-1,1), e7 = (-1,-1),
+// e8 = (1,-1); w0 = 4/9, w1-4 = 1/9, w5-8 = 1/36.
+__host__ __device__ constexpr int ex(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr float wt(int i) {
+  return i == 0 ? 4.0f / 9.0f : (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+
+// ------------------------------------------------------- fused step tiling
+// One CTA owns a strip of up to kTX columns and a run of rows; it marches up
+// the rows with a 3-stage pipeline (densities -> tension tensor -> force,
+// collision, recolouring) fed by bulk async copies of pulled rows.
+constexpr int kTX = 128;          // max strip width (columns)
+constexpr int kPW = kTX + 8;      // population row window: x0-4 .. x0+w+4
+constexpr int kDW = kTX + 4;      // density/phi window:     x0-2 .. x0+w+2
+constexpr int kTW = kTX + 2;      // tension-tensor window:  x0-1 .. x0+w+1
+constexpr int kSlots = 6;         // population ring depth (rows)
+constexpr int kConsumers = 128;   // 4 compute warps
+constexpr int kThreads = kConsumers + 32;  // + 1 copy-issuing warp
+
+struct StepArgs {
+  const float* fin;   // stored post-collision populations at t-1, [27][ny][nx]
+  float* fout;        // written at t (MODE_STEP)
+  int nx, ny;
+  int nstrips;        // ceil(nx / kTX)
+  int rows_per_cta;   // H
+  float inv_nu[3];    // 1/nu_k, nu_k = (tau_k - 1/2)/3
+  float cpair[3];     // 1e6 / (rho0_k rho0_l) for pairs (12, 13, 23)
+  float sigma[3];     // sigma_12, sigma_13, sigma_23
+  float beta0;
+  float beta_A;       // beta_kl = beta0 (1 + min(beta_A * r g b / rho^3, 1) * beta_h[kl])
+  float beta_h[3];
+  float wrec[9];      // recolouring weight per direction: w_i / |e_i|^p
+  unsigned int* err;  // device error word (bit 0: a bounded wait timed out)
+  // MODE_FIELDS outputs (FP64, [3][N] and [N]); NULL entries are skipped
+  double* out_rho;
+  double* out_ux;
+  double* out_uy;
+  double* out_p;
+};
+
+enum { MODE_STEP = 0, MODE_FIELDS = 1 };
+
+size_t step_smem_bytes();
+cudaError_t step_configure();  // sets the dynamic shared memory attribute
+cudaError_t launch_step(const StepArgs& a, int grid, int mode, cudaStream_t s);
+int step_occupancy(int* blocks_per_sm);
+
+// ------------------------------------------------------------- aux kernels
+cudaError_t launch_init_from_rho(const double* rho, float* f, int nx, int ny, cudaStream_t s);
+cudaError_t launch_set_planes(const double* fpost, float* f, int nx, int ny, int plane0, int nplanes,
+                              cudaStream_t s);
+cudaError_t launch_get_planes(const float* f, double* fpost, int nx, int ny, int plane0, int nplanes,
+                              cudaStream_t s);
+cudaError_t launch_check_rho(const double* rho, int n, unsigned int* bad, cudaStream_t s);
+// FP64 reductions: partial[blocks][5] then out[5] = (mass_r, mass_g, mass_b, mom_x, mom_y)
+int reduce_blocks(int N);
+cudaError_t launch_reduce(const float* f, int N, double* partial, int blocks, double* out, cudaStream_t s);
+
+}  // namespace lbm3

@@ -1,0 +1,278 @@
+"""Python binding of liblbm3 (the C ABI in include/lbm3.h), via ctypes.
+
+The functions below carry the C names and only marshal arguments: every step
+of the lattice Boltzmann update runs in the library's CUDA kernels.  PyTorch
+supplies device memory (``Simulation`` binds two torch tensors as the
+population buffers) and the CUDA stream (torch's current stream).  There is
+no CPU fallback: if the library is missing, loading fails with an error.
+
+Array conventions (see include/lbm3.h): colour densities (3, ny, nx) and
+post-streaming populations (3, 9, ny, nx), FP64, C order; host arrays are
+numpy arrays or CPU tensors, device arrays are CUDA float64 tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbm3.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ENUMERIC, ETIMEOUT = range(7)
+_STATUS = {OK: "LBM3_OK", EINVAL: "LBM3_EINVAL", ENOMEM: "LBM3_ENOMEM", ECUDA: "LBM3_ECUDA",
+           ESTATE: "LBM3_ESTATE", ENUMERIC: "LBM3_ENUMERIC", ETIMEOUT: "LBM3_ETIMEOUT"}
+BETA_PAPER, BETA_FU, BETA_SPENCER, BETA_LECLAIRE = range(4)
+RECOLOR_COSINE, RECOLOR_LITERAL = range(2)
+FP32 = 0
+
+
+class Lbm3Error(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class lbm3_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("tau", ctypes.c_double * 3), ("rho0", ctypes.c_double * 3),
+        ("sigma12", ctypes.c_double), ("sigma13", ctypes.c_double), ("sigma23", ctypes.c_double),
+        ("beta0", ctypes.c_double),
+        ("beta_form", ctypes.c_int32), ("recolor_form", ctypes.c_int32),
+        ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+@dataclass
+class Params:
+    """Problem statement of one simulation (arXiv 1808.08555, Sec. 2)."""
+
+    nx: int
+    ny: int
+    tau: tuple = (1.0, 1.0, 1.0)
+    rho0: tuple = (1.0, 1.0, 1.0)
+    sigma: tuple = (0.01, 0.01, 0.01)  # (sigma_12, sigma_13, sigma_23)
+    beta0: float = 0.7
+    beta_form: int = BETA_PAPER
+    recolor_form: int = RECOLOR_COSINE
+    storage: int = FP32
+
+    def to_c(self) -> lbm3_params:
+        p = lbm3_params()
+        p.nx, p.ny = int(self.nx), int(self.ny)
+        for k in range(3):
+            p.tau[k] = float(self.tau[k])
+            p.rho0[k] = float(self.rho0[k])
+        p.sigma12, p.sigma13, p.sigma23 = (float(s) for s in self.sigma)
+        p.beta0 = float(self.beta0)
+        p.beta_form, p.recolor_form = int(self.beta_form), int(self.recolor_form)
+        p.storage, p.reserved = int(self.storage), 0
+        return p
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load liblbm3.so (built by ``paper_1808_08555_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"liblbm3.so is not built ({LIB_PATH}); run paper_1808_08555_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, vp, dp = ctypes.POINTER(lbm3_params), ctypes.c_void_p, ctypes.c_void_p
+    st = ctypes.c_int
+    sig = {
+        "lbm3_buffer_bytes": (st, [P, ctypes.POINTER(ctypes.c_size_t)]),
+        "lbm3_create": (st, [P, vp, ctypes.POINTER(vp)]),
+        "lbm3_bind_buffers": (st, [vp, vp, vp, ctypes.c_size_t]),
+        "lbm3_init": (st, [vp, dp, ctypes.c_int]),
+        "lbm3_set_populations": (st, [vp, dp, ctypes.c_int]),
+        "lbm3_set_rows_per_cta": (st, [vp, ctypes.c_int32]),
+        "lbm3_step": (st, [vp, ctypes.c_int64]),
+        "lbm3_fields": (st, [vp, dp, dp, dp, dp, ctypes.c_int]),
+        "lbm3_populations": (st, [vp, dp, ctypes.c_int]),
+        "lbm3_mass": (st, [vp, dp, dp]),
+        "lbm3_sync": (st, [vp]),
+        "lbm3_time": (ctypes.c_int64, [vp]),
+        "lbm3_destroy": (st, [vp]),
+        "lbm3_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+    _lib = lib
+    return lib
+
+
+def _check(ctx, status: int):
+    if status != OK:
+        msg = load().lbm3_last_error(ctx).decode() if ctx else "(no context)"
+        raise Lbm3Error(status, msg)
+
+
+def _ptr(a):
+    """(pointer, on_device) for a numpy array or torch tensor of float64."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float64 or not a.is_contiguous():
+                raise TypeError("expected a contiguous float64 tensor")
+            return ctypes.c_void_p(a.data_ptr()), int(a.is_cuda)
+    except ImportError:  # pragma: no cover
+        pass
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+        raise TypeError("expected a C-contiguous float64 numpy array")
+    return ctypes.c_void_p(a.ctypes.data), 0
+
+
+# ------------------------------------------------------------ C-named calls
+
+def lbm3_buffer_bytes(params: Params) -> int:
+    n = ctypes.c_size_t()
+    p = params.to_c()
+    _check(None, load().lbm3_buffer_bytes(ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def lbm3_create(params: Params, stream: int | None = None) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    p = params.to_c()
+    s = load().lbm3_create(ctypes.byref(p), ctypes.c_void_p(stream or 0), ctypes.byref(ctx))
+    if s != OK:
+        raise Lbm3Error(s, "lbm3_create failed (parameters invalid or CUDA unavailable)")
+    return ctx
+
+
+def lbm3_bind_buffers(ctx, f0_ptr: int, f1_ptr: int, nbytes: int):
+    _check(ctx, load().lbm3_bind_buffers(ctx, ctypes.c_void_p(f0_ptr), ctypes.c_void_p(f1_ptr), nbytes))
+
+
+def lbm3_init(ctx, rho):
+    p, dev = _ptr(rho)
+    _check(ctx, load().lbm3_init(ctx, p, dev))
+
+
+def lbm3_set_populations(ctx, f):
+    p, dev = _ptr(f)
+    _check(ctx, load().lbm3_set_populations(ctx, p, dev))
+
+
+def lbm3_set_rows_per_cta(ctx, rows: int):
+    _check(ctx, load().lbm3_set_rows_per_cta(ctx, int(rows)))
+
+
+def lbm3_step(ctx, n: int = 1):
+    _check(ctx, load().lbm3_step(ctx, int(n)))
+
+
+def lbm3_fields(ctx, rho=None, ux=None, uy=None, p=None):
+    ptrs, devs = [], set()
+    for a in (rho, ux, uy, p):
+        if a is None:
+            ptrs.append(None)
+        else:
+            q, d = _ptr(a)
+            ptrs.append(q)
+            devs.add(d)
+    if len(devs) > 1:
+        raise ValueError("outputs must be all host or all device arrays")
+    _check(ctx, load().lbm3_fields(ctx, *ptrs, devs.pop() if devs else 0))
+
+
+def lbm3_populations(ctx, f):
+    p, dev = _ptr(f)
+    _check(ctx, load().lbm3_populations(ctx, p, dev))
+
+
+def lbm3_mass(ctx):
+    m = np.zeros(3)
+    mo = np.zeros(2)
+    _check(ctx, load().lbm3_mass(ctx, ctypes.c_void_p(m.ctypes.data), ctypes.c_void_p(mo.ctypes.data)))
+    return m, mo
+
+
+def lbm3_sync(ctx):
+    _check(ctx, load().lbm3_sync(ctx))
+
+
+def lbm3_time(ctx) -> int:
+    return int(load().lbm3_time(ctx))
+
+
+def lbm3_destroy(ctx):
+    load().lbm3_destroy(ctx)
+
+
+def lbm3_last_error(ctx) -> str:
+    return load().lbm3_last_error(ctx).decode()
+
+
+# ---------------------------------------------------------- convenience
+
+class Simulation:
+    """One simulation on the current CUDA device: torch-owned population
+    buffers bound to a library context on torch's current stream."""
+
+    def __init__(self, params: Params, device=None, rows_per_cta: int = 0):
+        import torch
+
+        self.params = params
+        self.device = torch.device(device if device is not None else "cuda")
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.current_stream(self.device)
+            nbytes = lbm3_buffer_bytes(params)
+            self._bufs = [torch.empty(nbytes // 4, dtype=torch.float32, device=self.device) for _ in range(2)]
+            self.ctx = lbm3_create(params, self.stream.cuda_stream)
+            lbm3_bind_buffers(self.ctx, self._bufs[0].data_ptr(), self._bufs[1].data_ptr(), nbytes)
+            if rows_per_cta:
+                lbm3_set_rows_per_cta(self.ctx, rows_per_cta)
+
+    def init(self, rho):
+        lbm3_init(self.ctx, rho)
+        return self
+
+    def set_populations(self, f):
+        lbm3_set_populations(self.ctx, f)
+        return self
+
+    def step(self, n: int = 1):
+        lbm3_step(self.ctx, n)
+        return self
+
+    def populations(self) -> np.ndarray:
+        f = np.empty((3, 9, self.params.ny, self.params.nx))
+        lbm3_populations(self.ctx, f)
+        return f
+
+    def fields(self) -> dict:
+        ny, nx = self.params.ny, self.params.nx
+        out = {"rho": np.empty((3, ny, nx)), "ux": np.empty((ny, nx)), "uy": np.empty((ny, nx)),
+               "p": np.empty((ny, nx))}
+        lbm3_fields(self.ctx, out["rho"], out["ux"], out["uy"], out["p"])
+        return out
+
+    def mass(self):
+        return lbm3_mass(self.ctx)
+
+    def sync(self):
+        lbm3_sync(self.ctx)
+
+    @property
+    def t(self) -> int:
+        return lbm3_time(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm3_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

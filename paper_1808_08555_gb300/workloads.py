@@ -100,6 +100,37 @@ def flat_band(nx: int, ny: int, y0: float, y1: float, sharp: bool = True, xi: fl
     return np.stack([1.0 - band, band, np.zeros_like(band)])
 
 
+def droplet_field(nx: int, ny: int, seed: int, count: int = 6, rmin: float = 4.0, rmax: float = 10.0,
+                  gap: float = 12.0, xi: float = XI) -> np.ndarray:
+    """Seeded scatter of up to `count` diffuse droplets of fluid 2 or 3 in a
+    fluid-1 matrix, every pair (periodic images included) at least `gap`
+    lattice units apart edge to edge, so interfaces never come close.  Used to
+    put interfaces across tile seams."""
+    rng = np.random.default_rng(seed)
+    drops = []
+    for _ in range(200 * count):
+        if len(drops) == count:
+            break
+        R = rng.uniform(rmin, rmax)
+        cx, cy = rng.uniform(0, nx), rng.uniform(0, ny)
+        ok = 2 * R + gap <= min(nx, ny)
+        for (dx, dy, dR, _) in drops:
+            ddx = min(abs(cx - dx), nx - abs(cx - dx))
+            ddy = min(abs(cy - dy), ny - abs(cy - dy))
+            if np.hypot(ddx, ddy) < R + dR + gap:
+                ok = False
+                break
+        if ok:
+            drops.append((cx, cy, R, 1 + int(rng.integers(0, 2))))
+    x, y = _grid(nx, ny)
+    p = [np.zeros((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx))]
+    for (cx, cy, R, k) in drops:
+        ddx = np.minimum(np.abs(x - cx), nx - np.abs(x - cx))
+        ddy = np.minimum(np.abs(y - cy), ny - np.abs(y - cy))
+        p[k] = p[k] + _edge(R - np.hypot(ddx, ddy), xi)
+    return _stack(p[1], p[2])
+
+
 def random_fields(nx: int, ny: int, seed: int, lo: float = 0.05, hi: float = 1.0) -> np.ndarray:
     """Uniform random positive colour densities (independent per node)."""
     rng = np.random.default_rng(seed)

@@ -1,0 +1,73 @@
+"""C-ABI checks that need no GPU: the library builds/loads, exports every
+symbol its header declares, and validates parameters on the host."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1808_08555_gb300 import build as B
+from paper_1808_08555_gb300 import lbm3 as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.load()
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(lbm3_\w+)\s*\(", txt))
+    return names
+
+
+def test_header_symbols_exported(lib):
+    names = _declared()
+    assert "lbm3_step" in names and "lbm3_create" in names
+    for n in sorted(names):
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_params_struct_layout_matches_header():
+    # int32 nx, ny; 3+3 doubles; 3 sigmas; beta0; 4 int32 -> 4*2 + 8*10 + 4*4 = 104 bytes
+    assert ctypes.sizeof(L.lbm3_params) == 104
+
+
+@pytest.mark.parametrize("kw", [
+    dict(nx=6, ny=8), dict(nx=0, ny=8), dict(nx=8, ny=0), dict(nx=8, ny=8, tau=(0.5, 1, 1)),
+    dict(nx=8, ny=8, rho0=(1, 0, 1)), dict(nx=8, ny=8, sigma=(0.01, -1, 0.01)),
+    dict(nx=8, ny=8, beta0=0.0), dict(nx=8, ny=8, beta0=1.5), dict(nx=8, ny=8, beta_form=7),
+    dict(nx=8, ny=8, recolor_form=2), dict(nx=8, ny=8, storage=9),
+])
+def test_invalid_params_rejected(lib, kw):
+    with pytest.raises(L.Lbm3Error) as e:
+        L.lbm3_buffer_bytes(L.Params(**kw))
+    assert e.value.status == L.EINVAL
+
+
+def test_buffer_bytes(lib):
+    assert L.lbm3_buffer_bytes(L.Params(8, 4)) == 27 * 32 * 4
+    assert L.lbm3_buffer_bytes(L.Params(2048, 2048)) == 27 * 2048 * 2048 * 4
+
+
+def test_null_context_is_einval(lib):
+    assert lib.lbm3_step(None, 1) == L.EINVAL
+    assert lib.lbm3_mass(None, None, None) == L.EINVAL
+    assert lib.lbm3_destroy(None) == L.OK
+    assert lib.lbm3_last_error(None)
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(L.Lbm3Error) as e:
+        L.lbm3_create(L.Params(8, 8))
+    assert e.value.status in (L.ECUDA, L.ENOMEM)

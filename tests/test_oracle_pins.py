@@ -317,7 +317,8 @@ def test_young_laplace_single_droplet():
 def test_shear_wave_decays_with_harmonic_mean_viscosity():
     """Eqs. vis_1 and tau: a uniform mixture carries a shear wave
     u_x = U sin(k y) that decays as exp(-nu k^2 t) with the harmonic-mean
-    viscosity rho/nu = sum_k rho_k/nu_k, nu_k = (tau_k - 1/2)/3."""
+    viscosity rho/nu = sum_k rho_k/nu_k, nu_k = (tau_k - 1/2)/3.  Recolouring
+    is switched off (beta^0 = 0): an immiscible mixture would demix."""
     nx, ny, U = 4, 64, 1e-4
     rk = np.array([0.3, 0.5, 0.2])
     taus = (0.6, 0.8, 1.4)
@@ -328,7 +329,7 @@ def test_shear_wave_decays_with_harmonic_mean_viscosity():
         feq = O.feq(1.0, U * np.sin(k * y[j]), 0.0)
         for c in range(3):
             f[c, :, j, :] = (rk[c] * feq)[:, None]
-    p = O.Params(nx, ny, tau=taus)
+    p = O.Params(nx, ny, tau=taus, beta0=0.0)
     steps = 400
     fl = O.fields(p, O.step(p, f, steps))
     amp = 2 * np.mean(fl["ux"][:, 0] * np.sin(k * y))

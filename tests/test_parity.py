@@ -1,0 +1,260 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerance (BASELINE spec reading): the relative population error
+max |f_gpu - f_oracle| / max(|f_oracle|, 1e-3 w_i) is at most 1e-5 after one
+step and 1e-4 after 1000 steps of a static case; per-colour mass of the GPU
+state, reduced in FP64 on the device, equals an exact host sum of the same
+state to 1e-12 relative.  Inputs are rounded to FP32 before both sides see
+them, so the comparison measures the arithmetic only.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1808_08555_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+WGT = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1808_08555_gb300 import build as B
+    B.build()
+    from paper_1808_08555_gb300 import lbm3
+    lbm3.load()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return lbm3
+
+
+def relerr(fg, fo):
+    floor = 1e-3 * WGT[None, :, None, None]
+    return float(np.max(np.abs(fg - fo) / np.maximum(np.abs(fo), floor)))
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def oparams(p):
+    return O.Params(p.nx, p.ny, tau=p.tau, rho0=p.rho0, sigma=p.sigma, beta0=p.beta0,
+                    beta_form=p.beta_form, recolor_form=p.recolor_form)
+
+
+def fp32_sensitivity(op, f0, steps, seed=0):
+    """How far the FP64 oracle itself moves when its input is perturbed at
+    the FP32 rounding level (relative 6e-8).  An FP32 implementation cannot
+    be expected to match the oracle more closely than this."""
+    rng = np.random.default_rng(seed)
+    fp = f0 * (1.0 + 6e-8 * rng.uniform(-1.0, 1.0, f0.shape))
+    return relerr(O.step(op, fp, steps), O.step(op, f0, steps))
+
+
+def run_pair(L, p, f0, steps, rows=0):
+    sim = L.Simulation(p, rows_per_cta=rows)
+    sim.set_populations(f0)
+    sim.step(steps)
+    fg = sim.populations()
+    sim.close()
+    fo = O.step(oparams(p), f0, steps)
+    return fg, fo
+
+
+def check_parity(L, p, f0, steps, rows=0, tol=1e-5, max_sens=1e-6):
+    """GPU vs oracle within `tol`, on an input whose own FP32-level
+    sensitivity is at most `max_sens` (so that `tol` is meaningful)."""
+    sens = fp32_sensitivity(oparams(p), f0, steps)
+    assert sens <= max_sens, f"test input is ill-conditioned at FP32 level: {sens:.2e}"
+    fg, fo = run_pair(L, p, f0, steps, rows)
+    err = relerr(fg, fo)
+    assert err <= tol, f"relative population error {err:.3e} > {tol:.0e} (oracle FP32 sensitivity {sens:.1e})"
+    return err
+
+
+# --------------------------------------------------------------- one step
+
+@pytest.mark.parametrize("beta_form", [0, 1, 2, 3])
+@pytest.mark.parametrize("recolor_form", [0, 1])
+def test_random_state_one_step_8x8(L, beta_form, recolor_form):
+    p = L.Params(8, 8, tau=(0.7, 1.0, 1.4), sigma=(0.012, 0.01, 0.008), beta_form=beta_form,
+                 recolor_form=recolor_form)
+    f0 = f32(W.random_populations(8, 8, seed=5 + beta_form))
+    check_parity(L, p, f0, 1)
+
+
+@pytest.mark.parametrize("nx,ny,rows", [(4, 3, 1), (12, 1, 1), (8, 4, 2)])
+def test_random_state_tiny_grids(L, nx, ny, rows):
+    """Grids smaller than the halo: every stencil wraps several times."""
+    p = L.Params(nx, ny, tau=(0.6, 0.9, 1.3), sigma=(0.01, 0.013, 0.007))
+    f0 = f32(W.random_populations(nx, ny, seed=nx + ny))
+    check_parity(L, p, f0, 2, rows)
+
+
+@pytest.mark.parametrize("nx,ny,rows,R", [(200, 37, 8, (4.0, 10.0)), (136, 21, 5, (3.0, 4.0)),
+                                           (260, 40, 0, (4.0, 8.0)), (320, 72, 8, (4.0, 10.0))])
+def test_droplets_across_tile_seams(L, nx, ny, rows, R):
+    """Droplets scattered over several strips (ragged last strip) and several
+    row chunks (ragged last chunk), ten steps from a relaxed-ish state."""
+    rho = W.droplet_field(nx, ny, seed=nx + ny, count=8, rmin=R[0], rmax=R[1], gap=10.0)
+    assert rho[1].sum() + rho[2].sum() > 50.0
+    p = L.Params(nx, ny, tau=(0.6, 0.9, 1.3), sigma=(0.01, 0.013, 0.007))
+    f0 = f32(O.step(oparams(p), O.init(oparams(p), rho), 3))
+    check_parity(L, p, f0, 10, rows)
+
+
+# ------------------------------------------------------------- long runs
+
+def test_two_droplets_64_1_and_1000_steps(L):
+    """64x64 two static droplets (R = 12, centres 32 apart), tau = 1,
+    sigma = 0.01, beta^0 = 0.7: 1e-5 after 1 step, 1e-4 after 1000 steps."""
+    c = W.case_two_droplets_64()
+    p = L.Params(c.nx, c.ny, tau=c.tau, sigma=c.sigma, beta0=c.beta0)
+    f0 = f32(O.init(oparams(p), c.rho))
+    sim = L.Simulation(p)
+    sim.set_populations(f0)
+    sim.step(1)
+    f1 = sim.populations()
+    sim.step(999)
+    f1000 = sim.populations()
+    m_gpu, mom_gpu = sim.mass()
+    sim.close()
+    op = oparams(p)
+    o1 = O.step(op, f0, 1)
+    o1000 = O.step(op, o1, 999)
+    assert relerr(f1, o1) <= 1e-5
+    assert relerr(f1000, o1000) <= 1e-4
+    # FP64 device reduction of the GPU's own state against an exact host sum
+    host = f1000.reshape(3, 9, -1).sum(axis=(1, 2))
+    np.testing.assert_allclose(m_gpu, host, rtol=1e-12)
+
+
+def test_compound_droplet_256_moving_case(L):
+    """The 2048^2 compound droplet scaled to 256^2 (viscosity ratio 1:2:4,
+    sigma = (0.01, 0.012, 0.005)), which is not in equilibrium and moves."""
+    c = W.case_compound_scaled(256)
+    p = L.Params(c.nx, c.ny, tau=c.tau, sigma=c.sigma, beta0=c.beta0)
+    f0 = f32(O.init(oparams(p), c.rho))
+    fg, fo = run_pair(L, p, f0, 100)
+    assert relerr(fg, fo) <= 1e-4
+
+
+# ---------------------------------------------------------------- read-out
+
+def test_fields_match_oracle(L):
+    nx, ny = 64, 48
+    p = L.Params(nx, ny, tau=(0.6, 0.8, 1.1), sigma=(0.01, 0.012, 0.005))
+    rho = W.two_droplets(nx, ny, R=10.0, c2=(20.0, 24.0), c3=(44.0, 24.0))
+    f0 = f32(O.step(oparams(p), O.init(oparams(p), rho), 5))
+    sim = L.Simulation(p)
+    sim.set_populations(f0)
+    fl = sim.fields()
+    sim.close()
+    fo = O.fields(oparams(p), f0)
+    np.testing.assert_allclose(fl["rho"], fo["rho"], rtol=1e-6, atol=1e-9)
+    np.testing.assert_allclose(fl["p"], fo["p"], rtol=1e-6)
+    assert np.abs(fl["ux"] - fo["ux"]).max() <= 1e-7
+    assert np.abs(fl["uy"] - fo["uy"]).max() <= 1e-7
+
+
+def test_device_pointers_roundtrip(L):
+    """on_device paths: init/set/read through CUDA tensors."""
+    nx, ny = 40, 24
+    p = L.Params(nx, ny)
+    rho = W.two_droplets(nx, ny, R=6.0, c2=(10.0, 12.0), c3=(30.0, 12.0))
+    sim = L.Simulation(p)
+    sim.init(torch.from_numpy(rho).cuda())
+    fd = torch.empty((3, 9, ny, nx), dtype=torch.float64, device="cuda")
+    L.lbm3_populations(sim.ctx, fd)
+    torch.cuda.synchronize()
+    fh = sim.populations()
+    np.testing.assert_array_equal(fd.cpu().numpy(), fh)
+    np.testing.assert_allclose(fh, f32(O.init(oparams(p), rho)), rtol=0, atol=0)
+    rd = torch.empty((3, ny, nx), dtype=torch.float64, device="cuda")
+    L.lbm3_fields(sim.ctx, rd, None, None, None)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(rd.cpu().numpy(), fh.sum(axis=1), rtol=1e-6)
+    sim.close()
+
+
+# ------------------------------------------------------------ edge cases
+
+def test_errors_and_degenerate_calls(L):
+    p = L.Params(8, 8)
+    sim = L.Simulation(p)
+    with pytest.raises(L.Lbm3Error) as e:
+        sim.step(1)                                 # before init
+    assert e.value.status == L.ESTATE
+    bad = np.ones((3, 8, 8))
+    bad[1, 3, 3] = -0.1
+    with pytest.raises(L.Lbm3Error) as e:
+        sim.init(bad)
+    assert e.value.status == L.EINVAL
+    zero = np.zeros((3, 8, 8))
+    with pytest.raises(L.Lbm3Error):
+        sim.init(torch.from_numpy(zero).cuda())     # device-side check
+    sim.init(np.full((3, 8, 8), 1 / 3))
+    f_before = sim.populations()
+    sim.step(0)                                     # empty step
+    np.testing.assert_array_equal(sim.populations(), f_before)
+    with pytest.raises(L.Lbm3Error) as e:
+        sim.step(-1)
+    assert e.value.status == L.EINVAL
+    sim.step(3)
+    assert sim.t == 3
+    np.testing.assert_allclose(sim.populations(), f_before, rtol=0, atol=1e-7)   # fixed point
+    sim.close()
+
+
+def test_nan_state_is_reported(L):
+    p = L.Params(8, 8)
+    sim = L.Simulation(p)
+    f = np.full((3, 9, 8, 8), 0.01)
+    f[0, 0, 2, 2] = np.nan
+    sim.set_populations(f)
+    with pytest.raises(L.Lbm3Error) as e:
+        sim.mass()
+    assert e.value.status == L.ENUMERIC
+    sim.close()
+
+
+# ------------------------------------------------------ full-size launch
+
+def _patch_check(L, p, f_t, f_t1, centres, half=8, radius=3):
+    """Nodes within `radius` of each centre depend on f(t) within 4 nodes, so
+    a periodic 2*half patch around them gives the exact one-step result."""
+    op_small = O.Params(2 * half, 2 * half, tau=p.tau, rho0=p.rho0, sigma=p.sigma, beta0=p.beta0,
+                        beta_form=p.beta_form, recolor_form=p.recolor_form)
+    worst = 0.0
+    for (cx, cy) in centres:
+        ys = (np.arange(cy - half, cy + half)) % p.ny
+        xs = (np.arange(cx - half, cx + half)) % p.nx
+        patch = f_t[:, :, ys][:, :, :, xs]
+        out = O.step(op_small, patch, 1)
+        sl = slice(half - radius, half + radius + 1)
+        got = f_t1[:, :, ys[sl]][:, :, :, xs[sl]]
+        worst = max(worst, relerr(got, out[:, :, sl, sl]))
+    return worst
+
+
+def test_full_size_compound_2048_sampled(L):
+    """2048^2 compound droplet in the benchmark's launch configuration:
+    sampled nodes (interfaces, tile seams, domain wrap) after one step from a
+    state 50 steps in, compared with the oracle on local patches; per-colour
+    mass against an exact host sum."""
+    c = W.case_compound_2048()
+    p = L.Params(c.nx, c.ny, tau=c.tau, sigma=c.sigma, beta0=c.beta0)
+    sim = L.Simulation(p)
+    sim.init(c.rho)
+    sim.step(50)
+    f_t = sim.populations()
+    sim.step(1)
+    f_t1 = sim.populations()
+    m_gpu, _ = sim.mass()
+    sim.close()
+    centres = [(1024 + 200, 1024), (1024, 1024 + 400), (1024 - 283, 1024 - 283), (1024 + 141, 1024 + 141),
+               (127, 107), (128, 108), (0, 0), (2047, 2047), (1023, 1620), (1280, 1455)]
+    assert _patch_check(L, p, f_t, f_t1, centres) <= 1e-5
+    host = f_t1.reshape(3, 9, -1).sum(axis=(1, 2))
+    np.testing.assert_allclose(m_gpu, host, rtol=1e-12)
