@@ -137,6 +137,31 @@ lbm3_status lbm3_populations(lbm3_ctx* ctx, double* f, int on_device);
  * Returns LBM3_ENUMERIC if a sum is NaN or Inf. */
 lbm3_status lbm3_mass(lbm3_ctx* ctx, double* mass, double* mom);
 
+/* Allocation-free FP64 mass/momentum reduction, for callers that cannot
+ * call cudaMalloc (all their device memory is owned by their own pool or
+ * allocator, or they run under a fixed device-memory budget).  The paper has
+ * no counterpart: this is a service of the library, not part of the method.
+ *
+ * dev_f: device array [27][ny][nx] of FP32 populations (either layout the
+ * library uses; the sums do not depend on the streaming shift), on the
+ * current CUDA device.  dev_out: device array of 5 doubles receiving
+ * (mass_r, mass_g, mass_b, mom_x, mom_y) as in lbm3_mass.  Work is enqueued on
+ * `cuda_stream` (a cudaStream_t of the current device; NULL = legacy default
+ * stream); the call does not synchronise.
+ *
+ * Scratch: block partial sums live in a file-scope device array of 1024 x 5
+ * doubles (40 KiB) that every GPU loading the library holds until exit, so
+ * nx*ny may be at most 16,777,216 (1024 blocks x 16384 nodes; e.g. 4096^2).
+ * Larger grids, NULL pointers or non-positive sizes return LBM3_EINVAL; CUDA
+ * failures return LBM3_ECUDA.  The first call on each device looks the
+ * array's device address up (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture.  No memory is allocated or
+ * freed.  All calls share the one array: calls whose work overlaps on the GPU
+ * (other streams, other threads) race on it and must be serialised by the
+ * caller.  Each call overwrites the partials it reads, so no clearing is
+ * needed between calls. */
+lbm3_status lbm3_mass_noalloc(const float* dev_f, int32_t nx, int32_t ny, void* cuda_stream, double* dev_out);
+
 /* Wait for the context's stream and report device-side errors (timed-out
  * waits) recorded since the last check. */
 lbm3_status lbm3_sync(lbm3_ctx* ctx);

@@ -101,6 +101,7 @@ def load() -> ctypes.CDLL:
         "lbm3_time": (ctypes.c_int64, [vp]),
         "lbm3_destroy": (st, [vp]),
         "lbm3_last_error": (ctypes.c_char_p, [vp]),
+        "lbm3_mass_noalloc": (st, [vp, ctypes.c_int32, ctypes.c_int32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -194,6 +195,15 @@ def lbm3_mass(ctx):
     mo = np.zeros(2)
     _check(ctx, load().lbm3_mass(ctx, ctypes.c_void_p(m.ctypes.data), ctypes.c_void_p(mo.ctypes.data)))
     return m, mo
+
+
+def lbm3_mass_noalloc(dev_f_ptr: int, nx: int, ny: int, stream: int | None, dev_out_ptr: int):
+    """Allocation-free reduction (see include/lbm3.h): device pointers in and
+    out, enqueued on `stream`, no synchronisation."""
+    s = load().lbm3_mass_noalloc(ctypes.c_void_p(dev_f_ptr), int(nx), int(ny), ctypes.c_void_p(stream or 0),
+                                 ctypes.c_void_p(dev_out_ptr))
+    if s != OK:
+        raise Lbm3Error(s, "lbm3_mass_noalloc failed")
 
 
 def lbm3_sync(ctx):
