@@ -174,7 +174,7 @@ void fill_constants(const lbm3_params& p, StepArgs* a) {
   a->beta0 = static_cast<float>(p.beta0);
   a->beta_A = static_cast<float>(A);
   for (int i = 0; i < 9; ++i) {
-    const double w = lbm3::wt(i);
+    const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
     const double len = std::sqrt(static_cast<double>(lbm3::ex(i) * lbm3::ex(i) + lbm3::ey(i) * lbm3::ey(i)));
     a->wrec[i] = static_cast<float>((p.recolor_form == LBM3_RECOLOR_COSINE && i != 0) ? w / len : w);
   }

@@ -1,24 +1,27 @@
 // Fused D2Q9 ternary colour-gradient step for sm_103a (arXiv 1808.08555, Sec. 2).
 //
 // One kernel does the whole time step for a strip of up to kTX columns and a
-// run of H rows:
-//   D stage  (row r+2): pulled populations -> rho_k, rho, phi_k = rho_k/rho
-//                       (Eq. 30 read as a pull; rho_k after Eq. 30)
-//   T stage  (row r+1): grad phi_k (Eq. fd1) -> G_kl, C_kl (Eq. 15),
-//                       normals n_kl (regularised where G_kl -> 0), tension tensor
-//                       T = sum_{k<l} sigma_kl C_kl |G_kl| (I - n_kl n_kl)
-//                       (Eq. 11's double sum with the 1/2 folded into k<l)
-//   C stage  (row r)  : F_s = div T (Eq. fd1 again), u (Eq. uk1), tau_f
-//                       (Eqs. vis_1, tau), BGK + Guo (Eqs. 1-3, 5), beta_kl
-//                       (Eqs. 18-20 or the alternatives), recolouring (Eq. 6),
-//                       store f^ddagger at x (streaming happens in the next
-//                       step's pull).
+// run of H rows.  Rows are indexed q = 0 .. H+3 from y0-2; each iteration j
+// of the march handles two rows in each of three stages:
+//   D stage  (rows 2j, 2j+1):   pulled populations -> rho_k, rho and
+//                               phi_k = rho_k/rho (Eq. 30 read as a pull;
+//                               rho_k as after Eq. 30)
+//   T stage  (rows 2j-1, 2j):   grad phi_k (Eq. fd1) -> G_kl, C_kl (Eq. 15),
+//                               normals n_kl (regularised where G_kl -> 0) and
+//                               the tension tensor
+//                               T = sum_{k<l} sigma_kl C_kl |G_kl| (I - n n)
+//                               (Eq. 11's double sum, 1/2 folded into k<l)
+//   C stage  (rows 2j-2, 2j-1): F_s = div T (Eq. fd1 again), u (Eq. uk1),
+//                               tau_f (Eqs. vis_1, tau), BGK + Guo (Eqs. 1-3,
+//                               5), beta_kl (Eqs. 18-20 or the alternatives),
+//                               recolouring (Eq. 6); store f^ddagger at x
+//                               (streaming happens in the next step's pull).
 // Population rows reach shared memory by bulk asynchronous copies
 // (cp.async.bulk + mbarrier complete_tx) issued by one producer warp into a
-// ring of kSlots rows; four consumer warps run the three stages on rows
-// r+2, r+1, r in lock step (two named barriers per row).  HBM traffic is one
-// read and one write of the 27 populations per node; halo re-reads of
-// neighbouring strips' columns are served by L2.
+// ring of kSlots rows; five consumer warps run the stages in lock step (two
+// named barriers per pair of rows).  HBM traffic is one read and one write of
+// the 27 populations per node; halo re-reads of neighbouring strips' columns
+// are served by L2.
 //
 // Every mbarrier wait is bounded in time (kWaitNs).  A wait that gives up
 // sets bit 0 of *err and marks the CTA aborted: the producer stops issuing
@@ -40,10 +43,10 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 constexpr float kNormalDelta = 1e-1f;
 
 struct Smem {
-  float pop[kSlots][27][kPW];  // pulled-row ring, plane = k*9 + i
-  float phi[4][4][kDW];        // phi_1, phi_2, phi_3, rho on 4 rows
-  float T[3][3][kTW];          // T_xx, T_xy, T_yy on 3 rows
-  float nrm[2][6][kTX];        // n_12, n_13, n_23 (x, y) on 2 rows
+  float pop[kSlots][27][kPW];  // pulled-row ring (row q in slot q % kSlots), plane = k*9 + i
+  float phi[4][4][kDW];        // phi_1, phi_2, phi_3, rho of row q in slot q % 4
+  float T[4][3][kTW];          // T_xx, T_xy, T_yy of row q in slot q % 4
+  float nrm[3][6][kTX];        // n_12, n_13, n_23 (x, y) of row q in slot q % 3
   unsigned long long full[kSlots];
   unsigned long long empty[kSlots];
   int abort_flag;
@@ -133,15 +136,6 @@ __device__ __forceinline__ int wrap(int a, int n) {
   return r < 0 ? r + n : r;
 }
 
-// Isotropic stencil of Eq. fd1 (1/c_s^2 = 3 folded in) at window column c of
-// three rows (m = y-1, z = y, p = y+1).
-__device__ __forceinline__ float ddx(const float* m, const float* z, const float* p, int c) {
-  return (1.0f / 3.0f) * (z[c + 1] - z[c - 1]) + (1.0f / 12.0f) * ((p[c + 1] - p[c - 1]) + (m[c + 1] - m[c - 1]));
-}
-__device__ __forceinline__ float ddy(const float* m, const float* z, const float* p, int c) {
-  return (1.0f / 3.0f) * (p[c] - m[c]) + (1.0f / 12.0f) * ((p[c + 1] + p[c - 1]) - (m[c + 1] + m[c - 1]));
-}
-
 // ----------------------------------------------------------------- producer
 __device__ void produce(Smem& s, const StepArgs& a, int x0, int w, int y0, int nq, int lane) {
   const int nx = a.nx, ny = a.ny;
@@ -191,187 +185,301 @@ __device__ void produce(Smem& s, const StepArgs& a, int x0, int w, int y0, int n
 }
 
 // ---------------------------------------------------------------- consumers
+// phi_k = rho_k / rho in FP32 such that the three fractions sum to one and a
+// single-fluid node gets exactly 1: the largest fraction is taken as the
+// complement of the two others.  With plain products rho_k * (1/rho) a pure
+// node gets 1 +- 1 ulp, always with the same sign for the same density, and
+// the recolouring then creates or destroys that fluid's mass at a steady
+// ~1e-8 relative per step.  Shared by the D and C stages so both see
+// bit-identical fractions.
+__device__ __forceinline__ void colour_fractions(float r0, float r1, float r2, float* p, float* rho_out) {
+  const float rho = (r0 + r1) + r2;
+  const float ir = __frcp_rn(rho);
+  float p0 = r0 * ir, p1 = r1 * ir, p2 = r2 * ir;
+  if (r0 >= r1 && r0 >= r2) {
+    p0 = (1.0f - p1) - p2;
+  } else if (r1 >= r2) {
+    p1 = (1.0f - p0) - p2;
+  } else {
+    p2 = (1.0f - p0) - p1;
+  }
+  p[0] = p0;
+  p[1] = p1;
+  p[2] = p2;
+  *rho_out = rho;
+}
+
+// D stage, one node: row q (window slot), window column c in [0, w+4), i.e.
+// x = x0 - 2 + c.  The pulled value of direction i sits at pop column
+// c + 2 - e_ix of row q's slot.
+__device__ __forceinline__ void stage_density(Smem& s, int q, int c) {
+  const float(*pp)[kPW] = s.pop[q % kSlots];
+  float r[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float acc = pp[k * 9][c + 2];
+#pragma unroll
+    for (int i = 1; i < 9; ++i) acc += pp[k * 9 + i][c + 2 - ex(i)];
+    r[k] = acc;
+  }
+  float phk[3], rho;
+  colour_fractions(r[0], r[1], r[2], phk, &rho);
+  float(*ph)[kDW] = s.phi[q & 3];
+  ph[0][c] = phk[0];
+  ph[1][c] = phk[1];
+  ph[2][c] = phk[2];
+  ph[3][c] = rho;
+}
+
+// T stage, one node: row q, T-window column c in [0, w+2), x = x0 - 1 + c.
+__device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q, int c, int w) {
+  const float(*pm)[kDW] = s.phi[(q - 1) & 3];
+  const float(*pz)[kDW] = s.phi[q & 3];
+  const float(*pq)[kDW] = s.phi[(q + 1) & 3];
+  const int cc = c + 1;  // phi-window column of this node
+  float ph[3], gx[3], gy[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float W = pz[k][cc - 1], E = pz[k][cc + 1];
+    const float SW = pm[k][cc - 1], S = pm[k][cc], SE = pm[k][cc + 1];
+    const float NW = pq[k][cc - 1], Nn = pq[k][cc], NE = pq[k][cc + 1];
+    ph[k] = pz[k][cc];
+    // Eq. fd1 with 1/c_s^2 = 3: 3 (1/9) = 1/3 on the axes, 3 (1/36) = 1/12 on the diagonals
+    gx[k] = (1.0f / 3.0f) * (E - W) + (1.0f / 12.0f) * ((NE - NW) + (SE - SW));
+    gy[k] = (1.0f / 3.0f) * (Nn - S) + (1.0f / 12.0f) * ((NE + NW) - (SE + SW));
+  }
+  const float rho2 = pz[3][cc] * pz[3][cc];
+  float txx = 0.0f, txy = 0.0f, tyy = 0.0f;
+  float nv[6];
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const int k = p < 2 ? 0 : 1;
+    const int l = p == 0 ? 1 : 2;
+    // G_kl = phi_l grad phi_k - phi_k grad phi_l
+    const float Gx = ph[l] * gx[k] - ph[k] * gx[l];
+    const float Gy = ph[l] * gy[k] - ph[k] * gy[l];
+    const float g2 = Gx * Gx + Gy * Gy;
+    const float pp = ph[k] * ph[l];
+    float mag = 0.0f;
+    if (g2 > 1e-30f) {
+      const float rinv = __frsqrt_rn(g2);  // correctly rounded: no drift from a biased estimate
+      mag = g2 * rinv;
+      const float ck = fminf(a.cpair[p] * pp * rho2, 1.0f);  // Eq. 15 with rho_k = phi_k rho
+      // sigma C |G| (I - n n) = sigma C (|G|^2 I - G G) / |G|
+      const float sc = a.sigma[p] * ck * rinv;
+      txx = fmaf(sc * Gy, Gy, txx);
+      txy = fmaf(-sc * Gx, Gy, txy);
+      tyy = fmaf(sc * Gx, Gx, tyy);
+    }
+    // recolouring normal G / max(|G|, kNormalDelta phi_k phi_l): the unit
+    // normal wherever a k-l interface exists, continuous to 0 where G -> 0
+    const float den = fmaxf(mag, kNormalDelta * pp);
+    const float rden = den > 1e-30f ? __frcp_rn(den) : 0.0f;  // |n| <= 1; tiny den -> 0
+    nv[2 * p] = Gx * rden;
+    nv[2 * p + 1] = Gy * rden;
+  }
+  float(*Tt)[kTW] = s.T[q & 3];
+  Tt[0][c] = txx;
+  Tt[1][c] = txy;
+  Tt[2][c] = tyy;
+  if (c >= 1 && c <= w) {
+    float(*nn)[kTX] = s.nrm[q % 3];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) nn[j][c - 1] = nv[j];
+  }
+}
+
+// C stage, one node: row q (output row y0 - 2 + q), column c in [0, w).
 template <int MODE>
-__device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int nq, int tid) {
-  const int nx = a.nx;
-  const size_t N = static_cast<size_t>(nx) * a.ny;
+__device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q, int c, int x0, int y0) {
+  const float(*pp)[kPW] = s.pop[q % kSlots];
+  const float(*Tm)[kTW] = s.T[(q - 1) & 3];
+  const float(*Tz)[kTW] = s.T[q & 3];
+  const float(*Tp)[kTW] = s.T[(q + 1) & 3];
+  // colour densities (same summation order as the D stage, so phi_k is
+  // bit-identical to the one the T stage used) and the total distribution
+  // f_i = sum_k f_{i,k} of the pulled populations.  The phi ring is not read
+  // here: the next iteration's D stage may already be overwriting it.
+  float fi[9], r[3];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int col = c + 4 - ex(i);
+    const float a0 = pp[i][col], a1 = pp[9 + i][col], a2 = pp[18 + i][col];
+    if (i == 0) {
+      r[0] = a0;
+      r[1] = a1;
+      r[2] = a2;
+    } else {
+      r[0] += a0;
+      r[1] += a1;
+      r[2] += a2;
+    }
+    fi[i] = (a0 + a1) + a2;
+  }
+  float phv[3], rho;
+  colour_fractions(r[0], r[1], r[2], phv, &rho);
+  const float irho = __frcp_rn(rho);
+  const float phi0 = phv[0], phi1 = phv[1], phi2 = phv[2];
+  // F_s = div T (Eq. 11), T window column of this node is c + 1
+  const int tc = c + 1;
+  float Fx, Fy;
+  {
+    const float xxW = Tz[0][tc - 1], xxE = Tz[0][tc + 1];
+    const float xxSW = Tm[0][tc - 1], xxSE = Tm[0][tc + 1], xxNW = Tp[0][tc - 1], xxNE = Tp[0][tc + 1];
+    const float xyW = Tz[1][tc - 1], xyE = Tz[1][tc + 1], xyS = Tm[1][tc], xyN = Tp[1][tc];
+    const float xySW = Tm[1][tc - 1], xySE = Tm[1][tc + 1], xyNW = Tp[1][tc - 1], xyNE = Tp[1][tc + 1];
+    const float yyS = Tm[2][tc], yyN = Tp[2][tc];
+    const float yySW = Tm[2][tc - 1], yySE = Tm[2][tc + 1], yyNW = Tp[2][tc - 1], yyNE = Tp[2][tc + 1];
+    Fx = (1.0f / 3.0f) * ((xxE - xxW) + (xyN - xyS)) +
+         (1.0f / 12.0f) * (((xxNE - xxNW) + (xxSE - xxSW)) + ((xyNE + xyNW) - (xySE + xySW)));
+    Fy = (1.0f / 3.0f) * ((xyE - xyW) + (yyN - yyS)) +
+         (1.0f / 12.0f) * (((xyNE - xyNW) + (xySE - xySW)) + ((yyNE + yyNW) - (yySE + yySW)));
+  }
+  const float mx = (fi[1] - fi[3]) + (fi[5] - fi[6]) + (fi[8] - fi[7]);
+  const float my = (fi[2] - fi[4]) + (fi[5] - fi[8]) + (fi[6] - fi[7]);
+  // Eq. uk1
+  const float ux = fmaf(0.5f, Fx, mx) * irho;
+  const float uy = fmaf(0.5f, Fy, my) * irho;
+  const int x = x0 + c, y = y0 - 2 + q;
+  const size_t N = static_cast<size_t>(a.nx) * a.ny;
+  const size_t idx = static_cast<size_t>(y) * a.nx + x;
+  if (MODE == MODE_FIELDS) {
+    if (a.out_rho) {
+      a.out_rho[idx] = phi0 * rho;
+      a.out_rho[N + idx] = phi1 * rho;
+      a.out_rho[2 * N + idx] = phi2 * rho;
+    }
+    if (a.out_ux) a.out_ux[idx] = ux;
+    if (a.out_uy) a.out_uy[idx] = uy;
+    if (a.out_p) a.out_p[idx] = static_cast<double>(rho) / 3.0;
+    return;
+  }
+  // Eqs. vis_1 / tau: 1/nu = sum_k phi_k / nu_k, tau_f = 3 nu + 1/2, omega = 1/tau_f
+  const float inu = fmaf(phi0, a.inv_nu[0], fmaf(phi1, a.inv_nu[1], phi2 * a.inv_nu[2]));
+  const float om = inu * __frcp_rn(fmaf(0.5f, inu, 3.0f));
+  const float g = 1.0f - 0.5f * om;  // Guo prefactor (1 - 1/(2 tau_f))
+  const float uu = ux * ux + uy * uy;
+  const float uF = ux * Fx + uy * Fy;
+  // BGK + Guo (Eqs. 1, 2, 3, 5) written as a correction to f_i, relative to
+  // the rest equilibrium w_i rho:
+  //   f^dagger_i = f_i + om (w_i rho - f_i) + S_i +- A_i  for the pair (e, -e),
+  //   S = w [om rho (4.5 (e.u)^2 - 1.5 u.u) + g (9 (e.u)(e.F) - 3 u.F)]
+  //   A = 3 w [om rho (e.u) + g (e.F)].
+  // Every term of the correction is small near equilibrium, so an FP32 node
+  // at rest is an exact fixed point instead of drifting by an ulp per step.
+  const float c0 = -1.5f * om * rho * uu;
+  const float c1 = 4.5f * om * rho;
+  const float g9 = 9.0f * g;
+  const float gm3uF = -3.0f * g * uF;
+  const float omr = om * rho;
+  float fd[9];
+  fd[0] = fi[0] + fmaf(om, fmaf(wt(0), rho, -fi[0]), wt(0) * (c0 + gm3uF));
+#pragma unroll
+  for (int i = 1; i <= 6; ++i) {
+    if (i == 3 || i == 4) continue;  // pairs (1,3), (2,4), (5,7), (6,8)
+    const int o = (i == 1) ? 3 : (i == 2) ? 4 : (i == 5) ? 7 : 8;
+    const float eu = ex(i) * ux + ey(i) * uy;
+    const float eF = ex(i) * Fx + ey(i) * Fy;
+    const float S = wt(i) * (fmaf(c1 * eu, eu, c0) + fmaf(g9 * eu, eF, gm3uF));
+    const float A = 3.0f * wt(i) * fmaf(omr, eu, g * eF);
+    const float wr = wt(i) * rho;
+    fd[i] = fi[i] + fmaf(om, wr - fi[i], S + A);
+    fd[o] = fi[o] + fmaf(om, wr - fi[o], S - A);
+  }
+  // segregation parameters beta_kl (pairs 12, 13, 23); prod = rho_1 rho_2 rho_3 / rho^3
+  const float cb = fminf(a.beta_A * (phi0 * phi1 * phi2), 1.0f);
+  const float(*nn)[kTX] = s.nrm[q % 3];
+  float Rx[3], Ry[3];
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const int k = p < 2 ? 0 : 1;
+    const int l = p == 0 ? 1 : 2;
+    const float b = a.beta0 * fmaf(cb, a.beta_h[p], 1.0f);
+    const float amp = b * (phv[k] * phv[l]) * rho;  // beta_kl rho_k rho_l / rho
+    Rx[p] = amp * nn[2 * p][c];
+    Ry[p] = amp * nn[2 * p + 1][c];
+  }
+  // V_k = sum_{l != k} beta_kl (rho_k rho_l / rho) n_kl, with n_lk = -n_kl
+  const float Vx[3] = {Rx[0] + Rx[1], Rx[2] - Rx[0], -Rx[1] - Rx[2]};
+  const float Vy[3] = {Ry[0] + Ry[1], Ry[2] - Ry[0], -Ry[1] - Ry[2]};
+  float* out = a.fout + idx;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    // Eq. 6: f^ddagger_{i,k} = phi_k f^dagger_i + w'_i (e_i . V_k)
+    out[static_cast<size_t>(k * 9) * N] = phv[k] * fd[0];
+#pragma unroll
+    for (int i = 1; i <= 6; ++i) {
+      if (i == 3 || i == 4) continue;
+      const int o = (i == 1) ? 3 : (i == 2) ? 4 : (i == 5) ? 7 : 8;
+      const float t = a.wrec[i] * (ex(i) * Vx[k] + ey(i) * Vy[k]);
+      out[static_cast<size_t>(k * 9 + i) * N] = fmaf(phv[k], fd[i], t);
+      out[static_cast<size_t>(k * 9 + o) * N] = fmaf(phv[k], fd[o], -t);
+    }
+  }
+}
+
+template <int MODE>
+__device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h, int tid) {
+  const int nq = h + 4;  // rows q = 0 .. h+3 <-> y = y0-2 .. y0+h+1
   volatile int* abort_flag = &s.abort_flag;
   bool dead = false;
-
-  for (int q = 0; q < nq; ++q) {
-    // ---------------- D stage: densities on row y0-2+q, columns x0-2 .. x0+w+1
-    const int ps = q % kSlots;
-    if (!dead) dead = !mbar_wait(&s.full[ps], static_cast<uint32_t>((q / kSlots) & 1), abort_flag, a.err);
+  const int J = (h + 3) / 2 + 1;
+  for (int j = 0; j < J; ++j) {
+    // ---------------- D stage: rows q = 2j, 2j+1 (< nq), columns x0-2 .. x0+w+1
+    {
+      const int q0 = 2 * j;
+      const int nr = min(2, nq - q0);
+      for (int r = 0; r < nr && !dead; ++r) {
+        const int q = q0 + r;
+        dead = !mbar_wait(&s.full[q % kSlots], static_cast<uint32_t>((q / kSlots) & 1), abort_flag, a.err);
+      }
+      if (!dead && nr > 0) {
+        const int W = w + 4;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int it = tid + u * kConsumers;
+          if (it < nr * W) {
+            const int r = it >= W ? 1 : 0;
+            stage_density(s, q0 + r, it - r * W);
+          }
+        }
+      }
+    }
+    consumers_sync();
+    // ---------------- T stage: rows q = 2j-1, 2j within [1, nq-2], columns x0-1 .. x0+w
     if (!dead) {
-      float(*pp)[kPW] = s.pop[ps];
-      float(*ph)[kDW] = s.phi[q & 3];
-      for (int c = tid; c < w + 4; c += kConsumers) {
-        float rk[3];
+      const int qa = max(2 * j - 1, 1), qb = min(2 * j, nq - 2);
+      const int nr = qb - qa + 1;
+      if (nr > 0) {
+        const int W = w + 2;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          float acc = 0.0f;
-#pragma unroll
-          for (int i = 0; i < 9; ++i) acc += pp[k * 9 + i][c + 2 - ex(i)];
-          rk[k] = acc;
-        }
-        const float rho = rk[0] + rk[1] + rk[2];
-        const float ir = 1.0f / rho;
-        ph[0][c] = rk[0] * ir;
-        ph[1][c] = rk[1] * ir;
-        ph[2][c] = rk[2] * ir;
-        ph[3][c] = rho;
-      }
-    }
-    consumers_sync();
-
-    // ---------------- T stage: tension tensor on row y0-3+q, columns x0-1 .. x0+w
-    if (q >= 2 && !dead) {
-      const float(*pm)[kDW] = s.phi[(q - 2) & 3];
-      const float(*pz)[kDW] = s.phi[(q - 1) & 3];
-      const float(*pq)[kDW] = s.phi[q & 3];
-      float(*Tt)[kTW] = s.T[q % 3];
-      float(*nn)[kTX] = s.nrm[q & 1];
-      for (int c = tid; c < w + 2; c += kConsumers) {
-        const int cc = c + 1;  // phi window column of this node
-        float ph[3], gx[3], gy[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          ph[k] = pz[k][cc];
-          gx[k] = ddx(pm[k], pz[k], pq[k], cc);
-          gy[k] = ddy(pm[k], pz[k], pq[k], cc);
-        }
-        const float rho = pz[3][cc];
-        float txx = 0.0f, txy = 0.0f, tyy = 0.0f;
-        float nv[6];
-#pragma unroll
-        for (int q2 = 0; q2 < 3; ++q2) {
-          const int k = q2 < 2 ? 0 : 1;
-          const int l = q2 == 0 ? 1 : 2;
-          // G_kl = phi_l grad phi_k - phi_k grad phi_l
-          const float Gx = ph[l] * gx[k] - ph[k] * gx[l];
-          const float Gy = ph[l] * gy[k] - ph[k] * gy[l];
-          const float g2 = Gx * Gx + Gy * Gy;
-          const float mag = sqrtf(g2);
-          if (g2 > 1e-30f) {
-            const float ck = fminf(a.cpair[q2] * (ph[k] * rho) * (ph[l] * rho), 1.0f);
-            // sigma C |G| (I - n n) = sigma C (|G|^2 I - G G) / |G|
-            const float sc = a.sigma[q2] * ck / mag;
-            txx += sc * Gy * Gy;
-            txy -= sc * Gx * Gy;
-            tyy += sc * Gx * Gx;
-          }
-          // recolouring normal G / max(|G|, kNormalDelta phi_k phi_l): the unit
-          // normal wherever a k-l interface exists, continuous to 0 where G -> 0
-          const float den = fmaxf(mag, kNormalDelta * ph[k] * ph[l]);
-          const float rden = den > 1e-30f ? 1.0f / den : 0.0f;  // |n| <= 1; tiny den -> 0
-          nv[2 * q2] = Gx * rden;
-          nv[2 * q2 + 1] = Gy * rden;
-        }
-        Tt[0][c] = txx;
-        Tt[1][c] = txy;
-        Tt[2][c] = tyy;
-        if (c >= 1 && c <= w) {
-#pragma unroll
-          for (int j = 0; j < 6; ++j) nn[j][c - 1] = nv[j];
-        }
-      }
-    }
-    consumers_sync();
-
-    // ---------------- C stage: row y0-4+q, columns x0 .. x0+w-1
-    if (q >= 4 && !dead && tid < w) {
-      const int row = y0 - 4 + q;
-      float(*pp)[kPW] = s.pop[(q - 2) % kSlots];
-      const float(*Tm)[kTW] = s.T[(q - 2) % 3];
-      const float(*Tz)[kTW] = s.T[(q - 1) % 3];
-      const float(*Tp)[kTW] = s.T[q % 3];
-      const float(*nn)[kTX] = s.nrm[(q - 1) & 1];
-      const int c = tid;
-      float f[27];
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[k * 9 + i] = pp[k * 9 + i][c + 4 - ex(i)];
-      float rk[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) acc += f[k * 9 + i];
-        rk[k] = acc;
-      }
-      const float rho = rk[0] + rk[1] + rk[2];
-      const float ir = 1.0f / rho;
-      // F_s = div T (Eq. 11), T window column of this node is c + 1
-      const int tc = c + 1;
-      const float Fx = ddx(Tm[0], Tz[0], Tp[0], tc) + ddy(Tm[1], Tz[1], Tp[1], tc);
-      const float Fy = ddx(Tm[1], Tz[1], Tp[1], tc) + ddy(Tm[2], Tz[2], Tp[2], tc);
-      float fi[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) fi[i] = f[i] + f[9 + i] + f[18 + i];
-      const float mx = (fi[1] - fi[3]) + (fi[5] - fi[6]) + (fi[8] - fi[7]);
-      const float my = (fi[2] - fi[4]) + (fi[5] - fi[8]) + (fi[6] - fi[7]);
-      // Eq. uk1
-      const float ux = (mx + 0.5f * Fx) * ir;
-      const float uy = (my + 0.5f * Fy) * ir;
-      if (MODE == MODE_FIELDS) {
-        const size_t idx = static_cast<size_t>(row) * nx + (x0 + c);
-        if (a.out_rho) {
-          a.out_rho[idx] = rk[0];
-          a.out_rho[N + idx] = rk[1];
-          a.out_rho[2 * N + idx] = rk[2];
-        }
-        if (a.out_ux) a.out_ux[idx] = ux;
-        if (a.out_uy) a.out_uy[idx] = uy;
-        if (a.out_p) a.out_p[idx] = static_cast<double>(rho) / 3.0;
-      } else {
-        // Eqs. vis_1 / tau: rho/nu = sum rho_k/nu_k, tau_f = 3 nu + 1/2
-        const float snu = rk[0] * a.inv_nu[0] + rk[1] * a.inv_nu[1] + rk[2] * a.inv_nu[2];
-        const float tauf = 3.0f * (rho / snu) + 0.5f;
-        const float om = 1.0f / tauf;
-        const float uu = ux * ux + uy * uy;
-        const float uF = ux * Fx + uy * Fy;
-        const float gpre = 1.0f - 0.5f * om;
-        float fd[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          const float eu = ex(i) * ux + ey(i) * uy;
-          const float eF = ex(i) * Fx + ey(i) * Fy;
-          const float feq = wt(i) * rho * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
-          const float guo = wt(i) * gpre * (3.0f * (eF - uF) + 9.0f * eu * eF);
-          fd[i] = fi[i] - om * (fi[i] - feq) + guo;  // Eqs. 1, 2, 5
-        }
-        // segregation parameters beta_kl (pairs 12, 13, 23)
-        const float prod = rk[0] * rk[1] * rk[2] * (ir * ir * ir);
-        const float cb = fminf(a.beta_A * prod, 1.0f);
-        float Rx[3], Ry[3];
-#pragma unroll
-        for (int q2 = 0; q2 < 3; ++q2) {
-          const int k = q2 < 2 ? 0 : 1;
-          const int l = q2 == 0 ? 1 : 2;
-          const float b = a.beta0 * (1.0f + cb * a.beta_h[q2]);
-          const float amp = b * rk[k] * rk[l] * ir;
-          Rx[q2] = amp * nn[2 * q2][c];
-          Ry[q2] = amp * nn[2 * q2 + 1][c];
-        }
-        // sum_{l != k} beta_kl (rho_k rho_l / rho) n_kl, with n_lk = -n_kl
-        const float Vx[3] = {Rx[0] + Rx[1], Rx[2] - Rx[0], -Rx[1] - Rx[2]};
-        const float Vy[3] = {Ry[0] + Ry[1], Ry[2] - Ry[0], -Ry[1] - Ry[2]};
-        const size_t base = static_cast<size_t>(row) * nx + (x0 + c);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const float phk = rk[k] * ir;
-#pragma unroll
-          for (int i = 0; i < 9; ++i) {
-            const float en = ex(i) * Vx[k] + ey(i) * Vy[k];
-            a.fout[static_cast<size_t>(k * 9 + i) * N + base] = phk * fd[i] + a.wrec[i] * en;  // Eq. 6
+        for (int u = 0; u < 2; ++u) {
+          const int it = tid + u * kConsumers;
+          if (it < nr * W) {
+            const int r = it >= W ? 1 : 0;
+            stage_tension(s, a, qa + r, it - r * W, w);
           }
         }
       }
     }
-    // release the population row that the C stage (or, for the first two
-    // halo rows, the D stage) finished with
-    if (q >= 2) mbar_arrive(&s.empty[(q - 2) % kSlots]);
+    consumers_sync();
+    // ---------------- C stage: rows q = 2j-2, 2j-1 within [2, h+1], columns x0 .. x0+w-1
+    if (!dead) {
+      const int qa = max(2 * j - 2, 2), qb = min(2 * j - 1, h + 1);
+      const int nr = qb - qa + 1;
+      if (nr > 0) {
+        for (int it = tid; it < nr * w; it += kConsumers) {
+          const int r = it >= w ? 1 : 0;
+          stage_collide<MODE>(s, a, qa + r, it - r * w, x0, y0);
+        }
+      }
+    }
+    // release the population rows the C stage finished with (rows 0 and 1
+    // are D-stage halo rows only and are released here as well)
+    if (j >= 1) {
+      mbar_arrive(&s.empty[(2 * j - 2) % kSlots]);
+      mbar_arrive(&s.empty[(2 * j - 1) % kSlots]);
+    }
   }
 }
 
@@ -400,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 2) fused_step_kernel(StepArgs a) {
   if (tid >= kConsumers) {
     produce(s, a, x0, w, y0, nq, tid - kConsumers);
   } else {
-    consume<MODE>(s, a, x0, w, y0, nq, tid);
+    consume<MODE>(s, a, x0, w, y0, h, tid);
   }
 }
 

@@ -111,23 +111,30 @@ def test_two_droplets_64_1_and_1000_steps(L):
     sigma = 0.01, beta^0 = 0.7: 1e-5 after 1 step, 1e-4 after 1000 steps."""
     c = W.case_two_droplets_64()
     p = L.Params(c.nx, c.ny, tau=c.tau, sigma=c.sigma, beta0=c.beta0)
-    f0 = f32(O.init(oparams(p), c.rho))
+    op = oparams(p)
+    f0 = f32(O.init(op, c.rho))
+    m0 = f0.reshape(3, 9, -1).sum(axis=(1, 2))
     sim = L.Simulation(p)
     sim.set_populations(f0)
-    sim.step(1)
-    f1 = sim.populations()
-    sim.step(999)
+    fo, done, errs = f0, 0, {}
+    for n in (1, 9, 90, 900):
+        sim.step(n)
+        fo = O.step(op, fo, n)
+        done += n
+        errs[done] = relerr(sim.populations(), fo)
     f1000 = sim.populations()
     m_gpu, mom_gpu = sim.mass()
     sim.close()
-    op = oparams(p)
-    o1 = O.step(op, f0, 1)
-    o1000 = O.step(op, o1, 999)
-    assert relerr(f1, o1) <= 1e-5
-    assert relerr(f1000, o1000) <= 1e-4
+    assert errs[1] <= 1e-5, errs
+    assert errs[1000] <= 1e-4, errs
     # FP64 device reduction of the GPU's own state against an exact host sum
     host = f1000.reshape(3, 9, -1).sum(axis=(1, 2))
     np.testing.assert_allclose(m_gpu, host, rtol=1e-12)
+    # physical per-colour mass drift of the FP32 state over 1000 steps.  The
+    # FP32 arithmetic leaves a few 1e-6; the earlier biased formulation
+    # (products rho_k * (1/rho) and f + om (feq - f) summed whole) drifted
+    # by 2e-5, which this bound rejects.
+    assert np.abs(m_gpu / m0 - 1).max() <= 5e-6, m_gpu / m0 - 1
 
 
 def test_compound_droplet_256_moving_case(L):
