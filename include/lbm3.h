@@ -81,8 +81,9 @@ typedef struct {
   int32_t reserved;   /* must be 0 */
 } lbm3_params;
 
-/* Bytes of ONE population buffer for these parameters (27 * nx * ny * 4 for
- * FP32).  Writes *bytes.  No device work. */
+/* Bytes of ONE population buffer for these parameters: 27 * ny * P * 4 for
+ * FP32 with the row pitch P = max(nx + 8, 136) (rows carry four ghost columns
+ * on each side that hold the periodic wrap).  Writes *bytes.  No device work. */
 lbm3_status lbm3_buffer_bytes(const lbm3_params* p, size_t* bytes);
 
 /* Validate p and create a context bound to the current CUDA device and to

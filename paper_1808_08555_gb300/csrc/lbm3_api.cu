@@ -4,7 +4,8 @@
 // ping-pong: one holds the current state (post-collision populations stored
 // where they were produced, read by the next step's pull), the other is the
 // target of the next step and, between steps, doubles as staging memory for
-// host input/output, so no extra full-grid allocation is made.
+// host input/output, so no extra full-grid allocation is made.  Each buffer
+// has a TMA tensor descriptor, encoded once when the buffer is set.
 
 #include <cmath>
 #include <cstdarg>
@@ -39,6 +40,7 @@ struct lbm3_ctx {
   int red_blocks = 1;
   int rows_override = 0;
   StepArgs base{};
+  alignas(64) unsigned char tmap[2][128];  // CUtensorMap of buf[0] and buf[1]
   std::string msg;
 };
 
@@ -67,6 +69,11 @@ lbm3_status cuda_fail(lbm3_ctx* c, cudaError_t e, const char* where) {
   } while (0)
 
 size_t nodes(const lbm3_params& p) { return static_cast<size_t>(p.nx) * static_cast<size_t>(p.ny); }
+
+// one population buffer: 27 planes of ny rows with the padded pitch nx + 8
+size_t buffer_bytes(const lbm3_params& p) {
+  return 27 * static_cast<size_t>(lbm3::pitch_of(p.nx)) * static_cast<size_t>(p.ny) * sizeof(float);
+}
 
 lbm3_status validate(const lbm3_params* p, std::string* why) {
   char b[256];
@@ -191,6 +198,14 @@ struct DeviceGuard {
   }
 };
 
+lbm3_status encode_maps(lbm3_ctx* c) {
+  for (int b = 0; b < 2; ++b) {
+    const cudaError_t e = lbm3::encode_population_map(c->tmap[b], c->buf[b], c->p.nx, c->p.ny);
+    if (e != cudaSuccess) return cuda_fail(c, e, "encoding the TMA descriptor of a population buffer");
+  }
+  return LBM3_OK;
+}
+
 lbm3_status ensure_buffers(lbm3_ctx* c) {
   if (c->buf[0]) return LBM3_OK;
   void* a = nullptr;
@@ -207,7 +222,7 @@ lbm3_status ensure_buffers(lbm3_ctx* c) {
   c->buf[0] = static_cast<float*>(a);
   c->buf[1] = static_cast<float*>(b);
   c->owns_bufs = true;
-  return LBM3_OK;
+  return encode_maps(c);
 }
 
 // Read and clear the device error word (synchronises the stream).
@@ -257,7 +272,7 @@ lbm3_status lbm3_buffer_bytes(const lbm3_params* p, size_t* bytes) {
   if (!bytes) return LBM3_EINVAL;
   lbm3_status st = validate(p, &why);
   if (st != LBM3_OK) return st;
-  *bytes = 27 * nodes(*p) * sizeof(float);
+  *bytes = buffer_bytes(*p);
   return LBM3_OK;
 }
 
@@ -274,7 +289,7 @@ lbm3_status lbm3_create(const lbm3_params* p, void* cuda_stream, lbm3_ctx** out)
   if (!c) return LBM3_ENOMEM;
   c->p = *p;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
-  c->buf_bytes = 27 * nodes(*p) * sizeof(float);
+  c->buf_bytes = buffer_bytes(*p);
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e == cudaSuccess) e = lbm3::step_configure();
@@ -306,6 +321,8 @@ lbm3_status lbm3_create(const lbm3_params* p, void* cuda_stream, lbm3_ctx** out)
   StepArgs& a = c->base;
   a.nx = p->nx;
   a.ny = p->ny;
+  a.pitch = lbm3::pitch_of(p->nx);
+  a.boxw = lbm3::kPW;  // pitch_of() is never below one box
   a.nstrips = (p->nx + lbm3::kTX - 1) / lbm3::kTX;
   a.err = c->err;
   fill_constants(*p, &a);
@@ -324,7 +341,8 @@ lbm3_status lbm3_bind_buffers(lbm3_ctx* c, void* f0, void* f1, size_t bytes_each
   c->buf[0] = static_cast<float*>(f0);
   c->buf[1] = static_cast<float*>(f1);
   c->owns_bufs = false;
-  return LBM3_OK;
+  DeviceGuard g(c->device);
+  return encode_maps(c);
 }
 
 lbm3_status lbm3_init(lbm3_ctx* c, const double* rho, int on_device) {
@@ -399,7 +417,7 @@ lbm3_status lbm3_step(lbm3_ctx* c, int64_t n) {
   for (int64_t s = 0; s < n; ++s) {
     int grid = 0;
     StepArgs a = args_for(c, c->buf[c->cur], c->buf[c->cur ^ 1], &grid);
-    LBM3_CUDA(c, lbm3::launch_step(a, grid, lbm3::MODE_STEP, c->stream));
+    LBM3_CUDA(c, lbm3::launch_step(a, c->tmap[c->cur], grid, lbm3::MODE_STEP, c->stream));
     c->cur ^= 1;
     c->t += 1;
   }
@@ -425,7 +443,7 @@ lbm3_status lbm3_fields(lbm3_ctx* c, double* rho, double* ux, double* uy, double
     a.out_uy = uy ? staging + 4 * N : nullptr;
     a.out_p = pr ? staging + 5 * N : nullptr;
   }
-  LBM3_CUDA(c, lbm3::launch_step(a, grid, lbm3::MODE_FIELDS, c->stream));
+  LBM3_CUDA(c, lbm3::launch_step(a, c->tmap[c->cur], grid, lbm3::MODE_FIELDS, c->stream));
   if (!on_device) {
     if (rho) LBM3_CUDA(c, cudaMemcpyAsync(rho, staging, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (ux) LBM3_CUDA(c, cudaMemcpyAsync(ux, staging + 3 * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -461,8 +479,8 @@ lbm3_status lbm3_mass(lbm3_ctx* c, double* mass, double* mom) {
   if (!c) return LBM3_EINVAL;
   if (!c->state_set) return fail(c, LBM3_ESTATE, "lbm3_mass: state not initialised");
   DeviceGuard g(c->device);
-  LBM3_CUDA(c, lbm3::launch_reduce(c->buf[c->cur], static_cast<int>(nodes(c->p)), c->partial, c->red_blocks,
-                                   c->red_out, c->stream));
+  LBM3_CUDA(c, lbm3::launch_reduce_padded(c->buf[c->cur], c->p.nx, c->p.ny, c->partial, c->red_blocks,
+                                          c->red_out, c->stream));
   double h[5];
   LBM3_CUDA(c, cudaMemcpyAsync(h, c->red_out, sizeof h, cudaMemcpyDeviceToHost, c->stream));
   lbm3_status st = check_device_errors(c);

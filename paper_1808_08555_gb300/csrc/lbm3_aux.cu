@@ -1,5 +1,6 @@
 // Auxiliary kernels of liblbm3: state set-up and read-out in the pull layout,
-// and the FP64 mass/momentum reductions.
+// and the FP64 mass/momentum reductions (over the library's padded layout,
+// and over a plain [27][ny][nx] array for the allocation-free entry point).
 //
 // The library stores, between steps, the post-collision populations
 // f^ddagger_{i,k}(x) at the node x where they were produced (before
@@ -23,46 +24,60 @@ __device__ __forceinline__ int wrapi(int a, int n) {
 __device__ __forceinline__ int dir_ex(int i) { return ex(i); }
 __device__ __forceinline__ int dir_ey(int i) { return ey(i); }
 
-// stored_{i,k}(x') = w_i rho_k(x' + e_i): the rest equilibrium w_i rho_k
-// after the pull of the next step.
+// Padded, group-ordered layout (see lbm3_internal.h): plane p of direction
+// i, row y, padded column xp holds the value of node x = (xp - 4) mod nx.
+
+// stored_{i,k}(x) = w_i rho_k(x + e_i): the rest equilibrium w_i rho_k after
+// the pull of the next step.
 __global__ void init_from_rho_kernel(const double* __restrict__ rho, float* __restrict__ f, int nx, int ny) {
-  const int plane = blockIdx.y;  // k*9 + i
+  const int plane = blockIdx.y;  // k*9 + i (input numbering)
   const int k = plane / 9, i = plane % 9;
+  const int P = pitch_of(nx);
   const size_t N = static_cast<size_t>(nx) * ny;
+  const size_t NP = static_cast<size_t>(P) * ny;
+  float* dst = f + static_cast<size_t>(plane_of(k, i)) * NP;
   const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
-  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < N;
+  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < NP;
        n += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
+    const int xp = static_cast<int>(n % P), y = static_cast<int>(n / P);
+    const int x = wrapi(xp - kGhost, nx);
     const size_t src = static_cast<size_t>(wrapi(y + dir_ey(i), ny)) * nx + wrapi(x + dir_ex(i), nx);
-    f[plane * N + n] = static_cast<float>(w * rho[k * N + src]);
+    dst[n] = static_cast<float>(w * rho[k * N + src]);
   }
 }
 
-// stored(x') = fpost(x' + e_i) for planes plane0 .. plane0+nplanes-1.
+// stored(x) = fpost(x + e_i) for input planes plane0 .. plane0+nplanes-1
+// (fpost numbered k*9 + i, unpadded).
 __global__ void set_planes_kernel(const double* __restrict__ fpost, float* __restrict__ f, int nx, int ny,
                                   int plane0) {
   const int pl = blockIdx.y;
-  const int plane = plane0 + pl, i = plane % 9;
+  const int plane = plane0 + pl, k = plane / 9, i = plane % 9;
+  const int P = pitch_of(nx);
   const size_t N = static_cast<size_t>(nx) * ny;
-  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < N;
+  const size_t NP = static_cast<size_t>(P) * ny;
+  float* dst = f + static_cast<size_t>(plane_of(k, i)) * NP;
+  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < NP;
        n += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
+    const int xp = static_cast<int>(n % P), y = static_cast<int>(n / P);
+    const int x = wrapi(xp - kGhost, nx);
     const size_t src = static_cast<size_t>(wrapi(y + dir_ey(i), ny)) * nx + wrapi(x + dir_ex(i), nx);
-    f[plane * N + n] = static_cast<float>(fpost[pl * N + src]);
+    dst[n] = static_cast<float>(fpost[pl * N + src]);
   }
 }
 
-// fpost(x) = stored(x - e_i).
+// fpost(x) = stored(x - e_i), written unpadded with numbering k*9 + i.
 __global__ void get_planes_kernel(const float* __restrict__ f, double* __restrict__ fpost, int nx, int ny,
                                   int plane0) {
   const int pl = blockIdx.y;
-  const int plane = plane0 + pl, i = plane % 9;
+  const int plane = plane0 + pl, k = plane / 9, i = plane % 9;
+  const int P = pitch_of(nx);
   const size_t N = static_cast<size_t>(nx) * ny;
+  const float* src = f + static_cast<size_t>(plane_of(k, i)) * static_cast<size_t>(P) * ny;
   for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < N;
        n += static_cast<size_t>(gridDim.x) * blockDim.x) {
     const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
-    const size_t src = static_cast<size_t>(wrapi(y - dir_ey(i), ny)) * nx + wrapi(x - dir_ex(i), nx);
-    fpost[pl * N + n] = static_cast<double>(f[plane * N + src]);
+    const size_t s = static_cast<size_t>(wrapi(y - dir_ey(i), ny)) * P + (wrapi(x - dir_ex(i), nx) + kGhost);
+    fpost[pl * N + n] = static_cast<double>(src[s]);
   }
 }
 
@@ -93,6 +108,45 @@ __global__ void reduce_partial_kernel(const float* __restrict__ f, int N, double
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
         const double v = static_cast<double>(f[static_cast<size_t>(k * 9 + i) * N + n]);
+        acc[k] += v;
+        acc[3] += v * ex(i);
+        acc[4] += v * ey(i);
+      }
+    }
+  }
+  __shared__ double red[kRedThreads / 32][5];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const double v = warp_sum(acc[j]);
+    if (lane == 0) red[warp][j] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      double v = lane < kRedThreads / 32 ? red[lane][j] : 0.0;
+      v = warp_sum(v);
+      if (lane == 0) partial[blockIdx.x * 5 + j] = v;
+    }
+  }
+}
+
+// Same sums over the library's padded, group-ordered layout (ghost columns
+// excluded).
+__global__ void reduce_partial_padded_kernel(const float* __restrict__ f, int nx, int ny,
+                                             double* __restrict__ partial) {
+  const int P = pitch_of(nx);
+  const int N = nx * ny;
+  const size_t NP = static_cast<size_t>(P) * ny;
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+    const size_t off = static_cast<size_t>(n / nx) * P + (n % nx) + kGhost;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const double v = static_cast<double>(f[static_cast<size_t>(plane_of(k, i)) * NP + off]);
         acc[k] += v;
         acc[3] += v * ex(i);
         acc[4] += v * ey(i);
@@ -148,14 +202,14 @@ int grid_for(size_t N) {
 }  // namespace
 
 cudaError_t launch_init_from_rho(const double* rho, float* f, int nx, int ny, cudaStream_t s) {
-  dim3 grid(grid_for(static_cast<size_t>(nx) * ny), 27);
+  dim3 grid(grid_for(static_cast<size_t>(pitch_of(nx)) * ny), 27);
   init_from_rho_kernel<<<grid, 256, 0, s>>>(rho, f, nx, ny);
   return cudaGetLastError();
 }
 
 cudaError_t launch_set_planes(const double* fpost, float* f, int nx, int ny, int plane0, int nplanes,
                               cudaStream_t s) {
-  dim3 grid(grid_for(static_cast<size_t>(nx) * ny), nplanes);
+  dim3 grid(grid_for(static_cast<size_t>(pitch_of(nx)) * ny), nplanes);
   set_planes_kernel<<<grid, 256, 0, s>>>(fpost, f, nx, ny, plane0);
   return cudaGetLastError();
 }
@@ -179,6 +233,15 @@ int reduce_blocks(int N) {
 
 cudaError_t launch_reduce(const float* f, int N, double* partial, int blocks, double* out, cudaStream_t s) {
   reduce_partial_kernel<<<blocks, kRedThreads, 0, s>>>(f, N, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  reduce_final_kernel<<<1, kRedThreads, 0, s>>>(partial, blocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_padded(const float* f, int nx, int ny, double* partial, int blocks, double* out,
+                                 cudaStream_t s) {
+  reduce_partial_padded_kernel<<<blocks, kRedThreads, 0, s>>>(f, nx, ny, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   reduce_final_kernel<<<1, kRedThreads, 0, s>>>(partial, blocks, out);

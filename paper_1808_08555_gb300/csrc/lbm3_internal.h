@@ -27,12 +27,33 @@ __host__ __device__ constexpr float wt(int i) {
   return i == 0 ? 0x1.c71c74p-2f : (i < 5 ? 0x1.c71c70p-4f : 0x1.c71c70p-6f);
 }
 
+// ------------------------------------------------------------ HBM layout
+// Populations are stored as 27 planes of ny rows with a padded pitch
+// P = max(nx + 8, 136): column xp = x + 4 holds node x, and the four ghost
+// columns on each side hold copies of the opposite edge (periodic wrap), so
+// that every strip's halo window is one contiguous, in-bounds span of a row.  Planes are
+// ordered by the y-component of their direction so that the nine planes a
+// pulled row needs from one source row are consecutive:
+//   group 0: e_y = +1 {2, 5, 6}; group 1: e_y = 0 {0, 1, 3}; group 2: e_y = -1 {4, 7, 8}
+//   plane(k, i) = 9 * group(i) + 3 * k + position of i in its group.
+constexpr int kGhost = 4;
+__host__ __device__ constexpr int dir_group(int i) { return ey(i) > 0 ? 0 : (ey(i) == 0 ? 1 : 2); }
+__host__ __device__ constexpr int dir_pos(int i) {
+  return (i == 2 || i == 0 || i == 4) ? 0 : ((i == 5 || i == 1 || i == 7) ? 1 : 2);
+}
+__host__ __device__ constexpr int plane_of(int k, int i) { return 9 * dir_group(i) + 3 * k + dir_pos(i); }
+// at least one full TMA box wide (kPW, defined below): narrow grids get unused
+// columns after the right ghosts so that every box row has the same pitch
+__host__ __device__ constexpr int pitch_of(int nx) { return nx + 2 * kGhost > 136 ? nx + 2 * kGhost : 136; }
+
 // ------------------------------------------------------- fused step tiling
 // One CTA owns a strip of up to kTX columns and a run of rows; it marches up
 // the rows two at a time with a 3-stage pipeline (densities -> tension tensor
 // -> force, collision, recolouring) fed by bulk async copies of pulled rows.
 constexpr int kTX = 128;          // max strip width (columns)
-constexpr int kPW = kTX + 8;      // population row window: x0-4 .. x0+w+4
+constexpr int kPW = kTX + 8;      // population row window: x0-4 .. x0+w+4 (one TMA box row)
+static_assert(kPW == 136, "pitch_of() assumes a 136-column box");
+constexpr int kGroupFloats = 1248;  // 9 planes x kPW = 1224 floats, padded to a 128-byte multiple
 constexpr int kDW = kTX + 4;      // density/phi window:     x0-2 .. x0+w+2
 constexpr int kTW = kTX + 2;      // tension-tensor window:  x0-1 .. x0+w+1
 constexpr int kSlots = 6;         // population ring depth (rows)
@@ -40,9 +61,11 @@ constexpr int kConsumers = 160;   // 5 compute warps: 2 rows x (w+4) <= 2 items 
 constexpr int kThreads = kConsumers + 32;  // + 1 copy-issuing warp
 
 struct StepArgs {
-  const float* fin;   // stored post-collision populations at t-1, [27][ny][nx]
-  float* fout;        // written at t (MODE_STEP)
+  const float* fin;   // stored post-collision populations at t-1, [27][ny][P] (padded layout)
+  float* fout;        // written at t (MODE_STEP), same layout
   int nx, ny;
+  int pitch;          // P = nx + 8
+  int boxw;           // TMA box width in columns: min(kPW, P)
   int nstrips;        // ceil(nx / kTX)
   int rows_per_cta;   // H
   float inv_nu[3];    // 1/nu_k, nu_k = (tau_k - 1/2)/3 (so 1/nu = sum_k phi_k/nu_k)
@@ -64,7 +87,11 @@ enum { MODE_STEP = 0, MODE_FIELDS = 1 };
 
 size_t step_smem_bytes();
 cudaError_t step_configure();  // sets the dynamic shared memory attribute
-cudaError_t launch_step(const StepArgs& a, int grid, int mode, cudaStream_t s);
+// tmap: a CUtensorMap (128 bytes) describing a.fin as a 3D tensor
+// (P, ny, 27) of FP32 with box (boxw, 1, 9)
+cudaError_t launch_step(const StepArgs& a, const void* tmap, int grid, int mode, cudaStream_t s);
+// encode that tensor map for a population buffer (uses the driver's encoder)
+cudaError_t encode_population_map(void* tmap, const float* buf, int nx, int ny);
 int step_occupancy(int* blocks_per_sm);
 
 // ------------------------------------------------------------- aux kernels
@@ -76,6 +103,10 @@ cudaError_t launch_get_planes(const float* f, double* fpost, int nx, int ny, int
 cudaError_t launch_check_rho(const double* rho, int n, unsigned int* bad, cudaStream_t s);
 // FP64 reductions: partial[blocks][5] then out[5] = (mass_r, mass_g, mass_b, mom_x, mom_y)
 int reduce_blocks(int N);
+// plain [27][ny][nx] array, plane = k*9 + i (the allocation-free entry point's input)
 cudaError_t launch_reduce(const float* f, int N, double* partial, int blocks, double* out, cudaStream_t s);
+// the library's padded, group-ordered layout
+cudaError_t launch_reduce_padded(const float* f, int nx, int ny, double* partial, int blocks, double* out,
+                                 cudaStream_t s);
 
 }  // namespace lbm3

@@ -16,10 +16,11 @@
 //                               5), beta_kl (Eqs. 18-20 or the alternatives),
 //                               recolouring (Eq. 6); store f^ddagger at x
 //                               (streaming happens in the next step's pull).
-// Population rows reach shared memory by bulk asynchronous copies
-// (cp.async.bulk + mbarrier complete_tx) issued by one producer warp into a
-// ring of kSlots rows; five consumer warps run the stages in lock step (two
-// named barriers per pair of rows).  HBM traffic is one read and one write of
+// Population rows reach shared memory by 3D tiled TMA loads
+// (cp.async.bulk.tensor + mbarrier complete_tx): per row three boxes of
+// 9 planes x 136 columns, issued by one producer warp into a ring of kSlots
+// rows; five consumer warps run the stages in lock step (two named barriers
+// per pair of rows).  HBM traffic is one read and one write of
 // the 27 populations per node; halo re-reads of neighbouring strips' columns
 // are served by L2.
 //
@@ -29,6 +30,10 @@
 // producer waits (bounded) for every copy it issued before the CTA exits.
 
 #include <cstdint>
+#include <cstring>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "lbm3_internal.h"
 
@@ -43,7 +48,9 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 constexpr float kNormalDelta = 1e-1f;
 
 struct Smem {
-  float pop[kSlots][27][kPW];  // pulled-row ring (row q in slot q % kSlots), plane = k*9 + i
+  // pulled-row ring (row q in slot q % kSlots): three TMA boxes of 9 planes x
+  // kPW columns, one per direction group, each starting on a 128-byte boundary
+  float pop[kSlots][3 * kGroupFloats];
   float phi[4][4][kDW];        // phi_1, phi_2, phi_3, rho of row q in slot q % 4
   float T[4][3][kTW];          // T_xx, T_xy, T_yy of row q in slot q % 4
   float nrm[3][6][kTX];        // n_12, n_13, n_23 (x, y) of row q in slot q % 3
@@ -120,13 +127,20 @@ __device__ void mbar_wait_drain(unsigned long long* bar, uint32_t parity) {
   }
 }
 
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         unsigned long long* bar) {
+// 3D tiled TMA load of one box (boxw, 1, 9) at (x, y, z) into shared memory,
+// completing on the given mbarrier.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar) {
   asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          su32(dst)),
-      "l"(src), "r"(bytes), "r"(su32(bar))
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(su32(bar))
       : "memory");
+}
+
+// Pulled value of colour k, direction i at ring column col of one slot.
+__device__ __forceinline__ float popv(const float* slot, int k, int i, int col) {
+  return slot[dir_group(i) * kGroupFloats + (3 * k + dir_pos(i)) * kPW + col];
 }
 
 __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory"); }
@@ -137,10 +151,13 @@ __device__ __forceinline__ int wrap(int a, int n) {
 }
 
 // ----------------------------------------------------------------- producer
-__device__ void produce(Smem& s, const StepArgs& a, int x0, int w, int y0, int nq, int lane) {
-  const int nx = a.nx, ny = a.ny;
-  const size_t N = static_cast<size_t>(nx) * ny;
-  const uint32_t row_bytes = 27u * static_cast<uint32_t>(w + 8) * 4u;
+// Row q of the march (y = y0 - 2 + q) needs, for the directions with
+// e_y = 1 - g, the source row y - e_y: three TMA boxes per row, one per group
+// g, each bringing the 9 planes of that group over columns [tma_x, tma_x + boxw).
+__device__ void produce(Smem& s, const StepArgs& a, const CUtensorMap* map, int x0, int y0, int nq, int lane) {
+  const int ny = a.ny;
+  const uint32_t row_bytes = 27u * static_cast<uint32_t>(a.boxw) * 4u;
+  const int tma_x = min(x0, a.pitch - a.boxw);
   volatile int* abort_flag = &s.abort_flag;
   int issued = 0;
   for (int q = 0; q < nq; ++q) {
@@ -157,22 +174,10 @@ __device__ void produce(Smem& s, const StepArgs& a, int x0, int w, int y0, int n
     if (!ok) break;
     if (lane == 0) mbar_arrive_expect_tx(&s.full[slot], row_bytes);
     __syncwarp();
-    if (lane < 27) {
-      const int i = lane % 9;
-      const int src_row = wrap(y0 - 2 + q - ey(i), ny);
-      const float* plane = a.fin + static_cast<size_t>(lane) * N + static_cast<size_t>(src_row) * nx;
-      float* dst = &s.pop[slot][lane][0];
-      // window [x0-4, x0+w+4) wrapped into [0, nx) in pieces; every piece
-      // starts and ends on a multiple of 4 floats (nx % 4 == 0, x0 % 4 == 0)
-      int start = x0 - 4, left = w + 8, off = 0;
-      while (left > 0) {
-        const int gx = wrap(start, nx);
-        const int len = min(left, nx - gx);
-        bulk_g2s(dst + off, plane + gx, static_cast<uint32_t>(len) * 4u, &s.full[slot]);
-        start += len;
-        off += len;
-        left -= len;
-      }
+    if (lane < 3) {
+      const int g = lane;  // e_y = 1 - g
+      const int src_row = wrap(y0 - 2 + q - (1 - g), ny);
+      tma_load_3d(&s.pop[slot][g * kGroupFloats], map, tma_x, src_row, 9 * g, &s.full[slot]);
     }
     __syncwarp();
     issued = q + 1;
@@ -210,16 +215,17 @@ __device__ __forceinline__ void colour_fractions(float r0, float r1, float r2, f
 }
 
 // D stage, one node: row q (window slot), window column c in [0, w+4), i.e.
-// x = x0 - 2 + c.  The pulled value of direction i sits at pop column
-// c + 2 - e_ix of row q's slot.
-__device__ __forceinline__ void stage_density(Smem& s, int q, int c) {
-  const float(*pp)[kPW] = s.pop[q % kSlots];
+// x = x0 - 2 + c.  The pulled value of direction i sits at ring column
+// colbase + c + 2 - e_ix of row q's slot.
+__device__ __forceinline__ void stage_density(Smem& s, int q, int c, int colbase) {
+  const float* pp = s.pop[q % kSlots];
+  const int cb = c + 2 + colbase;
   float r[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    float acc = pp[k * 9][c + 2];
+    float acc = popv(pp, k, 0, cb);
 #pragma unroll
-    for (int i = 1; i < 9; ++i) acc += pp[k * 9 + i][c + 2 - ex(i)];
+    for (int i = 1; i < 9; ++i) acc += popv(pp, k, i, cb - ex(i));
     r[k] = acc;
   }
   float phk[3], rho;
@@ -291,8 +297,9 @@ __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q,
 
 // C stage, one node: row q (output row y0 - 2 + q), column c in [0, w).
 template <int MODE>
-__device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q, int c, int x0, int y0) {
-  const float(*pp)[kPW] = s.pop[q % kSlots];
+__device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q, int c, int x0, int y0,
+                                              int colbase) {
+  const float* pp = s.pop[q % kSlots];
   const float(*Tm)[kTW] = s.T[(q - 1) & 3];
   const float(*Tz)[kTW] = s.T[q & 3];
   const float(*Tp)[kTW] = s.T[(q + 1) & 3];
@@ -303,8 +310,8 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
   float fi[9], r[3];
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const int col = c + 4 - ex(i);
-    const float a0 = pp[i][col], a1 = pp[9 + i][col], a2 = pp[18 + i][col];
+    const int col = c + 4 + colbase - ex(i);
+    const float a0 = popv(pp, 0, i, col), a1 = popv(pp, 1, i, col), a2 = popv(pp, 2, i, col);
     if (i == 0) {
       r[0] = a0;
       r[1] = a1;
@@ -341,9 +348,9 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
   const float ux = fmaf(0.5f, Fx, mx) * irho;
   const float uy = fmaf(0.5f, Fy, my) * irho;
   const int x = x0 + c, y = y0 - 2 + q;
-  const size_t N = static_cast<size_t>(a.nx) * a.ny;
-  const size_t idx = static_cast<size_t>(y) * a.nx + x;
   if (MODE == MODE_FIELDS) {
+    const size_t N = static_cast<size_t>(a.nx) * a.ny;
+    const size_t idx = static_cast<size_t>(y) * a.nx + x;
     if (a.out_rho) {
       a.out_rho[idx] = phi0 * rho;
       a.out_rho[N + idx] = phi1 * rho;
@@ -402,25 +409,41 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
   // V_k = sum_{l != k} beta_kl (rho_k rho_l / rho) n_kl, with n_lk = -n_kl
   const float Vx[3] = {Rx[0] + Rx[1], Rx[2] - Rx[0], -Rx[1] - Rx[2]};
   const float Vy[3] = {Ry[0] + Ry[1], Ry[2] - Ry[0], -Ry[1] - Ry[2]};
-  float* out = a.fout + idx;
+  // Eq. 6: f^ddagger_{i,k} = phi_k f^dagger_i + w'_i (e_i . V_k), stored at
+  // padded column x + 4 and, for the four columns next to each edge, also in
+  // the ghost column on the opposite side
+  float val[27];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    // Eq. 6: f^ddagger_{i,k} = phi_k f^dagger_i + w'_i (e_i . V_k)
-    out[static_cast<size_t>(k * 9) * N] = phv[k] * fd[0];
+    val[plane_of(k, 0)] = phv[k] * fd[0];
 #pragma unroll
     for (int i = 1; i <= 6; ++i) {
       if (i == 3 || i == 4) continue;
       const int o = (i == 1) ? 3 : (i == 2) ? 4 : (i == 5) ? 7 : 8;
       const float t = a.wrec[i] * (ex(i) * Vx[k] + ey(i) * Vy[k]);
-      out[static_cast<size_t>(k * 9 + i) * N] = fmaf(phv[k], fd[i], t);
-      out[static_cast<size_t>(k * 9 + o) * N] = fmaf(phv[k], fd[o], -t);
+      val[plane_of(k, i)] = fmaf(phv[k], fd[i], t);
+      val[plane_of(k, o)] = fmaf(phv[k], fd[o], -t);
     }
+  }
+  const size_t PS = static_cast<size_t>(a.ny) * a.pitch;  // plane stride
+  float* out = a.fout + static_cast<size_t>(y) * a.pitch + (x + kGhost);
+#pragma unroll
+  for (int p = 0; p < 27; ++p) out[p * PS] = val[p];
+  if (x < kGhost) {
+#pragma unroll
+    for (int p = 0; p < 27; ++p) out[p * PS + a.nx] = val[p];
+  }
+  if (x >= a.nx - kGhost) {
+#pragma unroll
+    for (int p = 0; p < 27; ++p) out[p * PS - a.nx] = val[p];
   }
 }
 
 template <int MODE>
 __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h, int tid) {
   const int nq = h + 4;  // rows q = 0 .. h+3 <-> y = y0-2 .. y0+h+1
+  // ring column of window column 0 (= padded column x0, node x0 - 4)
+  const int colbase = x0 - min(x0, a.pitch - a.boxw);
   volatile int* abort_flag = &s.abort_flag;
   bool dead = false;
   const int J = (h + 3) / 2 + 1;
@@ -440,7 +463,7 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
           const int it = tid + u * kConsumers;
           if (it < nr * W) {
             const int r = it >= W ? 1 : 0;
-            stage_density(s, q0 + r, it - r * W);
+            stage_density(s, q0 + r, it - r * W, colbase);
           }
         }
       }
@@ -470,7 +493,7 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
       if (nr > 0) {
         for (int it = tid; it < nr * w; it += kConsumers) {
           const int r = it >= w ? 1 : 0;
-          stage_collide<MODE>(s, a, qa + r, it - r * w, x0, y0);
+          stage_collide<MODE>(s, a, qa + r, it - r * w, x0, y0, colbase);
         }
       }
     }
@@ -484,9 +507,12 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 2) fused_step_kernel(StepArgs a) {
+__global__ void __launch_bounds__(kThreads, 2)
+    fused_step_kernel(StepArgs a, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  Smem& s = *reinterpret_cast<Smem*>(smem_raw);
+  // TMA destinations must be 128-byte aligned: align the block's base
+  const uint32_t pad = (128u - (su32(smem_raw) & 127u)) & 127u;
+  Smem& s = *reinterpret_cast<Smem*>(smem_raw + pad);
   const int strip = blockIdx.x % a.nstrips;
   const int chunk = blockIdx.x / a.nstrips;
   const int x0 = strip * kTX;
@@ -506,7 +532,7 @@ __global__ void __launch_bounds__(kThreads, 2) fused_step_kernel(StepArgs a) {
   }
   __syncthreads();
   if (tid >= kConsumers) {
-    produce(s, a, x0, w, y0, nq, tid - kConsumers);
+    produce(s, a, &tmap, x0, y0, nq, tid - kConsumers);
   } else {
     consume<MODE>(s, a, x0, w, y0, h, tid);
   }
@@ -514,27 +540,51 @@ __global__ void __launch_bounds__(kThreads, 2) fused_step_kernel(StepArgs a) {
 
 }  // namespace
 
-size_t step_smem_bytes() { return sizeof(Smem); }
+size_t step_smem_bytes() { return sizeof(Smem) + 128; }
 
 cudaError_t step_configure() {
-  cudaError_t e = cudaFuncSetAttribute(fused_step_kernel<MODE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(sizeof(Smem)));
+  const int bytes = static_cast<int>(step_smem_bytes());
+  cudaError_t e =
+      cudaFuncSetAttribute(fused_step_kernel<MODE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fused_step_kernel<MODE_FIELDS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              static_cast<int>(sizeof(Smem)));
+  return cudaFuncSetAttribute(fused_step_kernel<MODE_FIELDS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 int step_occupancy(int* blocks_per_sm) {
   return static_cast<int>(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      blocks_per_sm, fused_step_kernel<MODE_STEP>, kThreads, sizeof(Smem)));
+      blocks_per_sm, fused_step_kernel<MODE_STEP>, kThreads, step_smem_bytes()));
 }
 
-cudaError_t launch_step(const StepArgs& a, int grid, int mode, cudaStream_t st) {
+cudaError_t launch_step(const StepArgs& a, const void* tmap, int grid, int mode, cudaStream_t st) {
+  CUtensorMap m;
+  memcpy(&m, tmap, sizeof m);
   if (mode == MODE_STEP)
-    fused_step_kernel<MODE_STEP><<<grid, kThreads, sizeof(Smem), st>>>(a);
+    fused_step_kernel<MODE_STEP><<<grid, kThreads, step_smem_bytes(), st>>>(a, m);
   else
-    fused_step_kernel<MODE_FIELDS><<<grid, kThreads, sizeof(Smem), st>>>(a);
+    fused_step_kernel<MODE_FIELDS><<<grid, kThreads, step_smem_bytes(), st>>>(a, m);
   return cudaGetLastError();
+}
+
+cudaError_t encode_population_map(void* tmap, const float* buf, int nx, int ny) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const int P = pitch_of(nx);
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(P), static_cast<cuuint64_t>(ny), 27};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(P) * 4, static_cast<cuuint64_t>(ny) * P * 4};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(kPW), 1, 9};  // P >= kPW by construction
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode(static_cast<CUtensorMap*>(tmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                            const_cast<float*>(buf), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace lbm3

@@ -53,8 +53,9 @@ def test_invalid_params_rejected(lib, kw):
 
 
 def test_buffer_bytes(lib):
-    assert L.lbm3_buffer_bytes(L.Params(8, 4)) == 27 * 32 * 4
-    assert L.lbm3_buffer_bytes(L.Params(2048, 2048)) == 27 * 2048 * 2048 * 4
+    # 27 planes of ny rows with the padded pitch max(nx + 8, 136) (ghost columns for the periodic wrap)
+    assert L.lbm3_buffer_bytes(L.Params(8, 4)) == 27 * 4 * 136 * 4
+    assert L.lbm3_buffer_bytes(L.Params(2048, 2048)) == 27 * 2048 * 2056 * 4
 
 
 def test_null_context_is_einval(lib):
