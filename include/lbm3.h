@@ -82,7 +82,7 @@ typedef struct {
 } lbm3_params;
 
 /* Bytes of ONE population buffer for these parameters: 27 * ny * P * 4 for
- * FP32 with the row pitch P = max(nx + 8, 136) (rows carry four ghost columns
+ * FP32 with the row pitch P = max(nx + 8, 132) (rows carry four ghost columns
  * on each side that hold the periodic wrap).  Writes *bytes.  No device work. */
 lbm3_status lbm3_buffer_bytes(const lbm3_params* p, size_t* bytes);
 

@@ -29,7 +29,7 @@ __host__ __device__ constexpr float wt(int i) {
 
 // ------------------------------------------------------------ HBM layout
 // Populations are stored as 27 planes of ny rows with a padded pitch
-// P = max(nx + 8, 136): column xp = x + 4 holds node x, and the four ghost
+// P = max(nx + 8, 132): column xp = x + 4 holds node x, and the four ghost
 // columns on each side hold copies of the opposite edge (periodic wrap), so
 // that every strip's halo window is one contiguous, in-bounds span of a row.  Planes are
 // ordered by the y-component of their direction so that the nine planes a
@@ -44,20 +44,25 @@ __host__ __device__ constexpr int dir_pos(int i) {
 __host__ __device__ constexpr int plane_of(int k, int i) { return 9 * dir_group(i) + 3 * k + dir_pos(i); }
 // at least one full TMA box wide (kPW, defined below): narrow grids get unused
 // columns after the right ghosts so that every box row has the same pitch
-__host__ __device__ constexpr int pitch_of(int nx) { return nx + 2 * kGhost > 136 ? nx + 2 * kGhost : 136; }
+constexpr int kBoxCols = 132;  // = kPW below
+__host__ __device__ constexpr int pitch_of(int nx) {
+  return nx + 2 * kGhost > kBoxCols ? nx + 2 * kGhost : kBoxCols;
+}
 
 // ------------------------------------------------------- fused step tiling
 // One CTA owns a strip of up to kTX columns and a run of rows; it marches up
 // the rows two at a time with a 3-stage pipeline (densities -> tension tensor
 // -> force, collision, recolouring) fed by bulk async copies of pulled rows.
-constexpr int kTX = 128;          // max strip width (columns)
+// 124 columns: the D stage then has exactly 2 x 128 = 256 nodes per pair of
+// rows, one per consumer thread (T: 252, C: 248), so no warp does a second pass
+constexpr int kTX = 124;          // max strip width (columns)
 constexpr int kPW = kTX + 8;      // population row window: x0-4 .. x0+w+4 (one TMA box row)
-static_assert(kPW == 136, "pitch_of() assumes a 136-column box");
-constexpr int kGroupFloats = 1248;  // 9 planes x kPW = 1224 floats, padded to a 128-byte multiple
+static_assert(kPW == kBoxCols, "pitch_of() must cover one TMA box");
+constexpr int kGroupFloats = (9 * kPW + 31) / 32 * 32;  // 9 planes x kPW, padded to a 128-byte multiple
 constexpr int kDW = kTX + 4;      // density/phi window:     x0-2 .. x0+w+2
 constexpr int kTW = kTX + 2;      // tension-tensor window:  x0-1 .. x0+w+1
 constexpr int kSlots = 6;         // population ring depth (rows)
-constexpr int kConsumers = 160;   // 5 compute warps: 2 rows x (w+4) <= 2 items each
+constexpr int kConsumers = 256;   // 8 compute warps: one C-stage node each per pair of rows
 constexpr int kThreads = kConsumers + 32;  // + 1 copy-issuing warp
 
 struct StepArgs {

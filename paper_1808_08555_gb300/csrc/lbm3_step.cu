@@ -18,8 +18,8 @@
 //                               (streaming happens in the next step's pull).
 // Population rows reach shared memory by 3D tiled TMA loads
 // (cp.async.bulk.tensor + mbarrier complete_tx): per row three boxes of
-// 9 planes x 136 columns, issued by one producer warp into a ring of kSlots
-// rows; five consumer warps run the stages in lock step (two named barriers
+// 9 planes x 132 columns, issued by one producer warp into a ring of kSlots
+// rows; eight consumer warps run the stages in lock step (two named barriers
 // per pair of rows).  HBM traffic is one read and one write of
 // the 27 populations per node; halo re-reads of neighbouring strips' columns
 // are served by L2.
@@ -196,8 +196,8 @@ __device__ void produce(Smem& s, const StepArgs& a, const CUtensorMap* map, int 
 // node gets 1 +- 1 ulp, always with the same sign for the same density, and
 // the recolouring then creates or destroys that fluid's mass at a steady
 // ~1e-8 relative per step.  Shared by the D and C stages so both see
-// bit-identical fractions.
-__device__ __forceinline__ void colour_fractions(float r0, float r1, float r2, float* p, float* rho_out) {
+// bit-identical fractions.  Returns 1/rho (correctly rounded).
+__device__ __forceinline__ float colour_fractions(float r0, float r1, float r2, float* p, float* rho_out) {
   const float rho = (r0 + r1) + r2;
   const float ir = __frcp_rn(rho);
   float p0 = r0 * ir, p1 = r1 * ir, p2 = r2 * ir;
@@ -212,6 +212,7 @@ __device__ __forceinline__ void colour_fractions(float r0, float r1, float r2, f
   p[1] = p1;
   p[2] = p2;
   *rho_out = rho;
+  return ir;
 }
 
 // D stage, one node: row q (window slot), window column c in [0, w+4), i.e.
@@ -268,7 +269,9 @@ __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q,
     const float pp = ph[k] * ph[l];
     float mag = 0.0f;
     if (g2 > 1e-30f) {
-      const float rinv = __frsqrt_rn(g2);  // correctly rounded: no drift from a biased estimate
+      // hardware estimate (<= 2 ulp): it scales the tension and the normal's
+      // length, neither of which moves mass
+      const float rinv = rsqrtf(g2);
       mag = g2 * rinv;
       const float ck = fminf(a.cpair[p] * pp * rho2, 1.0f);  // Eq. 15 with rho_k = phi_k rho
       // sigma C |G| (I - n n) = sigma C (|G|^2 I - G G) / |G|
@@ -280,7 +283,7 @@ __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q,
     // recolouring normal G / max(|G|, kNormalDelta phi_k phi_l): the unit
     // normal wherever a k-l interface exists, continuous to 0 where G -> 0
     const float den = fmaxf(mag, kNormalDelta * pp);
-    const float rden = den > 1e-30f ? __frcp_rn(den) : 0.0f;  // |n| <= 1; tiny den -> 0
+    const float rden = den > 1e-30f ? __fdividef(1.0f, den) : 0.0f;  // |n| <= 1; tiny den -> 0
     nv[2 * p] = Gx * rden;
     nv[2 * p + 1] = Gy * rden;
   }
@@ -324,8 +327,7 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
     fi[i] = (a0 + a1) + a2;
   }
   float phv[3], rho;
-  colour_fractions(r[0], r[1], r[2], phv, &rho);
-  const float irho = __frcp_rn(rho);
+  const float irho = colour_fractions(r[0], r[1], r[2], phv, &rho);
   const float phi0 = phv[0], phi1 = phv[1], phi2 = phv[2];
   // F_s = div T (Eq. 11), T window column of this node is c + 1
   const int tc = c + 1;
@@ -363,7 +365,7 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
   }
   // Eqs. vis_1 / tau: 1/nu = sum_k phi_k / nu_k, tau_f = 3 nu + 1/2, omega = 1/tau_f
   const float inu = fmaf(phi0, a.inv_nu[0], fmaf(phi1, a.inv_nu[1], phi2 * a.inv_nu[2]));
-  const float om = inu * __frcp_rn(fmaf(0.5f, inu, 3.0f));
+  const float om = inu * __fdividef(1.0f, fmaf(0.5f, inu, 3.0f));  // relaxation rate; mass-neutral
   const float g = 1.0f - 0.5f * om;  // Guo prefactor (1 - 1/(2 tau_f))
   const float uu = ux * ux + uy * uy;
   const float uF = ux * Fx + uy * Fy;

@@ -53,8 +53,8 @@ def test_invalid_params_rejected(lib, kw):
 
 
 def test_buffer_bytes(lib):
-    # 27 planes of ny rows with the padded pitch max(nx + 8, 136) (ghost columns for the periodic wrap)
-    assert L.lbm3_buffer_bytes(L.Params(8, 4)) == 27 * 4 * 136 * 4
+    # 27 planes of ny rows with the padded pitch max(nx + 8, 132) (ghost columns for the periodic wrap)
+    assert L.lbm3_buffer_bytes(L.Params(8, 4)) == 27 * 4 * 132 * 4
     assert L.lbm3_buffer_bytes(L.Params(2048, 2048)) == 27 * 2048 * 2056 * 4
 
 
