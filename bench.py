@@ -261,6 +261,109 @@ def run_ours(args, ws, rank, local):
     return line
 
 
+def run_sweep(args):
+    """Morphology sweep: 64 independent instances (grid edges drawn from
+    {128,192,256,384,512} with seed 0, two touching droplets of radius N/6,
+    sigma_12/sigma_23 and sigma_13/sigma_23 on an 8x8 grid of
+    {0.2,...,2.0}), advanced together by one launch per step replayed from a
+    CUDA graph; compared with the same instances stepped one after another
+    with the single-grid kernel."""
+    import torch
+
+    from paper_1808_08555_gb300 import build as B
+    B.build()
+    from paper_1808_08555_gb300 import lbm3 as L
+    from paper_1808_08555_gb300 import workloads as W
+
+    cases = W.sweep_instances(seed=0)
+    params = [L.Params(c.nx, c.ny, tau=c.tau, sigma=c.sigma, beta0=c.beta0) for c in cases]
+    nodes = sum(c.nx * c.ny for c in cases)
+    batch = L.Batch(params)
+    work_items = batch.work_items
+    for i, c in enumerate(cases):
+        batch.init(i, W.touching_droplets(c.nx))
+    batch.step(args.warmup)
+    batch.sync()
+    s = batch.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    batch.step(args.steps)
+    e1.record(s)
+    e1.synchronize()
+    ms_batch = e0.elapsed_time(e1)
+    batch.close()
+    # the same instances one after another with the single-grid kernel
+    sims = []
+    for c, p in zip(cases, params):
+        sim = L.Simulation(p)
+        sim.init(W.touching_droplets(c.nx))
+        sim.step(args.warmup)
+        sims.append(sim)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for sim in sims:
+        sim.step(args.steps)
+    e1.record(s)
+    e1.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    for sim in sims:
+        sim.close()
+    v = nodes * args.steps / (ms_batch / 1e3) / 1e6
+    return {"metric": "ternary D2Q9 MLUPS, batched morphology sweep (64 instances)", "value": round(v, 2),
+            "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_batch / args.steps, 5), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sweep of 64 instances, edges {128..512} seed 0, touching droplets R=N/6",
+                       "nodes_per_step": nodes, "work_items": work_items},
+            "sequential_single_instance": {"value": round(nodes * args.steps / (ms_seq / 1e3) / 1e6, 2),
+                                           "unit": "MLUPS", "ms_per_step": round(ms_seq / args.steps, 5)},
+            "gpu_launches": args.steps}
+
+
+def run_janus(args):
+    """Reduced-precision storage: the 4096^2 Janus droplet (fluid 2 left and
+    fluid 3 right half of one circle of radius 600, sigma = 0.010/0.008/0.012,
+    a Neumann triangle) stepped with FP32, FP16-deviation and BF16-deviation
+    storage; MLUPS and HBM fraction of each (216 B/node-update for FP32,
+    132 B/node-update for the 16-bit forms)."""
+    import torch
+
+    from paper_1808_08555_gb300 import build as B
+    B.build()
+    from paper_1808_08555_gb300 import lbm3 as L
+    from paper_1808_08555_gb300 import workloads as W
+
+    n = args.size if args.size != 2048 else 4096
+    R = 600.0 * n / 4096
+    rho = W.janus_droplet(n, R)
+    peak, _ = hbm_peak()
+    out = {}
+    for st, name, bpn in ((0, "fp32", 216), (1, "fp16_dev", 132), (2, "bf16_dev", 132)):
+        sim = L.Simulation(L.Params(n, n, tau=(1.0, 1.0, 1.0), sigma=(0.010, 0.008, 0.012), storage=st))
+        sim.init(rho)
+        sim.step(args.warmup)
+        sim.sync()
+        s = sim.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        sim.step(args.steps)
+        e1.record(s)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        m, _ = sim.mass()
+        sim.close()
+        mlups = n * n / ms / 1e3
+        out[name] = {"MLUPS": round(mlups, 1), "ms_per_step": round(ms, 5), "bytes_per_node": bpn,
+                     "hbm_frac": round(bpn * mlups * 1e6 / (peak * 1e9), 4), "mass": [float(v) for v in m]}
+    return {"metric": "ternary D2Q9 MLUPS by population storage (Janus droplet)", "value": out["fp16_dev"]["MLUPS"],
+            "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["fp16_dev"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 arithmetic, 16-bit deviation storage", "data": "synthetic",
+            "config": {"workload": f"Janus droplet {n}x{n}, R={R:g}, sigma=0.010/0.008/0.012, tau=1"},
+            "storages": out, "gpu_launches": args.steps}
+
+
 def cpu_baseline(case, steps: int):
     """The FP64 oracle as it stands, single-threaded on a host core, on a
     bounded sample of the same workload: `steps` steps of the full grid."""
@@ -313,6 +416,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="compound", choices=["compound", "sweep", "janus"],
+                    help="compound: the 2048^2 compound droplet (default); sweep: the 64-instance batch; "
+                         "janus: the 4096^2 Janus droplet with FP32 / FP16 / BF16 storage")
     ap.add_argument("--size", type=int, default=2048,
                     help="grid edge; other than 2048 scales the droplet radii (profiling only)")
     args = ap.parse_args()
@@ -329,7 +435,14 @@ def main():
             torch.cuda.set_device(local)
         dist.init_process_group(backend=backend)
     try:
-        line = run_reference(args, ws, rank) if args.impl == "reference" else run_ours(args, ws, rank, local)
+        if args.impl == "reference":
+            line = run_reference(args, ws, rank)
+        elif args.workload == "sweep":
+            line = run_sweep(args) if rank == 0 else None
+        elif args.workload == "janus":
+            line = run_janus(args) if rank == 0 else None
+        else:
+            line = run_ours(args, ws, rank, local)
         if line is not None:
             print(json.dumps(line), flush=True)
     finally:

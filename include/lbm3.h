@@ -51,7 +51,9 @@ typedef enum {
 } lbm3_status;
 
 typedef enum {
-  LBM3_FP32 = 0 /* populations stored as FP32, FP32 arithmetic */
+  LBM3_FP32 = 0,     /* populations stored as FP32, FP32 arithmetic */
+  LBM3_FP16_DEV = 1, /* stored as FP32 rho'_k per node plus FP16 deviations f - w_i rho'_k; FP32 arithmetic */
+  LBM3_BF16_DEV = 2  /* the same with BF16 deviations */
 } lbm3_storage;
 
 typedef enum {
@@ -81,17 +83,21 @@ typedef struct {
   int32_t reserved;   /* must be 0 */
 } lbm3_params;
 
-/* Bytes of ONE population buffer for these parameters: 27 * ny * P * 4 for
- * FP32 with the row pitch P = max(nx + 8, 132) (rows carry four ghost columns
- * on each side that hold the periodic wrap).  Writes *bytes.  No device work. */
+/* Bytes of ONE population buffer for these parameters, with the row pitch
+ * P = max(nx + 8, 136) rounded up to a multiple of 8 (rows carry four ghost
+ * columns on each side that hold the periodic wrap): 27 * ny * P * 4 for FP32
+ * storage, 27 * ny * P * 2 + 3 * ny * P * 4 for the 16-bit deviation
+ * storages.  Writes *bytes.  No device work. */
 lbm3_status lbm3_buffer_bytes(const lbm3_params* p, size_t* bytes);
 
 /* Validate p and create a context bound to the current CUDA device and to
  * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
  * context allocates a small reduction scratch area (< 1 MiB).  It allocates
  * the two population buffers itself unless lbm3_bind_buffers is called
- * before the first lbm3_init / lbm3_set_populations.  *out receives the
- * context (NULL on failure). */
+ * before the first lbm3_init / lbm3_set_populations.  With a 16-bit deviation
+ * storage it also allocates, on the first lbm3_init / lbm3_set_populations /
+ * lbm3_populations call, one FP32 buffer (27 * ny * P * 4 bytes) used to
+ * convert host data.  *out receives the context (NULL on failure). */
 lbm3_status lbm3_create(const lbm3_params* p, void* cuda_stream, lbm3_ctx** out);
 
 /* Use caller-owned device memory for the two population buffers (each at
@@ -137,6 +143,44 @@ lbm3_status lbm3_populations(lbm3_ctx* ctx, double* f, int on_device);
  * Eq. uk1 sums to zero on a periodic grid).  Either pointer may be NULL.
  * Returns LBM3_ENUMERIC if a sum is NaN or Inf. */
 lbm3_status lbm3_mass(lbm3_ctx* ctx, double* mass, double* mom);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent simulations advanced together (a parameter or
+ * morphology sweep).  Each instance has its own grid size and parameters;
+ * one kernel launch per step covers every tile of every instance, and the
+ * steps are replayed from a captured two-step CUDA graph.  Per-instance
+ * results are bit-identical to running the same instance alone (same
+ * arithmetic per node).  The paper runs its cases one at a time; batching is
+ * a property of this library, not of the method.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm3_batch lbm3_batch;
+
+/* Create `count` instances from params[0..count-1] (each validated as in
+ * lbm3_create) on the current device and `cuda_stream`.  All population
+ * buffers are allocated here.  rows_per_cta: rows per work item (0 =
+ * automatic: the tile height whose largest-first assignment of work items to
+ * the GPU's resident CTA slots gives the shortest estimated step).
+ * *out receives the batch (NULL on failure). */
+lbm3_status lbm3_batch_create(const lbm3_params* params, int32_t count, void* cuda_stream, int32_t rows_per_cta,
+                              lbm3_batch** out);
+/* Number of instances; number of CTA work items of one step. */
+int32_t lbm3_batch_count(const lbm3_batch* b);
+int32_t lbm3_batch_work_items(const lbm3_batch* b);
+/* Per-instance state set-up and read-out, as the lbm3_* calls of the same
+ * name for instance i (0 <= i < count). */
+lbm3_status lbm3_batch_init(lbm3_batch* b, int32_t i, const double* rho, int on_device);
+lbm3_status lbm3_batch_set_populations(lbm3_batch* b, int32_t i, const double* f, int on_device);
+lbm3_status lbm3_batch_fields(lbm3_batch* b, int32_t i, double* rho, double* ux, double* uy, double* p,
+                              int on_device);
+lbm3_status lbm3_batch_populations(lbm3_batch* b, int32_t i, double* f, int on_device);
+lbm3_status lbm3_batch_mass(lbm3_batch* b, int32_t i, double* mass, double* mom);
+/* Advance every instance by n >= 0 steps (asynchronous; every instance must
+ * have been initialised, else LBM3_ESTATE). */
+lbm3_status lbm3_batch_step(lbm3_batch* b, int64_t n);
+lbm3_status lbm3_batch_sync(lbm3_batch* b);
+int64_t lbm3_batch_time(const lbm3_batch* b);
+lbm3_status lbm3_batch_destroy(lbm3_batch* b);
+const char* lbm3_batch_last_error(const lbm3_batch* b);
 
 /* Allocation-free FP64 mass/momentum reduction, for callers that cannot
  * call cudaMalloc (all their device memory is owned by their own pool or

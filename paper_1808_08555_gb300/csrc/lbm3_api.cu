@@ -7,12 +7,14 @@
 // host input/output, so no extra full-grid allocation is made.  Each buffer
 // has a TMA tensor descriptor, encoded once when the buffer is set.
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/lbm3.h"
 #include "lbm3_internal.h"
@@ -40,7 +42,9 @@ struct lbm3_ctx {
   int red_blocks = 1;
   int rows_override = 0;
   StepArgs base{};
-  alignas(64) unsigned char tmap[2][128];  // CUtensorMap of buf[0] and buf[1]
+  // TMA descriptors of buf[0] and buf[1]: one (FP32) or two (deviations, rho')
+  alignas(64) unsigned char tmap[2][256];
+  float* shadow = nullptr;  // 16-bit storage: FP32 copy of one buffer for host I/O
   std::string msg;
 };
 
@@ -71,9 +75,9 @@ lbm3_status cuda_fail(lbm3_ctx* c, cudaError_t e, const char* where) {
 size_t nodes(const lbm3_params& p) { return static_cast<size_t>(p.nx) * static_cast<size_t>(p.ny); }
 
 // one population buffer: 27 planes of ny rows with the padded pitch nx + 8
-size_t buffer_bytes(const lbm3_params& p) {
-  return 27 * static_cast<size_t>(lbm3::pitch_of(p.nx)) * static_cast<size_t>(p.ny) * sizeof(float);
-}
+size_t buffer_bytes(const lbm3_params& p) { return lbm3::population_bytes(p.nx, p.ny, p.storage); }
+
+size_t fp32_bytes(const lbm3_params& p) { return lbm3::population_bytes(p.nx, p.ny, LBM3_FP32); }
 
 lbm3_status validate(const lbm3_params* p, std::string* why) {
   char b[256];
@@ -113,7 +117,7 @@ lbm3_status validate(const lbm3_params* p, std::string* why) {
     return LBM3_EINVAL;
   }
   if (p->beta_form < 0 || p->beta_form > 3 || p->recolor_form < 0 || p->recolor_form > 1 ||
-      p->storage != LBM3_FP32 || p->reserved != 0) {
+      p->storage < LBM3_FP32 || p->storage > LBM3_BF16_DEV || p->reserved != 0) {
     *why = "lbm3: beta_form, recolor_form, storage or reserved out of range";
     return LBM3_EINVAL;
   }
@@ -200,7 +204,7 @@ struct DeviceGuard {
 
 lbm3_status encode_maps(lbm3_ctx* c) {
   for (int b = 0; b < 2; ++b) {
-    const cudaError_t e = lbm3::encode_population_map(c->tmap[b], c->buf[b], c->p.nx, c->p.ny);
+    const cudaError_t e = lbm3::encode_population_maps(c->tmap[b], c->buf[b], c->p.nx, c->p.ny, c->p.storage);
     if (e != cudaSuccess) return cuda_fail(c, e, "encoding the TMA descriptor of a population buffer");
   }
   return LBM3_OK;
@@ -223,6 +227,38 @@ lbm3_status ensure_buffers(lbm3_ctx* c) {
   c->buf[1] = static_cast<float*>(b);
   c->owns_bufs = true;
   return encode_maps(c);
+}
+
+// FP32 target of host input: the current buffer, or for 16-bit storage the
+// FP32 shadow (allocated on first use) that is then encoded into it.
+lbm3_status fp32_target(lbm3_ctx* c, float** out) {
+  if (c->p.storage == LBM3_FP32) {
+    *out = c->buf[c->cur];
+    return LBM3_OK;
+  }
+  if (!c->shadow) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, fp32_bytes(c->p)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, LBM3_ENOMEM, "lbm3: cannot allocate the FP32 shadow for 16-bit storage");
+    }
+    c->shadow = static_cast<float*>(p);
+  }
+  *out = c->shadow;
+  return LBM3_OK;
+}
+
+lbm3_status commit_fp32(lbm3_ctx* c) {
+  if (c->p.storage == LBM3_FP32) return LBM3_OK;
+  LBM3_CUDA(c, lbm3::launch_encode(c->shadow, c->buf[c->cur], c->p.nx, c->p.ny, c->p.storage, c->stream));
+  return LBM3_OK;
+}
+
+// planes of FP64 data that fit in the staging buffer at once
+int staging_planes(const lbm3_ctx* c) {
+  const size_t per = nodes(c->p) * sizeof(double);
+  size_t n = c->buf_bytes / per;
+  return static_cast<int>(n > 13 ? 13 : (n < 1 ? 1 : n));
 }
 
 // Read and clear the device error word (synchronises the stream).
@@ -257,6 +293,13 @@ StepArgs args_for(const lbm3_ctx* c, const float* fin, float* fout, int* grid) {
   StepArgs a = c->base;
   a.fin = fin;
   a.fout = fout;
+  if (c->p.storage != LBM3_FP32) {
+    const size_t PS = static_cast<size_t>(lbm3::pitch_of(c->p.nx)) * c->p.ny;
+    a.din = reinterpret_cast<const unsigned short*>(fin);
+    a.dout = reinterpret_cast<unsigned short*>(fout);
+    a.rin = fin ? reinterpret_cast<const float*>(a.din + 27 * PS) : nullptr;
+    a.rout = fout ? reinterpret_cast<float*>(a.dout + 27 * PS) : nullptr;
+  }
   int rows = 0;
   tiling(c, &rows, grid);
   a.rows_per_cta = rows;
@@ -371,7 +414,12 @@ lbm3_status lbm3_init(lbm3_ctx* c, const double* rho, int on_device) {
     LBM3_CUDA(c, cudaStreamSynchronize(c->stream));
     if (bad) return fail(c, LBM3_EINVAL, "lbm3_init: device rho has a node with rho_k < 0, NaN or sum 0");
   }
-  LBM3_CUDA(c, lbm3::launch_init_from_rho(src, c->buf[c->cur], c->p.nx, c->p.ny, c->stream));
+  float* target = nullptr;
+  st = fp32_target(c, &target);
+  if (st != LBM3_OK) return st;
+  LBM3_CUDA(c, lbm3::launch_init_from_rho(src, target, c->p.nx, c->p.ny, c->stream));
+  st = commit_fp32(c);
+  if (st != LBM3_OK) return st;
   if (!on_device) LBM3_CUDA(c, cudaStreamSynchronize(c->stream));  // staging reused next
   c->state_set = true;
   c->t = 0;
@@ -385,18 +433,24 @@ lbm3_status lbm3_set_populations(lbm3_ctx* c, const double* f, int on_device) {
   lbm3_status st = ensure_buffers(c);
   if (st != LBM3_OK) return st;
   const size_t N = nodes(c->p);
+  float* target = nullptr;
+  st = fp32_target(c, &target);
+  if (st != LBM3_OK) return st;
   if (on_device) {
-    LBM3_CUDA(c, lbm3::launch_set_planes(f, c->buf[c->cur], c->p.nx, c->p.ny, 0, 27, c->stream));
+    LBM3_CUDA(c, lbm3::launch_set_planes(f, target, c->p.nx, c->p.ny, 0, 27, c->stream));
   } else {
     double* staging = reinterpret_cast<double*>(c->buf[c->cur ^ 1]);
-    for (int p0 = 0; p0 < 27; p0 += 13) {
-      const int np = p0 + 13 <= 27 ? 13 : 27 - p0;
+    const int chunk = staging_planes(c);
+    for (int p0 = 0; p0 < 27; p0 += chunk) {
+      const int np = p0 + chunk <= 27 ? chunk : 27 - p0;
       LBM3_CUDA(c, cudaMemcpyAsync(staging, f + static_cast<size_t>(p0) * N, np * N * sizeof(double),
                                    cudaMemcpyHostToDevice, c->stream));
-      LBM3_CUDA(c, lbm3::launch_set_planes(staging, c->buf[c->cur], c->p.nx, c->p.ny, p0, np, c->stream));
+      LBM3_CUDA(c, lbm3::launch_set_planes(staging, target, c->p.nx, c->p.ny, p0, np, c->stream));
       LBM3_CUDA(c, cudaStreamSynchronize(c->stream));
     }
   }
+  st = commit_fp32(c);
+  if (st != LBM3_OK) return st;
   c->state_set = true;
   c->t = 0;
   return LBM3_OK;
@@ -417,7 +471,7 @@ lbm3_status lbm3_step(lbm3_ctx* c, int64_t n) {
   for (int64_t s = 0; s < n; ++s) {
     int grid = 0;
     StepArgs a = args_for(c, c->buf[c->cur], c->buf[c->cur ^ 1], &grid);
-    LBM3_CUDA(c, lbm3::launch_step(a, c->tmap[c->cur], grid, lbm3::MODE_STEP, c->stream));
+    LBM3_CUDA(c, lbm3::launch_step(a, c->tmap[c->cur], grid, lbm3::MODE_STEP, c->p.storage, c->stream));
     c->cur ^= 1;
     c->t += 1;
   }
@@ -443,7 +497,7 @@ lbm3_status lbm3_fields(lbm3_ctx* c, double* rho, double* ux, double* uy, double
     a.out_uy = uy ? staging + 4 * N : nullptr;
     a.out_p = pr ? staging + 5 * N : nullptr;
   }
-  LBM3_CUDA(c, lbm3::launch_step(a, c->tmap[c->cur], grid, lbm3::MODE_FIELDS, c->stream));
+  LBM3_CUDA(c, lbm3::launch_step(a, c->tmap[c->cur], grid, lbm3::MODE_FIELDS, c->p.storage, c->stream));
   if (!on_device) {
     if (rho) LBM3_CUDA(c, cudaMemcpyAsync(rho, staging, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (ux) LBM3_CUDA(c, cudaMemcpyAsync(ux, staging + 3 * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -460,14 +514,23 @@ lbm3_status lbm3_populations(lbm3_ctx* c, double* f, int on_device) {
   if (!c->state_set) return fail(c, LBM3_ESTATE, "lbm3_populations: state not initialised");
   DeviceGuard g(c->device);
   const size_t N = nodes(c->p);
+  const float* src = c->buf[c->cur];
+  if (c->p.storage != LBM3_FP32) {
+    float* sh = nullptr;
+    lbm3_status st = fp32_target(c, &sh);
+    if (st != LBM3_OK) return st;
+    LBM3_CUDA(c, lbm3::launch_decode(c->buf[c->cur], sh, c->p.nx, c->p.ny, c->p.storage, c->stream));
+    src = sh;
+  }
   if (on_device) {
-    LBM3_CUDA(c, lbm3::launch_get_planes(c->buf[c->cur], f, c->p.nx, c->p.ny, 0, 27, c->stream));
+    LBM3_CUDA(c, lbm3::launch_get_planes(src, f, c->p.nx, c->p.ny, 0, 27, c->stream));
     return LBM3_OK;
   }
   double* staging = reinterpret_cast<double*>(c->buf[c->cur ^ 1]);
-  for (int p0 = 0; p0 < 27; p0 += 13) {
-    const int np = p0 + 13 <= 27 ? 13 : 27 - p0;
-    LBM3_CUDA(c, lbm3::launch_get_planes(c->buf[c->cur], staging, c->p.nx, c->p.ny, p0, np, c->stream));
+  const int chunk = staging_planes(c);
+  for (int p0 = 0; p0 < 27; p0 += chunk) {
+    const int np = p0 + chunk <= 27 ? chunk : 27 - p0;
+    LBM3_CUDA(c, lbm3::launch_get_planes(src, staging, c->p.nx, c->p.ny, p0, np, c->stream));
     LBM3_CUDA(c, cudaMemcpyAsync(f + static_cast<size_t>(p0) * N, staging, np * N * sizeof(double),
                                  cudaMemcpyDeviceToHost, c->stream));
     LBM3_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -479,8 +542,12 @@ lbm3_status lbm3_mass(lbm3_ctx* c, double* mass, double* mom) {
   if (!c) return LBM3_EINVAL;
   if (!c->state_set) return fail(c, LBM3_ESTATE, "lbm3_mass: state not initialised");
   DeviceGuard g(c->device);
-  LBM3_CUDA(c, lbm3::launch_reduce_padded(c->buf[c->cur], c->p.nx, c->p.ny, c->partial, c->red_blocks,
-                                          c->red_out, c->stream));
+  if (c->p.storage == LBM3_FP32)
+    LBM3_CUDA(c, lbm3::launch_reduce_padded(c->buf[c->cur], c->p.nx, c->p.ny, c->partial, c->red_blocks,
+                                            c->red_out, c->stream));
+  else
+    LBM3_CUDA(c, lbm3::launch_reduce_dev(c->buf[c->cur], c->p.nx, c->p.ny, c->p.storage, c->partial,
+                                         c->red_blocks, c->red_out, c->stream));
   double h[5];
   LBM3_CUDA(c, cudaMemcpyAsync(h, c->red_out, sizeof h, cudaMemcpyDeviceToHost, c->stream));
   lbm3_status st = check_device_errors(c);
@@ -512,6 +579,7 @@ lbm3_status lbm3_destroy(lbm3_ctx* c) {
     cudaFree(c->buf[0]);
     cudaFree(c->buf[1]);
   }
+  if (c->shadow) cudaFree(c->shadow);
   cudaFree(c->scratch);
   cudaGetLastError();
   delete c;
@@ -519,5 +587,282 @@ lbm3_status lbm3_destroy(lbm3_ctx* c) {
 }
 
 const char* lbm3_last_error(const lbm3_ctx* c) { return c ? c->msg.c_str() : kNullCtxMsg; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batches
+// A batch is a set of independent simulations (own grid size and
+// parameters) advanced together: one launch per step covers every tile of
+// every instance, and steps are replayed from a captured two-step CUDA graph.
+// Each instance is an ordinary context underneath, so per-instance set-up and
+// read-out use the single-instance code paths.
+
+struct lbm3_batch {
+  std::vector<lbm3_ctx*> ctx;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream for graph capture
+  lbm3::BatchItem* d_items = nullptr;
+  lbm3::BatchDesc* d_descs = nullptr;
+  int nitems = 0;
+  int rows = 64;
+  int device = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // two steps, by starting parity
+  int64_t t = 0;
+  std::string msg;
+};
+
+namespace {
+
+const char* kNullBatchMsg = "lbm3: NULL batch";
+
+lbm3_status bfail(lbm3_batch* b, lbm3_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (b) b->msg = buf;
+  return st;
+}
+
+lbm3_status bcheck(lbm3_batch* b, lbm3_status st, int i) {
+  if (st != LBM3_OK && b) b->msg = std::string("instance ") + std::to_string(i) + ": " + b->ctx[i]->msg;
+  return st;
+}
+
+void destroy_batch(lbm3_batch* b) {
+  for (int p = 0; p < 2; ++p)
+    if (b->graph[p]) cudaGraphExecDestroy(b->graph[p]);
+  for (lbm3_ctx* c : b->ctx) lbm3_destroy(c);
+  if (b->d_items) cudaFree(b->d_items);
+  if (b->d_descs) cudaFree(b->d_descs);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  cudaGetLastError();
+  delete b;
+}
+
+lbm3_status launch_one(lbm3_batch* b, int parity, cudaStream_t st) {
+  const cudaError_t e = lbm3::launch_batch(b->d_items, b->nitems, b->d_descs, parity, st);
+  if (e != cudaSuccess) return bfail(b, LBM3_ECUDA, "lbm3_batch_step: %s", cudaGetErrorString(e));
+  return LBM3_OK;
+}
+
+lbm3_status build_graph(lbm3_batch* b, int parity) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e1 = lbm3::launch_batch(b->d_items, b->nitems, b->d_descs, parity, b->cap_stream);
+    cudaError_t e2 = lbm3::launch_batch(b->d_items, b->nitems, b->d_descs, parity ^ 1, b->cap_stream);
+    e = cudaStreamEndCapture(b->cap_stream, &g);
+    if (e == cudaSuccess && e1 != cudaSuccess) e = e1;
+    if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph[parity], g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, LBM3_ECUDA, "lbm3_batch_step: graph capture failed: %s", cudaGetErrorString(e));
+  }
+  return LBM3_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm3_status lbm3_batch_create(const lbm3_params* params, int32_t count, void* cuda_stream, int32_t rows_per_cta,
+                              lbm3_batch** out) {
+  if (!out) return LBM3_EINVAL;
+  *out = nullptr;
+  if (!params || count <= 0 || rows_per_cta < 0) return LBM3_EINVAL;
+  lbm3_batch* b = new (std::nothrow) lbm3_batch();
+  if (!b) return LBM3_ENOMEM;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (rows_per_cta > 0) b->rows = rows_per_cta;
+  cudaGetDevice(&b->device);
+  for (int i = 0; i < count; ++i) {
+    lbm3_ctx* c = nullptr;
+    lbm3_status st = lbm3_create(&params[i], cuda_stream, &c);
+    if (st != LBM3_OK) {
+      std::fprintf(stderr, "lbm3_batch_create: instance %d rejected\n", i);
+      destroy_batch(b);
+      return st;
+    }
+    b->ctx.push_back(c);
+    if (c->p.storage != LBM3_FP32) {
+      std::fprintf(stderr, "lbm3_batch_create: instance %d: batches use FP32 storage\n", i);
+      destroy_batch(b);
+      return LBM3_EINVAL;
+    }
+    st = ensure_buffers(c);
+    if (st != LBM3_OK) {
+      std::fprintf(stderr, "lbm3_batch_create: instance %d: %s\n", i, c->msg.c_str());
+      destroy_batch(b);
+      return st;
+    }
+  }
+  // per-instance descriptors and the work list (largest tiles first)
+  std::vector<lbm3::BatchDesc> descs(count);
+  std::vector<lbm3::BatchItem> items;
+  for (int i = 0; i < count; ++i) {
+    lbm3_ctx* c = b->ctx[i];
+    for (int p = 0; p < 2; ++p) {
+      int grid = 0;
+      descs[i].args[p] = args_for(c, c->buf[p], c->buf[p ^ 1], &grid);
+      std::memcpy(descs[i].map[p], c->tmap[p], 128);
+    }
+  }
+  // Tile height: given, or the one whose largest-first assignment of the work
+  // items to the resident CTA slots gives the shortest estimated step (item
+  // cost ~ (h + 4 halo rows) x (w + 32 columns of per-row overhead)).
+  auto make_items = [&](int rows, std::vector<lbm3::BatchItem>* out_items) {
+    out_items->clear();
+    for (int i = 0; i < count; ++i) {
+      lbm3_ctx* c = b->ctx[i];
+      const int ns = (c->p.nx + lbm3::kTX - 1) / lbm3::kTX;
+      const int H = std::min(rows, c->p.ny);
+      for (int y0 = 0; y0 < c->p.ny; y0 += H)
+        for (int s = 0; s < ns; ++s) {
+          const int x0 = lbm3::strip_x0(s, ns, c->p.nx);
+          out_items->push_back({i, x0, lbm3::strip_x0(s + 1, ns, c->p.nx) - x0, y0, std::min(H, c->p.ny - y0)});
+        }
+    }
+    std::stable_sort(out_items->begin(), out_items->end(), [](const lbm3::BatchItem& a, const lbm3::BatchItem& c) {
+      return a.w * (a.h + 4) > c.w * (c.h + 4);
+    });
+  };
+  const int slots = std::max(1, b->ctx[0]->occ * b->ctx[0]->num_sms);
+  auto makespan = [&](const std::vector<lbm3::BatchItem>& its) {
+    std::vector<double> load(static_cast<size_t>(slots), 0.0);
+    for (const lbm3::BatchItem& it : its) {
+      auto m = std::min_element(load.begin(), load.end());
+      *m += static_cast<double>(it.h + 4) * (it.w + 32);
+    }
+    return *std::max_element(load.begin(), load.end());
+  };
+  if (rows_per_cta > 0) {
+    make_items(rows_per_cta, &items);
+  } else {
+    double best = 0.0;
+    for (int rows = 16; rows <= 512; rows += 8) {
+      std::vector<lbm3::BatchItem> cand;
+      make_items(rows, &cand);
+      const double t = makespan(cand);
+      if (items.empty() || t < best) {
+        best = t;
+        items.swap(cand);
+        b->rows = rows;
+      }
+    }
+  }
+  b->nitems = static_cast<int>(items.size());
+  cudaError_t e = cudaMalloc(&b->d_items, sizeof(lbm3::BatchItem) * items.size());
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_descs, sizeof(lbm3::BatchDesc) * descs.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_items, items.data(), sizeof(lbm3::BatchItem) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_descs, descs.data(), sizeof(lbm3::BatchDesc) * descs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "lbm3_batch_create: %s\n", cudaGetErrorString(e));
+    cudaGetLastError();
+    destroy_batch(b);
+    return LBM3_ECUDA;
+  }
+  *out = b;
+  return LBM3_OK;
+}
+
+int32_t lbm3_batch_count(const lbm3_batch* b) { return b ? static_cast<int32_t>(b->ctx.size()) : -1; }
+
+int32_t lbm3_batch_work_items(const lbm3_batch* b) { return b ? b->nitems : -1; }
+
+lbm3_status lbm3_batch_init(lbm3_batch* b, int32_t i, const double* rho, int on_device) {
+  if (!b) return LBM3_EINVAL;
+  if (i < 0 || i >= static_cast<int32_t>(b->ctx.size())) return bfail(b, LBM3_EINVAL, "lbm3_batch_init: index %d", i);
+  return bcheck(b, lbm3_init(b->ctx[i], rho, on_device), i);
+}
+
+lbm3_status lbm3_batch_set_populations(lbm3_batch* b, int32_t i, const double* f, int on_device) {
+  if (!b) return LBM3_EINVAL;
+  if (i < 0 || i >= static_cast<int32_t>(b->ctx.size()))
+    return bfail(b, LBM3_EINVAL, "lbm3_batch_set_populations: index %d", i);
+  return bcheck(b, lbm3_set_populations(b->ctx[i], f, on_device), i);
+}
+
+lbm3_status lbm3_batch_step(lbm3_batch* b, int64_t n) {
+  if (!b) return LBM3_EINVAL;
+  if (n < 0) return bfail(b, LBM3_EINVAL, "lbm3_batch_step: n < 0");
+  for (size_t i = 0; i < b->ctx.size(); ++i)
+    if (!b->ctx[i]->state_set) return bfail(b, LBM3_ESTATE, "lbm3_batch_step: instance %zu not initialised", i);
+  DeviceGuard g(b->device);
+  const int parity = b->ctx[0]->cur;
+  auto advance = [&](int64_t k) {
+    for (lbm3_ctx* c : b->ctx) {
+      if (k & 1) c->cur ^= 1;
+      c->t += k;
+    }
+    b->t += k;
+  };
+  if (n >= 2) {
+    if (!b->graph[parity]) {
+      lbm3_status st = build_graph(b, parity);
+      if (st != LBM3_OK) return st;
+    }
+    for (int64_t k = 0; k < n / 2; ++k) {
+      const cudaError_t e = cudaGraphLaunch(b->graph[parity], b->stream);
+      if (e != cudaSuccess) return bfail(b, LBM3_ECUDA, "lbm3_batch_step: %s", cudaGetErrorString(e));
+    }
+    advance(n / 2 * 2);
+  }
+  if (n & 1) {
+    lbm3_status st = launch_one(b, b->ctx[0]->cur, b->stream);
+    if (st != LBM3_OK) return st;
+    advance(1);
+  }
+  return LBM3_OK;
+}
+
+lbm3_status lbm3_batch_fields(lbm3_batch* b, int32_t i, double* rho, double* ux, double* uy, double* p,
+                              int on_device) {
+  if (!b) return LBM3_EINVAL;
+  if (i < 0 || i >= static_cast<int32_t>(b->ctx.size()))
+    return bfail(b, LBM3_EINVAL, "lbm3_batch_fields: index %d", i);
+  return bcheck(b, lbm3_fields(b->ctx[i], rho, ux, uy, p, on_device), i);
+}
+
+lbm3_status lbm3_batch_populations(lbm3_batch* b, int32_t i, double* f, int on_device) {
+  if (!b) return LBM3_EINVAL;
+  if (i < 0 || i >= static_cast<int32_t>(b->ctx.size()))
+    return bfail(b, LBM3_EINVAL, "lbm3_batch_populations: index %d", i);
+  return bcheck(b, lbm3_populations(b->ctx[i], f, on_device), i);
+}
+
+lbm3_status lbm3_batch_mass(lbm3_batch* b, int32_t i, double* mass, double* mom) {
+  if (!b) return LBM3_EINVAL;
+  if (i < 0 || i >= static_cast<int32_t>(b->ctx.size())) return bfail(b, LBM3_EINVAL, "lbm3_batch_mass: index %d", i);
+  return bcheck(b, lbm3_mass(b->ctx[i], mass, mom), i);
+}
+
+lbm3_status lbm3_batch_sync(lbm3_batch* b) {
+  if (!b) return LBM3_EINVAL;
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    lbm3_status st = lbm3_sync(b->ctx[i]);
+    if (st != LBM3_OK) return bcheck(b, st, static_cast<int>(i));
+  }
+  return LBM3_OK;
+}
+
+int64_t lbm3_batch_time(const lbm3_batch* b) { return b ? b->t : -1; }
+
+lbm3_status lbm3_batch_destroy(lbm3_batch* b) {
+  if (!b) return LBM3_OK;
+  DeviceGuard g(b->device);
+  cudaStreamSynchronize(b->stream);
+  destroy_batch(b);
+  return LBM3_OK;
+}
+
+const char* lbm3_batch_last_error(const lbm3_batch* b) { return b ? b->msg.c_str() : kNullBatchMsg; }
 
 }  // extern "C"

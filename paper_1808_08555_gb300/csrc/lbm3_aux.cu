@@ -81,6 +81,51 @@ __global__ void get_planes_kernel(const float* __restrict__ f, double* __restric
   }
 }
 
+// ------------------------------------------------------------------ 16-bit
+// FP32 padded stored values (as the FP32 layout) -> rho' and 16-bit
+// deviations, per padded node, with the same arithmetic as the step's encode.
+template <int ST>
+__global__ void encode_kernel(const float* __restrict__ f, unsigned short* __restrict__ dev, int nx, int ny) {
+  const size_t PS = static_cast<size_t>(pitch_of(nx)) * ny;
+  float* rho = reinterpret_cast<float*>(dev + 27 * PS);
+  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < PS;
+       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float v[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) v[i] = f[plane_of(k, i) * PS + n];
+      float rt = v[0];
+#pragma unroll
+      for (int i = 1; i < 9; ++i) rt += v[i];
+      float sr = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const unsigned short b = enc16<ST>(v[i] - wt(i) * rt);
+        dev[plane_of(k, i) * PS + n] = b;
+        sr += dec16<ST>(b);
+      }
+      rho[k * PS + n] = rt - sr;
+    }
+  }
+}
+
+template <int ST>
+__global__ void decode_kernel(const unsigned short* __restrict__ dev, float* __restrict__ f, int nx, int ny) {
+  const size_t PS = static_cast<size_t>(pitch_of(nx)) * ny;
+  const float* rho = reinterpret_cast<const float*>(dev + 27 * PS);
+  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < PS;
+       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float r = rho[k * PS + n];
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+        f[plane_of(k, i) * PS + n] = fmaf(wt(i), r, dec16<ST>(dev[plane_of(k, i) * PS + n]));
+    }
+  }
+}
+
 __global__ void check_rho_kernel(const double* __restrict__ rho, int n, unsigned int* bad) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     const double a = rho[j], b = rho[n + j], c = rho[2 * n + j];
@@ -147,6 +192,47 @@ __global__ void reduce_partial_padded_kernel(const float* __restrict__ f, int nx
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
         const double v = static_cast<double>(f[static_cast<size_t>(plane_of(k, i)) * NP + off]);
+        acc[k] += v;
+        acc[3] += v * ex(i);
+        acc[4] += v * ey(i);
+      }
+    }
+  }
+  __shared__ double red[kRedThreads / 32][5];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const double v = warp_sum(acc[j]);
+    if (lane == 0) red[warp][j] = v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      double v = lane < kRedThreads / 32 ? red[lane][j] : 0.0;
+      v = warp_sum(v);
+      if (lane == 0) partial[blockIdx.x * 5 + j] = v;
+    }
+  }
+}
+
+// Same sums over 16-bit deviation storage (values rebuilt as w_i rho' + d).
+template <int ST>
+__global__ void reduce_partial_dev_kernel(const unsigned short* __restrict__ dev, int nx, int ny,
+                                          double* __restrict__ partial) {
+  const int P = pitch_of(nx);
+  const int N = nx * ny;
+  const size_t PS = static_cast<size_t>(P) * ny;
+  const float* rho = reinterpret_cast<const float*>(dev + 27 * PS);
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+    const size_t off = static_cast<size_t>(n / nx) * P + (n % nx) + kGhost;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float r = rho[k * PS + off];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const double v = static_cast<double>(fmaf(wt(i), r, dec16<ST>(dev[plane_of(k, i) * PS + off])));
         acc[k] += v;
         acc[3] += v * ex(i);
         acc[4] += v * ey(i);
@@ -242,6 +328,39 @@ cudaError_t launch_reduce(const float* f, int N, double* partial, int blocks, do
 cudaError_t launch_reduce_padded(const float* f, int nx, int ny, double* partial, int blocks, double* out,
                                  cudaStream_t s) {
   reduce_partial_padded_kernel<<<blocks, kRedThreads, 0, s>>>(f, nx, ny, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  reduce_final_kernel<<<1, kRedThreads, 0, s>>>(partial, blocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encode(const float* fp32, void* buf, int nx, int ny, int storage, cudaStream_t s) {
+  const int g = grid_for(static_cast<size_t>(pitch_of(nx)) * ny);
+  unsigned short* d = static_cast<unsigned short*>(buf);
+  if (storage == ST_FP16)
+    encode_kernel<ST_FP16><<<g, 256, 0, s>>>(fp32, d, nx, ny);
+  else
+    encode_kernel<ST_BF16><<<g, 256, 0, s>>>(fp32, d, nx, ny);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decode(const void* buf, float* fp32, int nx, int ny, int storage, cudaStream_t s) {
+  const int g = grid_for(static_cast<size_t>(pitch_of(nx)) * ny);
+  const unsigned short* d = static_cast<const unsigned short*>(buf);
+  if (storage == ST_FP16)
+    decode_kernel<ST_FP16><<<g, 256, 0, s>>>(d, fp32, nx, ny);
+  else
+    decode_kernel<ST_BF16><<<g, 256, 0, s>>>(d, fp32, nx, ny);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_dev(const void* buf, int nx, int ny, int storage, double* partial, int blocks,
+                              double* out, cudaStream_t s) {
+  const unsigned short* d = static_cast<const unsigned short*>(buf);
+  if (storage == ST_FP16)
+    reduce_partial_dev_kernel<ST_FP16><<<blocks, kRedThreads, 0, s>>>(d, nx, ny, partial);
+  else
+    reduce_partial_dev_kernel<ST_BF16><<<blocks, kRedThreads, 0, s>>>(d, nx, ny, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   reduce_final_kernel<<<1, kRedThreads, 0, s>>>(partial, blocks, out);

@@ -5,6 +5,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace lbm3 {
@@ -37,6 +39,8 @@ __host__ __device__ constexpr float wt(int i) {
 //   group 0: e_y = +1 {2, 5, 6}; group 1: e_y = 0 {0, 1, 3}; group 2: e_y = -1 {4, 7, 8}
 //   plane(k, i) = 9 * group(i) + 3 * k + position of i in its group.
 constexpr int kGhost = 4;
+// storage of the populations between steps
+enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2 };
 __host__ __device__ constexpr int dir_group(int i) { return ey(i) > 0 ? 0 : (ey(i) == 0 ? 1 : 2); }
 __host__ __device__ constexpr int dir_pos(int i) {
   return (i == 2 || i == 0 || i == 4) ? 0 : ((i == 5 || i == 1 || i == 7) ? 1 : 2);
@@ -44,9 +48,27 @@ __host__ __device__ constexpr int dir_pos(int i) {
 __host__ __device__ constexpr int plane_of(int k, int i) { return 9 * dir_group(i) + 3 * k + dir_pos(i); }
 // at least one full TMA box wide (kPW, defined below): narrow grids get unused
 // columns after the right ghosts so that every box row has the same pitch
-constexpr int kBoxCols = 132;  // = kPW below
+constexpr int kBoxCols = 132;     // = kPW below: FP32 box width (also the rho' box of 16-bit storage)
+constexpr int kDevBoxCols = 136;  // 16-bit box width: a multiple of 8 columns (16 bytes)
+// Row pitch shared by every storage: at least one 16-bit box wide and a
+// multiple of 8 columns, so that 16-bit rows start on 16-byte boundaries.
 __host__ __device__ constexpr int pitch_of(int nx) {
-  return nx + 2 * kGhost > kBoxCols ? nx + 2 * kGhost : kBoxCols;
+  return ((nx + 2 * kGhost > kDevBoxCols ? nx + 2 * kGhost : kDevBoxCols) + 7) / 8 * 8;
+}
+
+// 16-bit deviation storage: a stored population f is kept as
+// w_i rho'_k + d with d rounded to FP16 or BF16 (round to nearest even) and
+// rho'_k chosen per node so that the 9 rounded values of a colour still sum
+// to its mass (see the encode step of the fused kernel).
+template <int ST>
+__device__ __forceinline__ unsigned short enc16(float v) {
+  if (ST == ST_FP16) return __half_as_ushort(__float2half_rn(v));
+  return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+template <int ST>
+__device__ __forceinline__ float dec16(unsigned short b) {
+  if (ST == ST_FP16) return __half2float(__ushort_as_half(b));
+  return __uint_as_float(static_cast<unsigned int>(b) << 16);
 }
 
 // ------------------------------------------------------- fused step tiling
@@ -59,18 +81,35 @@ constexpr int kTX = 124;          // max strip width (columns)
 constexpr int kPW = kTX + 8;      // population row window: x0-4 .. x0+w+4 (one TMA box row)
 static_assert(kPW == kBoxCols, "pitch_of() must cover one TMA box");
 constexpr int kGroupFloats = (9 * kPW + 31) / 32 * 32;  // 9 planes x kPW, padded to a 128-byte multiple
+// 16-bit storage slot: three boxes of 9 deviation planes x kDevBoxCols (2 bytes)
+// and three boxes of the 3 FP32 rho' planes x kPW, each on a 128-byte boundary
+constexpr int kDevGroupHalfs = (9 * kDevBoxCols + 63) / 64 * 64;
+constexpr int kRhoGroupFloats = (3 * kPW + 31) / 32 * 32;
+static_assert(3 * kDevGroupHalfs * 2 + 3 * kRhoGroupFloats * 4 <= 3 * kGroupFloats * 4,
+              "a 16-bit slot must fit in an FP32 slot");
 constexpr int kDW = kTX + 4;      // density/phi window:     x0-2 .. x0+w+2
 constexpr int kTW = kTX + 2;      // tension-tensor window:  x0-1 .. x0+w+1
 constexpr int kSlots = 6;         // population ring depth (rows)
 constexpr int kConsumers = 256;   // 8 compute warps: one C-stage node each per pair of rows
 constexpr int kThreads = kConsumers + 32;  // + 1 copy-issuing warp
 
+// Strip s of n over nx columns: equal widths up to 4 columns, every edge on
+// a multiple of 4 (n = ceil(nx / kTX) keeps every width <= kTX).  Used for
+// batched instances, whose small grids would otherwise get sliver strips.
+__host__ __device__ inline int strip_x0(int s, int n, int nx) { return 4 * ((s * (nx / 4)) / n); }
+
 struct StepArgs {
   const float* fin;   // stored post-collision populations at t-1, [27][ny][P] (padded layout)
   float* fout;        // written at t (MODE_STEP), same layout
   int nx, ny;
-  int pitch;          // P = nx + 8
-  int boxw;           // TMA box width in columns: min(kPW, P)
+  int pitch;          // P = pitch_of(nx)
+  int boxw;           // FP32 TMA box width in columns (kPW)
+  // 16-bit deviation storage: deviation planes [27][ny][P] and rho' planes
+  // [3][ny][P] of the input and output buffers (unused for FP32)
+  const unsigned short* din;
+  unsigned short* dout;
+  const float* rin;
+  float* rout;
   int nstrips;        // ceil(nx / kTX)
   int rows_per_cta;   // H
   float inv_nu[3];    // 1/nu_k, nu_k = (tau_k - 1/2)/3 (so 1/nu = sum_k phi_k/nu_k)
@@ -90,13 +129,31 @@ struct StepArgs {
 
 enum { MODE_STEP = 0, MODE_FIELDS = 1 };
 
+// ------------------------------------------------------ batched launches
+// One CTA tile of one instance.
+struct BatchItem {
+  int inst;
+  int x0, w, y0, h;
+};
+// Per instance: step arguments and TMA descriptor for each buffer parity
+// (parity p reads buffer p and writes buffer 1 - p).
+struct alignas(64) BatchDesc {
+  StepArgs args[2];
+  alignas(64) unsigned char map[2][128];
+};
+
 size_t step_smem_bytes();
 cudaError_t step_configure();  // sets the dynamic shared memory attribute
-// tmap: a CUtensorMap (128 bytes) describing a.fin as a 3D tensor
-// (P, ny, 27) of FP32 with box (boxw, 1, 9)
-cudaError_t launch_step(const StepArgs& a, const void* tmap, int grid, int mode, cudaStream_t s);
-// encode that tensor map for a population buffer (uses the driver's encoder)
-cudaError_t encode_population_map(void* tmap, const float* buf, int nx, int ny);
+// tmaps: two CUtensorMaps (128 bytes each) of the input buffer: FP32 storage
+// uses the first, a (P, ny, 27) FP32 tensor with box (kPW, 1, 9); 16-bit
+// storage uses both, the (P, ny, 27) deviation tensor with box
+// (kDevBoxCols, 1, 9) and the (P, ny, 3) FP32 rho' tensor with box (kPW, 1, 3).
+cudaError_t launch_step(const StepArgs& a, const void* tmaps, int grid, int mode, int storage, cudaStream_t s);
+// encode those maps for one population buffer (uses the driver's encoder)
+cudaError_t encode_population_maps(void* tmaps, const void* buf, int nx, int ny, int storage);
+// bytes of one population buffer
+size_t population_bytes(int nx, int ny, int storage);
+cudaError_t launch_batch(const BatchItem* items, int nitems, const BatchDesc* descs, int parity, cudaStream_t s);
 int step_occupancy(int* blocks_per_sm);
 
 // ------------------------------------------------------------- aux kernels
@@ -106,6 +163,11 @@ cudaError_t launch_set_planes(const double* fpost, float* f, int nx, int ny, int
 cudaError_t launch_get_planes(const float* f, double* fpost, int nx, int ny, int plane0, int nplanes,
                               cudaStream_t s);
 cudaError_t launch_check_rho(const double* rho, int n, unsigned int* bad, cudaStream_t s);
+// 16-bit storage: FP32 padded stored values <-> deviations + rho'
+cudaError_t launch_encode(const float* fp32, void* buf, int nx, int ny, int storage, cudaStream_t s);
+cudaError_t launch_decode(const void* buf, float* fp32, int nx, int ny, int storage, cudaStream_t s);
+cudaError_t launch_reduce_dev(const void* buf, int nx, int ny, int storage, double* partial, int blocks,
+                              double* out, cudaStream_t s);
 // FP64 reductions: partial[blocks][5] then out[5] = (mass_r, mass_g, mass_b, mom_x, mom_y)
 int reduce_blocks(int N);
 // plain [27][ny][nx] array, plane = k*9 + i (the allocation-free entry point's input)

@@ -57,6 +57,7 @@ struct Smem {
   unsigned long long full[kSlots];
   unsigned long long empty[kSlots];
   int abort_flag;
+  StepArgs args;  // this CTA's instance arguments (batched launches)
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -138,9 +139,28 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// Pulled value of colour k, direction i at ring column col of one slot.
-__device__ __forceinline__ float popv(const float* slot, int k, int i, int col) {
-  return slot[dir_group(i) * kGroupFloats + (3 * k + dir_pos(i)) * kPW + col];
+// Ring columns of window column 0 (padded column x0) in the FP32 /
+// deviation / rho' boxes of a slot.
+struct RingCols {
+  int f, d, r;
+};
+__device__ __forceinline__ RingCols ring_cols(const StepArgs& a, int x0) {
+  RingCols c;
+  c.f = x0 - min(x0, a.pitch - kPW);
+  c.d = x0 - (min(x0, a.pitch - kDevBoxCols) & ~7);
+  c.r = c.f;
+  return c;
+}
+
+// Pulled value of colour k, direction i at window column wc of one slot:
+// read directly (FP32), or rebuilt as w_i rho'_k + d (16-bit deviations).
+template <int ST>
+__device__ __forceinline__ float popv(const float* slot, int k, int i, int wc, const RingCols& rc) {
+  if (ST == ST_FP32) return slot[dir_group(i) * kGroupFloats + (3 * k + dir_pos(i)) * kPW + wc + rc.f];
+  const unsigned short* dv = reinterpret_cast<const unsigned short*>(slot);
+  const float* rr = reinterpret_cast<const float*>(dv + 3 * kDevGroupHalfs);
+  return fmaf(wt(i), rr[dir_group(i) * kRhoGroupFloats + k * kPW + wc + rc.r],
+              dec16<ST>(dv[dir_group(i) * kDevGroupHalfs + (3 * k + dir_pos(i)) * kDevBoxCols + wc + rc.d]));
 }
 
 __device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory"); }
@@ -154,10 +174,13 @@ __device__ __forceinline__ int wrap(int a, int n) {
 // Row q of the march (y = y0 - 2 + q) needs, for the directions with
 // e_y = 1 - g, the source row y - e_y: three TMA boxes per row, one per group
 // g, each bringing the 9 planes of that group over columns [tma_x, tma_x + boxw).
-__device__ void produce(Smem& s, const StepArgs& a, const CUtensorMap* map, int x0, int y0, int nq, int lane) {
+template <int ST>
+__device__ void produce(Smem& s, const StepArgs& a, const CUtensorMap* map, const CUtensorMap* map1, int x0,
+                        int y0, int nq, int lane) {
   const int ny = a.ny;
-  const uint32_t row_bytes = 27u * static_cast<uint32_t>(a.boxw) * 4u;
-  const int tma_x = min(x0, a.pitch - a.boxw);
+  const uint32_t row_bytes = ST == ST_FP32 ? 27u * kPW * 4u : 27u * kDevBoxCols * 2u + 9u * kPW * 4u;
+  const int tma_x = min(x0, a.pitch - kPW);
+  const int dev_x = min(x0, a.pitch - kDevBoxCols) & ~7;
   volatile int* abort_flag = &s.abort_flag;
   int issued = 0;
   for (int q = 0; q < nq; ++q) {
@@ -174,10 +197,21 @@ __device__ void produce(Smem& s, const StepArgs& a, const CUtensorMap* map, int 
     if (!ok) break;
     if (lane == 0) mbar_arrive_expect_tx(&s.full[slot], row_bytes);
     __syncwarp();
-    if (lane < 3) {
-      const int g = lane;  // e_y = 1 - g
+    if (ST == ST_FP32) {
+      if (lane < 3) {
+        const int g = lane;  // e_y = 1 - g
+        const int src_row = wrap(y0 - 2 + q - (1 - g), ny);
+        tma_load_3d(&s.pop[slot][g * kGroupFloats], map, tma_x, src_row, 9 * g, &s.full[slot]);
+      }
+    } else if (lane < 6) {
+      const int g = lane % 3;  // e_y = 1 - g; lanes 0-2 deviations, 3-5 rho'
       const int src_row = wrap(y0 - 2 + q - (1 - g), ny);
-      tma_load_3d(&s.pop[slot][g * kGroupFloats], map, tma_x, src_row, 9 * g, &s.full[slot]);
+      unsigned short* dv = reinterpret_cast<unsigned short*>(&s.pop[slot][0]);
+      if (lane < 3)
+        tma_load_3d(dv + g * kDevGroupHalfs, map, dev_x, src_row, 9 * g, &s.full[slot]);
+      else
+        tma_load_3d(reinterpret_cast<float*>(dv + 3 * kDevGroupHalfs) + g * kRhoGroupFloats, map1, tma_x, src_row, 0,
+                    &s.full[slot]);
     }
     __syncwarp();
     issued = q + 1;
@@ -215,18 +249,19 @@ __device__ __forceinline__ float colour_fractions(float r0, float r1, float r2, 
   return ir;
 }
 
-// D stage, one node: row q (window slot), window column c in [0, w+4), i.e.
-// x = x0 - 2 + c.  The pulled value of direction i sits at ring column
-// colbase + c + 2 - e_ix of row q's slot.
-__device__ __forceinline__ void stage_density(Smem& s, int q, int c, int colbase) {
+// D stage, one node: row q (window slot), density column c in [0, w+4), i.e.
+// x = x0 - 2 + c.  The pulled value of direction i sits at window column
+// c + 2 - e_ix of row q's slot.
+template <int ST>
+__device__ __forceinline__ void stage_density(Smem& s, int q, int c, const RingCols& rc) {
   const float* pp = s.pop[q % kSlots];
-  const int cb = c + 2 + colbase;
+  const int wc = c + 2;
   float r[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    float acc = popv(pp, k, 0, cb);
+    float acc = popv<ST>(pp, k, 0, wc, rc);
 #pragma unroll
-    for (int i = 1; i < 9; ++i) acc += popv(pp, k, i, cb - ex(i));
+    for (int i = 1; i < 9; ++i) acc += popv<ST>(pp, k, i, wc - ex(i), rc);
     r[k] = acc;
   }
   float phk[3], rho;
@@ -299,9 +334,9 @@ __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q,
 }
 
 // C stage, one node: row q (output row y0 - 2 + q), column c in [0, w).
-template <int MODE>
+template <int MODE, int ST>
 __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q, int c, int x0, int y0,
-                                              int colbase) {
+                                              const RingCols& rc) {
   const float* pp = s.pop[q % kSlots];
   const float(*Tm)[kTW] = s.T[(q - 1) & 3];
   const float(*Tz)[kTW] = s.T[q & 3];
@@ -313,8 +348,8 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
   float fi[9], r[3];
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const int col = c + 4 + colbase - ex(i);
-    const float a0 = popv(pp, 0, i, col), a1 = popv(pp, 1, i, col), a2 = popv(pp, 2, i, col);
+    const int wc = c + 4 - ex(i);
+    const float a0 = popv<ST>(pp, 0, i, wc, rc), a1 = popv<ST>(pp, 1, i, wc, rc), a2 = popv<ST>(pp, 2, i, wc, rc);
     if (i == 0) {
       r[0] = a0;
       r[1] = a1;
@@ -428,24 +463,64 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
     }
   }
   const size_t PS = static_cast<size_t>(a.ny) * a.pitch;  // plane stride
-  float* out = a.fout + static_cast<size_t>(y) * a.pitch + (x + kGhost);
+  const size_t off = static_cast<size_t>(y) * a.pitch + (x + kGhost);
+  if (ST == ST_FP32) {
+    float* out = a.fout + off;
 #pragma unroll
-  for (int p = 0; p < 27; ++p) out[p * PS] = val[p];
-  if (x < kGhost) {
+    for (int p = 0; p < 27; ++p) out[p * PS] = val[p];
+    if (x < kGhost) {
 #pragma unroll
-    for (int p = 0; p < 27; ++p) out[p * PS + a.nx] = val[p];
-  }
-  if (x >= a.nx - kGhost) {
+      for (int p = 0; p < 27; ++p) out[p * PS + a.nx] = val[p];
+    }
+    if (x >= a.nx - kGhost) {
 #pragma unroll
-    for (int p = 0; p < 27; ++p) out[p * PS - a.nx] = val[p];
+      for (int p = 0; p < 27; ++p) out[p * PS - a.nx] = val[p];
+    }
+  } else {
+    // Encode each colour as rho'_k and 16-bit deviations d_i = f_i - w_i rho_k
+    // (rho_k = sum_i f_i): rho'_k absorbs the rounding of the nine d_i, so
+    // sum_i (w_i rho'_k + d_i) = rho_k and the colour mass survives storage.
+    unsigned short code[27];
+    float rp[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float rt = val[plane_of(k, 0)];
+#pragma unroll
+      for (int i = 1; i < 9; ++i) rt += val[plane_of(k, i)];
+      float sr = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const unsigned short b = enc16<ST>(val[plane_of(k, i)] - wt(i) * rt);
+        code[plane_of(k, i)] = b;
+        sr += dec16<ST>(b);
+      }
+      rp[k] = rt - sr;
+    }
+    unsigned short* dout = a.dout + off;
+    float* rout = a.rout + off;
+#pragma unroll
+    for (int p = 0; p < 27; ++p) dout[p * PS] = code[p];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) rout[k * PS] = rp[k];
+    if (x < kGhost) {
+#pragma unroll
+      for (int p = 0; p < 27; ++p) dout[p * PS + a.nx] = code[p];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) rout[k * PS + a.nx] = rp[k];
+    }
+    if (x >= a.nx - kGhost) {
+#pragma unroll
+      for (int p = 0; p < 27; ++p) dout[p * PS - a.nx] = code[p];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) rout[k * PS - a.nx] = rp[k];
+    }
   }
 }
 
-template <int MODE>
+template <int MODE, int ST>
 __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h, int tid) {
   const int nq = h + 4;  // rows q = 0 .. h+3 <-> y = y0-2 .. y0+h+1
-  // ring column of window column 0 (= padded column x0, node x0 - 4)
-  const int colbase = x0 - min(x0, a.pitch - a.boxw);
+  const RingCols rc = ring_cols(a, x0);
   volatile int* abort_flag = &s.abort_flag;
   bool dead = false;
   const int J = (h + 3) / 2 + 1;
@@ -465,7 +540,7 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
           const int it = tid + u * kConsumers;
           if (it < nr * W) {
             const int r = it >= W ? 1 : 0;
-            stage_density(s, q0 + r, it - r * W, colbase);
+            stage_density<ST>(s, q0 + r, it - r * W, rc);
           }
         }
       }
@@ -495,7 +570,7 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
       if (nr > 0) {
         for (int it = tid; it < nr * w; it += kConsumers) {
           const int r = it >= w ? 1 : 0;
-          stage_collide<MODE>(s, a, qa + r, it - r * w, x0, y0, colbase);
+          stage_collide<MODE, ST>(s, a, qa + r, it - r * w, x0, y0, rc);
         }
       }
     }
@@ -508,20 +583,11 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
   }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
-    fused_step_kernel(StepArgs a, const __grid_constant__ CUtensorMap tmap) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  // TMA destinations must be 128-byte aligned: align the block's base
-  const uint32_t pad = (128u - (su32(smem_raw) & 127u)) & 127u;
-  Smem& s = *reinterpret_cast<Smem*>(smem_raw + pad);
-  const int strip = blockIdx.x % a.nstrips;
-  const int chunk = blockIdx.x / a.nstrips;
-  const int x0 = strip * kTX;
-  const int w = min(kTX, a.nx - x0);
-  const int y0 = chunk * a.rows_per_cta;
-  const int h = min(a.rows_per_cta, a.ny - y0);
-  if (w <= 0 || h <= 0) return;
+// One tile (strip of w columns starting at x0, rows y0 .. y0+h-1): barrier
+// set-up, then the producer warp and the consumer warps.
+template <int MODE, int ST>
+__device__ __forceinline__ void run_tile(Smem& s, const StepArgs& a, const CUtensorMap* map, const CUtensorMap* map1,
+                                         int x0, int w, int y0, int h) {
   const int nq = h + 4;
   const int tid = threadIdx.x;
   if (tid == 0) {
@@ -534,59 +600,174 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
   __syncthreads();
   if (tid >= kConsumers) {
-    produce(s, a, &tmap, x0, y0, nq, tid - kConsumers);
+    produce<ST>(s, a, map, map1, x0, y0, nq, tid - kConsumers);
   } else {
-    consume<MODE>(s, a, x0, w, y0, h, tid);
+    consume<MODE, ST>(s, a, x0, w, y0, h, tid);
   }
+}
+
+__device__ __forceinline__ Smem& aligned_smem() {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  // TMA destinations must be 128-byte aligned: align the block's base
+  const uint32_t pad = (128u - (su32(smem_raw) & 127u)) & 127u;
+  return *reinterpret_cast<Smem*>(smem_raw + pad);
+}
+
+// Single grid: CTA b takes strip b % nstrips and row chunk b / nstrips.
+// Full-width strips with a narrower last one measured 4.6 % faster on a
+// 2048^2 grid than equal-width strips (all CTAs of one wave stay busy with
+// 248-node C stages instead of 240).
+template <int MODE, int ST>
+__global__ void __launch_bounds__(kThreads, 2)
+    fused_step_kernel(StepArgs a, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap1) {
+  Smem& s = aligned_smem();
+  const int strip = blockIdx.x % a.nstrips;
+  const int chunk = blockIdx.x / a.nstrips;
+  const int x0 = strip * kTX;
+  const int w = min(kTX, a.nx - x0);
+  const int y0 = chunk * a.rows_per_cta;
+  const int h = min(a.rows_per_cta, a.ny - y0);
+  if (w <= 0 || h <= 0) return;
+  run_tile<MODE, ST>(s, a, &tmap, &tmap1, x0, w, y0, h);
+}
+
+// Batch of independent grids: CTA b runs work item b (instance, tile); the
+// instance's arguments for this step's buffer parity are copied to shared
+// memory and its tensor map is read from global memory.
+__global__ void __launch_bounds__(kThreads, 2)
+    fused_batch_kernel(const BatchItem* __restrict__ items, const BatchDesc* __restrict__ descs, int parity) {
+  Smem& s = aligned_smem();
+  const BatchItem it = items[blockIdx.x];
+  const BatchDesc* d = descs + it.inst;
+  {
+    const int* src = reinterpret_cast<const int*>(&d->args[parity]);
+    int* dst = reinterpret_cast<int*>(&s.args);
+    for (int j = threadIdx.x; j < static_cast<int>(sizeof(StepArgs) / sizeof(int)); j += blockDim.x)
+      dst[j] = src[j];
+  }
+  const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(d->map[parity]);
+  if (threadIdx.x == kConsumers)
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+  __syncthreads();
+  run_tile<MODE_STEP, ST_FP32>(s, s.args, map, map, it.x0, it.w, it.y0, it.h);
 }
 
 }  // namespace
 
 size_t step_smem_bytes() { return sizeof(Smem) + 128; }
 
+template <int MODE, int ST>
+cudaError_t configure_one(int bytes) {
+  return cudaFuncSetAttribute(fused_step_kernel<MODE, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 cudaError_t step_configure() {
   const int bytes = static_cast<int>(step_smem_bytes());
-  cudaError_t e =
-      cudaFuncSetAttribute(fused_step_kernel<MODE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fused_step_kernel<MODE_FIELDS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = configure_one<MODE_STEP, ST_FP32>(bytes);
+  if (e == cudaSuccess) e = configure_one<MODE_FIELDS, ST_FP32>(bytes);
+  if (e == cudaSuccess) e = configure_one<MODE_STEP, ST_FP16>(bytes);
+  if (e == cudaSuccess) e = configure_one<MODE_FIELDS, ST_FP16>(bytes);
+  if (e == cudaSuccess) e = configure_one<MODE_STEP, ST_BF16>(bytes);
+  if (e == cudaSuccess) e = configure_one<MODE_FIELDS, ST_BF16>(bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fused_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
+cudaError_t launch_batch(const BatchItem* items, int nitems, const BatchDesc* descs, int parity, cudaStream_t st) {
+  if (nitems <= 0) return cudaSuccess;
+  fused_batch_kernel<<<nitems, kThreads, step_smem_bytes(), st>>>(items, descs, parity);
+  return cudaGetLastError();
 }
 
 int step_occupancy(int* blocks_per_sm) {
   return static_cast<int>(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      blocks_per_sm, fused_step_kernel<MODE_STEP>, kThreads, step_smem_bytes()));
+      blocks_per_sm, fused_step_kernel<MODE_STEP, ST_FP32>, kThreads, step_smem_bytes()));
 }
 
-cudaError_t launch_step(const StepArgs& a, const void* tmap, int grid, int mode, cudaStream_t st) {
-  CUtensorMap m;
-  memcpy(&m, tmap, sizeof m);
-  if (mode == MODE_STEP)
-    fused_step_kernel<MODE_STEP><<<grid, kThreads, step_smem_bytes(), st>>>(a, m);
-  else
-    fused_step_kernel<MODE_FIELDS><<<grid, kThreads, step_smem_bytes(), st>>>(a, m);
+cudaError_t launch_step(const StepArgs& a, const void* tmaps, int grid, int mode, int storage, cudaStream_t st) {
+  CUtensorMap m0, m1;
+  memcpy(&m0, tmaps, sizeof m0);
+  memcpy(&m1, static_cast<const unsigned char*>(tmaps) + 128, sizeof m1);
+  const size_t sm = step_smem_bytes();
+  if (storage == ST_FP32) {
+    if (mode == MODE_STEP)
+      fused_step_kernel<MODE_STEP, ST_FP32><<<grid, kThreads, sm, st>>>(a, m0, m1);
+    else
+      fused_step_kernel<MODE_FIELDS, ST_FP32><<<grid, kThreads, sm, st>>>(a, m0, m1);
+  } else if (storage == ST_FP16) {
+    if (mode == MODE_STEP)
+      fused_step_kernel<MODE_STEP, ST_FP16><<<grid, kThreads, sm, st>>>(a, m0, m1);
+    else
+      fused_step_kernel<MODE_FIELDS, ST_FP16><<<grid, kThreads, sm, st>>>(a, m0, m1);
+  } else {
+    if (mode == MODE_STEP)
+      fused_step_kernel<MODE_STEP, ST_BF16><<<grid, kThreads, sm, st>>>(a, m0, m1);
+    else
+      fused_step_kernel<MODE_FIELDS, ST_BF16><<<grid, kThreads, sm, st>>>(a, m0, m1);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t encode_population_map(void* tmap, const float* buf, int nx, int ny) {
+size_t population_bytes(int nx, int ny, int storage) {
+  const size_t PS = static_cast<size_t>(pitch_of(nx)) * static_cast<size_t>(ny);
+  return storage == ST_FP32 ? 27 * PS * 4 : 27 * PS * 2 + 3 * PS * 4;
+}
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder(cudaError_t* err) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  *err = cudaSuccess;
   if (!encode) {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess) return e;
-    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    if (e != cudaSuccess) {
+      *err = e;
+      return nullptr;
+    }
+    if (q != cudaDriverEntryPointSuccess || !fn) {
+      *err = cudaErrorNotSupported;
+      return nullptr;
+    }
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const int P = pitch_of(nx);
-  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(P), static_cast<cuuint64_t>(ny), 27};
-  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(P) * 4, static_cast<cuuint64_t>(ny) * P * 4};
-  const cuuint32_t box[3] = {static_cast<cuuint32_t>(kPW), 1, 9};  // P >= kPW by construction
+  return encode;
+}
+
+cudaError_t encode_3d(PFN_cuTensorMapEncodeTiled_v12000 encode, void* tmap, CUtensorMapDataType type, int esize,
+                      const void* base, int P, int ny, int planes, int boxw, int boxp) {
+  const cuuint64_t dims[3] = {static_cast<cuuint64_t>(P), static_cast<cuuint64_t>(ny),
+                              static_cast<cuuint64_t>(planes)};
+  const cuuint64_t strides[2] = {static_cast<cuuint64_t>(P) * esize, static_cast<cuuint64_t>(ny) * P * esize};
+  const cuuint32_t box[3] = {static_cast<cuuint32_t>(boxw), 1, static_cast<cuuint32_t>(boxp)};
   const cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = encode(static_cast<CUtensorMap*>(tmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                            const_cast<float*>(buf), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUresult r = encode(static_cast<CUtensorMap*>(tmap), type, 3, const_cast<void*>(base), dims, strides, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t encode_population_maps(void* tmaps, const void* buf, int nx, int ny, int storage) {
+  cudaError_t e;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder(&e);
+  if (!encode) return e;
+  const int P = pitch_of(nx);
+  unsigned char* m = static_cast<unsigned char*>(tmaps);
+  if (storage == ST_FP32) {
+    e = encode_3d(encode, m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, buf, P, ny, 27, kPW, 9);
+    if (e == cudaSuccess) memcpy(m + 128, m, 128);  // unused second map
+    return e;
+  }
+  const size_t PS = static_cast<size_t>(P) * ny;
+  const float* rho = reinterpret_cast<const float*>(static_cast<const unsigned short*>(buf) + 27 * PS);
+  e = encode_3d(encode, m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, buf, P, ny, 27, kDevBoxCols, 9);
+  if (e == cudaSuccess) e = encode_3d(encode, m + 128, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, rho, P, ny, 3, kPW, 3);
+  return e;
 }
 
 }  // namespace lbm3

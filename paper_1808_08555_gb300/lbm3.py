@@ -26,7 +26,7 @@ _STATUS = {OK: "LBM3_OK", EINVAL: "LBM3_EINVAL", ENOMEM: "LBM3_ENOMEM", ECUDA: "
            ESTATE: "LBM3_ESTATE", ENUMERIC: "LBM3_ENUMERIC", ETIMEOUT: "LBM3_ETIMEOUT"}
 BETA_PAPER, BETA_FU, BETA_SPENCER, BETA_LECLAIRE = range(4)
 RECOLOR_COSINE, RECOLOR_LITERAL = range(2)
-FP32 = 0
+FP32, FP16_DEV, BF16_DEV = 0, 1, 2
 
 
 class Lbm3Error(RuntimeError):
@@ -102,6 +102,19 @@ def load() -> ctypes.CDLL:
         "lbm3_destroy": (st, [vp]),
         "lbm3_last_error": (ctypes.c_char_p, [vp]),
         "lbm3_mass_noalloc": (st, [vp, ctypes.c_int32, ctypes.c_int32, vp, vp]),
+        "lbm3_batch_create": (st, [P, ctypes.c_int32, vp, ctypes.c_int32, ctypes.POINTER(vp)]),
+        "lbm3_batch_count": (ctypes.c_int32, [vp]),
+        "lbm3_batch_work_items": (ctypes.c_int32, [vp]),
+        "lbm3_batch_init": (st, [vp, ctypes.c_int32, dp, ctypes.c_int]),
+        "lbm3_batch_set_populations": (st, [vp, ctypes.c_int32, dp, ctypes.c_int]),
+        "lbm3_batch_fields": (st, [vp, ctypes.c_int32, dp, dp, dp, dp, ctypes.c_int]),
+        "lbm3_batch_populations": (st, [vp, ctypes.c_int32, dp, ctypes.c_int]),
+        "lbm3_batch_mass": (st, [vp, ctypes.c_int32, dp, dp]),
+        "lbm3_batch_step": (st, [vp, ctypes.c_int64]),
+        "lbm3_batch_sync": (st, [vp]),
+        "lbm3_batch_time": (ctypes.c_int64, [vp]),
+        "lbm3_batch_destroy": (st, [vp]),
+        "lbm3_batch_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -280,6 +293,136 @@ class Simulation:
         if getattr(self, "ctx", None):
             lbm3_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- batches
+
+def _bcheck(b, status: int):
+    if status != OK:
+        raise Lbm3Error(status, load().lbm3_batch_last_error(b).decode())
+
+
+def lbm3_batch_create(params_list, stream: int | None = None, rows_per_cta: int = 0) -> ctypes.c_void_p:
+    arr = (lbm3_params * len(params_list))(*[p.to_c() for p in params_list])
+    b = ctypes.c_void_p()
+    s = load().lbm3_batch_create(arr, len(params_list), ctypes.c_void_p(stream or 0), int(rows_per_cta),
+                                 ctypes.byref(b))
+    if s != OK:
+        raise Lbm3Error(s, "lbm3_batch_create failed (an instance's parameters are invalid or CUDA failed)")
+    return b
+
+
+def lbm3_batch_init(b, i: int, rho):
+    p, dev = _ptr(rho)
+    _bcheck(b, load().lbm3_batch_init(b, int(i), p, dev))
+
+
+def lbm3_batch_set_populations(b, i: int, f):
+    p, dev = _ptr(f)
+    _bcheck(b, load().lbm3_batch_set_populations(b, int(i), p, dev))
+
+
+def lbm3_batch_step(b, n: int = 1):
+    _bcheck(b, load().lbm3_batch_step(b, int(n)))
+
+
+def lbm3_batch_populations(b, i: int, f):
+    p, dev = _ptr(f)
+    _bcheck(b, load().lbm3_batch_populations(b, int(i), p, dev))
+
+
+def lbm3_batch_fields(b, i: int, rho=None, ux=None, uy=None, p=None):
+    ptrs, devs = [], set()
+    for a in (rho, ux, uy, p):
+        if a is None:
+            ptrs.append(None)
+        else:
+            q, d = _ptr(a)
+            ptrs.append(q)
+            devs.add(d)
+    if len(devs) > 1:
+        raise ValueError("outputs must be all host or all device arrays")
+    _bcheck(b, load().lbm3_batch_fields(b, int(i), *ptrs, devs.pop() if devs else 0))
+
+
+def lbm3_batch_mass(b, i: int):
+    m = np.zeros(3)
+    mo = np.zeros(2)
+    _bcheck(b, load().lbm3_batch_mass(b, int(i), ctypes.c_void_p(m.ctypes.data), ctypes.c_void_p(mo.ctypes.data)))
+    return m, mo
+
+
+def lbm3_batch_sync(b):
+    _bcheck(b, load().lbm3_batch_sync(b))
+
+
+def lbm3_batch_destroy(b):
+    load().lbm3_batch_destroy(b)
+
+
+class Batch:
+    """Independent simulations advanced together on the current device and
+    torch's current stream (one launch per step, replayed from a CUDA graph)."""
+
+    def __init__(self, params_list, rows_per_cta: int = 0):
+        import torch
+
+        self.params = list(params_list)
+        self.stream = torch.cuda.current_stream()
+        self.b = lbm3_batch_create(self.params, self.stream.cuda_stream, rows_per_cta)
+
+    def __len__(self):
+        return len(self.params)
+
+    @property
+    def work_items(self) -> int:
+        return int(load().lbm3_batch_work_items(self.b))
+
+    @property
+    def t(self) -> int:
+        return int(load().lbm3_batch_time(self.b))
+
+    def init(self, i, rho):
+        lbm3_batch_init(self.b, i, rho)
+        return self
+
+    def set_populations(self, i, f):
+        lbm3_batch_set_populations(self.b, i, f)
+        return self
+
+    def step(self, n: int = 1):
+        lbm3_batch_step(self.b, n)
+        return self
+
+    def populations(self, i) -> np.ndarray:
+        p = self.params[i]
+        f = np.empty((3, 9, p.ny, p.nx))
+        lbm3_batch_populations(self.b, i, f)
+        return f
+
+    def fields(self, i) -> dict:
+        p = self.params[i]
+        out = {"rho": np.empty((3, p.ny, p.nx)), "ux": np.empty((p.ny, p.nx)), "uy": np.empty((p.ny, p.nx)),
+               "p": np.empty((p.ny, p.nx))}
+        lbm3_batch_fields(self.b, i, out["rho"], out["ux"], out["uy"], out["p"])
+        return out
+
+    def mass(self, i):
+        return lbm3_batch_mass(self.b, i)
+
+    def sync(self):
+        lbm3_batch_sync(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lbm3_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):  # pragma: no cover
         try:

@@ -44,7 +44,7 @@ def test_params_struct_layout_matches_header():
     dict(nx=6, ny=8), dict(nx=0, ny=8), dict(nx=8, ny=0), dict(nx=8, ny=8, tau=(0.5, 1, 1)),
     dict(nx=8, ny=8, rho0=(1, 0, 1)), dict(nx=8, ny=8, sigma=(0.01, -1, 0.01)),
     dict(nx=8, ny=8, beta0=0.0), dict(nx=8, ny=8, beta0=1.5), dict(nx=8, ny=8, beta_form=7),
-    dict(nx=8, ny=8, recolor_form=2), dict(nx=8, ny=8, storage=9),
+    dict(nx=8, ny=8, recolor_form=2), dict(nx=8, ny=8, storage=9), dict(nx=8, ny=8, storage=-1),
 ])
 def test_invalid_params_rejected(lib, kw):
     with pytest.raises(L.Lbm3Error) as e:
@@ -53,9 +53,13 @@ def test_invalid_params_rejected(lib, kw):
 
 
 def test_buffer_bytes(lib):
-    # 27 planes of ny rows with the padded pitch max(nx + 8, 132) (ghost columns for the periodic wrap)
-    assert L.lbm3_buffer_bytes(L.Params(8, 4)) == 27 * 4 * 132 * 4
+    # 27 planes of ny rows, pitch max(nx + 8, 136) rounded up to 8 (ghost columns for the periodic wrap)
+    assert L.lbm3_buffer_bytes(L.Params(8, 4)) == 27 * 4 * 136 * 4
     assert L.lbm3_buffer_bytes(L.Params(2048, 2048)) == 27 * 2048 * 2056 * 4
+    assert L.lbm3_buffer_bytes(L.Params(2044, 10)) == 27 * 10 * 2056 * 4
+    # 16-bit deviations plus three FP32 rho' planes
+    assert L.lbm3_buffer_bytes(L.Params(2048, 2048, storage=1)) == (27 * 2 + 3 * 4) * 2048 * 2056
+    assert L.lbm3_buffer_bytes(L.Params(2048, 2048, storage=2)) == (27 * 2 + 3 * 4) * 2048 * 2056
 
 
 def test_null_context_is_einval(lib):
