@@ -51,7 +51,7 @@ struct Smem {
   // pulled-row ring (row q in slot q % kSlots): three TMA boxes of 9 planes x
   // kPW columns, one per direction group, each starting on a 128-byte boundary
   float pop[kSlots][3 * kGroupFloats];
-  float phi[4][4][kDW];        // phi_1, phi_2, phi_3, rho of row q in slot q % 4
+  float phi[6][4][kDW];        // phi_1, phi_2, phi_3, rho of row q in slot q % 6
   float T[4][3][kTW];          // T_xx, T_xy, T_yy of row q in slot q % 4
   float nrm[3][6][kTX];        // n_12, n_13, n_23 (x, y) of row q in slot q % 3
   unsigned long long full[kSlots];
@@ -266,7 +266,7 @@ __device__ __forceinline__ void stage_density(Smem& s, int q, int c, const RingC
   }
   float phk[3], rho;
   colour_fractions(r[0], r[1], r[2], phk, &rho);
-  float(*ph)[kDW] = s.phi[q & 3];
+  float(*ph)[kDW] = s.phi[q % 6];
   ph[0][c] = phk[0];
   ph[1][c] = phk[1];
   ph[2][c] = phk[2];
@@ -275,9 +275,9 @@ __device__ __forceinline__ void stage_density(Smem& s, int q, int c, const RingC
 
 // T stage, one node: row q, T-window column c in [0, w+2), x = x0 - 1 + c.
 __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q, int c, int w) {
-  const float(*pm)[kDW] = s.phi[(q - 1) & 3];
-  const float(*pz)[kDW] = s.phi[q & 3];
-  const float(*pq)[kDW] = s.phi[(q + 1) & 3];
+  const float(*pm)[kDW] = s.phi[(q - 1) % 6];
+  const float(*pz)[kDW] = s.phi[q % 6];
+  const float(*pq)[kDW] = s.phi[(q + 1) % 6];
   const int cc = c + 1;  // phi-window column of this node
   float ph[3], gx[3], gy[3];
 #pragma unroll
@@ -341,29 +341,19 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
   const float(*Tm)[kTW] = s.T[(q - 1) & 3];
   const float(*Tz)[kTW] = s.T[q & 3];
   const float(*Tp)[kTW] = s.T[(q + 1) & 3];
-  // colour densities (same summation order as the D stage, so phi_k is
-  // bit-identical to the one the T stage used) and the total distribution
-  // f_i = sum_k f_{i,k} of the pulled populations.  The phi ring is not read
-  // here: the next iteration's D stage may already be overwriting it.
-  float fi[9], r[3];
+  // colour fractions and density from the D stage (the phi ring keeps six
+  // rows, so the next iteration's D stage writes other slots), and the total
+  // distribution f_i = sum_k f_{i,k} of the pulled populations
+  const float(*ph)[kDW] = s.phi[q % 6];
+  const float phi0 = ph[0][c + 2], phi1 = ph[1][c + 2], phi2 = ph[2][c + 2], rho = ph[3][c + 2];
+  const float phv[3] = {phi0, phi1, phi2};
+  const float irho = __frcp_rn(rho);
+  float fi[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const int wc = c + 4 - ex(i);
-    const float a0 = popv<ST>(pp, 0, i, wc, rc), a1 = popv<ST>(pp, 1, i, wc, rc), a2 = popv<ST>(pp, 2, i, wc, rc);
-    if (i == 0) {
-      r[0] = a0;
-      r[1] = a1;
-      r[2] = a2;
-    } else {
-      r[0] += a0;
-      r[1] += a1;
-      r[2] += a2;
-    }
-    fi[i] = (a0 + a1) + a2;
+    fi[i] = (popv<ST>(pp, 0, i, wc, rc) + popv<ST>(pp, 1, i, wc, rc)) + popv<ST>(pp, 2, i, wc, rc);
   }
-  float phv[3], rho;
-  const float irho = colour_fractions(r[0], r[1], r[2], phv, &rho);
-  const float phi0 = phv[0], phi1 = phv[1], phi2 = phv[2];
   // F_s = div T (Eq. 11), T window column of this node is c + 1
   const int tc = c + 1;
   float Fx, Fy;
