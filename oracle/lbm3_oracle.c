@@ -31,8 +31,9 @@
  *    equals the paper's unit normal wherever a k-l interface exists (there
  *    |G_kl| is about 1.26 phi_k phi_l across the whole tanh profile of Eq. 21)
  *    and goes to zero continuously, with a bounded gain, where G_kl
- *    vanishes.  The tension tensor
- *    term |G|(I - n n) vanishes with |G| and is taken as 0 for |G| <= 1e-15.
+ *    vanishes.  Where |G_kl| <= 1e-15 no k-l interface is taken to exist:
+ *    the tension term |G|(I - n n) of Eq. 11, which vanishes with |G|, is 0
+ *    there, and so is n_kl in the recolouring.
  *  - the derivatives inside F_s (Eq. 11) are the isotropic stencil of
  *    Eq. fd1 applied to phi_k = rho_k/rho, and then again to each component
  *    of the tensor inside the divergence.
@@ -52,7 +53,7 @@ static const double WT[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
                              1.0 / 9.0,  1.0 / 9.0,  1.0 / 36.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 static const double CS2 = 1.0 / 3.0;
-static const double GEPS = 1e-15;   /* |G| below which the tension tensor term is 0 */
+static const double GEPS = 1e-15;   /* |G| at or below which no k-l interface exists */
 static const double NDELTA = 1e-1;  /* recolouring normal: n = G / max(|G|, NDELTA phi_k phi_l) */
 
 typedef struct {
@@ -343,9 +344,9 @@ static void orc_step_once(const orc_params* p, double* f, double* fn) {
             if (l == k) continue;
             double gx = G[((k * 3 + l) * 2 + 0) * N + n], gy = G[((k * 3 + l) * 2 + 1) * N + n];
             double mag = sqrt(gx * gx + gy * gy);
+            if (mag <= GEPS) continue;  /* no k-l interface: n_kl = 0, as in Eq. 11 */
             double den = NDELTA * (rloc[k] / r) * (rloc[l] / r);
             if (mag > den) den = mag;
-            if (den <= 1e-30) continue;  /* both fluids absent: no recolouring term */
             double en = (gx * EX[i] + gy * EY[i]) / den;
             if (p->recolor_form == 0 && i != 0) en /= sqrt((double)(EX[i] * EX[i] + EY[i] * EY[i]));
             int a = k < l ? k : l, b = k < l ? l : k;

@@ -316,9 +316,10 @@ __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q,
       tyy = fmaf(sc * Gx, Gx, tyy);
     }
     // recolouring normal G / max(|G|, kNormalDelta phi_k phi_l): the unit
-    // normal wherever a k-l interface exists, continuous to 0 where G -> 0
+    // normal wherever a k-l interface exists, continuous to 0 where G -> 0,
+    // and 0 at or below the |G| cutoff of the tension (no k-l interface)
     const float den = fmaxf(mag, kNormalDelta * pp);
-    const float rden = den > 1e-30f ? __fdividef(1.0f, den) : 0.0f;  // |n| <= 1; tiny den -> 0
+    const float rden = g2 > 1e-30f ? __fdividef(1.0f, den) : 0.0f;  // |n| <= 1
     nv[2 * p] = Gx * rden;
     nv[2 * p + 1] = Gy * rden;
   }
