@@ -364,6 +364,81 @@ def run_janus(args):
             "storages": out, "gpu_launches": args.steps}
 
 
+def run_adjoint(args):
+    """Reverse mode on the gradient workload: 256^2 touching discs (sigma =
+    0.01 each, tau = 1), J = sum (phi - phi_target)^2 after 2000 steps, the
+    gradient dJ/drho0 (all nodes) and dJ/dsigma by lbm3_tape_forward +
+    lbm3_tape_backward.  One timed step = one full gradient evaluation
+    (forward run recorded + reverse run), with every state kept
+    (checkpoint_every = 1: 2000 x 7 MB fit easily in HBM) and, beside it, with
+    checkpoints every 100 steps (segments recomputed).  MLUPS counts the
+    2000 x N node updates of the forward run per evaluation."""
+    import torch
+
+    from paper_1808_08555_gb300 import build as B
+    B.build()
+    from paper_1808_08555_gb300 import lbm3 as L
+    from paper_1808_08555_gb300 import workloads as W
+
+    n = args.size if args.size != 2048 else 256
+    horizon = 2000
+    rho0, tgt = W.case_adjoint(n)
+    phit = torch.tensor(tgt / tgt.sum(axis=0), device="cuda")
+    sim = L.Simulation(L.Params(n, n, sigma=(0.01, 0.01, 0.01)))
+    rho_d = torch.tensor(rho0, device="cuda")
+    phi = torch.empty_like(rho_d)
+    drho = torch.empty_like(rho_d)
+    s = sim.stream
+    res = {}
+    for every in (1, 100):
+        def evaluate():
+            L.lbm3_init(sim.ctx, rho_d)
+            L.lbm3_tape_forward(sim.ctx, horizon, every)
+            L.lbm3_phi(sim.ctx, phi)
+            return L.lbm3_tape_backward(sim.ctx, 2 * (phi - phit), None, drho)
+        for _ in range(args.warmup):
+            ds = evaluate()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        fwd = 0.0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e[0].record(s)
+            L.lbm3_init(sim.ctx, rho_d)
+            L.lbm3_tape_forward(sim.ctx, horizon, every)
+            L.lbm3_phi(sim.ctx, phi)
+            e[1].record(s)
+            ds = L.lbm3_tape_backward(sim.ctx, 2 * (phi - phit), None, drho)
+            e[2].record(s)
+            e[2].synchronize()
+            fwd += e[0].elapsed_time(e[1])
+        ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        J = float(((phi - phit) ** 2).sum())
+        res[every] = {"ms_per_gradient": round(ms, 3), "ms_forward_recorded": round(fwd / args.steps, 3),
+                      "ms_reverse": round(ms - fwd / args.steps, 3),
+                      "MLUPS": round(n * n * horizon / (ms / 1e3) / 1e6, 1), "loss": J,
+                      "dJ_dsigma": [float(v) for v in ds]}
+    sim.close()
+    golden = os.path.join(ROOT, "tests", "golden", f"adjoint_fd_{n}.json")
+    check = None
+    if os.path.exists(golden):
+        g = json.load(open(golden))
+        if g["steps"] == horizon:
+            check = {"max_rel_err_dJ_dsigma_vs_oracle_differences":
+                     float(max(abs(a / b - 1) for a, b in zip(res[1]["dJ_dsigma"], g["dJ_dsigma"])))}
+    best = res[1]
+    return {"metric": "ternary D2Q9 gradient evaluations: forward-run MLUPS through reverse mode",
+            "value": best["MLUPS"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": best["ms_per_gradient"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (gradient sums f64)", "data": "synthetic",
+            "config": {"workload": f"gradient workload {n}x{n}: touching discs R=n/6, sigma=0.01, tau=1, "
+                                   f"J = sum (phi - phi_target)^2 after {horizon} steps, dJ/drho0 and dJ/dsigma",
+                       "horizon_steps": horizon, "step": "one full gradient evaluation (recorded forward + reverse)",
+                       "l2": "state 7 MB per step: L2-resident at this size"},
+            "checkpoint_every": {str(k): v for k, v in res.items()}, "checks": check,
+            "gpu_launches": args.steps * (1 + horizon + 1 + 3 + 6 * horizon + 1)}
+
+
 def cpu_baseline(case, steps: int):
     """The FP64 oracle as it stands, single-threaded on a host core, on a
     bounded sample of the same workload: `steps` steps of the full grid."""
@@ -416,9 +491,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="compound", choices=["compound", "sweep", "janus"],
+    ap.add_argument("--workload", default="compound", choices=["compound", "sweep", "janus", "adjoint"],
                     help="compound: the 2048^2 compound droplet (default); sweep: the 64-instance batch; "
-                         "janus: the 4096^2 Janus droplet with FP32 / FP16 / BF16 storage")
+                         "janus: the 4096^2 Janus droplet with FP32 / FP16 / BF16 storage; "
+                         "adjoint: gradient evaluations of the 256^2 gradient workload")
     ap.add_argument("--size", type=int, default=2048,
                     help="grid edge; other than 2048 scales the droplet radii (profiling only)")
     args = ap.parse_args()
@@ -441,6 +517,8 @@ def main():
             line = run_sweep(args) if rank == 0 else None
         elif args.workload == "janus":
             line = run_janus(args) if rank == 0 else None
+        elif args.workload == "adjoint":
+            line = run_adjoint(args) if rank == 0 else None
         else:
             line = run_ours(args, ws, rank, local)
         if line is not None:

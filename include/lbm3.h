@@ -144,6 +144,52 @@ lbm3_status lbm3_populations(lbm3_ctx* ctx, double* f, int on_device);
  * Returns LBM3_ENUMERIC if a sum is NaN or Inf. */
 lbm3_status lbm3_mass(lbm3_ctx* ctx, double* mass, double* mom);
 
+/* Replace the physical parameters (tau, rho0, sigma_kl, beta0, beta_form,
+ * recolor_form) of a context; nx, ny and storage must stay the same
+ * (LBM3_EINVAL otherwise).  The state is kept; a recorded run (below) is
+ * dropped. */
+lbm3_status lbm3_set_params(lbm3_ctx* ctx, const lbm3_params* p);
+
+/* Colour fractions phi_k = rho_k / rho (after Eq. 30) at the current time,
+ * phi[3][ny][nx] in FP64 (FP32 storage only, LBM3_EINVAL otherwise).
+ * Synchronises the stream when on_device is 0. */
+lbm3_status lbm3_phi(lbm3_ctx* ctx, double* phi, int on_device);
+
+/* ------------------------------------------------------------------------
+ * Reverse mode.  Gradients of a scalar loss J(phi(t_end)) of the final colour
+ * fractions with respect to the initial state and to the interfacial
+ * tensions sigma_kl, through every step of Sec. 2 (the force of Eq. 11 and
+ * the segregation parameters of Eqs. 16-20 both depend on sigma_kl).  The
+ * paper defines no adjoint; this is the exact transpose of the linearised
+ * step, taken in FP32 with the scalar gradients summed in FP64.
+ *
+ * lbm3_tape_forward advances nsteps >= 1 steps from the current state like
+ * lbm3_step and records the run: it keeps a copy of the state every
+ * checkpoint_every >= 1 steps (ceil(nsteps / checkpoint_every) states) and
+ * allocates room for checkpoint_every - 1 more, into which lbm3_tape_backward
+ * recomputes one segment at a time.  State memory: lbm3_buffer_bytes() each,
+ * so checkpoint_every near sqrt(nsteps) minimises it and checkpoint_every = 1
+ * stores every state and recomputes nothing.  FP32 storage only
+ * (LBM3_EINVAL), LBM3_ENOMEM if the states do not fit.
+ *
+ * lbm3_tape_backward takes dJ/dphi[3][ny][nx] (FP64, host or device) at the
+ * end of the recorded run and writes, for any non-NULL output:
+ *   dpop0[3][9][ny][nx]  dJ/df_{i,k}(x, 0) of the post-streaming populations
+ *                        the run started from (FP64, the layout of
+ *                        lbm3_set_populations),
+ *   drho0[3][ny][nx]     dJ/drho_k(x, 0) for a start from lbm3_init (rest
+ *                        equilibrium f_{i,k} = w_i rho_k), i.e.
+ *                        sum_i w_i dpop0_{i,k}(x),
+ *   dsigma[3]            dJ/d(sigma_12, sigma_13, sigma_23) (host memory).
+ * dpop0 and drho0 are host arrays when out_on_device is 0 (the call then
+ * synchronises) and device arrays otherwise.  LBM3_ESTATE without a recorded
+ * run (lbm3_init, lbm3_set_populations, lbm3_step and lbm3_set_params drop
+ * it); LBM3_ENUMERIC if a gradient is not finite.  The context's state is
+ * left at the end of the run. */
+lbm3_status lbm3_tape_forward(lbm3_ctx* ctx, int64_t nsteps, int32_t checkpoint_every);
+lbm3_status lbm3_tape_backward(lbm3_ctx* ctx, const double* dphi, int dphi_on_device, double* dpop0, double* drho0,
+                               int out_on_device, double* dsigma);
+
 /* ------------------------------------------------------------------------
  * Batches: many independent simulations advanced together (a parameter or
  * morphology sweep).  Each instance has its own grid size and parameters;

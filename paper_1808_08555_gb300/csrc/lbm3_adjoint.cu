@@ -1,0 +1,574 @@
+// Reverse mode (adjoint) of the fused step: hand-written vector-Jacobian
+// products of the ternary colour-gradient update (arXiv 1808.08555, Sec. 2),
+// for gradients of a loss of the colour fractions with respect to the
+// initial state and the interfacial tensions.
+//
+// One step maps the stored post-collision state S_{t-1} to S_t.  Its
+// adjoint, given the cotangent L_t = dJ/dS_t, is taken as a chain of
+// gathers, each node written by exactly one thread:
+//   recompute:  rho_k (pulled densities), grad phi_k (Eq. fd1) and the
+//               tension tensor T (Eq. 11) of S_{t-1};
+//   node VJP:   collision with the Guo force and recolouring (Eqs. 1-3, 5,
+//               6, uk1, vis_1, tau, 18-20) at each node -> cotangents of the
+//               total distribution f_i, of rho_k, of grad phi_k and of F_s;
+//   tension:    F_s = div T transposed (a gather), then T's dependence on
+//               phi, grad phi, rho_k (through C_kl) and sigma;
+//   gradient:   Eq. fd1 transposed: dJ/dphi_k(y) = sum_j c_j e_j . dJ/d(grad phi_k)(y - e_j);
+//   pull:       L_{t-1,ik}(z) = dJ/df_ik(z + e_i), the transpose of streaming.
+// All arithmetic is FP32 (the recomputed forward quantities and the
+// cotangents); the scalar gradients are summed per block in FP64 into a
+// block-owned row, so the result does not depend on scheduling.
+//
+// Array conventions: cotangents of a stored state are plain [27][ny][nx]
+// arrays (plane k*9 + i) indexed by the node where the value is stored;
+// per-node fields are [c][ny][nx].  The tape states are in the library's
+// padded, group-ordered layout.
+
+#include <cmath>
+#include <cstdint>
+
+#include "lbm3_adjoint.h"
+#include "lbm3_internal.h"
+
+namespace lbm3 {
+namespace {
+
+constexpr float kNormalDeltaA = 0.1f;  // recolouring normal G / max(|G|, 0.1 phi_k phi_l)
+constexpr int kAdjThreads = 256;
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ int nbr(int x, int y, int dx, int dy, int nx, int ny) {
+  return wrapi(y + dy, ny) * nx + wrapi(x + dx, nx);
+}
+
+// pulled population f_{i,k}(x) = stored_{i,k}(x - e_i) of a padded state
+__device__ __forceinline__ float pulled(const float* __restrict__ st, int k, int i, int x, int y, int nx, int ny,
+                                        size_t PS, int P) {
+  return st[plane_of(k, i) * PS + static_cast<size_t>(wrapi(y - ey(i), ny)) * P + (wrapi(x - ex(i), nx) + kGhost)];
+}
+
+// Sum three FP64 values over the block and add them to row[0..2] (the row
+// belongs to this block only).  Every thread of the block must call it.
+__device__ __forceinline__ void block_add3(double v0, double v1, double v2, double* row) {
+  __shared__ double sh[3][kAdjThreads / 32];
+  for (int off = 16; off > 0; off >>= 1) {
+    v0 += __shfl_down_sync(0xffffffffu, v0, off);
+    v1 += __shfl_down_sync(0xffffffffu, v1, off);
+    v2 += __shfl_down_sync(0xffffffffu, v2, off);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sh[0][warp] = v0;
+    sh[1][warp] = v1;
+    sh[2][warp] = v2;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0.0;
+    for (int w = 0; w < kAdjThreads / 32; ++w) s += sh[threadIdx.x][w];
+    row[threadIdx.x] += s;
+  }
+}
+
+// ------------------------------------------------------------- recompute
+__global__ void __launch_bounds__(kAdjThreads) adj_density_kernel(const float* __restrict__ st,
+                                                                  float* __restrict__ rho3, int nx, int ny) {
+  const int N = nx * ny;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int x = n % nx, y = n / nx, P = pitch_of(nx);
+  const size_t PS = static_cast<size_t>(P) * ny;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) s += pulled(st, k, i, x, y, nx, ny, PS, P);
+    rho3[static_cast<size_t>(k) * N + n] = s;
+  }
+}
+
+// grad phi_k (Eq. fd1) and T = sum_pairs sigma C |G| (I - n n) (Eq. 11)
+__global__ void __launch_bounds__(kAdjThreads) adj_tension_fwd_kernel(const float* __restrict__ rho3,
+                                                                      float* __restrict__ gphi,
+                                                                      float* __restrict__ T, StepArgs a) {
+  const int nx = a.nx, ny = a.ny, N = nx * ny;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int x = n % nx, y = n / nx;
+  float gx[3] = {0.0f, 0.0f, 0.0f}, gy[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int j = 1; j < 9; ++j) {
+    const int m = nbr(x, y, ex(j), ey(j), nx, ny);
+    const float r0 = rho3[m], r1 = rho3[N + m], r2 = rho3[2 * N + m];
+    const float ir = 1.0f / (r0 + r1 + r2);
+    const float c = 3.0f * wt(j);
+    const float ph[3] = {r0 * ir, r1 * ir, r2 * ir};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      gx[k] += c * ex(j) * ph[k];
+      gy[k] += c * ey(j) * ph[k];
+    }
+  }
+  const float rk[3] = {rho3[n], rho3[N + n], rho3[2 * N + n]};
+  const float ir = 1.0f / (rk[0] + rk[1] + rk[2]);
+  const float ph[3] = {rk[0] * ir, rk[1] * ir, rk[2] * ir};
+  float txx = 0.0f, txy = 0.0f, tyy = 0.0f;
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const int k = p < 2 ? 0 : 1, l = p == 0 ? 1 : 2;
+    const float Gx = ph[l] * gx[k] - ph[k] * gx[l];
+    const float Gy = ph[l] * gy[k] - ph[k] * gy[l];
+    const float g2 = Gx * Gx + Gy * Gy;
+    if (g2 > 1e-30f) {
+      const float ck = fminf(a.cpair[p] * rk[k] * rk[l], 1.0f);
+      const float sc = a.sigma[p] * ck / sqrtf(g2);
+      txx += sc * Gy * Gy;
+      txy -= sc * Gx * Gy;
+      tyy += sc * Gx * Gx;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gphi[static_cast<size_t>(2 * k) * N + n] = gx[k];
+    gphi[static_cast<size_t>(2 * k + 1) * N + n] = gy[k];
+  }
+  T[n] = txx;
+  T[N + n] = txy;
+  T[2 * N + n] = tyy;
+}
+
+// ------------------------------------------------------------- node VJP
+// lam_in: cotangent of the step's output stored at each node.  Writes the
+// cotangents of the total distribution f_i (lam9), of rho_k (lamr, including
+// every dependence through phi_k, rho and beta), of grad phi_k (lamg) and of
+// F_s (lamF); adds sum dJ/dh_q (the per-pair beta coefficients) to acc[3..5].
+__global__ void __launch_bounds__(kAdjThreads) adj_node_kernel(const float* __restrict__ st,
+                                                               const float* __restrict__ gphi,
+                                                               const float* __restrict__ T,
+                                                               const float* __restrict__ lam_in,
+                                                               float* __restrict__ lam9, float* __restrict__ lamr,
+                                                               float* __restrict__ lamg, float* __restrict__ lamF,
+                                                               double* __restrict__ acc, StepArgs a) {
+  const int nx = a.nx, ny = a.ny, N = nx * ny;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  double dh0 = 0.0, dh1 = 0.0, dh2 = 0.0;
+  if (n < N) {
+    const int x = n % nx, y = n / nx, P = pitch_of(nx);
+    const size_t PS = static_cast<size_t>(P) * ny;
+    // ---- forward recompute at this node
+    float fi[9], rk[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const float f0 = pulled(st, 0, i, x, y, nx, ny, PS, P);
+      const float f1 = pulled(st, 1, i, x, y, nx, ny, PS, P);
+      const float f2 = pulled(st, 2, i, x, y, nx, ny, PS, P);
+      rk[0] += f0;
+      rk[1] += f1;
+      rk[2] += f2;
+      fi[i] = f0 + f1 + f2;
+    }
+    const float rho = rk[0] + rk[1] + rk[2];
+    const float ir = 1.0f / rho;
+    const float ph[3] = {rk[0] * ir, rk[1] * ir, rk[2] * ir};
+    float Fx = 0.0f, Fy = 0.0f;
+#pragma unroll
+    for (int j = 1; j < 9; ++j) {
+      const int m = nbr(x, y, ex(j), ey(j), nx, ny);
+      const float c = 3.0f * wt(j);
+      Fx += c * (ex(j) * T[m] + ey(j) * T[N + m]);
+      Fy += c * (ex(j) * T[N + m] + ey(j) * T[2 * N + m]);
+    }
+    float mx = 0.0f, my = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+      mx += ex(i) * fi[i];
+      my += ey(i) * fi[i];
+    }
+    const float ux = (mx + 0.5f * Fx) * ir, uy = (my + 0.5f * Fy) * ir;
+    const float inu = ph[0] * a.inv_nu[0] + ph[1] * a.inv_nu[1] + ph[2] * a.inv_nu[2];
+    const float dom = 3.0f + 0.5f * inu;
+    const float om = inu / dom;  // 1/tau_f
+    const float g = 1.0f - 0.5f * om;
+    const float uu = ux * ux + uy * uy, uF = ux * Fx + uy * Fy;
+    float feq[9], Ai[9], fd[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const float eu = ex(i) * ux + ey(i) * uy, eF = ex(i) * Fx + ey(i) * Fy;
+      feq[i] = wt(i) * rho * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);
+      Ai[i] = 3.0f * eF - 3.0f * uF + 9.0f * eu * eF;  // Guo: Phi_i = w_i g A_i
+      fd[i] = fi[i] + om * (feq[i] - fi[i]) + g * wt(i) * Ai[i];
+    }
+    const float prod = ph[0] * ph[1] * ph[2];
+    const float cbr = a.beta_A * prod, cb = fminf(cbr, 1.0f);
+    float gpx[3], gpy[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      gpx[k] = gphi[static_cast<size_t>(2 * k) * N + n];
+      gpy[k] = gphi[static_cast<size_t>(2 * k + 1) * N + n];
+    }
+    // ---- reverse: recolouring (Eq. 6)
+    float lfd[9], lph[3] = {0.0f, 0.0f, 0.0f}, mux[3] = {0.0f, 0.0f, 0.0f}, muy[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      float s = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const float L = lam_in[static_cast<size_t>(k * 9 + i) * N + n];
+        s += ph[k] * L;
+        lph[k] += fd[i] * L;
+        mux[k] += a.wrec[i] * ex(i) * L;
+        muy[k] += a.wrec[i] * ey(i) * L;
+      }
+      lfd[i] = s;
+    }
+    float lrho = 0.0f, lcb = 0.0f;
+    float lgx[3] = {0.0f, 0.0f, 0.0f}, lgy[3] = {0.0f, 0.0f, 0.0f};
+    double dh[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const int k = p < 2 ? 0 : 1, l = p == 0 ? 1 : 2;
+      const float Gx = ph[l] * gpx[k] - ph[k] * gpx[l];
+      const float Gy = ph[l] * gpy[k] - ph[k] * gpy[l];
+      const float g2 = Gx * Gx + Gy * Gy;
+      if (!(g2 > 1e-30f)) continue;  // no k-l interface: n = 0
+      const float mag = sqrtf(g2);
+      const float pp = ph[k] * ph[l];
+      const float den = fmaxf(mag, kNormalDeltaA * pp);
+      const float nxv = Gx / den, nyv = Gy / den;
+      const float b = a.beta0 * (1.0f + cb * a.beta_h[p]);
+      const float amp = b * pp * rho;  // beta_kl rho_k rho_l / rho
+      // colour k gains amp n . e_i w'_i, colour l loses it
+      const float vx = mux[k] - mux[l], vy = muy[k] - muy[l];
+      const float lamp = nxv * vx + nyv * vy;
+      const float lnx = amp * vx, lny = amp * vy;
+      const float lb = lamp * pp * rho;
+      lph[k] += lamp * b * ph[l] * rho;
+      lph[l] += lamp * b * ph[k] * rho;
+      lrho += lamp * b * pp;
+      lcb += lb * a.beta0 * a.beta_h[p];
+      dh[p] = static_cast<double>(lb * a.beta0 * cb);
+      float lGx, lGy;
+      if (mag >= kNormalDeltaA * pp) {  // unit normal G/|G|
+        const float nl = nxv * lnx + nyv * lny;
+        lGx = (lnx - nxv * nl) / mag;
+        lGy = (lny - nyv * nl) / mag;
+      } else {  // G / (delta phi_k phi_l)
+        lGx = lnx / den;
+        lGy = lny / den;
+        const float lden = -(lnx * nxv + lny * nyv) / den;
+        lph[k] += lden * kNormalDeltaA * ph[l];
+        lph[l] += lden * kNormalDeltaA * ph[k];
+      }
+      // G = phi_l grad phi_k - phi_k grad phi_l
+      lgx[k] += ph[l] * lGx;
+      lgy[k] += ph[l] * lGy;
+      lgx[l] -= ph[k] * lGx;
+      lgy[l] -= ph[k] * lGy;
+      lph[l] += gpx[k] * lGx + gpy[k] * lGy;
+      lph[k] -= gpx[l] * lGx + gpy[l] * lGy;
+    }
+    dh0 = dh[0];
+    dh1 = dh[1];
+    dh2 = dh[2];
+    if (cbr < 1.0f) {  // c = min(A phi_1 phi_2 phi_3, 1) (Eq. 19)
+      lph[0] += lcb * a.beta_A * ph[1] * ph[2];
+      lph[1] += lcb * a.beta_A * ph[0] * ph[2];
+      lph[2] += lcb * a.beta_A * ph[0] * ph[1];
+    }
+    // ---- reverse: BGK collision with the Guo force
+    float lfi[9], lom = 0.0f, lux = 0.0f, luy = 0.0f, lFx = 0.0f, lFy = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      lfi[i] = (1.0f - om) * lfd[i];
+      lom += lfd[i] * (feq[i] - fi[i] - 0.5f * wt(i) * Ai[i]);
+      const float lfeq = om * lfd[i], lA = g * wt(i) * lfd[i];
+      const float eu = ex(i) * ux + ey(i) * uy, eF = ex(i) * Fx + ey(i) * Fy;
+      lFx += lA * (3.0f * ex(i) - 3.0f * ux + 9.0f * eu * ex(i));
+      lFy += lA * (3.0f * ey(i) - 3.0f * uy + 9.0f * eu * ey(i));
+      lux += lA * (-3.0f * Fx + 9.0f * eF * ex(i));
+      luy += lA * (-3.0f * Fy + 9.0f * eF * ey(i));
+      lrho += lfeq * feq[i] * ir;
+      const float wr = wt(i) * rho * lfeq;
+      lux += wr * (3.0f * ex(i) + 9.0f * eu * ex(i) - 3.0f * ux);
+      luy += wr * (3.0f * ey(i) + 9.0f * eu * ey(i) - 3.0f * uy);
+    }
+    // omega = inu / (3 + inu/2), inu = sum_k phi_k / nu_k (Eqs. vis_1, tau)
+    const float linu = lom * 3.0f / (dom * dom);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) lph[k] += linu * a.inv_nu[k];
+    // u = (m + F/2) / rho (Eq. uk1)
+    const float lmx = lux * ir, lmy = luy * ir;
+    lFx += 0.5f * lmx;
+    lFy += 0.5f * lmy;
+    lrho -= (lux * ux + luy * uy) * ir;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) lfi[i] += lmx * ex(i) + lmy * ey(i);
+    // phi_k = rho_k / rho, rho = sum_k rho_k
+    const float sph = ph[0] * lph[0] + ph[1] * lph[1] + ph[2] * lph[2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) lamr[static_cast<size_t>(k) * N + n] = (lph[k] - sph) * ir + lrho;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) lam9[static_cast<size_t>(i) * N + n] = lfi[i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      lamg[static_cast<size_t>(2 * k) * N + n] = lgx[k];
+      lamg[static_cast<size_t>(2 * k + 1) * N + n] = lgy[k];
+    }
+    lamF[n] = lFx;
+    lamF[N + n] = lFy;
+  }
+  block_add3(dh0, dh1, dh2, acc + static_cast<size_t>(blockIdx.x) * 6 + 3);
+}
+
+// ------------------------------------------------------------ tension VJP
+// dJ/dT from dJ/dF_s (the divergence of Eq. 11 transposed), then T's
+// dependence on grad phi_k, phi_k, rho_k (C_kl) and sigma_kl.  Adds to
+// lamg and lamr of this node and sum dJ/dsigma_q to acc[0..2].
+__global__ void __launch_bounds__(kAdjThreads) adj_tension_kernel(const float* __restrict__ rho3,
+                                                                  const float* __restrict__ gphi,
+                                                                  const float* __restrict__ lamF,
+                                                                  float* __restrict__ lamg, float* __restrict__ lamr,
+                                                                  double* __restrict__ acc, StepArgs a) {
+  const int nx = a.nx, ny = a.ny, N = nx * ny;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  double ds0 = 0.0, ds1 = 0.0, ds2 = 0.0;
+  if (n < N) {
+    const int x = n % nx, y = n / nx;
+    float lxx = 0.0f, lxy = 0.0f, lyy = 0.0f;
+#pragma unroll
+    for (int j = 1; j < 9; ++j) {
+      const int m = nbr(x, y, -ex(j), -ey(j), nx, ny);
+      const float c = 3.0f * wt(j), Lx = lamF[m], Ly = lamF[N + m];
+      lxx += c * ex(j) * Lx;
+      lxy += c * (ey(j) * Lx + ex(j) * Ly);
+      lyy += c * ey(j) * Ly;
+    }
+    const float rk[3] = {rho3[n], rho3[N + n], rho3[2 * N + n]};
+    const float ir = 1.0f / (rk[0] + rk[1] + rk[2]);
+    const float ph[3] = {rk[0] * ir, rk[1] * ir, rk[2] * ir};
+    float gpx[3], gpy[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      gpx[k] = gphi[static_cast<size_t>(2 * k) * N + n];
+      gpy[k] = gphi[static_cast<size_t>(2 * k + 1) * N + n];
+    }
+    float lph[3] = {0.0f, 0.0f, 0.0f}, lrk[3] = {0.0f, 0.0f, 0.0f};
+    float lgx[3] = {0.0f, 0.0f, 0.0f}, lgy[3] = {0.0f, 0.0f, 0.0f};
+    double ds[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const int k = p < 2 ? 0 : 1, l = p == 0 ? 1 : 2;
+      const float Gx = ph[l] * gpx[k] - ph[k] * gpx[l];
+      const float Gy = ph[l] * gpy[k] - ph[k] * gpy[l];
+      const float g2 = Gx * Gx + Gy * Gy;
+      if (!(g2 > 1e-30f)) continue;
+      // with m = |G| and the unit normal n = G/m: T_q = sigma C m (ny^2, -nx ny, nx^2),
+      // dJ/dT : T_q = sigma C m q with q = lxx ny^2 - lxy nx ny + lyy nx^2, and
+      // d(m q)/dG = (2 lyy nx - lxy ny - q nx, 2 lxx ny - lxy nx - q ny): no
+      // negative powers of m, which would overflow FP32 where |G| is tiny
+      const float m = sqrtf(g2), nxv = Gx / m, nyv = Gy / m;
+      const float cr = a.cpair[p] * rk[k] * rk[l], ck = fminf(cr, 1.0f);
+      const float q = lxx * nyv * nyv - lxy * nxv * nyv + lyy * nxv * nxv;
+      ds[p] = static_cast<double>(ck * m * q);
+      const float lck = a.sigma[p] * m * q;
+      if (cr < 1.0f) {
+        lrk[k] += lck * a.cpair[p] * rk[l];
+        lrk[l] += lck * a.cpair[p] * rk[k];
+      }
+      const float aa = a.sigma[p] * ck;
+      const float lGx = aa * (2.0f * lyy * nxv - lxy * nyv - q * nxv);
+      const float lGy = aa * (2.0f * lxx * nyv - lxy * nxv - q * nyv);
+      lgx[k] += ph[l] * lGx;
+      lgy[k] += ph[l] * lGy;
+      lgx[l] -= ph[k] * lGx;
+      lgy[l] -= ph[k] * lGy;
+      lph[l] += gpx[k] * lGx + gpy[k] * lGy;
+      lph[k] -= gpx[l] * lGx + gpy[l] * lGy;
+    }
+    ds0 = ds[0];
+    ds1 = ds[1];
+    ds2 = ds[2];
+    const float sph = ph[0] * lph[0] + ph[1] * lph[1] + ph[2] * lph[2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      lamr[static_cast<size_t>(k) * N + n] += (lph[k] - sph) * ir + lrk[k];
+      lamg[static_cast<size_t>(2 * k) * N + n] += lgx[k];
+      lamg[static_cast<size_t>(2 * k + 1) * N + n] += lgy[k];
+    }
+  }
+  block_add3(ds0, ds1, ds2, acc + static_cast<size_t>(blockIdx.x) * 6);
+}
+
+// --------------------------------------------------- gradient stencil VJP
+__global__ void __launch_bounds__(kAdjThreads) adj_phi_grad_kernel(const float* __restrict__ rho3,
+                                                                   const float* __restrict__ lamg,
+                                                                   float* __restrict__ lamr, int nx, int ny) {
+  const int N = nx * ny;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int x = n % nx, y = n / nx;
+  float lph[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int j = 1; j < 9; ++j) {
+    const int m = nbr(x, y, -ex(j), -ey(j), nx, ny);
+    const float c = 3.0f * wt(j);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      lph[k] += c * (ex(j) * lamg[static_cast<size_t>(2 * k) * N + m] +
+                     ey(j) * lamg[static_cast<size_t>(2 * k + 1) * N + m]);
+  }
+  const float rk[3] = {rho3[n], rho3[N + n], rho3[2 * N + n]};
+  const float ir = 1.0f / (rk[0] + rk[1] + rk[2]);
+  const float sph = (rk[0] * lph[0] + rk[1] * lph[1] + rk[2] * lph[2]) * ir;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) lamr[static_cast<size_t>(k) * N + n] += (lph[k] - sph) * ir;
+}
+
+// ------------------------------------------------------------- pull VJP
+// L_out,ik(z) = lam9_i(z + e_i) + lamr_k(z + e_i); lam9 may be NULL.
+__global__ void __launch_bounds__(kAdjThreads) adj_pull_kernel(const float* __restrict__ lam9,
+                                                               const float* __restrict__ lamr,
+                                                               float* __restrict__ lam_out, int nx, int ny) {
+  const int N = nx * ny;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int x = n % nx, y = n / nx;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int m = nbr(x, y, ex(i), ey(i), nx, ny);
+    const float l9 = lam9 ? lam9[static_cast<size_t>(i) * N + m] : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      lam_out[static_cast<size_t>(k * 9 + i) * N + n] = l9 + lamr[static_cast<size_t>(k) * N + m];
+  }
+}
+
+// -------------------------------------------------- loss-side and outputs
+// phi_k of a stored state, FP64 (the colour fractions at the time the state
+// is pulled into)
+__global__ void phi_kernel(const float* __restrict__ st, double* __restrict__ phi, int nx, int ny) {
+  const int N = nx * ny;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int x = n % nx, y = n / nx, P = pitch_of(nx);
+  const size_t PS = static_cast<size_t>(P) * ny;
+  float r[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) s += pulled(st, k, i, x, y, nx, ny, PS, P);
+    r[k] = s;
+  }
+  const double rho = static_cast<double>(r[0]) + r[1] + r[2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) phi[static_cast<size_t>(k) * N + n] = r[k] / rho;
+}
+
+// dJ/drho_k from dJ/dphi_k at the final state
+__global__ void adj_phi_seed_kernel(const float* __restrict__ rho3, const double* __restrict__ dphi,
+                                    float* __restrict__ lamr, int N) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const double r[3] = {rho3[n], rho3[N + n], rho3[2 * N + n]};
+  const double ir = 1.0 / (r[0] + r[1] + r[2]);
+  const double d[3] = {dphi[n], dphi[N + n], dphi[2 * static_cast<size_t>(N) + n]};
+  const double s = (r[0] * d[0] + r[1] * d[1] + r[2] * d[2]) * ir;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) lamr[static_cast<size_t>(k) * N + n] = static_cast<float>((d[k] - s) * ir);
+}
+
+// dJ/df_ik(x) (post-streaming populations, numbering k*9+i) = L_ik(x - e_i),
+// planes plane0 .. plane0 + nplanes - 1 into out (plane 0 of out = plane0)
+__global__ void adj_dpop_kernel(const float* __restrict__ lam, double* __restrict__ out, int nx, int ny,
+                                int plane0) {
+  const int N = nx * ny;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int pl = plane0 + blockIdx.y, i = pl % 9;
+  const int x = n % nx, y = n / nx;
+  out[static_cast<size_t>(blockIdx.y) * N + n] = lam[static_cast<size_t>(pl) * N + nbr(x, y, -ex(i), -ey(i), nx, ny)];
+}
+
+// dJ/drho_k(x) for the rest equilibrium f_ik = w_i rho_k
+__global__ void adj_drho_kernel(const float* __restrict__ lam, double* __restrict__ out, int nx, int ny) {
+  const int N = nx * ny;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const int x = n % nx, y = n / nx;
+  const double w[3] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+      s += w[i == 0 ? 0 : (i < 5 ? 1 : 2)] *
+           lam[static_cast<size_t>(k * 9 + i) * N + nbr(x, y, -ex(i), -ey(i), nx, ny)];
+    out[static_cast<size_t>(k) * N + n] = s;
+  }
+}
+
+int blocks_for(int N) { return (N + kAdjThreads - 1) / kAdjThreads; }
+
+}  // namespace
+
+int adj_blocks(int N) { return blocks_for(N); }
+
+size_t adj_scratch_floats(int N) { return static_cast<size_t>(86) * N; }
+
+void adj_layout(float* base, int N, AdjBuffers* b) {
+  const size_t n = static_cast<size_t>(N);
+  b->lam[0] = base;
+  b->lam[1] = base + 27 * n;
+  b->lam9 = base + 54 * n;
+  b->lamr = base + 63 * n;
+  b->lamg = base + 66 * n;
+  b->lamF = base + 72 * n;
+  b->rho3 = base + 74 * n;
+  b->gphi = base + 77 * n;
+  b->T = base + 83 * n;
+}
+
+cudaError_t launch_phi(const float* st, double* phi, int nx, int ny, cudaStream_t s) {
+  phi_kernel<<<blocks_for(nx * ny), kAdjThreads, 0, s>>>(st, phi, nx, ny);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_seed(const float* st_final, const double* dphi, const AdjBuffers& b, int lam_out,
+                            int nx, int ny, cudaStream_t s) {
+  const int N = nx * ny, g = blocks_for(N);
+  adj_density_kernel<<<g, kAdjThreads, 0, s>>>(st_final, b.rho3, nx, ny);
+  adj_phi_seed_kernel<<<g, kAdjThreads, 0, s>>>(b.rho3, dphi, b.lamr, N);
+  adj_pull_kernel<<<g, kAdjThreads, 0, s>>>(nullptr, b.lamr, b.lam[lam_out], nx, ny);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_step(const float* st_prev, const StepArgs& a, const AdjBuffers& b, int lam_in,
+                            double* acc, cudaStream_t s) {
+  const int nx = a.nx, ny = a.ny, N = nx * ny, g = blocks_for(N);
+  adj_density_kernel<<<g, kAdjThreads, 0, s>>>(st_prev, b.rho3, nx, ny);
+  adj_tension_fwd_kernel<<<g, kAdjThreads, 0, s>>>(b.rho3, b.gphi, b.T, a);
+  adj_node_kernel<<<g, kAdjThreads, 0, s>>>(st_prev, b.gphi, b.T, b.lam[lam_in], b.lam9, b.lamr, b.lamg, b.lamF,
+                                            acc, a);
+  adj_tension_kernel<<<g, kAdjThreads, 0, s>>>(b.rho3, b.gphi, b.lamF, b.lamg, b.lamr, acc, a);
+  adj_phi_grad_kernel<<<g, kAdjThreads, 0, s>>>(b.rho3, b.lamg, b.lamr, nx, ny);
+  adj_pull_kernel<<<g, kAdjThreads, 0, s>>>(b.lam9, b.lamr, b.lam[lam_in ^ 1], nx, ny);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_dpop(const float* lam, double* out, int nx, int ny, int plane0, int nplanes,
+                            cudaStream_t s) {
+  adj_dpop_kernel<<<dim3(blocks_for(nx * ny), nplanes), kAdjThreads, 0, s>>>(lam, out, nx, ny, plane0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_drho(const float* lam, double* out, int nx, int ny, cudaStream_t s) {
+  adj_drho_kernel<<<blocks_for(nx * ny), kAdjThreads, 0, s>>>(lam, out, nx, ny);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm3

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/lbm3.h"
+#include "lbm3_adjoint.h"
 #include "lbm3_internal.h"
 
 using lbm3::StepArgs;
@@ -45,6 +46,17 @@ struct lbm3_ctx {
   // TMA descriptors of buf[0] and buf[1]: one (FP32) or two (deviations, rho')
   alignas(64) unsigned char tmap[2][256];
   float* shadow = nullptr;  // 16-bit storage: FP32 copy of one buffer for host I/O
+  // reverse mode: checkpoints S_0, S_K, S_2K, ... of a recorded run, the
+  // recomputed states of one segment, the adjoint scratch and accumulator
+  unsigned char* ckpt = nullptr;
+  size_t ckpt_slots = 0;
+  unsigned char* tape = nullptr;
+  size_t tape_slots = 0;
+  float* adj = nullptr;
+  double* acc = nullptr;
+  int64_t tape_steps = 0;
+  int tape_every = 0;
+  bool tape_valid = false;
   std::string msg;
 };
 
@@ -306,6 +318,118 @@ StepArgs args_for(const lbm3_ctx* c, const float* fin, float* fout, int* grid) {
   return a;
 }
 
+
+// ------------------------------------------------------------ reverse mode
+// d h_q / d sigma_r of the per-pair beta coefficients that fill_constants()
+// derives from the tensions (h_q = g(X_q) for Eqs. 19-20; the sine terms of
+// Eqs. 16 and 17), with X_q of Eq. 18.  Zero where h does not depend on sigma.
+void beta_h_jacobian(const lbm3_params& p, double J[3][3]) {
+  const double s[3] = {p.sigma12, p.sigma13, p.sigma23};
+  const int pk[3] = {0, 0, 1}, pl[3] = {1, 2, 2};
+  auto pidx = [](int k, int l) {
+    const int lo = k < l ? k : l, hi = k < l ? l : k;
+    return lo == 0 ? (hi == 1 ? 0 : 1) : 2;
+  };
+  double X[3], dX[3][3] = {{0.0}};
+  bool tri = true;
+  for (int q = 0; q < 3; ++q) {
+    const int k = pk[q], l = pl[q], m = 3 - k - l;
+    const int ia = pidx(m, k), ib = pidx(m, l), ic = pidx(k, l);
+    const double a = s[ia], b = s[ib], c = s[ic];
+    X[q] = (a * a + b * b - c * c) / (2.0 * a * b);
+    dX[q][ia] = (a * a - b * b + c * c) / (2.0 * a * a * b);
+    dX[q][ib] = (b * b - a * a + c * c) / (2.0 * a * b * b);
+    dX[q][ic] = -c / (a * b);
+    tri = tri && std::fabs(X[q]) < 1.0;
+  }
+  double dh_dX[3][3] = {{0.0}};  // dh_q / dX_r
+  switch (p.beta_form) {
+    case LBM3_BETA_PAPER:  // g(X) = -sgn(X)(1 - sqrt(1 - X^2)) inside [-1, 1]
+      for (int q = 0; q < 3; ++q)
+        if (std::fabs(X[q]) < 1.0) dh_dX[q][q] = -std::fabs(X[q]) / std::sqrt(1.0 - X[q] * X[q]);
+      break;
+    case LBM3_BETA_SPENCER:  // h_1 = sin(acos X_23) - 1, h_2 = sin(acos X_13) - 1
+      if (tri) {
+        dh_dX[1][2] = -X[2] / std::sqrt(1.0 - X[2] * X[2]);
+        dh_dX[2][1] = -X[1] / std::sqrt(1.0 - X[1] * X[1]);
+      }
+      break;
+    case LBM3_BETA_LECLAIRE:  // h_q = sin(a_m + a_q) - 1, a = acos X, m the largest angle
+      if (tri) {
+        double ang[3];
+        for (int q = 0; q < 3; ++q) ang[q] = std::acos(X[q]);
+        int qm = 0;
+        for (int q = 1; q < 3; ++q)
+          if (ang[q] > ang[qm]) qm = q;
+        for (int q = 0; q < 3; ++q) {
+          if (q == qm) continue;
+          const double cq = std::cos(ang[qm] + ang[q]);
+          dh_dX[q][q] += -cq / std::sqrt(1.0 - X[q] * X[q]);
+          dh_dX[q][qm] += -cq / std::sqrt(1.0 - X[qm] * X[qm]);
+        }
+      }
+      break;
+    default:
+      break;
+  }
+  for (int q = 0; q < 3; ++q)
+    for (int r = 0; r < 3; ++r) {
+      double v = 0.0;
+      for (int j = 0; j < 3; ++j) v += dh_dX[q][j] * dX[j][r];
+      J[q][r] = v;
+    }
+}
+
+size_t slot_bytes(const lbm3_ctx* c) { return (c->buf_bytes + 255) / 256 * 256; }
+
+float* slot(unsigned char* base, const lbm3_ctx* c, size_t i) {
+  return reinterpret_cast<float*>(base + i * slot_bytes(c));
+}
+
+lbm3_status grow(lbm3_ctx* c, unsigned char** p, size_t* have, size_t want, const char* what) {
+  if (*have >= want) return LBM3_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  if (want == 0) return LBM3_OK;
+  void* q = nullptr;
+  if (cudaMalloc(&q, want * slot_bytes(c)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, LBM3_ENOMEM, "lbm3: cannot allocate %zu states (%zu bytes) for %s", want, want * slot_bytes(c),
+                what);
+  }
+  *p = static_cast<unsigned char*>(q);
+  *have = want;
+  return LBM3_OK;
+}
+
+lbm3_status ensure_adjoint(lbm3_ctx* c) {
+  if (c->adj) return LBM3_OK;
+  const int N = static_cast<int>(nodes(c->p));
+  void* a = nullptr;
+  void* b = nullptr;
+  if (cudaMalloc(&a, lbm3::adj_scratch_floats(N) * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&b, static_cast<size_t>(lbm3::adj_blocks(N)) * 6 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    if (a) cudaFree(a);
+    return fail(c, LBM3_ENOMEM, "lbm3: cannot allocate the reverse-mode scratch");
+  }
+  c->adj = static_cast<float*>(a);
+  c->acc = static_cast<double*>(b);
+  return LBM3_OK;
+}
+
+// one forward step from state `in` into `out` (FP32 storage)
+lbm3_status step_into(lbm3_ctx* c, const float* in, float* out) {
+  alignas(64) unsigned char map[256];
+  const cudaError_t e = lbm3::encode_population_maps(map, in, c->p.nx, c->p.ny, c->p.storage);
+  if (e != cudaSuccess) return cuda_fail(c, e, "encoding the TMA descriptor of a tape state");
+  int grid = 0;
+  StepArgs a = args_for(c, in, out, &grid);
+  LBM3_CUDA(c, lbm3::launch_step(a, map, grid, lbm3::MODE_STEP, c->p.storage, c->stream));
+  return LBM3_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -422,6 +546,7 @@ lbm3_status lbm3_init(lbm3_ctx* c, const double* rho, int on_device) {
   if (st != LBM3_OK) return st;
   if (!on_device) LBM3_CUDA(c, cudaStreamSynchronize(c->stream));  // staging reused next
   c->state_set = true;
+  c->tape_valid = false;
   c->t = 0;
   return LBM3_OK;
 }
@@ -452,6 +577,7 @@ lbm3_status lbm3_set_populations(lbm3_ctx* c, const double* f, int on_device) {
   st = commit_fp32(c);
   if (st != LBM3_OK) return st;
   c->state_set = true;
+  c->tape_valid = false;
   c->t = 0;
   return LBM3_OK;
 }
@@ -468,6 +594,7 @@ lbm3_status lbm3_step(lbm3_ctx* c, int64_t n) {
   if (n < 0) return fail(c, LBM3_EINVAL, "lbm3_step: n = %lld < 0", static_cast<long long>(n));
   if (!c->state_set) return fail(c, LBM3_ESTATE, "lbm3_step: state not initialised");
   DeviceGuard g(c->device);
+  if (n > 0) c->tape_valid = false;
   for (int64_t s = 0; s < n; ++s) {
     int grid = 0;
     StepArgs a = args_for(c, c->buf[c->cur], c->buf[c->cur ^ 1], &grid);
@@ -580,9 +707,152 @@ lbm3_status lbm3_destroy(lbm3_ctx* c) {
     cudaFree(c->buf[1]);
   }
   if (c->shadow) cudaFree(c->shadow);
+  if (c->ckpt) cudaFree(c->ckpt);
+  if (c->tape) cudaFree(c->tape);
+  if (c->adj) cudaFree(c->adj);
+  if (c->acc) cudaFree(c->acc);
   cudaFree(c->scratch);
   cudaGetLastError();
   delete c;
+  return LBM3_OK;
+}
+
+
+lbm3_status lbm3_set_params(lbm3_ctx* c, const lbm3_params* p) {
+  if (!c) return LBM3_EINVAL;
+  std::string why;
+  if (validate(p, &why) != LBM3_OK) return fail(c, LBM3_EINVAL, "%s", why.c_str());
+  if (p->nx != c->p.nx || p->ny != c->p.ny || p->storage != c->p.storage)
+    return fail(c, LBM3_EINVAL, "lbm3_set_params: nx, ny and storage cannot change");
+  c->p = *p;
+  fill_constants(*p, &c->base);
+  c->tape_valid = false;
+  return LBM3_OK;
+}
+
+lbm3_status lbm3_phi(lbm3_ctx* c, double* phi, int on_device) {
+  if (!c) return LBM3_EINVAL;
+  if (!phi) return fail(c, LBM3_EINVAL, "lbm3_phi: NULL phi");
+  if (!c->state_set) return fail(c, LBM3_ESTATE, "lbm3_phi: state not initialised");
+  if (c->p.storage != LBM3_FP32) return fail(c, LBM3_EINVAL, "lbm3_phi: needs FP32 storage (use lbm3_fields)");
+  DeviceGuard g(c->device);
+  const size_t N = nodes(c->p);
+  double* dst = on_device ? phi : reinterpret_cast<double*>(c->buf[c->cur ^ 1]);
+  LBM3_CUDA(c, lbm3::launch_phi(c->buf[c->cur], dst, c->p.nx, c->p.ny, c->stream));
+  if (on_device) return LBM3_OK;
+  LBM3_CUDA(c, cudaMemcpyAsync(phi, dst, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return check_device_errors(c);
+}
+
+lbm3_status lbm3_tape_forward(lbm3_ctx* c, int64_t nsteps, int32_t every) {
+  if (!c) return LBM3_EINVAL;
+  if (nsteps < 1 || every < 1)
+    return fail(c, LBM3_EINVAL, "lbm3_tape_forward: nsteps = %lld and checkpoint_every = %d must be >= 1",
+                static_cast<long long>(nsteps), every);
+  if (!c->state_set) return fail(c, LBM3_ESTATE, "lbm3_tape_forward: state not initialised");
+  if (c->p.storage != LBM3_FP32) return fail(c, LBM3_EINVAL, "lbm3_tape_forward: reverse mode needs FP32 storage");
+  DeviceGuard g(c->device);
+  c->tape_valid = false;
+  const size_t nseg = static_cast<size_t>((nsteps + every - 1) / every);
+  const size_t seg = static_cast<size_t>(nsteps < every ? nsteps : every);
+  lbm3_status st = grow(c, &c->ckpt, &c->ckpt_slots, nseg, "checkpoints");
+  if (st == LBM3_OK) st = grow(c, &c->tape, &c->tape_slots, seg - 1, "the segment tape");
+  if (st == LBM3_OK) st = ensure_adjoint(c);
+  if (st != LBM3_OK) return st;
+  for (int64_t t = 0; t < nsteps; ++t) {
+    if (t % every == 0)
+      LBM3_CUDA(c, cudaMemcpyAsync(slot(c->ckpt, c, static_cast<size_t>(t / every)), c->buf[c->cur], c->buf_bytes,
+                                   cudaMemcpyDeviceToDevice, c->stream));
+    st = step_into(c, c->buf[c->cur], c->buf[c->cur ^ 1]);
+    if (st != LBM3_OK) return st;
+    c->cur ^= 1;
+    c->t += 1;
+  }
+  c->tape_steps = nsteps;
+  c->tape_every = every;
+  c->tape_valid = true;
+  return LBM3_OK;
+}
+
+lbm3_status lbm3_tape_backward(lbm3_ctx* c, const double* dphi, int dphi_on_device, double* dpop0, double* drho0,
+                               int out_on_device, double* dsigma) {
+  if (!c) return LBM3_EINVAL;
+  if (!dphi) return fail(c, LBM3_EINVAL, "lbm3_tape_backward: NULL dphi");
+  if (!c->tape_valid) return fail(c, LBM3_ESTATE, "lbm3_tape_backward: no recorded run (lbm3_tape_forward)");
+  DeviceGuard g(c->device);
+  const int nx = c->p.nx, ny = c->p.ny, N = nx * ny;
+  lbm3::AdjBuffers b;
+  lbm3::adj_layout(c->adj, N, &b);
+  const int nblk = lbm3::adj_blocks(N);
+  LBM3_CUDA(c, cudaMemsetAsync(c->acc, 0, static_cast<size_t>(nblk) * 6 * sizeof(double), c->stream));
+  const double* dphi_d = dphi;
+  if (!dphi_on_device) {  // staged in the second cotangent buffer, free until the first adjoint step
+    double* stage = reinterpret_cast<double*>(b.lam[1]);
+    LBM3_CUDA(c, cudaMemcpyAsync(stage, dphi, 3 * static_cast<size_t>(N) * sizeof(double), cudaMemcpyHostToDevice,
+                                 c->stream));
+    dphi_d = stage;
+  }
+  LBM3_CUDA(c, lbm3::launch_adj_seed(c->buf[c->cur], dphi_d, b, 0, nx, ny, c->stream));
+  int cur = 0;
+  const int64_t T = c->tape_steps, K = c->tape_every;
+  const int64_t nseg = (T + K - 1) / K;
+  int grid = 0;
+  const StepArgs a = args_for(c, nullptr, nullptr, &grid);
+  for (int64_t s = nseg - 1; s >= 0; --s) {
+    const int64_t len = (T - s * K) < K ? (T - s * K) : K;
+    float* base = slot(c->ckpt, c, static_cast<size_t>(s));
+    auto state = [&](int64_t j) { return j == 0 ? base : slot(c->tape, c, static_cast<size_t>(j - 1)); };
+    for (int64_t j = 1; j < len; ++j) {
+      lbm3_status st = step_into(c, state(j - 1), state(j));
+      if (st != LBM3_OK) return st;
+    }
+    for (int64_t j = len - 1; j >= 0; --j) {
+      LBM3_CUDA(c, lbm3::launch_adj_step(state(j), a, b, cur, c->acc, c->stream));
+      cur ^= 1;
+    }
+  }
+  const float* lam0 = b.lam[cur];
+  double* staging = reinterpret_cast<double*>(c->buf[c->cur ^ 1]);
+  if (dpop0) {
+    if (out_on_device) {
+      LBM3_CUDA(c, lbm3::launch_adj_dpop(lam0, dpop0, nx, ny, 0, 27, c->stream));
+    } else {
+      const int chunk = staging_planes(c);
+      for (int p0 = 0; p0 < 27; p0 += chunk) {
+        const int np = p0 + chunk <= 27 ? chunk : 27 - p0;
+        LBM3_CUDA(c, lbm3::launch_adj_dpop(lam0, staging, nx, ny, p0, np, c->stream));
+        LBM3_CUDA(c, cudaMemcpyAsync(dpop0 + static_cast<size_t>(p0) * N, staging,
+                                     static_cast<size_t>(np) * N * sizeof(double), cudaMemcpyDeviceToHost,
+                                     c->stream));
+        LBM3_CUDA(c, cudaStreamSynchronize(c->stream));
+      }
+    }
+  }
+  if (drho0) {
+    double* dst = out_on_device ? drho0 : staging;
+    LBM3_CUDA(c, lbm3::launch_adj_drho(lam0, dst, nx, ny, c->stream));
+    if (!out_on_device)
+      LBM3_CUDA(c, cudaMemcpyAsync(drho0, dst, 3 * static_cast<size_t>(N) * sizeof(double), cudaMemcpyDeviceToHost,
+                                   c->stream));
+  }
+  std::vector<double> rows(static_cast<size_t>(nblk) * 6);
+  LBM3_CUDA(c, cudaMemcpyAsync(rows.data(), c->acc, rows.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  lbm3_status st = check_device_errors(c);
+  if (st != LBM3_OK) return st;
+  double tot[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int r = 0; r < nblk; ++r)
+    for (int j = 0; j < 6; ++j) tot[j] += rows[static_cast<size_t>(r) * 6 + j];
+  for (int j = 0; j < 6; ++j)
+    if (!std::isfinite(tot[j])) return fail(c, LBM3_ENUMERIC, "lbm3_tape_backward: non-finite gradient");
+  if (dsigma) {
+    double J[3][3];
+    beta_h_jacobian(c->p, J);
+    for (int r = 0; r < 3; ++r) {
+      double v = tot[r];
+      for (int q = 0; q < 3; ++q) v += tot[3 + q] * J[q][r];
+      dsigma[r] = v;
+    }
+  }
   return LBM3_OK;
 }
 

@@ -13,6 +13,7 @@ numpy arrays or CPU tensors, device arrays are CUDA float64 tensors.
 from __future__ import annotations
 
 import ctypes
+import dataclasses
 import os
 from dataclasses import dataclass
 
@@ -102,6 +103,10 @@ def load() -> ctypes.CDLL:
         "lbm3_destroy": (st, [vp]),
         "lbm3_last_error": (ctypes.c_char_p, [vp]),
         "lbm3_mass_noalloc": (st, [vp, ctypes.c_int32, ctypes.c_int32, vp, vp]),
+        "lbm3_set_params": (st, [vp, P]),
+        "lbm3_phi": (st, [vp, dp, ctypes.c_int]),
+        "lbm3_tape_forward": (st, [vp, ctypes.c_int64, ctypes.c_int32]),
+        "lbm3_tape_backward": (st, [vp, dp, ctypes.c_int, dp, dp, ctypes.c_int, dp]),
         "lbm3_batch_create": (st, [P, ctypes.c_int32, vp, ctypes.c_int32, ctypes.POINTER(vp)]),
         "lbm3_batch_count": (ctypes.c_int32, [vp]),
         "lbm3_batch_work_items": (ctypes.c_int32, [vp]),
@@ -219,6 +224,40 @@ def lbm3_mass_noalloc(dev_f_ptr: int, nx: int, ny: int, stream: int | None, dev_
         raise Lbm3Error(s, "lbm3_mass_noalloc failed")
 
 
+def lbm3_set_params(ctx, params: Params):
+    p = params.to_c()
+    _check(ctx, load().lbm3_set_params(ctx, ctypes.byref(p)))
+
+
+def lbm3_phi(ctx, phi):
+    p, dev = _ptr(phi)
+    _check(ctx, load().lbm3_phi(ctx, p, dev))
+
+
+def lbm3_tape_forward(ctx, nsteps: int, checkpoint_every: int):
+    _check(ctx, load().lbm3_tape_forward(ctx, int(nsteps), int(checkpoint_every)))
+
+
+def lbm3_tape_backward(ctx, dphi, dpop0=None, drho0=None, want_dsigma: bool = True):
+    """Returns dJ/dsigma (numpy (3,)) or None; fills dpop0 / drho0 if given
+    (both host or both device arrays)."""
+    pd, ddev = _ptr(dphi)
+    outs, devs = [], set()
+    for a in (dpop0, drho0):
+        if a is None:
+            outs.append(None)
+        else:
+            q, d = _ptr(a)
+            outs.append(q)
+            devs.add(d)
+    if len(devs) > 1:
+        raise ValueError("dpop0 and drho0 must be both host or both device arrays")
+    ds = np.zeros(3)
+    dsp = ctypes.c_void_p(ds.ctypes.data) if want_dsigma else None
+    _check(ctx, load().lbm3_tape_backward(ctx, pd, ddev, outs[0], outs[1], devs.pop() if devs else 0, dsp))
+    return ds if want_dsigma else None
+
+
 def lbm3_sync(ctx):
     _check(ctx, load().lbm3_sync(ctx))
 
@@ -281,6 +320,23 @@ class Simulation:
 
     def mass(self):
         return lbm3_mass(self.ctx)
+
+    def phi(self) -> np.ndarray:
+        out = np.empty((3, self.params.ny, self.params.nx))
+        lbm3_phi(self.ctx, out)
+        return out
+
+    def set_params(self, params: Params):
+        lbm3_set_params(self.ctx, params)
+        self.params = params
+        return self
+
+    def tape_forward(self, nsteps: int, checkpoint_every: int):
+        lbm3_tape_forward(self.ctx, nsteps, checkpoint_every)
+        return self
+
+    def tape_backward(self, dphi, dpop0=None, drho0=None):
+        return lbm3_tape_backward(self.ctx, dphi, dpop0, drho0)
 
     def sync(self):
         lbm3_sync(self.ctx)
@@ -429,3 +485,37 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------- autograd
+
+def phi_after(sim: "Simulation", rho0, sigma, nsteps: int, checkpoint_every: int = 0):
+    """phi(t = nsteps) of a run from the rest state f = w_i rho0_k, as a
+    differentiable torch function of rho0 ((3, ny, nx) float64 CUDA tensor)
+    and sigma ((3,) float64 tensor of sigma_12, sigma_13, sigma_23).  The
+    backward pass is the library's reverse mode (lbm3_tape_backward);
+    checkpoint_every = 0 picks about sqrt(nsteps)."""
+    import torch
+
+    class _PhiAfter(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, rho0, sigma):
+            p = sim.params
+            s = [float(v) for v in sigma.detach().cpu()]
+            if tuple(s) != tuple(p.sigma):
+                sim.set_params(dataclasses.replace(p, sigma=tuple(s)))
+            sim.init(rho0.detach().contiguous())
+            every = checkpoint_every or max(1, int(round(nsteps ** 0.5)))
+            sim.tape_forward(nsteps, every)
+            phi = torch.empty_like(rho0)
+            lbm3_phi(sim.ctx, phi)
+            ctx.sigma_device = sigma.device
+            return phi
+
+        @staticmethod
+        def backward(ctx, gphi):
+            drho = torch.empty_like(gphi)
+            ds = lbm3_tape_backward(sim.ctx, gphi.contiguous(), None, drho)
+            return drho, torch.from_numpy(ds).to(ctx.sigma_device)
+
+    return _PhiAfter.apply(rho0, sigma)

@@ -79,6 +79,31 @@ def touching_droplets(n: int, R: float | None = None, xi: float = XI) -> np.ndar
     return _stack(p2, p3)
 
 
+def two_discs(n: int, c2, c3, R2: float, R3: float, xi: float = XI) -> np.ndarray:
+    """A fluid-2 disc (centre c2, radius R2) and a fluid-3 disc (c3, R3) in
+    an n x n matrix of fluid 1, tanh edges (Eq. 21)."""
+    x, y = _grid(n, n)
+    p2 = _edge(R2 - np.hypot(x - c2[0], y - c2[1]), xi)
+    p3 = _edge(R3 - np.hypot(x - c3[0], y - c3[1]), xi)
+    return _stack(p2, p3)
+
+
+def case_adjoint(n: int = 256, seed: int = 1):
+    """Gradient workload: the touching discs of radius n/6 (Sec. 4.1
+    geometry) as the initial field, and as target the same geometry with
+    each centre shifted by U(-4, 4) n/256 per axis and each radius scaled by
+    U(0.9, 1.1), drawn from numpy's default_rng(seed).  Returns (rho0,
+    rho_target), each (3, n, n)."""
+    R = n / 6.0
+    c = n / 2.0
+    rng = np.random.default_rng(seed)
+    d = rng.uniform(-4.0, 4.0, size=4) * (n / 256.0)
+    s = rng.uniform(0.9, 1.1, size=2)
+    rho0 = two_discs(n, (c - R, c), (c + R, c), R, R)
+    tgt = two_discs(n, (c - R + d[0], c + d[1]), (c + R + d[2], c + d[3]), R * s[0], R * s[1])
+    return rho0, tgt
+
+
 def janus_droplet(n: int, R: float, xi: float = XI) -> np.ndarray:
     """One circle of radius R split on the vertical line through its centre:
     fluid 2 on the left, fluid 3 on the right, in a fluid-1 matrix."""
