@@ -169,7 +169,7 @@ def run_ours(args, ws, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    case = make_case(args.size)
+    case = make_case(args.size or 2048)
     p = L.Params(case.nx, case.ny, tau=case.tau, sigma=case.sigma, beta0=case.beta0)
     nodes = case.nx * case.ny
     sim = L.Simulation(p, device=dev)
@@ -334,7 +334,7 @@ def run_janus(args):
     from paper_1808_08555_gb300 import lbm3 as L
     from paper_1808_08555_gb300 import workloads as W
 
-    n = args.size if args.size != 2048 else 4096
+    n = args.size or 4096
     R = 600.0 * n / 4096
     rho = W.janus_droplet(n, R)
     peak, _ = hbm_peak()
@@ -380,8 +380,8 @@ def run_adjoint(args):
     from paper_1808_08555_gb300 import lbm3 as L
     from paper_1808_08555_gb300 import workloads as W
 
-    n = args.size if args.size != 2048 else 256
-    horizon = 2000
+    n = args.size or 256
+    horizon = args.horizon
     rho0, tgt = W.case_adjoint(n)
     phit = torch.tensor(tgt / tgt.sum(axis=0), device="cuda")
     sim = L.Simulation(L.Params(n, n, sigma=(0.01, 0.01, 0.01)))
@@ -455,7 +455,7 @@ def cpu_baseline(case, steps: int):
 def run_reference(args, ws, rank):
     if rank != 0:
         return None
-    case = make_case(args.size)
+    case = make_case(args.size or 2048)
     import oracle as O
     O.build()
     op = O.Params(case.nx, case.ny, tau=case.tau, sigma=case.sigma, beta0=case.beta0)
@@ -495,8 +495,11 @@ def main():
                     help="compound: the 2048^2 compound droplet (default); sweep: the 64-instance batch; "
                          "janus: the 4096^2 Janus droplet with FP32 / FP16 / BF16 storage; "
                          "adjoint: gradient evaluations of the 256^2 gradient workload")
-    ap.add_argument("--size", type=int, default=2048,
-                    help="grid edge; other than 2048 scales the droplet radii (profiling only)")
+    ap.add_argument("--horizon", type=int, default=2000,
+                    help="adjoint workload: steps of the differentiated run (2000 is the workload; fewer for profiling)")
+    ap.add_argument("--size", type=int, default=None,
+                    help="grid edge (default: 2048 compound, 4096 janus, 256 adjoint); other edges scale the "
+                         "droplet radii (profiling and larger cases only)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = 3 if args.impl == "reference" else 5000

@@ -15,14 +15,20 @@
 //               phi, grad phi, rho_k (through C_kl) and sigma;
 //   gradient:   Eq. fd1 transposed: dJ/dphi_k(y) = sum_j c_j e_j . dJ/d(grad phi_k)(y - e_j);
 //   pull:       L_{t-1,ik}(z) = dJ/df_ik(z + e_i), the transpose of streaming.
+// The cotangent of the pulled populations is kept factored as
+// dJ/df_ik(x) = lam9_i(x) + lamr_k(x) (total-distribution and density
+// parts), so the pull of the next (earlier) step is folded into its node VJP,
+// which reads lam9 and lamr at x + e_i: no 27-plane cotangent array exists.
+// Three launches per step: node VJP; tension VJP beside the densities of the
+// next state to differentiate; gradient VJP beside that state's grad phi and
+// T (the recompute of step t-1 is independent of the cotangents of step t,
+// so it rides in the same launches as extra blocks).
 // All arithmetic is FP32 (the recomputed forward quantities and the
-// cotangents); the scalar gradients are summed per block in FP64 into a
-// block-owned row, so the result does not depend on scheduling.
+// cotangents); the scalar gradients are summed per block in FP32 and added
+// in FP64 to a block-owned row, so the result does not depend on scheduling.
 //
-// Array conventions: cotangents of a stored state are plain [27][ny][nx]
-// arrays (plane k*9 + i) indexed by the node where the value is stored;
-// per-node fields are [c][ny][nx].  The tape states are in the library's
-// padded, group-ordered layout.
+// Array conventions: per-node fields are [c][ny][nx] arrays; the tape states
+// are in the library's padded, group-ordered layout.
 
 #include <cmath>
 #include <cstdint>
@@ -36,25 +42,28 @@ namespace {
 constexpr float kNormalDeltaA = 0.1f;  // recolouring normal G / max(|G|, 0.1 phi_k phi_l)
 constexpr int kAdjThreads = 256;
 
-__device__ __forceinline__ int wrapi(int a, int n) {
-  int r = a % n;
-  return r < 0 ? r + n : r;
-}
+// periodic wrap of a coordinate at most one cell outside [0, n)
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 __device__ __forceinline__ int nbr(int x, int y, int dx, int dy, int nx, int ny) {
-  return wrapi(y + dy, ny) * nx + wrapi(x + dx, nx);
+  return wrap1(y + dy, ny) * nx + wrap1(x + dx, nx);
 }
 
-// pulled population f_{i,k}(x) = stored_{i,k}(x - e_i) of a padded state
+// pulled population f_{i,k}(x) = stored_{i,k}(x - e_i) of a padded state;
+// the ghost columns hold the periodic copies, so only the row wraps
 __device__ __forceinline__ float pulled(const float* __restrict__ st, int k, int i, int x, int y, int nx, int ny,
                                         size_t PS, int P) {
-  return st[plane_of(k, i) * PS + static_cast<size_t>(wrapi(y - ey(i), ny)) * P + (wrapi(x - ex(i), nx) + kGhost)];
+  (void)nx;
+  return st[plane_of(k, i) * PS + static_cast<size_t>(wrap1(y - ey(i), ny)) * P + (x - ex(i) + kGhost)];
 }
 
-// Sum three FP64 values over the block and add them to row[0..2] (the row
-// belongs to this block only).  Every thread of the block must call it.
-__device__ __forceinline__ void block_add3(double v0, double v1, double v2, double* row) {
-  __shared__ double sh[3][kAdjThreads / 32];
+// Sum three values over the block and add the totals to row[0..2] in FP64
+// (the row belongs to this block only).  The in-block tree is FP32 (8 levels,
+// relative error ~5e-7 of the block total): FP64 arithmetic is a small
+// fraction of the FP32 rate on this GPU, and an FP64 tree per thread would
+// cost more than the kernel's memory traffic.  Every thread must call it.
+__device__ __forceinline__ void block_add3(float v0, float v1, float v2, double* row) {
+  __shared__ float sh[3][kAdjThreads / 32];
   for (int off = 16; off > 0; off >>= 1) {
     v0 += __shfl_down_sync(0xffffffffu, v0, off);
     v1 += __shfl_down_sync(0xffffffffu, v1, off);
@@ -68,18 +77,17 @@ __device__ __forceinline__ void block_add3(double v0, double v1, double v2, doub
   }
   __syncthreads();
   if (threadIdx.x < 3) {
-    double s = 0.0;
+    float s = 0.0f;
+#pragma unroll
     for (int w = 0; w < kAdjThreads / 32; ++w) s += sh[threadIdx.x][w];
-    row[threadIdx.x] += s;
+    row[threadIdx.x] += static_cast<double>(s);
   }
 }
 
 // ------------------------------------------------------------- recompute
-__global__ void __launch_bounds__(kAdjThreads) adj_density_kernel(const float* __restrict__ st,
-                                                                  float* __restrict__ rho3, int nx, int ny) {
+__device__ __forceinline__ void density_node(const float* __restrict__ st, float* __restrict__ rho3, int n, int nx,
+                                             int ny) {
   const int N = nx * ny;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
   const int x = n % nx, y = n / nx, P = pitch_of(nx);
   const size_t PS = static_cast<size_t>(P) * ny;
 #pragma unroll
@@ -92,12 +100,9 @@ __global__ void __launch_bounds__(kAdjThreads) adj_density_kernel(const float* _
 }
 
 // grad phi_k (Eq. fd1) and T = sum_pairs sigma C |G| (I - n n) (Eq. 11)
-__global__ void __launch_bounds__(kAdjThreads) adj_tension_fwd_kernel(const float* __restrict__ rho3,
-                                                                      float* __restrict__ gphi,
-                                                                      float* __restrict__ T, StepArgs a) {
+__device__ __forceinline__ void tension_fwd_node(const float* __restrict__ rho3, float* __restrict__ gphi,
+                                                 float* __restrict__ T, const StepArgs& a, int n) {
   const int nx = a.nx, ny = a.ny, N = nx * ny;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
   const int x = n % nx, y = n / nx;
   float gx[3] = {0.0f, 0.0f, 0.0f}, gy[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
@@ -141,21 +146,37 @@ __global__ void __launch_bounds__(kAdjThreads) adj_tension_fwd_kernel(const floa
   T[2 * N + n] = tyy;
 }
 
+__global__ void __launch_bounds__(kAdjThreads) adj_density_kernel(const float* __restrict__ st,
+                                                                  float* __restrict__ rho3, int nx, int ny) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < nx * ny) density_node(st, rho3, n, nx, ny);
+}
+
+__global__ void __launch_bounds__(kAdjThreads) adj_tension_fwd_kernel(const float* __restrict__ rho3,
+                                                                      float* __restrict__ gphi,
+                                                                      float* __restrict__ T, StepArgs a) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < a.nx * a.ny) tension_fwd_node(rho3, gphi, T, a, n);
+}
+
 // ------------------------------------------------------------- node VJP
-// lam_in: cotangent of the step's output stored at each node.  Writes the
-// cotangents of the total distribution f_i (lam9), of rho_k (lamr, including
-// every dependence through phi_k, rho and beta), of grad phi_k (lamg) and of
-// F_s (lamF); adds sum dJ/dh_q (the per-pair beta coefficients) to acc[3..5].
-__global__ void __launch_bounds__(kAdjThreads) adj_node_kernel(const float* __restrict__ st,
+// The cotangent of the step's output stored at x is that of the pulled
+// populations of the later step at x + e_i: L_ik(x) = lam9p_i(x + e_i) +
+// lamrp_k(x + e_i).  Writes the cotangents of the total distribution f_i
+// (lam9), of rho_k (lamr, including every dependence through phi_k, rho and
+// beta), of grad phi_k (lamg) and of F_s (lamF); adds sum dJ/dh_q (the
+// per-pair beta coefficients) to acc[3..5].
+__global__ void __launch_bounds__(kAdjThreads, 3) adj_node_kernel(const float* __restrict__ st,
                                                                const float* __restrict__ gphi,
                                                                const float* __restrict__ T,
-                                                               const float* __restrict__ lam_in,
+                                                               const float* __restrict__ lam9p,
+                                                               const float* __restrict__ lamrp,
                                                                float* __restrict__ lam9, float* __restrict__ lamr,
                                                                float* __restrict__ lamg, float* __restrict__ lamF,
                                                                double* __restrict__ acc, StepArgs a) {
   const int nx = a.nx, ny = a.ny, N = nx * ny;
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  double dh0 = 0.0, dh1 = 0.0, dh2 = 0.0;
+  float dh0 = 0.0f, dh1 = 0.0f, dh2 = 0.0f;
   if (n < N) {
     const int x = n % nx, y = n / nx, P = pitch_of(nx);
     const size_t PS = static_cast<size_t>(P) * ny;
@@ -214,10 +235,12 @@ __global__ void __launch_bounds__(kAdjThreads) adj_node_kernel(const float* __re
     float lfd[9], lph[3] = {0.0f, 0.0f, 0.0f}, mux[3] = {0.0f, 0.0f, 0.0f}, muy[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
+      const int m = nbr(x, y, ex(i), ey(i), nx, ny);
+      const float l9 = lam9p[static_cast<size_t>(i) * N + m];
       float s = 0.0f;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        const float L = lam_in[static_cast<size_t>(k * 9 + i) * N + n];
+        const float L = l9 + lamrp[static_cast<size_t>(k) * N + m];
         s += ph[k] * L;
         lph[k] += fd[i] * L;
         mux[k] += a.wrec[i] * ex(i) * L;
@@ -227,7 +250,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_node_kernel(const float* __re
     }
     float lrho = 0.0f, lcb = 0.0f;
     float lgx[3] = {0.0f, 0.0f, 0.0f}, lgy[3] = {0.0f, 0.0f, 0.0f};
-    double dh[3] = {0.0, 0.0, 0.0};
+    float dh[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
     for (int p = 0; p < 3; ++p) {
       const int k = p < 2 ? 0 : 1, l = p == 0 ? 1 : 2;
@@ -250,7 +273,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_node_kernel(const float* __re
       lph[l] += lamp * b * ph[k] * rho;
       lrho += lamp * b * pp;
       lcb += lb * a.beta0 * a.beta_h[p];
-      dh[p] = static_cast<double>(lb * a.beta0 * cb);
+      dh[p] = lb * a.beta0 * cb;
       float lGx, lGy;
       if (mag >= kNormalDeltaA * pp) {  // unit normal G/|G|
         const float nl = nxv * lnx + nyv * lny;
@@ -327,89 +350,80 @@ __global__ void __launch_bounds__(kAdjThreads) adj_node_kernel(const float* __re
 // ------------------------------------------------------------ tension VJP
 // dJ/dT from dJ/dF_s (the divergence of Eq. 11 transposed), then T's
 // dependence on grad phi_k, phi_k, rho_k (C_kl) and sigma_kl.  Adds to
-// lamg and lamr of this node and sum dJ/dsigma_q to acc[0..2].
-__global__ void __launch_bounds__(kAdjThreads) adj_tension_kernel(const float* __restrict__ rho3,
-                                                                  const float* __restrict__ gphi,
-                                                                  const float* __restrict__ lamF,
-                                                                  float* __restrict__ lamg, float* __restrict__ lamr,
-                                                                  double* __restrict__ acc, StepArgs a) {
+// lamg and lamr of this node; ds_out = this node's dJ/dsigma_q.
+__device__ __forceinline__ void tension_vjp_node(const float* __restrict__ rho3, const float* __restrict__ gphi,
+                                                 const float* __restrict__ lamF, float* __restrict__ lamg,
+                                                 float* __restrict__ lamr, const StepArgs& a, int n,
+                                                 float* ds_out) {
   const int nx = a.nx, ny = a.ny, N = nx * ny;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  double ds0 = 0.0, ds1 = 0.0, ds2 = 0.0;
-  if (n < N) {
-    const int x = n % nx, y = n / nx;
-    float lxx = 0.0f, lxy = 0.0f, lyy = 0.0f;
+  const int x = n % nx, y = n / nx;
+  float lxx = 0.0f, lxy = 0.0f, lyy = 0.0f;
 #pragma unroll
-    for (int j = 1; j < 9; ++j) {
-      const int m = nbr(x, y, -ex(j), -ey(j), nx, ny);
-      const float c = 3.0f * wt(j), Lx = lamF[m], Ly = lamF[N + m];
-      lxx += c * ex(j) * Lx;
-      lxy += c * (ey(j) * Lx + ex(j) * Ly);
-      lyy += c * ey(j) * Ly;
-    }
-    const float rk[3] = {rho3[n], rho3[N + n], rho3[2 * N + n]};
-    const float ir = 1.0f / (rk[0] + rk[1] + rk[2]);
-    const float ph[3] = {rk[0] * ir, rk[1] * ir, rk[2] * ir};
-    float gpx[3], gpy[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      gpx[k] = gphi[static_cast<size_t>(2 * k) * N + n];
-      gpy[k] = gphi[static_cast<size_t>(2 * k + 1) * N + n];
-    }
-    float lph[3] = {0.0f, 0.0f, 0.0f}, lrk[3] = {0.0f, 0.0f, 0.0f};
-    float lgx[3] = {0.0f, 0.0f, 0.0f}, lgy[3] = {0.0f, 0.0f, 0.0f};
-    double ds[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      const int k = p < 2 ? 0 : 1, l = p == 0 ? 1 : 2;
-      const float Gx = ph[l] * gpx[k] - ph[k] * gpx[l];
-      const float Gy = ph[l] * gpy[k] - ph[k] * gpy[l];
-      const float g2 = Gx * Gx + Gy * Gy;
-      if (!(g2 > 1e-30f)) continue;
-      // with m = |G| and the unit normal n = G/m: T_q = sigma C m (ny^2, -nx ny, nx^2),
-      // dJ/dT : T_q = sigma C m q with q = lxx ny^2 - lxy nx ny + lyy nx^2, and
-      // d(m q)/dG = (2 lyy nx - lxy ny - q nx, 2 lxx ny - lxy nx - q ny): no
-      // negative powers of m, which would overflow FP32 where |G| is tiny
-      const float m = sqrtf(g2), nxv = Gx / m, nyv = Gy / m;
-      const float cr = a.cpair[p] * rk[k] * rk[l], ck = fminf(cr, 1.0f);
-      const float q = lxx * nyv * nyv - lxy * nxv * nyv + lyy * nxv * nxv;
-      ds[p] = static_cast<double>(ck * m * q);
-      const float lck = a.sigma[p] * m * q;
-      if (cr < 1.0f) {
-        lrk[k] += lck * a.cpair[p] * rk[l];
-        lrk[l] += lck * a.cpair[p] * rk[k];
-      }
-      const float aa = a.sigma[p] * ck;
-      const float lGx = aa * (2.0f * lyy * nxv - lxy * nyv - q * nxv);
-      const float lGy = aa * (2.0f * lxx * nyv - lxy * nxv - q * nyv);
-      lgx[k] += ph[l] * lGx;
-      lgy[k] += ph[l] * lGy;
-      lgx[l] -= ph[k] * lGx;
-      lgy[l] -= ph[k] * lGy;
-      lph[l] += gpx[k] * lGx + gpy[k] * lGy;
-      lph[k] -= gpx[l] * lGx + gpy[l] * lGy;
-    }
-    ds0 = ds[0];
-    ds1 = ds[1];
-    ds2 = ds[2];
-    const float sph = ph[0] * lph[0] + ph[1] * lph[1] + ph[2] * lph[2];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      lamr[static_cast<size_t>(k) * N + n] += (lph[k] - sph) * ir + lrk[k];
-      lamg[static_cast<size_t>(2 * k) * N + n] += lgx[k];
-      lamg[static_cast<size_t>(2 * k + 1) * N + n] += lgy[k];
-    }
+  for (int j = 1; j < 9; ++j) {
+    const int m = nbr(x, y, -ex(j), -ey(j), nx, ny);
+    const float c = 3.0f * wt(j), Lx = lamF[m], Ly = lamF[N + m];
+    lxx += c * ex(j) * Lx;
+    lxy += c * (ey(j) * Lx + ex(j) * Ly);
+    lyy += c * ey(j) * Ly;
   }
-  block_add3(ds0, ds1, ds2, acc + static_cast<size_t>(blockIdx.x) * 6);
+  const float rk[3] = {rho3[n], rho3[N + n], rho3[2 * N + n]};
+  const float ir = 1.0f / (rk[0] + rk[1] + rk[2]);
+  const float ph[3] = {rk[0] * ir, rk[1] * ir, rk[2] * ir};
+  float gpx[3], gpy[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    gpx[k] = gphi[static_cast<size_t>(2 * k) * N + n];
+    gpy[k] = gphi[static_cast<size_t>(2 * k + 1) * N + n];
+  }
+  float lph[3] = {0.0f, 0.0f, 0.0f}, lrk[3] = {0.0f, 0.0f, 0.0f};
+  float lgx[3] = {0.0f, 0.0f, 0.0f}, lgy[3] = {0.0f, 0.0f, 0.0f};
+  float ds[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const int k = p < 2 ? 0 : 1, l = p == 0 ? 1 : 2;
+    const float Gx = ph[l] * gpx[k] - ph[k] * gpx[l];
+    const float Gy = ph[l] * gpy[k] - ph[k] * gpy[l];
+    const float g2 = Gx * Gx + Gy * Gy;
+    if (!(g2 > 1e-30f)) continue;
+    // with m = |G| and the unit normal n = G/m: T_q = sigma C m (ny^2, -nx ny, nx^2),
+    // dJ/dT : T_q = sigma C m q with q = lxx ny^2 - lxy nx ny + lyy nx^2, and
+    // d(m q)/dG = (2 lyy nx - lxy ny - q nx, 2 lxx ny - lxy nx - q ny): no
+    // negative powers of m, which would overflow FP32 where |G| is tiny
+    const float m = sqrtf(g2), nxv = Gx / m, nyv = Gy / m;
+    const float cr = a.cpair[p] * rk[k] * rk[l], ck = fminf(cr, 1.0f);
+    const float q = lxx * nyv * nyv - lxy * nxv * nyv + lyy * nxv * nxv;
+    ds[p] = ck * m * q;
+    const float lck = a.sigma[p] * m * q;
+    if (cr < 1.0f) {
+      lrk[k] += lck * a.cpair[p] * rk[l];
+      lrk[l] += lck * a.cpair[p] * rk[k];
+    }
+    const float aa = a.sigma[p] * ck;
+    const float lGx = aa * (2.0f * lyy * nxv - lxy * nyv - q * nxv);
+    const float lGy = aa * (2.0f * lxx * nyv - lxy * nxv - q * nyv);
+    lgx[k] += ph[l] * lGx;
+    lgy[k] += ph[l] * lGy;
+    lgx[l] -= ph[k] * lGx;
+    lgy[l] -= ph[k] * lGy;
+    lph[l] += gpx[k] * lGx + gpy[k] * lGy;
+    lph[k] -= gpx[l] * lGx + gpy[l] * lGy;
+  }
+  ds_out[0] = ds[0];
+  ds_out[1] = ds[1];
+  ds_out[2] = ds[2];
+  const float sph = ph[0] * lph[0] + ph[1] * lph[1] + ph[2] * lph[2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    lamr[static_cast<size_t>(k) * N + n] += (lph[k] - sph) * ir + lrk[k];
+    lamg[static_cast<size_t>(2 * k) * N + n] += lgx[k];
+    lamg[static_cast<size_t>(2 * k + 1) * N + n] += lgy[k];
+  }
 }
 
 // --------------------------------------------------- gradient stencil VJP
-__global__ void __launch_bounds__(kAdjThreads) adj_phi_grad_kernel(const float* __restrict__ rho3,
-                                                                   const float* __restrict__ lamg,
-                                                                   float* __restrict__ lamr, int nx, int ny) {
+__device__ __forceinline__ void grad_vjp_node(const float* __restrict__ rho3, const float* __restrict__ lamg,
+                                              float* __restrict__ lamr, int nx, int ny, int n) {
   const int N = nx * ny;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
   const int x = n % nx, y = n / nx;
   float lph[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
@@ -428,22 +442,42 @@ __global__ void __launch_bounds__(kAdjThreads) adj_phi_grad_kernel(const float* 
   for (int k = 0; k < 3; ++k) lamr[static_cast<size_t>(k) * N + n] += (lph[k] - sph) * ir;
 }
 
-// ------------------------------------------------------------- pull VJP
-// L_out,ik(z) = lam9_i(z + e_i) + lamr_k(z + e_i); lam9 may be NULL.
-__global__ void __launch_bounds__(kAdjThreads) adj_pull_kernel(const float* __restrict__ lam9,
-                                                               const float* __restrict__ lamr,
-                                                               float* __restrict__ lam_out, int nx, int ny) {
-  const int N = nx * ny;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
-  const int x = n % nx, y = n / nx;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const int m = nbr(x, y, ex(i), ey(i), nx, ny);
-    const float l9 = lam9 ? lam9[static_cast<size_t>(i) * N + m] : 0.0f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-      lam_out[static_cast<size_t>(k * 9 + i) * N + n] = l9 + lamr[static_cast<size_t>(k) * N + m];
+// Blocks [0, G): tension VJP of this step (acc row = block).  Blocks [G, 2G)
+// when st_next is set: densities of the next state to differentiate.
+__global__ void __launch_bounds__(kAdjThreads) adj_tension_kernel(const float* __restrict__ rho3,
+                                                                  const float* __restrict__ gphi,
+                                                                  const float* __restrict__ lamF,
+                                                                  float* __restrict__ lamg, float* __restrict__ lamr,
+                                                                  double* __restrict__ acc, StepArgs a, int G,
+                                                                  const float* __restrict__ st_next,
+                                                                  float* __restrict__ rho3_next) {
+  const int N = a.nx * a.ny;
+  if (static_cast<int>(blockIdx.x) < G) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    float ds[3] = {0.0f, 0.0f, 0.0f};
+    if (n < N) tension_vjp_node(rho3, gphi, lamF, lamg, lamr, a, n, ds);
+    block_add3(ds[0], ds[1], ds[2], acc + static_cast<size_t>(blockIdx.x) * 6);
+  } else {
+    const int n = (blockIdx.x - G) * blockDim.x + threadIdx.x;
+    if (n < N) density_node(st_next, rho3_next, n, a.nx, a.ny);
+  }
+}
+
+// Blocks [0, G): gradient-stencil VJP of this step.  Blocks [G, 2G) when
+// the next state's densities exist: its grad phi and T.
+__global__ void __launch_bounds__(kAdjThreads) adj_grad_kernel(const float* __restrict__ rho3,
+                                                               const float* __restrict__ lamg,
+                                                               float* __restrict__ lamr, StepArgs a, int G,
+                                                               const float* __restrict__ rho3_next,
+                                                               float* __restrict__ gphi_next,
+                                                               float* __restrict__ T_next) {
+  const int N = a.nx * a.ny;
+  if (static_cast<int>(blockIdx.x) < G) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n < N) grad_vjp_node(rho3, lamg, lamr, a.nx, a.ny, n);
+  } else {
+    const int n = (blockIdx.x - G) * blockDim.x + threadIdx.x;
+    if (n < N) tension_fwd_node(rho3_next, gphi_next, T_next, a, n);
   }
 }
 
@@ -469,9 +503,10 @@ __global__ void phi_kernel(const float* __restrict__ st, double* __restrict__ ph
   for (int k = 0; k < 3; ++k) phi[static_cast<size_t>(k) * N + n] = r[k] / rho;
 }
 
-// dJ/drho_k from dJ/dphi_k at the final state
-__global__ void adj_phi_seed_kernel(const float* __restrict__ rho3, const double* __restrict__ dphi,
-                                    float* __restrict__ lamr, int N) {
+// Cotangent of the pulled populations at the end of the run from dJ/dphi_k:
+// lamr_k = dJ/drho_k = (dphi_k - sum_m phi_m dphi_m) / rho, lam9 = 0.
+__global__ void adj_seed_kernel(const float* __restrict__ rho3, const double* __restrict__ dphi,
+                                float* __restrict__ lamr, float* __restrict__ lam9, int N) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const double r[3] = {rho3[n], rho3[N + n], rho3[2 * N + n]};
@@ -480,36 +515,32 @@ __global__ void adj_phi_seed_kernel(const float* __restrict__ rho3, const double
   const double s = (r[0] * d[0] + r[1] * d[1] + r[2] * d[2]) * ir;
 #pragma unroll
   for (int k = 0; k < 3; ++k) lamr[static_cast<size_t>(k) * N + n] = static_cast<float>((d[k] - s) * ir);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) lam9[static_cast<size_t>(i) * N + n] = 0.0f;
 }
 
-// dJ/df_ik(x) (post-streaming populations, numbering k*9+i) = L_ik(x - e_i),
-// planes plane0 .. plane0 + nplanes - 1 into out (plane 0 of out = plane0)
-__global__ void adj_dpop_kernel(const float* __restrict__ lam, double* __restrict__ out, int nx, int ny,
-                                int plane0) {
-  const int N = nx * ny;
+// dJ/df_ik(x) = lam9_i(x) + lamr_k(x) of the post-streaming populations at
+// t = 0, planes plane0 .. plane0 + gridDim.y - 1 (numbering k*9 + i) into out
+__global__ void adj_dpop_kernel(const float* __restrict__ lam9, const float* __restrict__ lamr,
+                                double* __restrict__ out, int N, int plane0) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
-  const int pl = plane0 + blockIdx.y, i = pl % 9;
-  const int x = n % nx, y = n / nx;
-  out[static_cast<size_t>(blockIdx.y) * N + n] = lam[static_cast<size_t>(pl) * N + nbr(x, y, -ex(i), -ey(i), nx, ny)];
+  const int pl = plane0 + blockIdx.y, k = pl / 9, i = pl % 9;
+  out[static_cast<size_t>(blockIdx.y) * N + n] =
+      static_cast<double>(lam9[static_cast<size_t>(i) * N + n]) + lamr[static_cast<size_t>(k) * N + n];
 }
 
-// dJ/drho_k(x) for the rest equilibrium f_ik = w_i rho_k
-__global__ void adj_drho_kernel(const float* __restrict__ lam, double* __restrict__ out, int nx, int ny) {
-  const int N = nx * ny;
+// dJ/drho_k(x) for the rest equilibrium f_ik = w_i rho_k: sum_i w_i dJ/df_ik
+__global__ void adj_drho_kernel(const float* __restrict__ lam9, const float* __restrict__ lamr,
+                                double* __restrict__ out, int N) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
-  const int x = n % nx, y = n / nx;
   const double w[3] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0};
+  double s9 = 0.0;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    double s = 0.0;
+  for (int i = 0; i < 9; ++i) s9 += w[i == 0 ? 0 : (i < 5 ? 1 : 2)] * lam9[static_cast<size_t>(i) * N + n];
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-      s += w[i == 0 ? 0 : (i < 5 ? 1 : 2)] *
-           lam[static_cast<size_t>(k * 9 + i) * N + nbr(x, y, -ex(i), -ey(i), nx, ny)];
-    out[static_cast<size_t>(k) * N + n] = s;
-  }
+  for (int k = 0; k < 3; ++k) out[static_cast<size_t>(k) * N + n] = s9 + lamr[static_cast<size_t>(k) * N + n];
 }
 
 int blocks_for(int N) { return (N + kAdjThreads - 1) / kAdjThreads; }
@@ -518,19 +549,22 @@ int blocks_for(int N) { return (N + kAdjThreads - 1) / kAdjThreads; }
 
 int adj_blocks(int N) { return blocks_for(N); }
 
-size_t adj_scratch_floats(int N) { return static_cast<size_t>(86) * N; }
+size_t adj_scratch_floats(int N) { return static_cast<size_t>(56) * N; }
 
 void adj_layout(float* base, int N, AdjBuffers* b) {
   const size_t n = static_cast<size_t>(N);
-  b->lam[0] = base;
-  b->lam[1] = base + 27 * n;
-  b->lam9 = base + 54 * n;
-  b->lamr = base + 63 * n;
-  b->lamg = base + 66 * n;
-  b->lamF = base + 72 * n;
-  b->rho3 = base + 74 * n;
-  b->gphi = base + 77 * n;
-  b->T = base + 83 * n;
+  b->lam9[0] = base;
+  b->lam9[1] = base + 9 * n;
+  b->lamr[0] = base + 18 * n;
+  b->lamr[1] = base + 21 * n;
+  b->lamg = base + 24 * n;
+  b->lamF = base + 30 * n;
+  b->rho3[0] = base + 32 * n;
+  b->rho3[1] = base + 35 * n;
+  b->gphi[0] = base + 38 * n;
+  b->gphi[1] = base + 44 * n;
+  b->T[0] = base + 50 * n;
+  b->T[1] = base + 53 * n;
 }
 
 cudaError_t launch_phi(const float* st, double* phi, int nx, int ny, cudaStream_t s) {
@@ -538,36 +572,46 @@ cudaError_t launch_phi(const float* st, double* phi, int nx, int ny, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_seed(const float* st_final, const double* dphi, const AdjBuffers& b, int lam_out,
-                            int nx, int ny, cudaStream_t s) {
-  const int N = nx * ny, g = blocks_for(N);
-  adj_density_kernel<<<g, kAdjThreads, 0, s>>>(st_final, b.rho3, nx, ny);
-  adj_phi_seed_kernel<<<g, kAdjThreads, 0, s>>>(b.rho3, dphi, b.lamr, N);
-  adj_pull_kernel<<<g, kAdjThreads, 0, s>>>(nullptr, b.lamr, b.lam[lam_out], nx, ny);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_adj_step(const float* st_prev, const StepArgs& a, const AdjBuffers& b, int lam_in,
-                            double* acc, cudaStream_t s) {
-  const int nx = a.nx, ny = a.ny, N = nx * ny, g = blocks_for(N);
-  adj_density_kernel<<<g, kAdjThreads, 0, s>>>(st_prev, b.rho3, nx, ny);
-  adj_tension_fwd_kernel<<<g, kAdjThreads, 0, s>>>(b.rho3, b.gphi, b.T, a);
-  adj_node_kernel<<<g, kAdjThreads, 0, s>>>(st_prev, b.gphi, b.T, b.lam[lam_in], b.lam9, b.lamr, b.lamg, b.lamF,
-                                            acc, a);
-  adj_tension_kernel<<<g, kAdjThreads, 0, s>>>(b.rho3, b.gphi, b.lamF, b.lamg, b.lamr, acc, a);
-  adj_phi_grad_kernel<<<g, kAdjThreads, 0, s>>>(b.rho3, b.lamg, b.lamr, nx, ny);
-  adj_pull_kernel<<<g, kAdjThreads, 0, s>>>(b.lam9, b.lamr, b.lam[lam_in ^ 1], nx, ny);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_adj_dpop(const float* lam, double* out, int nx, int ny, int plane0, int nplanes,
+cudaError_t launch_adj_seed(const float* st_final, const double* dphi, const AdjBuffers& b, int lam, int nx, int ny,
                             cudaStream_t s) {
-  adj_dpop_kernel<<<dim3(blocks_for(nx * ny), nplanes), kAdjThreads, 0, s>>>(lam, out, nx, ny, plane0);
+  const int N = nx * ny, g = blocks_for(N);
+  float* scratch = b.rho3[1];
+  adj_density_kernel<<<g, kAdjThreads, 0, s>>>(st_final, scratch, nx, ny);
+  adj_seed_kernel<<<g, kAdjThreads, 0, s>>>(scratch, dphi, b.lamr[lam], b.lam9[lam], N);
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_drho(const float* lam, double* out, int nx, int ny, cudaStream_t s) {
-  adj_drho_kernel<<<blocks_for(nx * ny), kAdjThreads, 0, s>>>(lam, out, nx, ny);
+cudaError_t launch_adj_fields(const float* st, const StepArgs& a, const AdjBuffers& b, int slot, cudaStream_t s) {
+  const int g = blocks_for(a.nx * a.ny);
+  adj_density_kernel<<<g, kAdjThreads, 0, s>>>(st, b.rho3[slot], a.nx, a.ny);
+  adj_tension_fwd_kernel<<<g, kAdjThreads, 0, s>>>(b.rho3[slot], b.gphi[slot], b.T[slot], a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_step(const float* st_prev, const float* st_next, const StepArgs& a, const AdjBuffers& b,
+                            int slot, int lam, double* acc, cudaStream_t s) {
+  const int N = a.nx * a.ny, G = blocks_for(N);
+  const int o = lam ^ 1, nslot = slot ^ 1;
+  const int g2 = st_next ? 2 * G : G;
+  adj_node_kernel<<<G, kAdjThreads, 0, s>>>(st_prev, b.gphi[slot], b.T[slot], b.lam9[lam], b.lamr[lam], b.lam9[o],
+                                            b.lamr[o], b.lamg, b.lamF, acc, a);
+  adj_tension_kernel<<<g2, kAdjThreads, 0, s>>>(b.rho3[slot], b.gphi[slot], b.lamF, b.lamg, b.lamr[o], acc, a, G,
+                                                st_next, b.rho3[nslot]);
+  adj_grad_kernel<<<g2, kAdjThreads, 0, s>>>(b.rho3[slot], b.lamg, b.lamr[o], a, G, b.rho3[nslot], b.gphi[nslot],
+                                             b.T[nslot]);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_dpop(const AdjBuffers& b, int lam, double* out, int nx, int ny, int plane0, int nplanes,
+                            cudaStream_t s) {
+  const int N = nx * ny;
+  adj_dpop_kernel<<<dim3(blocks_for(N), nplanes), kAdjThreads, 0, s>>>(b.lam9[lam], b.lamr[lam], out, N, plane0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_drho(const AdjBuffers& b, int lam, double* out, int nx, int ny, cudaStream_t s) {
+  const int N = nx * ny;
+  adj_drho_kernel<<<blocks_for(N), kAdjThreads, 0, s>>>(b.lam9[lam], b.lamr[lam], out, N);
   return cudaGetLastError();
 }
 

@@ -52,6 +52,8 @@ struct lbm3_ctx {
   size_t ckpt_slots = 0;
   unsigned char* tape = nullptr;
   size_t tape_slots = 0;
+  std::vector<unsigned char> ckpt_maps;  // 256 bytes of TMA descriptors per slot
+  std::vector<unsigned char> tape_maps;
   float* adj = nullptr;
   double* acc = nullptr;
   int64_t tape_steps = 0;
@@ -293,7 +295,7 @@ void tiling(const lbm3_ctx* c, int* rows, int* grid) {
     int chunks = resident / nstrips;
     if (chunks < 1) chunks = 1;
     H = (c->p.ny + chunks - 1) / chunks;
-    if (H < 8) H = 8;
+    if (H < 4) H = 4;  // small grids: short columns keep the pipeline fill short
   }
   if (H > c->p.ny) H = c->p.ny;
   const int chunks = (c->p.ny + H - 1) / H;
@@ -386,11 +388,13 @@ float* slot(unsigned char* base, const lbm3_ctx* c, size_t i) {
   return reinterpret_cast<float*>(base + i * slot_bytes(c));
 }
 
-lbm3_status grow(lbm3_ctx* c, unsigned char** p, size_t* have, size_t want, const char* what) {
+lbm3_status grow(lbm3_ctx* c, unsigned char** p, size_t* have, std::vector<unsigned char>* maps, size_t want,
+                 const char* what) {
   if (*have >= want) return LBM3_OK;
   if (*p) cudaFree(*p);
   *p = nullptr;
   *have = 0;
+  maps->clear();
   if (want == 0) return LBM3_OK;
   void* q = nullptr;
   if (cudaMalloc(&q, want * slot_bytes(c)) != cudaSuccess) {
@@ -400,6 +404,12 @@ lbm3_status grow(lbm3_ctx* c, unsigned char** p, size_t* have, size_t want, cons
   }
   *p = static_cast<unsigned char*>(q);
   *have = want;
+  maps->assign(want * 256, 0);
+  for (size_t i = 0; i < want; ++i) {
+    const cudaError_t e =
+        lbm3::encode_population_maps(maps->data() + i * 256, slot(*p, c, i), c->p.nx, c->p.ny, c->p.storage);
+    if (e != cudaSuccess) return cuda_fail(c, e, "encoding the TMA descriptor of a tape state");
+  }
   return LBM3_OK;
 }
 
@@ -419,14 +429,39 @@ lbm3_status ensure_adjoint(lbm3_ctx* c) {
   return LBM3_OK;
 }
 
-// one forward step from state `in` into `out` (FP32 storage)
-lbm3_status step_into(lbm3_ctx* c, const float* in, float* out) {
-  alignas(64) unsigned char map[256];
-  const cudaError_t e = lbm3::encode_population_maps(map, in, c->p.nx, c->p.ny, c->p.storage);
-  if (e != cudaSuccess) return cuda_fail(c, e, "encoding the TMA descriptor of a tape state");
+// one forward step from state `in` (TMA descriptors `map`) into `out`
+lbm3_status step_into(lbm3_ctx* c, const float* in, const void* map, float* out) {
   int grid = 0;
   StepArgs a = args_for(c, in, out, &grid);
   LBM3_CUDA(c, lbm3::launch_step(a, map, grid, lbm3::MODE_STEP, c->p.storage, c->stream));
+  return LBM3_OK;
+}
+
+// State S_t of the recorded run: a checkpoint (t a multiple of the
+// checkpoint interval) or a recomputed state of the current segment.
+struct TapeState {
+  const float* p;
+  const void* map;
+};
+TapeState tape_state(lbm3_ctx* c, int64_t t) {
+  const int64_t K = c->tape_every;
+  if (t % K == 0) {
+    const size_t i = static_cast<size_t>(t / K);
+    return {slot(c->ckpt, c, i), c->ckpt_maps.data() + i * 256};
+  }
+  const size_t j = static_cast<size_t>(t % K - 1);
+  return {slot(c->tape, c, j), c->tape_maps.data() + j * 256};
+}
+
+// recompute the non-checkpoint states of segment r into the tape
+lbm3_status recompute_segment(lbm3_ctx* c, int64_t r) {
+  const int64_t K = c->tape_every, t0 = r * K;
+  const int64_t end = (t0 + K < c->tape_steps) ? t0 + K : c->tape_steps;  // exclusive; S_end is not needed
+  for (int64_t t = t0 + 1; t < end; ++t) {
+    const TapeState in = tape_state(c, t - 1), out = tape_state(c, t);
+    lbm3_status st = step_into(c, in.p, in.map, const_cast<float*>(out.p));
+    if (st != LBM3_OK) return st;
+  }
   return LBM3_OK;
 }
 
@@ -755,21 +790,31 @@ lbm3_status lbm3_tape_forward(lbm3_ctx* c, int64_t nsteps, int32_t every) {
   c->tape_valid = false;
   const size_t nseg = static_cast<size_t>((nsteps + every - 1) / every);
   const size_t seg = static_cast<size_t>(nsteps < every ? nsteps : every);
-  lbm3_status st = grow(c, &c->ckpt, &c->ckpt_slots, nseg, "checkpoints");
-  if (st == LBM3_OK) st = grow(c, &c->tape, &c->tape_slots, seg - 1, "the segment tape");
+  lbm3_status st = grow(c, &c->ckpt, &c->ckpt_slots, &c->ckpt_maps, nseg, "checkpoints");
+  if (st == LBM3_OK) st = grow(c, &c->tape, &c->tape_slots, &c->tape_maps, seg - 1, "the segment tape");
   if (st == LBM3_OK) st = ensure_adjoint(c);
   if (st != LBM3_OK) return st;
-  for (int64_t t = 0; t < nsteps; ++t) {
-    if (t % every == 0)
-      LBM3_CUDA(c, cudaMemcpyAsync(slot(c->ckpt, c, static_cast<size_t>(t / every)), c->buf[c->cur], c->buf_bytes,
-                                   cudaMemcpyDeviceToDevice, c->stream));
-    st = step_into(c, c->buf[c->cur], c->buf[c->cur ^ 1]);
+  c->tape_every = every;
+  c->tape_steps = nsteps;
+  // S_0 into its checkpoint; each later checkpoint is written by the step
+  // that produces it, other states ping-pong through the context's buffers
+  LBM3_CUDA(c, cudaMemcpyAsync(slot(c->ckpt, c, 0), c->buf[c->cur], c->buf_bytes, cudaMemcpyDeviceToDevice,
+                               c->stream));
+  TapeState cur = tape_state(c, 0);
+  for (int64_t t = 1; t <= nsteps; ++t) {
+    const bool keep = (t % every == 0) && t < nsteps;
+    float* out = keep ? const_cast<float*>(tape_state(c, t).p) : (cur.p == c->buf[0] ? c->buf[1] : c->buf[0]);
+    st = step_into(c, cur.p, cur.map, out);
     if (st != LBM3_OK) return st;
-    c->cur ^= 1;
+    if (keep) {
+      cur = tape_state(c, t);
+    } else {
+      const int b = out == c->buf[0] ? 0 : 1;
+      cur = {c->buf[b], c->tmap[b]};
+    }
     c->t += 1;
   }
-  c->tape_steps = nsteps;
-  c->tape_every = every;
+  c->cur = cur.p == c->buf[0] ? 0 : 1;  // S_nsteps is in a context buffer
   c->tape_valid = true;
   return LBM3_OK;
 }
@@ -786,41 +831,45 @@ lbm3_status lbm3_tape_backward(lbm3_ctx* c, const double* dphi, int dphi_on_devi
   const int nblk = lbm3::adj_blocks(N);
   LBM3_CUDA(c, cudaMemsetAsync(c->acc, 0, static_cast<size_t>(nblk) * 6 * sizeof(double), c->stream));
   const double* dphi_d = dphi;
-  if (!dphi_on_device) {  // staged in the second cotangent buffer, free until the first adjoint step
-    double* stage = reinterpret_cast<double*>(b.lam[1]);
+  if (!dphi_on_device) {  // staged in the second lam9 buffer, free until the first adjoint step
+    double* stage = reinterpret_cast<double*>(b.lam9[1]);
     LBM3_CUDA(c, cudaMemcpyAsync(stage, dphi, 3 * static_cast<size_t>(N) * sizeof(double), cudaMemcpyHostToDevice,
                                  c->stream));
     dphi_d = stage;
   }
   LBM3_CUDA(c, lbm3::launch_adj_seed(c->buf[c->cur], dphi_d, b, 0, nx, ny, c->stream));
-  int cur = 0;
   const int64_t T = c->tape_steps, K = c->tape_every;
-  const int64_t nseg = (T + K - 1) / K;
   int grid = 0;
   const StepArgs a = args_for(c, nullptr, nullptr, &grid);
-  for (int64_t s = nseg - 1; s >= 0; --s) {
-    const int64_t len = (T - s * K) < K ? (T - s * K) : K;
-    float* base = slot(c->ckpt, c, static_cast<size_t>(s));
-    auto state = [&](int64_t j) { return j == 0 ? base : slot(c->tape, c, static_cast<size_t>(j - 1)); };
-    for (int64_t j = 1; j < len; ++j) {
-      lbm3_status st = step_into(c, state(j - 1), state(j));
-      if (st != LBM3_OK) return st;
+  int64_t seg = (T - 1) / K;  // segment whose states are in the tape
+  lbm3_status st = recompute_segment(c, seg);
+  if (st != LBM3_OK) return st;
+  LBM3_CUDA(c, lbm3::launch_adj_fields(tape_state(c, T - 1).p, a, b, 0, c->stream));
+  int slotf = 0, lam = 0;
+  for (int64_t t = T; t >= 1; --t) {
+    const float* prev = tape_state(c, t - 1).p;
+    const float* next = nullptr;
+    if (t >= 2) {
+      if ((t - 2) / K != seg) {  // S_{t-1} is a checkpoint: the tape is free to refill
+        seg = (t - 2) / K;
+        st = recompute_segment(c, seg);
+        if (st != LBM3_OK) return st;
+      }
+      next = tape_state(c, t - 2).p;
     }
-    for (int64_t j = len - 1; j >= 0; --j) {
-      LBM3_CUDA(c, lbm3::launch_adj_step(state(j), a, b, cur, c->acc, c->stream));
-      cur ^= 1;
-    }
+    LBM3_CUDA(c, lbm3::launch_adj_step(prev, next, a, b, slotf, lam, c->acc, c->stream));
+    slotf ^= 1;
+    lam ^= 1;
   }
-  const float* lam0 = b.lam[cur];
   double* staging = reinterpret_cast<double*>(c->buf[c->cur ^ 1]);
   if (dpop0) {
     if (out_on_device) {
-      LBM3_CUDA(c, lbm3::launch_adj_dpop(lam0, dpop0, nx, ny, 0, 27, c->stream));
+      LBM3_CUDA(c, lbm3::launch_adj_dpop(b, lam, dpop0, nx, ny, 0, 27, c->stream));
     } else {
       const int chunk = staging_planes(c);
       for (int p0 = 0; p0 < 27; p0 += chunk) {
         const int np = p0 + chunk <= 27 ? chunk : 27 - p0;
-        LBM3_CUDA(c, lbm3::launch_adj_dpop(lam0, staging, nx, ny, p0, np, c->stream));
+        LBM3_CUDA(c, lbm3::launch_adj_dpop(b, lam, staging, nx, ny, p0, np, c->stream));
         LBM3_CUDA(c, cudaMemcpyAsync(dpop0 + static_cast<size_t>(p0) * N, staging,
                                      static_cast<size_t>(np) * N * sizeof(double), cudaMemcpyDeviceToHost,
                                      c->stream));
@@ -830,14 +879,14 @@ lbm3_status lbm3_tape_backward(lbm3_ctx* c, const double* dphi, int dphi_on_devi
   }
   if (drho0) {
     double* dst = out_on_device ? drho0 : staging;
-    LBM3_CUDA(c, lbm3::launch_adj_drho(lam0, dst, nx, ny, c->stream));
+    LBM3_CUDA(c, lbm3::launch_adj_drho(b, lam, dst, nx, ny, c->stream));
     if (!out_on_device)
       LBM3_CUDA(c, cudaMemcpyAsync(drho0, dst, 3 * static_cast<size_t>(N) * sizeof(double), cudaMemcpyDeviceToHost,
                                    c->stream));
   }
   std::vector<double> rows(static_cast<size_t>(nblk) * 6);
   LBM3_CUDA(c, cudaMemcpyAsync(rows.data(), c->acc, rows.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  lbm3_status st = check_device_errors(c);
+  st = check_device_errors(c);
   if (st != LBM3_OK) return st;
   double tot[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int r = 0; r < nblk; ++r)
