@@ -68,9 +68,17 @@ typedef enum {
   LBM3_RECOLOR_LITERAL = 1 /* Eq. 6 with n_kl.e_i exactly as printed */
 } lbm3_recolor_form;
 
+typedef enum {
+  LBM3_FORCE_BODY = 0,         /* the paper's: the force of Eq. 11 through Guo's forcing term (Eq. 5) */
+  LBM3_FORCE_PERTURBATION = 1  /* Leclaire et al.'s perturbation operator, Eqs. phi1 / phi_old, with
+                                  A_kl = A_lk = 9 sigma_kl / (2 tau_f) and B_0 = -4/27, B_1-4 = 2/27,
+                                  B_5-8 = 5/108; u = sum_i f_i e_i / rho.  FP32 storage only. */
+} lbm3_force_form;
+
 /* Problem statement (Sec. 2).  Validation in lbm3_create:
  * nx >= 4 and a multiple of 4, ny >= 1, nx*ny < 2^31; tau[k] > 0.5;
- * rho0[k] > 0; sigma_kl > 0; 0 < beta0 <= 1; forms and storage in range. */
+ * rho0[k] > 0; sigma_kl > 0; 0 < beta0 <= 1; forms and storage in range;
+ * force_form 1 with FP32 storage only. */
 typedef struct {
   int32_t nx, ny;
   double tau[3];      /* per-fluid relaxation time; nu_k = (tau_k - 1/2)/3 (Eq. tau) */
@@ -80,7 +88,7 @@ typedef struct {
   int32_t beta_form;  /* lbm3_beta_form */
   int32_t recolor_form; /* lbm3_recolor_form */
   int32_t storage;    /* lbm3_storage */
-  int32_t reserved;   /* must be 0 */
+  int32_t force_form; /* lbm3_force_form (0 for the paper's model) */
 } lbm3_params;
 
 /* Bytes of ONE population buffer for these parameters, with the row pitch
@@ -129,7 +137,8 @@ lbm3_status lbm3_set_rows_per_cta(lbm3_ctx* ctx, int32_t rows);
 lbm3_status lbm3_step(lbm3_ctx* ctx, int64_t n);
 
 /* Macroscopic fields at the current time t: rho[3][ny][nx] = rho_k
- * (after Eq. 30), ux/uy[ny][nx] from Eq. uk1 (including the F_s/2 term),
+ * (after Eq. 30), ux/uy[ny][nx] from Eq. uk1 (including the F_s/2 term;
+ * sum_i f_i e_i / rho with the perturbation-operator force form),
  * p[ny][nx] = rho c_s^2 = rho/3 (the paper gives no pressure formula).
  * Any output pointer may be NULL.  Synchronises the stream when on_device is
  * 0.  Returns LBM3_ETIMEOUT if an earlier kernel reported a timed-out wait. */
@@ -170,7 +179,8 @@ lbm3_status lbm3_phi(lbm3_ctx* ctx, double* phi, int on_device);
  * recomputes one segment at a time.  State memory: lbm3_buffer_bytes() each,
  * so checkpoint_every near sqrt(nsteps) minimises it and checkpoint_every = 1
  * stores every state and recomputes nothing.  FP32 storage only
- * (LBM3_EINVAL), LBM3_ENOMEM if the states do not fit.
+ * and the paper's force form (LBM3_EINVAL otherwise), LBM3_ENOMEM if the
+ * states do not fit.
  *
  * lbm3_tape_backward takes dJ/dphi[3][ny][nx] (FP64, host or device) at the
  * end of the recorded run and writes, for any non-NULL output:

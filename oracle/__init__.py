@@ -38,6 +38,7 @@ class _Params(ctypes.Structure):
         ("beta0", ctypes.c_double),
         ("beta_form", ctypes.c_int),
         ("recolor_form", ctypes.c_int),
+        ("force_form", ctypes.c_int),
     ]
 
 
@@ -53,6 +54,7 @@ class Params:
     beta0: float = 0.7
     beta_form: int = 0
     recolor_form: int = 0
+    force_form: int = 0  # 0: Eq. 11 force via Eq. 5; 1: perturbation operator (Eqs. phi1, phi_old)
     extra: dict = field(default_factory=dict)
 
     def _c(self) -> _Params:
@@ -65,6 +67,7 @@ class Params:
         p.beta0 = float(self.beta0)
         p.beta_form = int(self.beta_form)
         p.recolor_form = int(self.recolor_form)
+        p.force_form = int(self.force_form)
         return p
 
 
@@ -92,6 +95,7 @@ def _load():
         lib.orc_X.argtypes = [dp, dp]
         lib.orc_feq.argtypes = [ctypes.c_double] * 3 + [dp]
         lib.orc_guo.argtypes = [ctypes.c_double] * 5 + [dp]
+        lib.orc_perturbation.argtypes = [dp, dp, dp, ctypes.c_double, dp]
         lib.orc_grad.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
         lib.orc_colour_gradients.argtypes = [pp, dp, dp, dp]
         lib.orc_force.argtypes = [pp, dp, dp, dp, dp]
@@ -139,6 +143,15 @@ def guo(tau: float, ux: float, uy: float, Fx: float, Fy: float) -> np.ndarray:
     """Eq. 5 for one node."""
     out = np.zeros(9)
     _load().orc_guo(tau, ux, uy, Fx, Fy, _ptr(out))
+    return out
+
+
+
+def perturbation(sigma, G, C, tauf: float) -> np.ndarray:
+    """Eqs. phi1 / phi_old for one node.  G: (3, 3, 2) colour gradients
+    G_kl (G_lk = -G_kl), C: (3, 3) concentration factors."""
+    out = np.zeros(9)
+    _load().orc_perturbation(_ptr(_f64(sigma)), _ptr(_f64(G)), _ptr(_f64(C)), float(tauf), _ptr(out))
     return out
 
 

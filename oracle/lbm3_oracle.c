@@ -39,6 +39,9 @@
  *    of the tensor inside the divergence.
  *  - the local tau_f of Eqs. vis_1/tau is used in both the BGK and the Guo
  *    prefactor; u of Eq. uk1 is used in both f^eq and Phi_i.
+ *  - the perturbation operator (force_form 1, Eqs. phi1 / phi_old) replaces
+ *    the force and Guo's term: u = sum_i f_i e_i / rho (no body force), and
+ *    A_kl = A_lk = 9 sigma_kl / (2 tau_f) with the local tau_f.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -64,6 +67,8 @@ typedef struct {
   double beta0;      /* reference segregation parameter beta^0 */
   int beta_form;     /* 0 = Eqs. 19-20 (the paper's); 1 = Eq. fu; 2 = Eq. 16; 3 = Eq. 17 */
   int recolor_form;  /* 0 = n.e_i/|e_i| (cosine form); 1 = n.e_i as printed in Eq. 6 */
+  int force_form;    /* 0 = force of Eq. 11 through Guo's scheme (Eq. 5), the paper's;
+                        1 = perturbation operator of Eqs. phi1 / phi_old (Leclaire et al.) */
 } orc_params;
 
 /* ---------------------------------------------------------------- helpers */
@@ -124,6 +129,34 @@ void orc_guo(double tau, double ux, double uy, double Fx, double Fy, double* phi
     double cy = (EY[i] - uy) / CS2 + eu / (CS2 * CS2) * EY[i];
     phi[i] = WT[i] * (1.0 - 1.0 / (2.0 * tau)) * (cx * Fx + cy * Fy);
   }
+}
+
+/* B_i of Eq. phi_old as Leclaire et al. take them (Sec. 2): B_0 = -4/27,
+ * B_1-4 = 2/27, B_5-8 = 5/108. */
+static const double BPERT[9] = {-4.0 / 27.0, 2.0 / 27.0,  2.0 / 27.0,  2.0 / 27.0, 2.0 / 27.0,
+                                5.0 / 108.0, 5.0 / 108.0, 5.0 / 108.0, 5.0 / 108.0};
+
+/* Eqs. phi1 / phi_old at one node: Phi_i = sum_k sum_{l != k} (A_kl C_kl / 2)
+ * |G_kl| [w_i (e_i . G_kl)^2 / |G_kl|^2 - B_i], with A_kl = A_lk read from
+ * sigma_kl = (A_kl + A_lk) tau_f / 9, i.e. A_kl = 9 sigma_kl / (2 tau_f).
+ * G: the node's colour gradients [3][3][2] (k, l, component; G_lk = -G_kl),
+ * C: [3][3]; sig = (s12, s13, s23).  Terms with |G_kl| <= 1e-15 are 0. */
+void orc_perturbation(const double* sig, const double* G, const double* C, double tauf, double* phi) {
+  for (int i = 0; i < 9; ++i) phi[i] = 0.0;
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) {
+      if (l == k) continue;
+      int a = k < l ? k : l, b = k < l ? l : k;
+      double s = (a == 0 && b == 1) ? sig[0] : (a == 0 ? sig[1] : sig[2]);
+      double A = 9.0 * s / (2.0 * tauf);
+      double gx = G[(k * 3 + l) * 2 + 0], gy = G[(k * 3 + l) * 2 + 1];
+      double mag = sqrt(gx * gx + gy * gy);
+      if (mag <= GEPS) continue;
+      for (int i = 0; i < 9; ++i) {
+        double eg = EX[i] * gx + EY[i] * gy;
+        phi[i] += A * C[k * 3 + l] / 2.0 * mag * (WT[i] * eg * eg / (mag * mag) - BPERT[i]);
+      }
+    }
 }
 
 /* Eq. fd1: d_alpha v(x) = (1/cs2) sum_i w_i v(x + e_i) e_i,alpha on a periodic grid. */
@@ -270,7 +303,12 @@ void orc_fields(const orc_params* p, const double* f, double* rho, double* ux, d
   for (int k = 0; k < 3; ++k)
     for (int i = 0; i < 9; ++i)
       for (int n = 0; n < N; ++n) rk[k * N + n] += f[(k * 9 + i) * N + n];
-  orc_force(p, rk, Fx, Fy, NULL);
+  if (p->force_form == 1) {
+    memset(Fx, 0, sizeof(double) * (size_t)N);
+    memset(Fy, 0, sizeof(double) * (size_t)N);
+  } else {
+    orc_force(p, rk, Fx, Fy, NULL);
+  }
   for (int n = 0; n < N; ++n) {
     double r = rk[n] + rk[N + n] + rk[2 * N + n];
     double mx = 0.0, my = 0.0;
@@ -305,8 +343,14 @@ static void orc_step_once(const orc_params* p, double* f, double* fn) {
   for (int k = 0; k < 3; ++k)
     for (int i = 0; i < 9; ++i)
       for (int n = 0; n < N; ++n) rk[k * N + n] += f[(k * 9 + i) * N + n];
-  /* interfacial force (Eq. 11) and colour gradients */
-  orc_force(p, rk, Fx, Fy, NULL);
+  /* interfacial force (Eq. 11; none with the perturbation operator) and
+   * colour gradients */
+  if (p->force_form == 1) {
+    memset(Fx, 0, sizeof(double) * (size_t)N);
+    memset(Fy, 0, sizeof(double) * (size_t)N);
+  } else {
+    orc_force(p, rk, Fx, Fy, NULL);
+  }
   orc_colour_gradients(p, rk, G, C);
 
   for (int y = 0; y < ny; ++y)
@@ -329,10 +373,17 @@ static void orc_step_once(const orc_params* p, double* f, double* fn) {
       for (int k = 0; k < 3; ++k) s += rloc[k] / nu[k];
       double nuloc = r / s;
       double tauf = nuloc / CS2 + 0.5;
-      /* Eqs. 1-3, 5 */
+      /* Eqs. 1-3, with Phi_i of Eq. 5 or of Eqs. phi1 / phi_old */
       double feq[9], phi[9], fdag[9];
       orc_feq(r, ux, uy, feq);
-      orc_guo(tauf, ux, uy, Fx[n], Fy[n], phi);
+      if (p->force_form == 1) {
+        double Gn[18], Cn[9];
+        for (int j = 0; j < 18; ++j) Gn[j] = G[(size_t)j * N + n];
+        for (int j = 0; j < 9; ++j) Cn[j] = C[(size_t)j * N + n];
+        orc_perturbation(p->sigma, Gn, Cn, tauf, phi);
+      } else {
+        orc_guo(tauf, ux, uy, Fx[n], Fy[n], phi);
+      }
       for (int i = 0; i < 9; ++i) fdag[i] = fi[i] - (fi[i] - feq[i]) / tauf + phi[i];
       /* recolouring, Eq. 6 */
       double beta[3];

@@ -131,8 +131,12 @@ lbm3_status validate(const lbm3_params* p, std::string* why) {
     return LBM3_EINVAL;
   }
   if (p->beta_form < 0 || p->beta_form > 3 || p->recolor_form < 0 || p->recolor_form > 1 ||
-      p->storage < LBM3_FP32 || p->storage > LBM3_BF16_DEV || p->reserved != 0) {
-    *why = "lbm3: beta_form, recolor_form, storage or reserved out of range";
+      p->storage < LBM3_FP32 || p->storage > LBM3_BF16_DEV || p->force_form < 0 || p->force_form > 1) {
+    *why = "lbm3: beta_form, recolor_form, storage or force_form out of range";
+    return LBM3_EINVAL;
+  }
+  if (p->force_form == LBM3_FORCE_PERTURBATION && p->storage != LBM3_FP32) {
+    *why = "lbm3: the perturbation-operator force form needs FP32 storage";
     return LBM3_EINVAL;
   }
   return LBM3_OK;
@@ -433,7 +437,7 @@ lbm3_status ensure_adjoint(lbm3_ctx* c) {
 lbm3_status step_into(lbm3_ctx* c, const float* in, const void* map, float* out) {
   int grid = 0;
   StepArgs a = args_for(c, in, out, &grid);
-  LBM3_CUDA(c, lbm3::launch_step(a, map, grid, lbm3::MODE_STEP, c->p.storage, c->stream));
+  LBM3_CUDA(c, lbm3::launch_step(a, map, grid, lbm3::MODE_STEP, c->p.storage, c->p.force_form, c->stream));
   return LBM3_OK;
 }
 
@@ -633,7 +637,7 @@ lbm3_status lbm3_step(lbm3_ctx* c, int64_t n) {
   for (int64_t s = 0; s < n; ++s) {
     int grid = 0;
     StepArgs a = args_for(c, c->buf[c->cur], c->buf[c->cur ^ 1], &grid);
-    LBM3_CUDA(c, lbm3::launch_step(a, c->tmap[c->cur], grid, lbm3::MODE_STEP, c->p.storage, c->stream));
+    LBM3_CUDA(c, lbm3::launch_step(a, c->tmap[c->cur], grid, lbm3::MODE_STEP, c->p.storage, c->p.force_form, c->stream));
     c->cur ^= 1;
     c->t += 1;
   }
@@ -659,7 +663,7 @@ lbm3_status lbm3_fields(lbm3_ctx* c, double* rho, double* ux, double* uy, double
     a.out_uy = uy ? staging + 4 * N : nullptr;
     a.out_p = pr ? staging + 5 * N : nullptr;
   }
-  LBM3_CUDA(c, lbm3::launch_step(a, c->tmap[c->cur], grid, lbm3::MODE_FIELDS, c->p.storage, c->stream));
+  LBM3_CUDA(c, lbm3::launch_step(a, c->tmap[c->cur], grid, lbm3::MODE_FIELDS, c->p.storage, c->p.force_form, c->stream));
   if (!on_device) {
     if (rho) LBM3_CUDA(c, cudaMemcpyAsync(rho, staging, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (ux) LBM3_CUDA(c, cudaMemcpyAsync(ux, staging + 3 * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -785,7 +789,8 @@ lbm3_status lbm3_tape_forward(lbm3_ctx* c, int64_t nsteps, int32_t every) {
     return fail(c, LBM3_EINVAL, "lbm3_tape_forward: nsteps = %lld and checkpoint_every = %d must be >= 1",
                 static_cast<long long>(nsteps), every);
   if (!c->state_set) return fail(c, LBM3_ESTATE, "lbm3_tape_forward: state not initialised");
-  if (c->p.storage != LBM3_FP32) return fail(c, LBM3_EINVAL, "lbm3_tape_forward: reverse mode needs FP32 storage");
+  if (c->p.storage != LBM3_FP32 || c->p.force_form != LBM3_FORCE_BODY)
+    return fail(c, LBM3_EINVAL, "lbm3_tape_forward: reverse mode needs FP32 storage and the body force form");
   DeviceGuard g(c->device);
   c->tape_valid = false;
   const size_t nseg = static_cast<size_t>((nsteps + every - 1) / every);
@@ -1008,8 +1013,8 @@ lbm3_status lbm3_batch_create(const lbm3_params* params, int32_t count, void* cu
       return st;
     }
     b->ctx.push_back(c);
-    if (c->p.storage != LBM3_FP32) {
-      std::fprintf(stderr, "lbm3_batch_create: instance %d: batches use FP32 storage\n", i);
+    if (c->p.storage != LBM3_FP32 || c->p.force_form != LBM3_FORCE_BODY) {
+      std::fprintf(stderr, "lbm3_batch_create: instance %d: batches use FP32 storage and the body force\n", i);
       destroy_batch(b);
       return LBM3_EINVAL;
     }

@@ -148,7 +148,10 @@ cudaError_t step_configure();  // sets the dynamic shared memory attribute
 // uses the first, a (P, ny, 27) FP32 tensor with box (kPW, 1, 9); 16-bit
 // storage uses both, the (P, ny, 27) deviation tensor with box
 // (kDevBoxCols, 1, 9) and the (P, ny, 3) FP32 rho' tensor with box (kPW, 1, 3).
-cudaError_t launch_step(const StepArgs& a, const void* tmaps, int grid, int mode, int storage, cudaStream_t s);
+// force: 0 = the force of Eq. 11 through Guo's term (Eq. 5); 1 = the
+// perturbation operator of Eqs. phi1 / phi_old (FP32 storage only)
+cudaError_t launch_step(const StepArgs& a, const void* tmaps, int grid, int mode, int storage, int force,
+                        cudaStream_t s);
 // encode those maps for one population buffer (uses the driver's encoder)
 cudaError_t encode_population_maps(void* tmaps, const void* buf, int nx, int ny, int storage);
 // bytes of one population buffer

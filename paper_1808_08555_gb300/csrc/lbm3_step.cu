@@ -274,6 +274,11 @@ __device__ __forceinline__ void stage_density(Smem& s, int q, int c, const RingC
 }
 
 // T stage, one node: row q, T-window column c in [0, w+2), x = x0 - 1 + c.
+// FORCE 0 stores the tension tensor T of Eq. 11; FORCE 1 (the perturbation
+// operator of Eqs. phi1 / phi_old) stores S = sum_kl (9/2) sigma_kl C_kl |G_kl|
+// n_kl n_kl in the same three slots, from which Phi_i = (w_i e_i.S.e_i -
+// B_i tr S) / tau_f at the node itself.
+template <int FORCE>
 __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q, int c, int w) {
   const float(*pm)[kDW] = s.phi[(q - 1) % 6];
   const float(*pz)[kDW] = s.phi[q % 6];
@@ -309,11 +314,19 @@ __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q,
       const float rinv = rsqrtf(g2);
       mag = g2 * rinv;
       const float ck = fminf(a.cpair[p] * pp * rho2, 1.0f);  // Eq. 15 with rho_k = phi_k rho
-      // sigma C |G| (I - n n) = sigma C (|G|^2 I - G G) / |G|
-      const float sc = a.sigma[p] * ck * rinv;
-      txx = fmaf(sc * Gy, Gy, txx);
-      txy = fmaf(-sc * Gx, Gy, txy);
-      tyy = fmaf(sc * Gx, Gx, tyy);
+      if (FORCE == 0) {
+        // sigma C |G| (I - n n) = sigma C (|G|^2 I - G G) / |G|
+        const float sc = a.sigma[p] * ck * rinv;
+        txx = fmaf(sc * Gy, Gy, txx);
+        txy = fmaf(-sc * Gx, Gy, txy);
+        tyy = fmaf(sc * Gx, Gx, tyy);
+      } else {
+        // (9/2) sigma C |G| n n = (9/2) sigma C G G / |G|
+        const float sc = 4.5f * a.sigma[p] * ck * rinv;
+        txx = fmaf(sc * Gx, Gx, txx);
+        txy = fmaf(sc * Gx, Gy, txy);
+        tyy = fmaf(sc * Gy, Gy, tyy);
+      }
     }
     // recolouring normal G / max(|G|, kNormalDelta phi_k phi_l): the unit
     // normal wherever a k-l interface exists, continuous to 0 where G -> 0,
@@ -335,7 +348,7 @@ __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q,
 }
 
 // C stage, one node: row q (output row y0 - 2 + q), column c in [0, w).
-template <int MODE, int ST>
+template <int MODE, int ST, int FORCE>
 __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q, int c, int x0, int y0,
                                               const RingCols& rc) {
   const float* pp = s.pop[q % kSlots];
@@ -355,10 +368,15 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
     const int wc = c + 4 - ex(i);
     fi[i] = (popv<ST>(pp, 0, i, wc, rc) + popv<ST>(pp, 1, i, wc, rc)) + popv<ST>(pp, 2, i, wc, rc);
   }
-  // F_s = div T (Eq. 11), T window column of this node is c + 1
+  // F_s = div T (Eq. 11), T window column of this node is c + 1; none with
+  // the perturbation operator, whose S is read at the node instead
   const int tc = c + 1;
-  float Fx, Fy;
-  {
+  float Fx = 0.0f, Fy = 0.0f, Sxx = 0.0f, Sxy = 0.0f, Syy = 0.0f;
+  if (FORCE == 1) {
+    Sxx = Tz[0][tc];
+    Sxy = Tz[1][tc];
+    Syy = Tz[2][tc];
+  } else {
     const float xxW = Tz[0][tc - 1], xxE = Tz[0][tc + 1];
     const float xxSW = Tm[0][tc - 1], xxSE = Tm[0][tc + 1], xxNW = Tp[0][tc - 1], xxNE = Tp[0][tc + 1];
     const float xyW = Tz[1][tc - 1], xyE = Tz[1][tc + 1], xyS = Tm[1][tc], xyN = Tp[1][tc];
@@ -408,19 +426,32 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
   const float gm3uF = -3.0f * g * uF;
   const float omr = om * rho;
   float fd[9];
-  fd[0] = fi[0] + fmaf(om, fmaf(wt(0), rho, -fi[0]), wt(0) * (c0 + gm3uF));
+  // perturbation operator (FORCE 1): Phi_i = om (w_i e_i.S.e_i - B_i tr S),
+  // even in e_i, with Leclaire's B_1-4 = 2/27, B_5-8 = 5/108; Phi_0 is the
+  // negated sum of the others (-om B_0 tr S in exact arithmetic, as
+  // sum_i B_i = 1/3), so the operator moves no mass in FP32 either
+  const float trS = Sxx + Syy;
+  float phisum = 0.0f;
 #pragma unroll
   for (int i = 1; i <= 6; ++i) {
     if (i == 3 || i == 4) continue;  // pairs (1,3), (2,4), (5,7), (6,8)
     const int o = (i == 1) ? 3 : (i == 2) ? 4 : (i == 5) ? 7 : 8;
     const float eu = ex(i) * ux + ey(i) * uy;
     const float eF = ex(i) * Fx + ey(i) * Fy;
-    const float S = wt(i) * (fmaf(c1 * eu, eu, c0) + fmaf(g9 * eu, eF, gm3uF));
+    float S = wt(i) * (fmaf(c1 * eu, eu, c0) + fmaf(g9 * eu, eF, gm3uF));
+    if (FORCE == 1) {
+      const float eSe = (ex(i) * ex(i)) * Sxx + (2.0f * ex(i) * ey(i)) * Sxy + (ey(i) * ey(i)) * Syy;
+      const float Bi = i <= 4 ? 2.0f / 27.0f : 5.0f / 108.0f;
+      const float ph = om * fmaf(wt(i), eSe, -Bi * trS);
+      S += ph;
+      phisum += 2.0f * ph;
+    }
     const float A = 3.0f * wt(i) * fmaf(omr, eu, g * eF);
     const float wr = wt(i) * rho;
     fd[i] = fi[i] + fmaf(om, wr - fi[i], S + A);
     fd[o] = fi[o] + fmaf(om, wr - fi[o], S - A);
   }
+  fd[0] = fi[0] + fmaf(om, fmaf(wt(0), rho, -fi[0]), wt(0) * (c0 + gm3uF) - phisum);
   // segregation parameters beta_kl (pairs 12, 13, 23); prod = rho_1 rho_2 rho_3 / rho^3
   const float cb = fminf(a.beta_A * (phi0 * phi1 * phi2), 1.0f);
   const float(*nn)[kTX] = s.nrm[q % 3];
@@ -508,7 +539,7 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
   }
 }
 
-template <int MODE, int ST>
+template <int MODE, int ST, int FORCE>
 __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h, int tid) {
   const int nq = h + 4;  // rows q = 0 .. h+3 <-> y = y0-2 .. y0+h+1
   const RingCols rc = ring_cols(a, x0);
@@ -548,7 +579,7 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
           const int it = tid + u * kConsumers;
           if (it < nr * W) {
             const int r = it >= W ? 1 : 0;
-            stage_tension(s, a, qa + r, it - r * W, w);
+            stage_tension<FORCE>(s, a, qa + r, it - r * W, w);
           }
         }
       }
@@ -561,7 +592,7 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
       if (nr > 0) {
         for (int it = tid; it < nr * w; it += kConsumers) {
           const int r = it >= w ? 1 : 0;
-          stage_collide<MODE, ST>(s, a, qa + r, it - r * w, x0, y0, rc);
+          stage_collide<MODE, ST, FORCE>(s, a, qa + r, it - r * w, x0, y0, rc);
         }
       }
     }
@@ -576,7 +607,7 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
 
 // One tile (strip of w columns starting at x0, rows y0 .. y0+h-1): barrier
 // set-up, then the producer warp and the consumer warps.
-template <int MODE, int ST>
+template <int MODE, int ST, int FORCE>
 __device__ __forceinline__ void run_tile(Smem& s, const StepArgs& a, const CUtensorMap* map, const CUtensorMap* map1,
                                          int x0, int w, int y0, int h) {
   const int nq = h + 4;
@@ -593,7 +624,7 @@ __device__ __forceinline__ void run_tile(Smem& s, const StepArgs& a, const CUten
   if (tid >= kConsumers) {
     produce<ST>(s, a, map, map1, x0, y0, nq, tid - kConsumers);
   } else {
-    consume<MODE, ST>(s, a, x0, w, y0, h, tid);
+    consume<MODE, ST, FORCE>(s, a, x0, w, y0, h, tid);
   }
 }
 
@@ -608,7 +639,7 @@ __device__ __forceinline__ Smem& aligned_smem() {
 // Full-width strips with a narrower last one measured 4.6 % faster on a
 // 2048^2 grid than equal-width strips (all CTAs of one wave stay busy with
 // 248-node C stages instead of 240).
-template <int MODE, int ST>
+template <int MODE, int ST, int FORCE>
 __global__ void __launch_bounds__(kThreads, 2)
     fused_step_kernel(StepArgs a, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap1) {
   Smem& s = aligned_smem();
@@ -619,7 +650,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int y0 = chunk * a.rows_per_cta;
   const int h = min(a.rows_per_cta, a.ny - y0);
   if (w <= 0 || h <= 0) return;
-  run_tile<MODE, ST>(s, a, &tmap, &tmap1, x0, w, y0, h);
+  run_tile<MODE, ST, FORCE>(s, a, &tmap, &tmap1, x0, w, y0, h);
 }
 
 // Batch of independent grids: CTA b runs work item b (instance, tile); the
@@ -641,7 +672,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
                  : "memory");
   __syncthreads();
-  run_tile<MODE_STEP, ST_FP32>(s, s.args, map, map, it.x0, it.w, it.y0, it.h);
+  run_tile<MODE_STEP, ST_FP32, 0>(s, s.args, map, map, it.x0, it.w, it.y0, it.h);
 }
 
 }  // namespace
@@ -650,7 +681,7 @@ size_t step_smem_bytes() { return sizeof(Smem) + 128; }
 
 template <int MODE, int ST>
 cudaError_t configure_one(int bytes) {
-  return cudaFuncSetAttribute(fused_step_kernel<MODE, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return cudaFuncSetAttribute(fused_step_kernel<MODE, ST, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 cudaError_t step_configure() {
@@ -661,6 +692,12 @@ cudaError_t step_configure() {
   if (e == cudaSuccess) e = configure_one<MODE_FIELDS, ST_FP16>(bytes);
   if (e == cudaSuccess) e = configure_one<MODE_STEP, ST_BF16>(bytes);
   if (e == cudaSuccess) e = configure_one<MODE_FIELDS, ST_BF16>(bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fused_step_kernel<MODE_STEP, ST_FP32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fused_step_kernel<MODE_FIELDS, ST_FP32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(fused_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return e;
@@ -674,29 +711,36 @@ cudaError_t launch_batch(const BatchItem* items, int nitems, const BatchDesc* de
 
 int step_occupancy(int* blocks_per_sm) {
   return static_cast<int>(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      blocks_per_sm, fused_step_kernel<MODE_STEP, ST_FP32>, kThreads, step_smem_bytes()));
+      blocks_per_sm, fused_step_kernel<MODE_STEP, ST_FP32, 0>, kThreads, step_smem_bytes()));
 }
 
-cudaError_t launch_step(const StepArgs& a, const void* tmaps, int grid, int mode, int storage, cudaStream_t st) {
+cudaError_t launch_step(const StepArgs& a, const void* tmaps, int grid, int mode, int storage, int force,
+                        cudaStream_t st) {
   CUtensorMap m0, m1;
   memcpy(&m0, tmaps, sizeof m0);
   memcpy(&m1, static_cast<const unsigned char*>(tmaps) + 128, sizeof m1);
   const size_t sm = step_smem_bytes();
-  if (storage == ST_FP32) {
+  if (force == 1) {  // perturbation operator: FP32 storage only
+    if (storage != ST_FP32) return cudaErrorInvalidValue;
     if (mode == MODE_STEP)
-      fused_step_kernel<MODE_STEP, ST_FP32><<<grid, kThreads, sm, st>>>(a, m0, m1);
+      fused_step_kernel<MODE_STEP, ST_FP32, 1><<<grid, kThreads, sm, st>>>(a, m0, m1);
     else
-      fused_step_kernel<MODE_FIELDS, ST_FP32><<<grid, kThreads, sm, st>>>(a, m0, m1);
+      fused_step_kernel<MODE_FIELDS, ST_FP32, 1><<<grid, kThreads, sm, st>>>(a, m0, m1);
+  } else if (storage == ST_FP32) {
+    if (mode == MODE_STEP)
+      fused_step_kernel<MODE_STEP, ST_FP32, 0><<<grid, kThreads, sm, st>>>(a, m0, m1);
+    else
+      fused_step_kernel<MODE_FIELDS, ST_FP32, 0><<<grid, kThreads, sm, st>>>(a, m0, m1);
   } else if (storage == ST_FP16) {
     if (mode == MODE_STEP)
-      fused_step_kernel<MODE_STEP, ST_FP16><<<grid, kThreads, sm, st>>>(a, m0, m1);
+      fused_step_kernel<MODE_STEP, ST_FP16, 0><<<grid, kThreads, sm, st>>>(a, m0, m1);
     else
-      fused_step_kernel<MODE_FIELDS, ST_FP16><<<grid, kThreads, sm, st>>>(a, m0, m1);
+      fused_step_kernel<MODE_FIELDS, ST_FP16, 0><<<grid, kThreads, sm, st>>>(a, m0, m1);
   } else {
     if (mode == MODE_STEP)
-      fused_step_kernel<MODE_STEP, ST_BF16><<<grid, kThreads, sm, st>>>(a, m0, m1);
+      fused_step_kernel<MODE_STEP, ST_BF16, 0><<<grid, kThreads, sm, st>>>(a, m0, m1);
     else
-      fused_step_kernel<MODE_FIELDS, ST_BF16><<<grid, kThreads, sm, st>>>(a, m0, m1);
+      fused_step_kernel<MODE_FIELDS, ST_BF16, 0><<<grid, kThreads, sm, st>>>(a, m0, m1);
   }
   return cudaGetLastError();
 }

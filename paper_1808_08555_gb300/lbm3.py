@@ -28,6 +28,7 @@ _STATUS = {OK: "LBM3_OK", EINVAL: "LBM3_EINVAL", ENOMEM: "LBM3_ENOMEM", ECUDA: "
 BETA_PAPER, BETA_FU, BETA_SPENCER, BETA_LECLAIRE = range(4)
 RECOLOR_COSINE, RECOLOR_LITERAL = range(2)
 FP32, FP16_DEV, BF16_DEV = 0, 1, 2
+FORCE_BODY, FORCE_PERTURBATION = 0, 1
 
 
 class Lbm3Error(RuntimeError):
@@ -43,7 +44,7 @@ class lbm3_params(ctypes.Structure):
         ("sigma12", ctypes.c_double), ("sigma13", ctypes.c_double), ("sigma23", ctypes.c_double),
         ("beta0", ctypes.c_double),
         ("beta_form", ctypes.c_int32), ("recolor_form", ctypes.c_int32),
-        ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("storage", ctypes.c_int32), ("force_form", ctypes.c_int32),
     ]
 
 
@@ -60,6 +61,7 @@ class Params:
     beta_form: int = BETA_PAPER
     recolor_form: int = RECOLOR_COSINE
     storage: int = FP32
+    force_form: int = FORCE_BODY  # 1: perturbation operator (Eqs. phi1 / phi_old)
 
     def to_c(self) -> lbm3_params:
         p = lbm3_params()
@@ -70,7 +72,7 @@ class Params:
         p.sigma12, p.sigma13, p.sigma23 = (float(s) for s in self.sigma)
         p.beta0 = float(self.beta0)
         p.beta_form, p.recolor_form = int(self.beta_form), int(self.recolor_form)
-        p.storage, p.reserved = int(self.storage), 0
+        p.storage, p.force_form = int(self.storage), int(self.force_form)
         return p
 
 

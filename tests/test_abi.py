@@ -36,7 +36,8 @@ def test_header_symbols_exported(lib):
 
 
 def test_params_struct_layout_matches_header():
-    # int32 nx, ny; 3+3 doubles; 3 sigmas; beta0; 4 int32 -> 4*2 + 8*10 + 4*4 = 104 bytes
+    # int32 nx, ny; 3+3 doubles; 3 sigmas; beta0; 4 int32 (beta, recolour, storage, force
+    # forms) -> 4*2 + 8*10 + 4*4 = 104 bytes
     assert ctypes.sizeof(L.lbm3_params) == 104
 
 
@@ -45,6 +46,7 @@ def test_params_struct_layout_matches_header():
     dict(nx=8, ny=8, rho0=(1, 0, 1)), dict(nx=8, ny=8, sigma=(0.01, -1, 0.01)),
     dict(nx=8, ny=8, beta0=0.0), dict(nx=8, ny=8, beta0=1.5), dict(nx=8, ny=8, beta_form=7),
     dict(nx=8, ny=8, recolor_form=2), dict(nx=8, ny=8, storage=9), dict(nx=8, ny=8, storage=-1),
+    dict(nx=8, ny=8, force_form=2), dict(nx=8, ny=8, force_form=-1), dict(nx=8, ny=8, force_form=1, storage=1),
 ])
 def test_invalid_params_rejected(lib, kw):
     with pytest.raises(L.Lbm3Error) as e:

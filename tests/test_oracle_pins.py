@@ -16,6 +16,7 @@ from paper_1808_08555_gb300 import workloads as W
 # D2Q9 lattice as the paper defines it (Sec. 2, after Eq. 3).
 E = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]], float)
 WGT = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+EX, EY = E[:, 0], E[:, 1]
 
 
 # ------------------------------------------------------------ lattice pieces
@@ -44,6 +45,34 @@ def test_guo_moments(tau):
     np.testing.assert_allclose(E.T @ ph, a * F, atol=1e-18)
     P = np.einsum("i,ia,ib->ab", ph, E, E)
     np.testing.assert_allclose(P, a * (np.outer(u, F) + np.outer(F, u)), atol=1e-18)
+
+
+@pytest.mark.parametrize("tauf", [0.6, 0.8, 1.5])
+def test_perturbation_operator_moments(tauf):
+    """Eqs. phi1 / phi_old with Leclaire's B_i (sum B_i = 1/3): zero mass and
+    momentum, and second moment sum_i Phi_i e_i e_i = -sum_{k<l} sigma_kl
+    C_kl |G_kl| (I - n n) / tau_f, so that -div(tau_f sum_i Phi_i e_i e_i)
+    is the force of Eq. 11 (the Chapman-Enskog link the paper states)."""
+    rng = np.random.default_rng(int(tauf * 10))
+    G = np.zeros((3, 3, 2))
+    C = np.zeros((3, 3))
+    sig = (0.01, 0.013, 0.007)
+    for q, (k, l) in enumerate([(0, 1), (0, 2), (1, 2)]):
+        g = rng.standard_normal(2) * 0.2
+        G[k, l], G[l, k] = g, -g
+        C[k, l] = C[l, k] = rng.uniform(0.2, 1.0)
+    ph = O.perturbation(sig, G, C, tauf)
+    assert abs(ph.sum()) < 1e-18
+    assert abs((ph * EX).sum()) < 1e-18 and abs((ph * EY).sum()) < 1e-18
+    M = np.array([[(ph * EX * EX).sum(), (ph * EX * EY).sum()], [(ph * EY * EX).sum(), (ph * EY * EY).sum()]])
+    ref = np.zeros((2, 2))
+    for q, (k, l) in enumerate([(0, 1), (0, 2), (1, 2)]):
+        m = np.linalg.norm(G[k, l])
+        n = G[k, l] / m
+        ref -= sig[q] * C[k, l] * m * (np.eye(2) - np.outer(n, n)) / tauf
+    np.testing.assert_allclose(M, ref, rtol=1e-13, atol=1e-19)
+    # no interface (G = 0): no perturbation
+    assert np.abs(O.perturbation(sig, np.zeros((3, 3, 2)), C, tauf)).max() == 0.0
 
 
 @pytest.mark.parametrize("mx,my", [(1, 0), (0, 2), (3, 1), (2, 5)])
@@ -179,12 +208,14 @@ def test_force_integrates_to_laplace_jump(pair):
     assert abs(Fx.sum()) < 1e-15 and abs(Fy.sum()) < 1e-15      # periodic divergence
 
 
-def test_flat_interface_has_no_force_and_no_flow():
+@pytest.mark.parametrize("force_form", [0, 1])
+def test_flat_interface_has_no_force_and_no_flow(force_form):
     """A flat two-phase interface has a tension tensor that depends on y only
-    with T_xy = T_yy = 0, so F_s = 0 and the fluid stays at rest."""
+    with T_xy = T_yy = 0, so F_s = 0 and the fluid stays at rest (also with
+    the perturbation operator, whose stress has the same divergence)."""
     nx, ny = 8, 32
     rho = W.flat_band(nx, ny, 8, 24, sharp=True)
-    p = O.Params(nx, ny, tau=(0.8, 1.0, 1.0))
+    p = O.Params(nx, ny, tau=(0.8, 1.0, 1.0), force_form=force_form)
     Fx, Fy, _ = O.force(p, rho)
     assert np.abs(Fx).max() < 1e-17 and np.abs(Fy).max() < 1e-17
     f = O.step(p, O.init(p, rho), 300)
@@ -212,8 +243,8 @@ def test_random_state_conserves_mass_and_momentum():
     conserved from any state, here a random non-equilibrium one."""
     nx, ny = 12, 10
     f0 = W.random_populations(nx, ny, seed=3)
-    for form in (0, 1):
-        p = O.Params(nx, ny, tau=(0.7, 1.0, 1.4), sigma=(0.01, 0.02, 0.015), recolor_form=form)
+    for form, force in ((0, 0), (1, 0), (0, 1)):
+        p = O.Params(nx, ny, tau=(0.7, 1.0, 1.4), sigma=(0.01, 0.02, 0.015), recolor_form=form, force_form=force)
         m0, mo0 = O.mass(p, f0)
         f = O.step(p, f0, 20)
         m1, mo1 = O.mass(p, f)
@@ -242,13 +273,13 @@ def _mirror_x(f):
     return g
 
 
-@pytest.mark.parametrize("form", [0, 1])
-def test_step_commutes_with_lattice_symmetries(form):
+@pytest.mark.parametrize("form,force", [(0, 0), (1, 0), (0, 1)])
+def test_step_commutes_with_lattice_symmetries(form, force):
     """The update is built from isotropic pieces, so it commutes with the
     square lattice's 90-degree rotation and its mirror (up to roundoff)."""
     n = 10
     f0 = W.random_populations(n, n, seed=11)
-    p = O.Params(n, n, tau=(0.7, 1.0, 1.4), sigma=(0.01, 0.02, 0.015), recolor_form=form)
+    p = O.Params(n, n, tau=(0.7, 1.0, 1.4), sigma=(0.01, 0.02, 0.015), recolor_form=form, force_form=force)
     a = _rot90(O.step(p, f0, 2))
     b = O.step(p, _rot90(f0), 2)
     np.testing.assert_allclose(a, b, rtol=0, atol=1e-14)
@@ -296,14 +327,17 @@ def test_interface_thickness_matches_paper():
     assert abs(xi_fit(1) / 1.5831 - 1) > 0.05
 
 
-def test_young_laplace_single_droplet():
+@pytest.mark.parametrize("force_form", [0, 1])
+def test_young_laplace_single_droplet(force_form):
     """Eq. laplace: a relaxed two-phase droplet has a pressure jump sigma/R
-    (R from the droplet's area).  48x48, R = 10, sigma = 0.01."""
+    (R from the droplet's area).  48x48, R = 10, sigma = 0.01.  With the
+    perturbation operator (Eqs. phi1 / phi_old) the same jump follows, as
+    its Chapman-Enskog force is Eq. 11."""
     n, R, sig = 48, 10.0, 0.01
     rho = W.compound_droplet(n, n, 0.0, R)
     rho[2] = 0.0
     rho[0] = 1.0 - rho[1]
-    p = O.Params(n, n, sigma=(sig, sig, sig))
+    p = O.Params(n, n, sigma=(sig, sig, sig), force_form=force_form)
     f = O.step(p, O.init(p, rho), 9000)
     fl = O.fields(p, f)
     phi2 = fl["rho"][1] / fl["rho"].sum(0)

@@ -40,7 +40,7 @@ def f32(a):
 
 def oparams(p):
     return O.Params(p.nx, p.ny, tau=p.tau, rho0=p.rho0, sigma=p.sigma, beta0=p.beta0,
-                    beta_form=p.beta_form, recolor_form=p.recolor_form)
+                    beta_form=p.beta_form, recolor_form=p.recolor_form, force_form=p.force_form)
 
 
 def fp32_sensitivity(op, f0, steps, seed=0):
