@@ -48,3 +48,111 @@ def young_laplace_compound(R_r: float, force_form: int = L.FORCE_BODY, steps: in
     return {"R_r": R_r, "force_form": force_form, "steps": steps, "R_r_eq": R_r_eq, "R_g_eq": R_g_eq,
             "dp_rg": float(dp_rg), "dp_gb": float(dp_gb),
             "eps": A.laplace_error(dp_gb, R_g_eq, dp_rg, R_r_eq, sigma, sigma), "umax": umax}
+
+
+def _crossing(v: np.ndarray, level: float = 0.5) -> list:
+    """Positions (linear interpolation) where the 1-D profile v crosses level."""
+    out = []
+    for j in range(len(v) - 1):
+        a, b = v[j] - level, v[j + 1] - level
+        if a == 0.0:
+            out.append(float(j))
+        elif a * b < 0.0:
+            out.append(j + a / (a - b))
+    return out
+
+
+def lens(sigma_rb: float, sigma_rg: float, sigma_gb: float = 0.01, steps: int = 60000, n: int = 160,
+         R: float = 20.0, nu: float = 0.1) -> dict:
+    """Sec. 3.3 partial spreading (Tab. 3): a red droplet of radius R at the
+    centre of an n x n periodic box, green below and blue above it, relaxed
+    into a lens.  Measures on the phi_r = 1/2 contour the lens length D (at
+    the level of the flat green-blue interface, read in a far column) and the
+    cap heights, and gives Eq. 23's values for the simulated droplet area
+    with the contact angles of Eq. theta_kl.  h_i is the height of the cap
+    with contact angle theta_i (Eq. 23): theta_1 = phi_rg is the red-blue
+    cap (above the green-blue level), theta_2 = phi_rb the red-green cap
+    below it (the force balance at the triple point puts the steeper cap on
+    the side of the smaller tension)."""
+    tau = 3.0 * nu + 0.5
+    # fluids r, g, b = colours 0, 1, 2; pairs (12, 13, 23) = (rg, rb, gb)
+    p = L.Params(n, n, tau=(tau, tau, tau), sigma=(sigma_rg, sigma_rb, sigma_gb))
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    c = n / 2.0
+    r_ = (np.hypot(x - c, y - c) <= R).astype(float)
+    g_ = ((1.0 - r_) * (y < c)).astype(float)
+    b_ = 1.0 - r_ - g_
+    sim = L.Simulation(p)
+    sim.init(np.stack([r_, g_, b_]))
+    sim.step(steps)
+    rho = sim.fields()["rho"]
+    sim.close()
+    phi = rho / rho.sum(axis=0)
+    ic = n // 2
+    # flat green-blue level far from the lens (column 0), crossing near y = c
+    gb = [t for t in _crossing(phi[1][:, 0] - phi[2][:, 0], 0.0) if abs(t - c) < n / 4]
+    y_gb = gb[0]
+    ys = _crossing(phi[0][:, ic])
+    bottom, top = min(ys), max(ys)
+    j = int(np.floor(y_gb))
+    row = phi[0][j] + (y_gb - j) * (phi[0][j + 1] - phi[0][j])
+    xs = _crossing(row)
+    D = max(xs) - min(xs)
+    area = float(phi[0].sum())
+    t1, t2, _ = A.neumann_angles(sigma_rg, sigma_rb, sigma_gb)
+    Da, h1a, h2a = A.lens_geometry(area, t1, t2)
+    return {"D": D, "h1": top - y_gb, "h2": y_gb - bottom, "D_eq23": Da, "h1_eq23": h1a, "h2_eq23": h2a,
+            "area": area, "theta1_deg": math.degrees(t1), "theta2_deg": math.degrees(t2), "y_gb": y_gb}
+
+
+def interface_capturing(steps: int = 20000, nx: int = 200, ny: int = 100, R: float = 20.0, sigma: float = 0.01,
+                        nu: float = 0.1) -> dict:
+    """Sec. 3.1: a red and a green droplet of radius R centred at (50, 50)
+    and (150, 50) in blue, nx x ny periodic, relaxed; the colour fractions
+    along y = 50 compared with the tanh profiles of Eq. 21 (xi = 1.5831).
+    Returns the largest deviation from Eq. 21 on that line and the fitted
+    radii."""
+    tau = 3.0 * nu + 0.5
+    p = L.Params(nx, ny, tau=(tau, tau, tau), sigma=(sigma, sigma, sigma))
+    rho0 = W.two_droplets(nx, ny, R=R, c2=(50.0, 50.0), c3=(150.0, 50.0))
+    # the paper's red and green droplets are fluids r, g in a blue matrix
+    rho0 = np.stack([rho0[1], rho0[2], rho0[0]])
+    sim = L.Simulation(p)
+    sim.init(rho0)
+    sim.step(steps)
+    rho = sim.fields()["rho"]
+    sim.close()
+    phi = rho[:, 50, :] / rho[:, 50, :].sum(axis=0)
+    x = np.arange(nx, dtype=float)
+    ar = 0.5 + 0.5 * np.tanh((R - np.abs(x - 50.0)) / W.XI)
+    ag = 0.5 + 0.5 * np.tanh((R - np.abs(x - 150.0)) / W.XI)
+    dev = max(np.abs(phi[0] - ar).max(), np.abs(phi[1] - ag).max(), np.abs(phi[2] - (1 - ar - ag)).max())
+    return {"max_dev_eq21": float(dev), "phi_r_centre": float(phi[0, 50]), "phi_g_centre": float(phi[1, 150])}
+
+
+def complete_spreading(sigma_rg: float, sigma_gb: float = 0.005, sigma_rb: float = 0.005, steps: int = 40000,
+                       n: int = 160, R: float = 20.0, nu: float = 0.05) -> dict:
+    """Sec. 3.3 complete spreading: the lens set-up with sigma_rg >= sigma_gb
+    + sigma_rb (no Neumann triangle).  At the critical sigma_rg = sigma_gb +
+    sigma_rb the red droplet ends sitting on the green-blue interface; above
+    it, it leaves the interface and rises into the blue fluid.  Returns the
+    red droplet's lowest point and centroid relative to the green-blue level
+    (far column), and the red-green contact sum(phi_r phi_g)."""
+    tau = 3.0 * nu + 0.5
+    p = L.Params(n, n, tau=(tau, tau, tau), sigma=(sigma_rg, sigma_rb, sigma_gb))
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    c = n / 2.0
+    r_ = (np.hypot(x - c, y - c) <= R).astype(float)
+    g_ = ((1.0 - r_) * (y < c)).astype(float)
+    sim = L.Simulation(p)
+    sim.init(np.stack([r_, g_, 1.0 - r_ - g_]))
+    sim.step(steps)
+    rho = sim.fields()["rho"]
+    sim.close()
+    phi = rho / rho.sum(axis=0)
+    gb = [t for t in _crossing(phi[1][:, 0] - phi[2][:, 0], 0.0) if abs(t - c) < n / 4]
+    y_gb = gb[0]
+    ys = _crossing(phi[0][:, int(round(float((phi[0] * x).sum() / phi[0].sum())))])
+    yc = float((phi[0] * y).sum() / phi[0].sum())
+    return {"bottom_above_gb": min(ys) - y_gb, "centroid_above_gb": yc - y_gb,
+            "rg_contact": float((phi[0] * phi[1]).sum()), "y_gb": y_gb}

@@ -1,0 +1,56 @@
+"""The paper's validation experiments run on the GPU library
+(``experiments``), compared with the numbers the paper prints."""
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def X():
+    from paper_1808_08555_gb300 import build as B
+    B.build()
+    from paper_1808_08555_gb300 import experiments, lbm3
+    lbm3.load()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return experiments
+
+
+# Tab. 3: simulated D, h1, h2 of the partial-spreading lenses (sigma_gb = 0.01;
+# (sigma_rb, sigma_rg) as in the caption of the lens figure, Sec. 3.3)
+TAB3 = [("a", 0.01, 0.01, 53.59, 15.92, 15.92), ("b", 0.0087, 0.005, 61.79, 8.79, 18.97),
+        ("c", 0.02, 0.0173, 45.39, 13.35, 22.51), ("d", 0.0115, 0.0058, 50.93, 6.77, 25.22)]
+
+
+@pytest.mark.parametrize("case,srb,srg,D,h1,h2", TAB3)
+def test_lens_matches_table_3(X, case, srb, srg, D, h1, h2):
+    """160^2, red droplet R = 20 between green (below) and blue (above),
+    nu = 0.1, 60000 steps.  The lens length and cap heights agree with the
+    paper's simulated values to 5 % (observed 0.1-4 %) and with Eq. 23 to
+    7 % (the paper's own largest deviation is 5.2 %, for D in case b)."""
+    r = X.lens(srb, srg)
+    for got, want in ((r["D"], D), (r["h1"], h1), (r["h2"], h2)):
+        assert got == pytest.approx(want, rel=0.05), (case, r)
+    for got, want in ((r["D"], r["D_eq23"]), (r["h1"], r["h1_eq23"]), (r["h2"], r["h2_eq23"])):
+        assert got == pytest.approx(want, rel=0.07), (case, r)
+
+
+def test_interface_capturing_follows_eq_21(X):
+    """Sec. 3.1: two separate droplets (R = 20) in a 200 x 100 box relax to
+    the tanh profiles of Eq. 21 with xi = 1.5831 along y = 50 (observed
+    largest deviation 0.012)."""
+    r = X.interface_capturing()
+    assert r["max_dev_eq21"] < 0.02, r
+    assert r["phi_r_centre"] > 0.999 and r["phi_g_centre"] > 0.999, r
+
+
+def test_complete_spreading_critical_and_supercritical(X):
+    """Sec. 3.3, sigma_gb = sigma_rb = 0.005, nu = 0.05: at the critical
+    sigma_rg = 0.01 the red droplet ends on the green-blue interface (its
+    lowest point within the diffuse interface, 2.5 xi); at sigma_rg = 0.015
+    it has left it (lowest point more than 5 xi above, no red-green contact)."""
+    crit = X.complete_spreading(0.01)
+    sup = X.complete_spreading(0.015)
+    assert abs(crit["bottom_above_gb"]) < 2.5 * 1.5831, crit
+    assert sup["bottom_above_gb"] > 5 * 1.5831, sup
+    assert sup["rg_contact"] < 1e-6 < crit["rg_contact"], (crit, sup)
