@@ -156,3 +156,42 @@ def complete_spreading(sigma_rg: float, sigma_gb: float = 0.005, sigma_rb: float
     yc = float((phi[0] * y).sum() / phi[0].sum())
     return {"bottom_above_gb": min(ys) - y_gb, "centroid_above_gb": yc - y_gb,
             "rg_contact": float((phi[0] * phi[1]).sum()), "y_gb": y_gb}
+
+
+# Sec. 4.1: the seven double-droplet cases, (sigma_gb, sigma_rb) / sigma_rg,
+# and the morphology the paper reports for each
+DOUBLE_DROPLET_CASES = {
+    "i": (1.7, 0.5, "complete engulfing of green by red"),
+    "ii": (2.0, 1.0, "critical engulfing of green by red"),
+    "iii": (0.4, 0.4, "non-engulfing (separate droplets)"),
+    "iv": (0.5, 0.5, "kissing"),
+    "v": (1.0, 1.0, "partial engulfing (Janus droplet)"),
+    "vi": (1.0, 2.0, "critical engulfing of red by green"),
+    "vii": (0.5, 1.7, "complete engulfing of red by green"),
+}
+
+
+def double_droplet(case: str, steps: int = 60000, n: int = 120, R: float = 20.0, sigma_rg: float = 0.01,
+                   nu: float = 0.1) -> dict:
+    """Sec. 4.1: a red and a green droplet of radius R touching at the centre
+    of an n x n periodic box (red above, green below; centres (60.5, 60.5 +- R)
+    on the paper's 1-based grid), in blue, relaxed.  Returns the interface
+    lengths L_kl = sum_x phi_k phi_l / (xi / 2) (a tanh interface of width xi
+    carries xi/2 of sum phi_k phi_l per unit length) in units of the
+    droplet circumference 2 pi R."""
+    a, b, _ = DOUBLE_DROPLET_CASES[case]
+    tau = 3.0 * nu + 0.5
+    p = L.Params(n, n, tau=(tau, tau, tau), sigma=(sigma_rg, b * sigma_rg, a * sigma_rg))
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    c = (n + 1) / 2.0 - 1.0  # 60.5 on the 1-based grid
+    pr = 0.5 + 0.5 * np.tanh((R - np.hypot(x - c, y - c - R)) / W.XI)
+    pg = 0.5 + 0.5 * np.tanh((R - np.hypot(x - c, y - c + R)) / W.XI)
+    sim = L.Simulation(p)
+    sim.init(np.stack([pr, pg, np.clip(1.0 - pr - pg, 0.0, None)]))
+    sim.step(steps)
+    rho = sim.fields()["rho"]
+    sim.close()
+    phi = rho / rho.sum(axis=0)
+    scale = (W.XI / 2.0) * 2.0 * math.pi * R
+    return {"L_rg": float((phi[0] * phi[1]).sum() / scale), "L_rb": float((phi[0] * phi[2]).sum() / scale),
+            "L_gb": float((phi[1] * phi[2]).sum() / scale)}

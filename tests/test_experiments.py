@@ -54,3 +54,27 @@ def test_complete_spreading_critical_and_supercritical(X):
     assert abs(crit["bottom_above_gb"]) < 2.5 * 1.5831, crit
     assert sup["bottom_above_gb"] > 5 * 1.5831, sup
     assert sup["rg_contact"] < 1e-6 < crit["rg_contact"], (crit, sup)
+
+
+def test_double_droplet_morphologies(X):
+    """Sec. 4.1: the seven cases reach the morphologies the paper reports,
+    read from which interfaces exist (lengths in units of 2 pi R; observed:
+    absent interfaces <= 0.02, critical ones ~0.05).  Exchanging red and
+    green with their tensions mirrors the result exactly."""
+    r = {c: X.double_droplet(c) for c in X.DOUBLE_DROPLET_CASES}
+    # complete engulfing: the engulfed droplet keeps its perimeter, the outer
+    # interface encloses twice the area (sqrt 2 longer), the third is absent
+    assert r["i"]["L_gb"] < 0.01 and r["vii"]["L_rb"] < 0.01, r
+    assert r["i"]["L_rg"] == pytest.approx(1.0, abs=0.05) and r["i"]["L_rb"] == pytest.approx(2 ** 0.5, abs=0.05)
+    # critical engulfing: the vanishing interface is down to a few per cent
+    assert r["ii"]["L_gb"] < 0.1 and r["vi"]["L_rb"] < 0.1, r
+    # non-engulfing and kissing: no (or a point-like) red-green interface
+    assert r["iii"]["L_rg"] < 0.015 and r["iv"]["L_rg"] < 0.03, r
+    for c in ("iii", "iv"):
+        assert r[c]["L_rb"] == pytest.approx(1.0, abs=0.05) and r[c]["L_gb"] == pytest.approx(1.0, abs=0.05)
+    # partial engulfing: all three interfaces
+    assert r["v"]["L_rg"] > 0.2 and r["v"]["L_rb"] > 0.5 and r["v"]["L_gb"] > 0.5, r
+    for a, b in (("i", "vii"), ("ii", "vi")):
+        assert r[a]["L_rg"] == pytest.approx(r[b]["L_rg"], rel=1e-4)
+        assert r[a]["L_rb"] == pytest.approx(r[b]["L_gb"], rel=1e-4)
+        assert r[a]["L_gb"] == pytest.approx(r[b]["L_rb"], rel=1e-4)
