@@ -195,3 +195,80 @@ def double_droplet(case: str, steps: int = 60000, n: int = 120, R: float = 20.0,
     scale = (W.XI / 2.0) * 2.0 * math.pi * R
     return {"L_rg": float((phi[0] * phi[1]).sum() / scale), "L_rb": float((phi[0] * phi[2]).sum() / scale),
             "L_gb": float((phi[1] * phi[2]).sum() / scale)}
+
+
+def _interface_lengths(phi: np.ndarray) -> dict:
+    """L_kl = sum_x phi_k phi_l / (xi / 2) in lattice units."""
+    s = W.XI / 2.0
+    return {"L_rg": float((phi[0] * phi[1]).sum() / s), "L_rb": float((phi[0] * phi[2]).sum() / s),
+            "L_gb": float((phi[1] * phi[2]).sum() / s)}
+
+
+def kissing_length_eq(sigma_gb: float, R: float = 60.0, sigma_rg: float = 0.01) -> float:
+    """Sec. 4.3, Eq. drg: equilibrium rg-interface length of two equal
+    droplets (radius R, sigma_rb = sigma_gb): the flat chord between circles
+    d_rg = R sigma_rg / sigma_gb apart, 0 at and below the kissing point."""
+    if sigma_gb <= sigma_rg / 2.0:
+        return 0.0
+    d = R * sigma_rg / sigma_gb
+    return 2.0 * math.sqrt(max(R * R - d * d / 4.0, 0.0))
+
+
+def engulfing_length_eq(sigma_rb: float, R_r: float = 60.0, R_g: float = 80.0, sigma_gb: float = 0.01) -> float:
+    """Sec. 4.3: equilibrium rb-interface length of a red droplet (R_r)
+    partially engulfed by a green one (R_g), sigma_gb = sigma_rg: cos alpha =
+    sigma_rb / (2 sigma_gb), d_rg = sqrt(R_r^2 + R_g^2 - 2 R_r R_g cos alpha);
+    the rb interface is the arc of the red circle outside the green one; 0
+    at and above the critical sigma_rb = 2 sigma_gb."""
+    ca = sigma_rb / (2.0 * sigma_gb)
+    if ca >= 1.0:
+        return 0.0
+    d = math.sqrt(R_r * R_r + R_g * R_g - 2.0 * R_r * R_g * ca)
+    x_ab = (R_g * R_g - R_r * R_r + d * d) / (2.0 * d)   # chord AB from O_g along the centre line
+    theta_r = math.acos(max(-1.0, min(1.0, (x_ab - d) / R_r)))
+    return 2.0 * theta_r * R_r
+
+
+def near_critical(kind: str, sigma: float, beta_form: int = L.BETA_PAPER, force_form: int = L.FORCE_BODY,
+                  steps: int = 60000, n: int = 300, nu: float = 0.1, recolor_form: int = L.RECOLOR_COSINE) -> dict:
+    """Sec. 4.3 near-critical states, n x n periodic, viscosities nu.
+    kind = "kissing": two droplets R = 60, sigma_rg = 0.01, sigma_gb =
+    sigma_rb = `sigma`, centres d_rg (Eq. drg) apart across y = 150.5, the
+    rg interface initially the flat midline.  kind = "engulfing": a red
+    droplet R_r = 60 partially engulfed by a green one R_g = 80, sigma_gb =
+    sigma_rg = 0.01, sigma_rb = `sigma`, centres d_rg apart (the analytic
+    value, R_g - R_r at and above the critical 0.02), the red droplet
+    initially whole.  Returns the interface lengths after `steps` steps and
+    the analytic length of the interface that vanishes at the critical
+    point."""
+    tau = 3.0 * nu + 0.5
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    c = (n + 1) / 2.0 - 1.0
+    edge = lambda d: 0.5 + 0.5 * np.tanh(d / W.XI)
+    if kind == "kissing":
+        R, srg = 60.0, 0.01
+        d = R * srg / sigma if sigma > srg / 2.0 else 2.0 * R
+        sig = (srg, sigma, sigma)
+        dr = np.minimum(R - np.hypot(x - c, y - (c + d / 2.0)), y - c)
+        dg = np.minimum(R - np.hypot(x - c, y - (c - d / 2.0)), c - y)
+        pr, pg = edge(dr), edge(dg)
+        want, key = kissing_length_eq(sigma), "L_rg"
+    else:
+        R_r, R_g, s = 60.0, 80.0, 0.01
+        ca = min(sigma / (2.0 * s), 1.0)
+        d = math.sqrt(R_r * R_r + R_g * R_g - 2.0 * R_r * R_g * ca)
+        sig = (s, sigma, s)
+        pr = edge(R_r - np.hypot(x - c, y - (c + d)))
+        pg = np.clip(edge(R_g - np.hypot(x - c, y - c)) - pr, 0.0, None)
+        want, key = engulfing_length_eq(sigma), "L_rb"
+    p = L.Params(n, n, tau=(tau, tau, tau), sigma=sig, beta_form=beta_form, force_form=force_form,
+                 recolor_form=recolor_form)
+    sim = L.Simulation(p)
+    sim.init(np.stack([pr, pg, np.clip(1.0 - pr - pg, 0.0, None)]))
+    sim.step(steps)
+    rho = sim.fields()["rho"]
+    sim.close()
+    out = _interface_lengths(rho / rho.sum(axis=0))
+    out.update({"kind": kind, "sigma": sigma, "beta_form": beta_form, "force_form": force_form,
+                "analytic": want, "measured": out[key]})
+    return out

@@ -78,3 +78,27 @@ def test_double_droplet_morphologies(X):
         assert r[a]["L_rg"] == pytest.approx(r[b]["L_rg"], rel=1e-4)
         assert r[a]["L_rb"] == pytest.approx(r[b]["L_gb"], rel=1e-4)
         assert r[a]["L_gb"] == pytest.approx(r[b]["L_rb"], rel=1e-4)
+
+
+def test_near_critical_states_paper_beta_vs_fu(X):
+    """Sec. 4.3 (Fig. critical_state): with the paper's beta (Eqs. 19-20)
+    the interface lengths follow the analytic ones on both sides of the
+    kissing and the critical-engulfing points, while Fu's constant beta
+    (Eq. fu) keeps interfaces the geometry does not have.  Observed at
+    60000 steps (measured / analytic):
+      kissing sigma_gb = 0.0048: paper 2.7 / 0, Fu 42.0 / 0
+      kissing sigma_gb = 0.0056: paper 56.0 / 54.0, Fu 65.1 / 54.0
+      engulfing sigma_rb = 0.0194: paper 102.7 / 100.2, Fu 199.4 / 100.2
+      engulfing sigma_rb = 0.0204: paper 12.5 / 0, Fu 172.3 / 0."""
+    from paper_1808_08555_gb300 import lbm3 as L
+    run = lambda kind, s, bf: X.near_critical(kind, s, beta_form=bf)
+    a, f = run("kissing", 0.0048, L.BETA_PAPER), run("kissing", 0.0048, L.BETA_FU)
+    assert a["analytic"] == 0.0 and a["measured"] < 5.0 and f["measured"] > 30.0, (a, f)
+    a, f = run("kissing", 0.0056, L.BETA_PAPER), run("kissing", 0.0056, L.BETA_FU)
+    assert a["measured"] == pytest.approx(a["analytic"], rel=0.1), a
+    assert abs(f["measured"] / f["analytic"] - 1) > 0.15, f
+    a, f = run("engulfing", 0.0194, L.BETA_PAPER), run("engulfing", 0.0194, L.BETA_FU)
+    assert a["measured"] == pytest.approx(a["analytic"], rel=0.1), a
+    assert f["measured"] > 1.5 * f["analytic"], f
+    a, f = run("engulfing", 0.0204, L.BETA_PAPER), run("engulfing", 0.0204, L.BETA_FU)
+    assert a["analytic"] == 0.0 and a["measured"] < 0.1 * f["measured"], (a, f)
