@@ -48,19 +48,21 @@ def test_complete_spreading_critical_and_supercritical(X):
     """Sec. 3.3, sigma_gb = sigma_rb = 0.005, nu = 0.05: at the critical
     sigma_rg = 0.01 the red droplet ends on the green-blue interface (its
     lowest point within the diffuse interface, 2.5 xi); at sigma_rg = 0.015
-    it has left it (lowest point more than 5 xi above, no red-green contact)."""
+    it has left it (lowest point more than 5 xi above, red-green contact
+    sum phi_r phi_g below 1e-3, against ~3 in the critical case)."""
     crit = X.complete_spreading(0.01)
     sup = X.complete_spreading(0.015)
     assert abs(crit["bottom_above_gb"]) < 2.5 * 1.5831, crit
     assert sup["bottom_above_gb"] > 5 * 1.5831, sup
-    assert sup["rg_contact"] < 1e-6 < crit["rg_contact"], (crit, sup)
+    assert sup["rg_contact"] < 1e-3 < crit["rg_contact"], (crit, sup)
 
 
 def test_double_droplet_morphologies(X):
     """Sec. 4.1: the seven cases reach the morphologies the paper reports,
     read from which interfaces exist (lengths in units of 2 pi R; observed:
     absent interfaces <= 0.02, critical ones ~0.05).  Exchanging red and
-    green with their tensions mirrors the result exactly."""
+    green with their tensions mirrors the result (to FP32 rounding: 1e-4
+    relative, 1e-5 absolute on the vanishing interfaces)."""
     r = {c: X.double_droplet(c) for c in X.DOUBLE_DROPLET_CASES}
     # complete engulfing: the engulfed droplet keeps its perimeter, the outer
     # interface encloses twice the area (sqrt 2 longer), the third is absent
@@ -75,9 +77,9 @@ def test_double_droplet_morphologies(X):
     # partial engulfing: all three interfaces
     assert r["v"]["L_rg"] > 0.2 and r["v"]["L_rb"] > 0.5 and r["v"]["L_gb"] > 0.5, r
     for a, b in (("i", "vii"), ("ii", "vi")):
-        assert r[a]["L_rg"] == pytest.approx(r[b]["L_rg"], rel=1e-4)
-        assert r[a]["L_rb"] == pytest.approx(r[b]["L_gb"], rel=1e-4)
-        assert r[a]["L_gb"] == pytest.approx(r[b]["L_rb"], rel=1e-4)
+        assert r[a]["L_rg"] == pytest.approx(r[b]["L_rg"], rel=1e-4, abs=1e-5)
+        assert r[a]["L_rb"] == pytest.approx(r[b]["L_gb"], rel=1e-4, abs=1e-5)
+        assert r[a]["L_gb"] == pytest.approx(r[b]["L_rb"], rel=1e-4, abs=1e-5)
 
 
 def test_near_critical_states_paper_beta_vs_fu(X):
