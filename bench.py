@@ -156,6 +156,13 @@ def make_case(size: int = 2048):
     return W.case_compound_2048() if size == 2048 else W.case_compound_scaled(size)
 
 
+def workload_name(size: int) -> str:
+    if size == 2048:
+        return WORKLOAD
+    return (f"compound double droplet {size}x{size} periodic (the 2048^2 workload with radii scaled by "
+            f"{size}/2048), tau=(0.6,0.7,0.9), sigma12/13/23=0.01/0.012/0.005, beta0=0.7, FP32 populations")
+
+
 def run_ours(args, ws, rank, local):
     import torch
 
@@ -240,11 +247,14 @@ def run_ours(args, ws, rank, local):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seedless analytic droplet fields, Eq. 21 tanh edges)",
-        "config": {"workload": WORKLOAD, "nx": case.nx, "ny": case.ny, "nodes_per_step": nodes,
+        "config": {"workload": workload_name(case.nx), "nx": case.nx, "ny": case.ny, "nodes_per_step": nodes,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                   "l2": "inputs larger than L2: two 453 MB population buffers vs 129 MB L2"},
+                   "l2": (f"inputs larger than L2: two {27 * 4 * case.ny * (case.nx + 8) / 1e6:.0f} MB "
+                          "population buffers vs 129 MB L2") if case.nx >= 1024 else
+                         "inputs smaller than L2 (small profiling case)"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": recorded_traffic(),
+                     "frac": round(achieved / peak, 4),
+                     "traffic": recorded_traffic() if case.nx == 2048 else None,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.8 TB/s", "bytes_per_node": BYTES_PER_NODE,
                      "kernel": STEP_KERNEL},
@@ -476,7 +486,7 @@ def run_reference(args, ws, rank):
         "value": round(value, 4), "unit": "MLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(total / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": case.nx, "ny": case.ny},
+        "config": {"workload": workload_name(case.nx), "nx": case.nx, "ny": case.ny},
         "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
                          "sample": f"each step = {sample} lattice step(s) of the full {case.nx}x{case.ny} grid"},
         "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

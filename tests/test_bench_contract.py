@@ -1,0 +1,54 @@
+"""bench.py prints the one-line JSON contract: the oracle arm (CPU) and the
+library arm (GPU) on small grids, every required key present and consistent."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(args, timeout=900):
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT, capture_output=True,
+                         text=True, timeout=timeout)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    return json.loads(lines[0])
+
+
+def _common(d):
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "e2e"):
+        assert k in d, k
+    assert d["value"] > 0 and d["unit"] == "MLUPS" and d["higher_is_better"] is True
+    assert d["scaling"] == "weak" and "workload" in d["config"]
+    for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"):
+        assert k in d["e2e"], k
+
+
+def test_reference_arm_contract():
+    d = _run(["--impl", "reference", "--size", "64", "--steps", "1", "--warmup", "1", "--cpu-steps", "2"])
+    _common(d)
+    assert d["impl"] == "reference" and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["value"] == d["value"] and d["e2e"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    assert "64x64" in d["config"]["workload"]
+
+
+@pytest.mark.gpu
+def test_library_arm_contract():
+    d = _run(["--size", "256", "--steps", "20", "--warmup", "3", "--cpu-steps", "1"])
+    _common(d)
+    r = d["roofline"]
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert k in r, k
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] is None
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"], rel=1e-3)
+    assert d["gpu_launches"] == d["steps"]
+    for k in ("sm_mhz", "sm_max_mhz", "reasons"):
+        assert k in d["clocks"], k
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["value"] == pytest.approx(256 * 256 * d["steps"] / (d["ms_per_step"] * d["steps"] / 1e3) / 1e6, rel=1e-3)
