@@ -114,3 +114,43 @@ def test_fields_and_device_paths(L, storage):
     torch.cuda.synchronize()
     np.testing.assert_array_equal(fd.cpu().numpy(), sim.populations())
     sim.close()
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_janus_512_against_oracle(L, storage):
+    """The reduced-precision workload's 512^2 copy (Janus droplet R = 75,
+    1000 steps) in each storage against the FP64 oracle
+    (tests/golden/janus_512.json): colour fractions at 64 interface nodes,
+    colour masses, and the pressure jumps of the two halves.
+
+    Bars: FP32 the 1e-4 bar of 1000-step parity.  The 16-bit storages carry
+    one rounding of the deviations per step (u = 2^-11 for FP16, 2^-8 for
+    BF16, relative to the equilibrium scale); roundings of either sign over
+    n = 1000 steps add up to about sqrt(n) u ~ 32 u at worst, and phi is
+    held to 16 u, the pressure jump to 32 u.  Observed: phi 1.9e-5 / 8.7 u /
+    7.3 u, mass 1.5e-6 / 5.1e-6 / 2.4e-6, pressure jump 6.7e-5 / 15 u / 12 u
+    (FP32 / FP16 / BF16)."""
+    import json
+    import os
+    import sys
+    here = os.path.dirname(os.path.abspath(__file__))
+    sys.path.insert(0, os.path.join(here, "golden"))
+    import make_janus_512 as G
+    g = json.load(open(os.path.join(here, "golden", "janus_512.json")))
+    sim = L.Simulation(L.Params(g["n"], g["n"], tau=(1.0, 1.0, 1.0), sigma=tuple(g["sigma"]), storage=storage))
+    sim.init(W.janus_droplet(g["n"], g["R"]))
+    sim.step(g["steps"])
+    fl = sim.fields()
+    sim.close()
+    rho = fl["rho"]
+    phi = rho / rho.sum(axis=0)
+    got = np.array([phi[k, y, x] for (k, y, x) in g["nodes_kyx"]])
+    err = float(np.abs(got - np.array(g["phi"])).max())
+    mass = rho.sum(axis=(1, 2))
+    d2, d3, far = G.regions(g["n"], g["R"])
+    pf = fl["p"][far].mean()
+    dp = np.array([fl["p"][d2].mean() - pf, fl["p"][d3].mean() - pf])
+    u = UNIT.get(storage, 0.0)
+    assert err <= (1e-4 if storage == 0 else 16 * u), (storage, err)
+    np.testing.assert_allclose(mass, g["mass"], rtol=1e-5)
+    np.testing.assert_allclose(dp, [g["dp2"], g["dp3"]], rtol=1e-3 if storage == 0 else 32 * u)
