@@ -1,6 +1,6 @@
 """Analytic geometry and diagnostics of the paper's test cases (Secs. 3-4).
 
-These are closed forms the paper uses to judge its simulations: Neumann
+These are closed forms the paper uses to assess its simulations: Neumann
 contact angles, the liquid lens, general and perfect Janus droplets, and the
 Young-Laplace error of a compound droplet, plus a pressure-jump helper for
 fields read back from the library.  Plain numpy, no part of the time step.

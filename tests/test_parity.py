@@ -1,6 +1,6 @@
 """CUDA path (through the C ABI) against the FP64 oracle, element by element.
 
-Tolerance (BASELINE spec reading): the relative population error
+Tolerance (the stated FP32 parity bars): the relative population error
 max |f_gpu - f_oracle| / max(|f_oracle|, 1e-3 w_i) is at most 1e-5 after one
 step and 1e-4 after 1000 steps of a static case; per-colour mass of the GPU
 state, reduced in FP64 on the device, equals an exact host sum of the same
