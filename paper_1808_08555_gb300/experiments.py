@@ -272,3 +272,61 @@ def near_critical(kind: str, sigma: float, beta_form: int = L.BETA_PAPER, force_
     out.update({"kind": kind, "sigma": sigma, "beta_form": beta_form, "force_form": force_form,
                 "analytic": want, "measured": out[key]})
     return out
+
+
+def _axis_crossings(phi: np.ndarray, xc: int) -> dict:
+    """Along the column x = xc: the lowest point of the droplet (phi_b falls
+    through 1/2), the red-green interface (phi_r = phi_g) and the highest
+    point (phi_b rises through 1/2), by linear interpolation."""
+    b = _crossing(phi[2][:, xc])
+    rg = _crossing(phi[0][:, xc] - phi[1][:, xc], 0.0)
+    return {"bottom": min(b), "top": max(b), "rg": rg}
+
+
+def janus(kind: str, value: float, steps: int = 80000, n: int = 300, nu: float = 0.1) -> dict:
+    """Sec. 4.2 Janus droplets in an n x n periodic box, viscosities nu.
+    kind = "general": R_r = 60, R_g = 80, R_b = 160 and d_rg = `value`, the
+    tensions sigma_gb, sigma_rb of Eqs. gjd_01-06 for sigma_rg = 0.01.
+    kind = "perfect": R_r = R_g = 80, red area fraction `value`,
+    sigma_rb = sigma_gb = 0.01, sigma_rg = 1e-8, R_b and d_gb of Eq. pjd.
+    The initial fields follow the analytic geometry on the vertical axis
+    (green centre O_g below the red centre O_r, the rg arc of radius R_b
+    centred d_gb above O_g): the droplet is the red circle above the chord AB
+    and the green circle below it; red is the part of it inside the rg arc's
+    circle.  Returns, along the axis, the droplet length (top - bottom) and
+    the rg interface's height above the bottom, simulated and analytic."""
+    tau = 3.0 * nu + 0.5
+    if kind == "general":
+        R_r, R_g, R_b, d_rg = 60.0, 80.0, 160.0, float(value)
+        geo = A.gjd_geometry(R_r, R_g, R_b, d_rg, 0.01)
+        sig = (0.01, geo["sigma_rb"], geo["sigma_gb"])
+        d_gb, tg = geo["d_gb"], geo["theta_g"]
+    else:
+        R_r = R_g = 80.0
+        geo = A.pjd_geometry(80.0, float(value))
+        R_b, d_rg, d_gb, tg = geo["R_b"], 0.0, geo["d_gb"], geo["theta_g"]
+        sig = (1e-8, 0.01, 0.01)
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    c = (n + 1) / 2.0 - 1.0
+    top_rel = d_rg + R_r
+    yg = c - (top_rel - R_g) / 2.0            # centre the droplet's axial extent in the box
+    x_ab = yg + R_g * math.cos(tg)            # chord AB (height on the axis)
+    in_r = np.hypot(x - c, y - (yg + d_rg)) <= R_r
+    in_g = np.hypot(x - c, y - yg) <= R_g
+    drop = np.where(y >= x_ab, in_r, in_g)
+    red = drop & (np.hypot(x - c, y - (yg + d_gb)) <= R_b)
+    green = drop & ~red
+    smooth = lambda m: m.astype(float)
+    pr, pg = smooth(red), smooth(green)
+    p = L.Params(n, n, tau=(tau, tau, tau), sigma=sig)
+    sim = L.Simulation(p)
+    sim.init(np.stack([pr, pg, 1.0 - pr - pg]))
+    sim.step(steps)
+    rho = sim.fields()["rho"]
+    sim.close()
+    phi = rho / rho.sum(axis=0)
+    ax = _axis_crossings(phi, int(round(c)))
+    rg = [t for t in ax["rg"] if ax["bottom"] < t < ax["top"]]
+    return {"kind": kind, "value": value, "sigma": sig, "length": ax["top"] - ax["bottom"],
+            "length_eq": top_rel + R_g, "rg_above_bottom": (rg[0] - ax["bottom"]) if rg else float("nan"),
+            "rg_above_bottom_eq": R_g + d_gb - R_b}

@@ -104,3 +104,17 @@ def test_near_critical_states_paper_beta_vs_fu(X):
     assert f["measured"] > 1.5 * f["analytic"], f
     a, f = run("engulfing", 0.0204, L.BETA_PAPER), run("engulfing", 0.0204, L.BETA_FU)
     assert a["analytic"] == 0.0 and a["measured"] < 0.1 * f["measured"], (a, f)
+
+
+@pytest.mark.parametrize("kind,value", [("general", 40), ("general", 80), ("general", 120), ("perfect", 0.1),
+                                        ("perfect", 0.3)])
+def test_janus_droplets_follow_analytic_geometry(X, kind, value):
+    """Sec. 4.2 (Figs. general_ball, perfect_ball): general Janus droplets
+    (R_r = 60, R_g = 80, R_b = 160, tensions of tab_gjd) and perfect ones
+    (R = 80, area fractions of tab_pjd) relaxed from the analytic geometry
+    keep it: on the symmetry axis, the droplet length and the red-green
+    interface height agree with Eqs. gjd / pjd to 2.5 xi (observed 0.02-3.0
+    lattice units, the largest for d_rg = 40)."""
+    r = X.janus(kind, value, steps=40000)
+    assert r["length"] == pytest.approx(r["length_eq"], abs=2.5 * 1.5831), r
+    assert r["rg_above_bottom"] == pytest.approx(r["rg_above_bottom_eq"], abs=2.5 * 1.5831), r
