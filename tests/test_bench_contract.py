@@ -29,13 +29,23 @@ def _common(d):
         assert k in d["e2e"], k
 
 
+def test_reference_arm_bounded_for_many_steps():
+    """A large step count shrinks the sampled window instead of the run
+    growing without bound (the oracle at ~1 MLUPS on one core)."""
+    import time
+    t0 = time.time()
+    d = _run(["--impl", "reference", "--steps", "2000", "--warmup", "3", "--ref-seconds", "10"], timeout=600)
+    assert time.time() - t0 < 60
+    assert d["config"]["sample_window"] < 2048 and d["steps"] == 2000
+
+
 def test_reference_arm_contract():
     d = _run(["--impl", "reference", "--size", "64", "--steps", "1", "--warmup", "1", "--cpu-steps", "2"])
     _common(d)
     assert d["impl"] == "reference" and d["cpu_baseline"]["kind"] == "oracle"
     assert d["cpu_baseline"]["value"] == d["value"] and d["e2e"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    assert "64x64" in d["config"]["workload"]
+    assert "64x64" in d["config"]["workload"] and d["config"]["sample_window"] <= 64
 
 
 @pytest.mark.gpu
