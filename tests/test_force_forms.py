@@ -82,3 +82,37 @@ def test_tables_1_and_2_young_laplace_and_spurious_velocities(L):
     assert np.all(ub < up), (ub, up)
     assert ub.max() / ub.min() < 1.5, ub
     assert np.all((ub > 0.5e-5) & (ub < 5e-5)) and np.all((up > 1e-5) & (up < 1e-4)), (ub, up)
+
+
+def test_set_params_switches_force_form_and_validates(L):
+    """lbm3_set_params swaps the physical parameters of a live context (here
+    the force form and the tensions) and the next steps follow the oracle
+    with the new ones; a different grid, storage or an invalid form is
+    refused, as is the perturbation operator in a batch."""
+    nx, ny = 64, 40
+    rho = W.droplet_field(nx, ny, seed=9, count=4, rmin=4.0, rmax=8.0, gap=8.0)
+    p0 = L.Params(nx, ny, sigma=(0.01, 0.013, 0.007))
+    p1 = L.Params(nx, ny, sigma=(0.012, 0.009, 0.011), force_form=L.FORCE_PERTURBATION)
+    f0 = f32(O.step(oparams(p0), O.init(oparams(p0), rho), 3))
+    sim = L.Simulation(p0)
+    sim.set_populations(f0)
+    sim.set_params(p1)
+    sim.step(5)
+    err = relerr(sim.populations(), O.step(oparams(p1), f0, 5))
+    assert err <= 1e-5, err
+    for bad in (L.Params(nx + 4, ny), L.Params(nx, ny, storage=L.FP16_DEV), L.Params(nx, ny, force_form=3)):
+        with pytest.raises(L.Lbm3Error) as e:
+            L.lbm3_set_params(sim.ctx, bad)
+        assert e.value.status == L.EINVAL
+    sim.close()
+    with pytest.raises(L.Lbm3Error):
+        L.Batch([L.Params(128, 128, force_form=L.FORCE_PERTURBATION)])
+
+
+def test_phi_needs_fp32_storage(L):
+    sim = L.Simulation(L.Params(32, 32, storage=L.FP16_DEV))
+    sim.init(W.two_droplets(32, 32, R=5.0, c2=(8.0, 16.0), c3=(24.0, 16.0)))
+    with pytest.raises(L.Lbm3Error) as e:
+        sim.phi()
+    assert e.value.status == L.EINVAL
+    sim.close()
