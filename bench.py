@@ -321,6 +321,8 @@ def run_sweep(args):
     for sim in sims:
         sim.close()
     v = nodes * args.steps / (ms_batch / 1e3) / 1e6
+    peak, peak_kind = hbm_peak()
+    achieved = BYTES_PER_NODE * nodes / (ms_batch / 1e3 / args.steps) / 1e9
     return {"metric": "ternary D2Q9 MLUPS, batched morphology sweep (64 instances)", "value": round(v, 2),
             "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms_batch / args.steps, 5), "higher_is_better": True, "scaling": "weak",
@@ -329,6 +331,9 @@ def run_sweep(args):
                        "nodes_per_step": nodes, "work_items": work_items},
             "sequential_single_instance": {"value": round(nodes * args.steps / (ms_seq / 1e3) / 1e6, 2),
                                            "unit": "MLUPS", "ms_per_step": round(ms_seq / args.steps, 5)},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None, "bytes_per_node": BYTES_PER_NODE,
+                         "kernel": "fused_batch_kernel", "peak_source": peak_kind},
             "gpu_launches": args.steps}
 
 
@@ -372,7 +377,11 @@ def run_janus(args):
             "ms_per_step": out["fp16_dev"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 arithmetic, 16-bit deviation storage", "data": "synthetic",
             "config": {"workload": f"Janus droplet {n}x{n}, R={R:g}, sigma=0.010/0.008/0.012, tau=1"},
-            "storages": out, "gpu_launches": args.steps}
+            "storages": out,
+            "roofline": {"bound": "hbm", "achieved": round(132 * out["fp16_dev"]["MLUPS"] / 1e3, 1),
+                         "peak": peak, "unit": "GB/s", "frac": out["fp16_dev"]["hbm_frac"], "traffic": None,
+                         "bytes_per_node": 132, "kernel": "fused_step_kernel<FP16 deviations>"},
+            "gpu_launches": args.steps}
 
 
 def run_adjoint(args):
@@ -438,6 +447,15 @@ def run_adjoint(args):
             check = {"max_rel_err_dJ_dsigma_vs_oracle_differences":
                      float(max(abs(a / b - 1) for a, b in zip(res[1]["dJ_dsigma"], g["dJ_dsigma"])))}
     best = res[1]
+    peak, peak_kind = hbm_peak()
+    # algorithmic bytes per node-step of one evaluation with every state kept:
+    # 216 forward + 616 reverse (272 node VJP, 236 tension VJP + densities,
+    # 108 gradient VJP + grad phi and T of the next state)
+    achieved = 832 * best["MLUPS"] / 1e3
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "bytes_per_node": 832,
+                "kernel": "one gradient evaluation (fused step + three adjoint kernels per step)",
+                "peak_source": peak_kind}
     return {"metric": "ternary D2Q9 gradient evaluations: forward-run MLUPS through reverse mode",
             "value": best["MLUPS"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": best["ms_per_gradient"], "higher_is_better": True, "scaling": "weak",
@@ -446,7 +464,7 @@ def run_adjoint(args):
                                    f"J = sum (phi - phi_target)^2 after {horizon} steps, dJ/drho0 and dJ/dsigma",
                        "horizon_steps": horizon, "step": "one full gradient evaluation (recorded forward + reverse)",
                        "l2": "state 7 MB per step: L2-resident at this size"},
-            "checkpoint_every": {str(k): v for k, v in res.items()}, "checks": check,
+            "checkpoint_every": {str(k): v for k, v in res.items()}, "checks": check, "roofline": roofline,
             "gpu_launches": args.steps * (1 + horizon + 1 + 3 + 6 * horizon + 1)}
 
 
