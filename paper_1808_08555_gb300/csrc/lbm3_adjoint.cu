@@ -42,6 +42,18 @@ namespace {
 constexpr float kNormalDeltaA = 0.1f;  // recolouring normal G / max(|G|, 0.1 phi_k phi_l)
 constexpr int kAdjThreads = 256;
 
+// Programmatic dependent launch: the adjoint's kernels are launched with
+// programmatic stream serialisation, so a kernel's launch and prologue
+// overlap the tail of the one before it.  Each waits here until its
+// predecessor grid has completed and its writes are visible, then lets its
+// own successor launch.  The wait always ends: the predecessor does not wait
+// on this grid, and a successor starts only once every block of this grid is
+// resident.
+__device__ __forceinline__ void pdl_wait_then_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // periodic wrap of a coordinate at most one cell outside [0, n)
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
@@ -148,6 +160,7 @@ __device__ __forceinline__ void tension_fwd_node(const float* __restrict__ rho3,
 
 __global__ void __launch_bounds__(kAdjThreads) adj_density_kernel(const float* __restrict__ st,
                                                                   float* __restrict__ rho3, int nx, int ny) {
+  pdl_wait_then_release();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n < nx * ny) density_node(st, rho3, n, nx, ny);
 }
@@ -155,6 +168,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_density_kernel(const float* _
 __global__ void __launch_bounds__(kAdjThreads) adj_tension_fwd_kernel(const float* __restrict__ rho3,
                                                                       float* __restrict__ gphi,
                                                                       float* __restrict__ T, StepArgs a) {
+  pdl_wait_then_release();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n < a.nx * a.ny) tension_fwd_node(rho3, gphi, T, a, n);
 }
@@ -174,6 +188,7 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adj_node_kernel(const float* _
                                                                float* __restrict__ lam9, float* __restrict__ lamr,
                                                                float* __restrict__ lamg, float* __restrict__ lamF,
                                                                double* __restrict__ acc, StepArgs a) {
+  pdl_wait_then_release();
   const int nx = a.nx, ny = a.ny, N = nx * ny;
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   float dh0 = 0.0f, dh1 = 0.0f, dh2 = 0.0f;
@@ -451,6 +466,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_tension_kernel(const float* _
                                                                   double* __restrict__ acc, StepArgs a, int G,
                                                                   const float* __restrict__ st_next,
                                                                   float* __restrict__ rho3_next) {
+  pdl_wait_then_release();
   const int N = a.nx * a.ny;
   if (static_cast<int>(blockIdx.x) < G) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -471,6 +487,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_grad_kernel(const float* __re
                                                                const float* __restrict__ rho3_next,
                                                                float* __restrict__ gphi_next,
                                                                float* __restrict__ T_next) {
+  pdl_wait_then_release();
   const int N = a.nx * a.ny;
   if (static_cast<int>(blockIdx.x) < G) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -507,6 +524,7 @@ __global__ void phi_kernel(const float* __restrict__ st, double* __restrict__ ph
 // lamr_k = dJ/drho_k = (dphi_k - sum_m phi_m dphi_m) / rho, lam9 = 0.
 __global__ void adj_seed_kernel(const float* __restrict__ rho3, const double* __restrict__ dphi,
                                 float* __restrict__ lamr, float* __restrict__ lam9, int N) {
+  pdl_wait_then_release();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const double r[3] = {rho3[n], rho3[N + n], rho3[2 * N + n]};
@@ -545,6 +563,21 @@ __global__ void adj_drho_kernel(const float* __restrict__ lam9, const float* __r
 
 int blocks_for(int N) { return (N + kAdjThreads - 1) / kAdjThreads; }
 
+template <typename... K, typename... A>
+cudaError_t launch_pdl(void (*kernel)(K...), int grid, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kAdjThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<K>(args)...);
+}
+
 }  // namespace
 
 int adj_blocks(int N) { return blocks_for(N); }
@@ -576,16 +609,16 @@ cudaError_t launch_adj_seed(const float* st_final, const double* dphi, const Adj
                             cudaStream_t s) {
   const int N = nx * ny, g = blocks_for(N);
   float* scratch = b.rho3[1];
-  adj_density_kernel<<<g, kAdjThreads, 0, s>>>(st_final, scratch, nx, ny);
-  adj_seed_kernel<<<g, kAdjThreads, 0, s>>>(scratch, dphi, b.lamr[lam], b.lam9[lam], N);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(adj_density_kernel, g, s, st_final, scratch, nx, ny);
+  if (e == cudaSuccess) e = launch_pdl(adj_seed_kernel, g, s, scratch, dphi, b.lamr[lam], b.lam9[lam], N);
+  return e;
 }
 
 cudaError_t launch_adj_fields(const float* st, const StepArgs& a, const AdjBuffers& b, int slot, cudaStream_t s) {
   const int g = blocks_for(a.nx * a.ny);
-  adj_density_kernel<<<g, kAdjThreads, 0, s>>>(st, b.rho3[slot], a.nx, a.ny);
-  adj_tension_fwd_kernel<<<g, kAdjThreads, 0, s>>>(b.rho3[slot], b.gphi[slot], b.T[slot], a);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(adj_density_kernel, g, s, st, b.rho3[slot], a.nx, a.ny);
+  if (e == cudaSuccess) e = launch_pdl(adj_tension_fwd_kernel, g, s, b.rho3[slot], b.gphi[slot], b.T[slot], a);
+  return e;
 }
 
 cudaError_t launch_adj_step(const float* st_prev, const float* st_next, const StepArgs& a, const AdjBuffers& b,
@@ -593,13 +626,15 @@ cudaError_t launch_adj_step(const float* st_prev, const float* st_next, const St
   const int N = a.nx * a.ny, G = blocks_for(N);
   const int o = lam ^ 1, nslot = slot ^ 1;
   const int g2 = st_next ? 2 * G : G;
-  adj_node_kernel<<<G, kAdjThreads, 0, s>>>(st_prev, b.gphi[slot], b.T[slot], b.lam9[lam], b.lamr[lam], b.lam9[o],
-                                            b.lamr[o], b.lamg, b.lamF, acc, a);
-  adj_tension_kernel<<<g2, kAdjThreads, 0, s>>>(b.rho3[slot], b.gphi[slot], b.lamF, b.lamg, b.lamr[o], acc, a, G,
-                                                st_next, b.rho3[nslot]);
-  adj_grad_kernel<<<g2, kAdjThreads, 0, s>>>(b.rho3[slot], b.lamg, b.lamr[o], a, G, b.rho3[nslot], b.gphi[nslot],
-                                             b.T[nslot]);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(adj_node_kernel, G, s, st_prev, b.gphi[slot], b.T[slot], b.lam9[lam], b.lamr[lam],
+                             b.lam9[o], b.lamr[o], b.lamg, b.lamF, acc, a);
+  if (e == cudaSuccess)
+    e = launch_pdl(adj_tension_kernel, g2, s, b.rho3[slot], b.gphi[slot], b.lamF, b.lamg, b.lamr[o], acc, a, G, st_next,
+                   b.rho3[nslot]);
+  if (e == cudaSuccess)
+    e = launch_pdl(adj_grad_kernel, g2, s, b.rho3[slot], b.lamg, b.lamr[o], a, G, b.rho3[nslot], b.gphi[nslot],
+                   b.T[nslot]);
+  return e;
 }
 
 cudaError_t launch_adj_dpop(const AdjBuffers& b, int lam, double* out, int nx, int ny, int plane0, int nplanes,
