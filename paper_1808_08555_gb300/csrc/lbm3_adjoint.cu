@@ -120,7 +120,7 @@ __device__ __forceinline__ void tension_fwd_node(const float* __restrict__ rho3,
 #pragma unroll
   for (int j = 1; j < 9; ++j) {
     const int m = nbr(x, y, ex(j), ey(j), nx, ny);
-    const float r0 = rho3[m], r1 = rho3[N + m], r2 = rho3[2 * N + m];
+    const float r0 = rho3[m], r1 = rho3[static_cast<size_t>(N) + m], r2 = rho3[2 * static_cast<size_t>(N) + m];
     const float ir = 1.0f / (r0 + r1 + r2);
     const float c = 3.0f * wt(j);
     const float ph[3] = {r0 * ir, r1 * ir, r2 * ir};
@@ -130,7 +130,7 @@ __device__ __forceinline__ void tension_fwd_node(const float* __restrict__ rho3,
       gy[k] += c * ey(j) * ph[k];
     }
   }
-  const float rk[3] = {rho3[n], rho3[N + n], rho3[2 * N + n]};
+  const float rk[3] = {rho3[n], rho3[static_cast<size_t>(N) + n], rho3[2 * static_cast<size_t>(N) + n]};
   const float ir = 1.0f / (rk[0] + rk[1] + rk[2]);
   const float ph[3] = {rk[0] * ir, rk[1] * ir, rk[2] * ir};
   float txx = 0.0f, txy = 0.0f, tyy = 0.0f;
@@ -154,8 +154,8 @@ __device__ __forceinline__ void tension_fwd_node(const float* __restrict__ rho3,
     gphi[static_cast<size_t>(2 * k + 1) * N + n] = gy[k];
   }
   T[n] = txx;
-  T[N + n] = txy;
-  T[2 * N + n] = tyy;
+  T[static_cast<size_t>(N) + n] = txy;
+  T[2 * static_cast<size_t>(N) + n] = tyy;
 }
 
 __global__ void __launch_bounds__(kAdjThreads) adj_density_kernel(const float* __restrict__ st,
@@ -215,8 +215,8 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adj_node_kernel(const float* _
     for (int j = 1; j < 9; ++j) {
       const int m = nbr(x, y, ex(j), ey(j), nx, ny);
       const float c = 3.0f * wt(j);
-      Fx += c * (ex(j) * T[m] + ey(j) * T[N + m]);
-      Fy += c * (ex(j) * T[N + m] + ey(j) * T[2 * N + m]);
+      Fx += c * (ex(j) * T[m] + ey(j) * T[static_cast<size_t>(N) + m]);
+      Fy += c * (ex(j) * T[static_cast<size_t>(N) + m] + ey(j) * T[2 * static_cast<size_t>(N) + m]);
     }
     float mx = 0.0f, my = 0.0f;
 #pragma unroll
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adj_node_kernel(const float* _
       lamg[static_cast<size_t>(2 * k + 1) * N + n] = lgy[k];
     }
     lamF[n] = lFx;
-    lamF[N + n] = lFy;
+    lamF[static_cast<size_t>(N) + n] = lFy;
   }
   block_add3(dh0, dh1, dh2, acc + static_cast<size_t>(blockIdx.x) * 6 + 3);
 }
@@ -376,12 +376,12 @@ __device__ __forceinline__ void tension_vjp_node(const float* __restrict__ rho3,
 #pragma unroll
   for (int j = 1; j < 9; ++j) {
     const int m = nbr(x, y, -ex(j), -ey(j), nx, ny);
-    const float c = 3.0f * wt(j), Lx = lamF[m], Ly = lamF[N + m];
+    const float c = 3.0f * wt(j), Lx = lamF[m], Ly = lamF[static_cast<size_t>(N) + m];
     lxx += c * ex(j) * Lx;
     lxy += c * (ey(j) * Lx + ex(j) * Ly);
     lyy += c * ey(j) * Ly;
   }
-  const float rk[3] = {rho3[n], rho3[N + n], rho3[2 * N + n]};
+  const float rk[3] = {rho3[n], rho3[static_cast<size_t>(N) + n], rho3[2 * static_cast<size_t>(N) + n]};
   const float ir = 1.0f / (rk[0] + rk[1] + rk[2]);
   const float ph[3] = {rk[0] * ir, rk[1] * ir, rk[2] * ir};
   float gpx[3], gpy[3];
@@ -450,7 +450,7 @@ __device__ __forceinline__ void grad_vjp_node(const float* __restrict__ rho3, co
       lph[k] += c * (ex(j) * lamg[static_cast<size_t>(2 * k) * N + m] +
                      ey(j) * lamg[static_cast<size_t>(2 * k + 1) * N + m]);
   }
-  const float rk[3] = {rho3[n], rho3[N + n], rho3[2 * N + n]};
+  const float rk[3] = {rho3[n], rho3[static_cast<size_t>(N) + n], rho3[2 * static_cast<size_t>(N) + n]};
   const float ir = 1.0f / (rk[0] + rk[1] + rk[2]);
   const float sph = (rk[0] * lph[0] + rk[1] * lph[1] + rk[2] * lph[2]) * ir;
 #pragma unroll
@@ -527,9 +527,9 @@ __global__ void adj_seed_kernel(const float* __restrict__ rho3, const double* __
   pdl_wait_then_release();
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
-  const double r[3] = {rho3[n], rho3[N + n], rho3[2 * N + n]};
+  const double r[3] = {rho3[n], rho3[static_cast<size_t>(N) + n], rho3[2 * static_cast<size_t>(N) + n]};
   const double ir = 1.0 / (r[0] + r[1] + r[2]);
-  const double d[3] = {dphi[n], dphi[N + n], dphi[2 * static_cast<size_t>(N) + n]};
+  const double d[3] = {dphi[n], dphi[static_cast<size_t>(N) + n], dphi[2 * static_cast<size_t>(N) + n]};
   const double s = (r[0] * d[0] + r[1] * d[1] + r[2] * d[2]) * ir;
 #pragma unroll
   for (int k = 0; k < 3; ++k) lamr[static_cast<size_t>(k) * N + n] = static_cast<float>((d[k] - s) * ir);
