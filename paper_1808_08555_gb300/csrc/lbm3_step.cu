@@ -489,15 +489,21 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
     // each colour's nine values are stored, with their ghost copies, as soon
     // as they exist: shorter live ranges at the 96-register cap of two CTAs
     // per SM (2.6 % faster than storing all 27 at the end)
+    // (a node within kGhost columns of both edges, on grids narrower than
+    // 2 kGhost, gets both ghost copies)
     float* out = a.fout + off;
-    const int gsh = x < kGhost ? a.nx : (x >= a.nx - kGhost ? -a.nx : 0);
+    const bool glo = x < kGhost, ghi = x >= a.nx - kGhost;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) out[plane_of(k, i) * PS] = val[plane_of(k, i)];
-      if (gsh != 0) {
+      if (glo) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) out[plane_of(k, i) * PS + gsh] = val[plane_of(k, i)];
+        for (int i = 0; i < 9; ++i) out[plane_of(k, i) * PS + a.nx] = val[plane_of(k, i)];
+      }
+      if (ghi) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) out[plane_of(k, i) * PS - a.nx] = val[plane_of(k, i)];
       }
     }
   } else {
