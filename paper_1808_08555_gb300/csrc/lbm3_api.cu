@@ -108,6 +108,13 @@ lbm3_status validate(const lbm3_params* p, std::string* why) {
     *why = "lbm3: nx*ny must be below 2^31";
     return LBM3_EINVAL;
   }
+  // the step kernel addresses a population plane with a 32-bit byte stride
+  if (static_cast<double>(lbm3::pitch_of(p->nx)) * p->ny * 4.0 >= 4294967296.0) {
+    std::snprintf(b, sizeof b, "lbm3: grid %d x %d: one padded FP32 plane (%d x %d x 4 bytes) must be below 4 GiB",
+                  p->nx, p->ny, lbm3::pitch_of(p->nx), p->ny);
+    *why = b;
+    return LBM3_EINVAL;
+  }
   for (int k = 0; k < 3; ++k) {
     if (!(p->tau[k] > 0.5) || !std::isfinite(p->tau[k])) {
       std::snprintf(b, sizeof b, "lbm3: tau[%d] = %g must be > 0.5", k, p->tau[k]);

@@ -51,9 +51,9 @@ struct Smem {
   // pulled-row ring (row q in slot q % kSlots): three TMA boxes of 9 planes x
   // kPW columns, one per direction group, each starting on a 128-byte boundary
   float pop[kSlots][3 * kGroupFloats];
-  float phi[6][4][kDW];        // phi_1, phi_2, phi_3, rho of row q in slot q % 6
+  float4 phi[6][kDW];          // (phi_1, phi_2, phi_3, rho) of row q in slot q % 6
   float T[4][3][kTW];          // T_xx, T_xy, T_yy of row q in slot q % 4
-  float nrm[3][6][kTX];        // n_12, n_13, n_23 (x, y) of row q in slot q % 3
+  float2 nrm[3][3][kTX];       // (x, y) of n_12, n_13, n_23 of row q in slot q % 3
   unsigned long long full[kSlots];
   unsigned long long empty[kSlots];
   int abort_flag;
@@ -62,6 +62,16 @@ struct Smem {
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
+// Packed FP32 pairs (the f32x2 add / mul / fma of sm_100 and later): each
+// lane is rounded exactly as the scalar operation, so a pair of identical
+// scalar expressions is evaluated in one instruction.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
@@ -255,21 +265,17 @@ template <int ST>
 __device__ __forceinline__ void stage_density(Smem& s, int q, int c, const RingCols& rc) {
   const float* pp = s.pop[q % kSlots];
   const int wc = c + 2;
-  float r[3];
+  // rho_k = sum_i f_{i,k}: colours 1 and 2 as one packed pair, colour 3 alone
+  float2 r01 = make_float2(popv<ST>(pp, 0, 0, wc, rc), popv<ST>(pp, 1, 0, wc, rc));
+  float r2 = popv<ST>(pp, 2, 0, wc, rc);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    float acc = popv<ST>(pp, k, 0, wc, rc);
-#pragma unroll
-    for (int i = 1; i < 9; ++i) acc += popv<ST>(pp, k, i, wc - ex(i), rc);
-    r[k] = acc;
+  for (int i = 1; i < 9; ++i) {
+    r01 = add2(r01, make_float2(popv<ST>(pp, 0, i, wc - ex(i), rc), popv<ST>(pp, 1, i, wc - ex(i), rc)));
+    r2 += popv<ST>(pp, 2, i, wc - ex(i), rc);
   }
   float phk[3], rho;
-  colour_fractions(r[0], r[1], r[2], phk, &rho);
-  float(*ph)[kDW] = s.phi[q % 6];
-  ph[0][c] = phk[0];
-  ph[1][c] = phk[1];
-  ph[2][c] = phk[2];
-  ph[3][c] = rho;
+  colour_fractions(r01.x, r01.y, r2, phk, &rho);
+  s.phi[q % 6][c] = make_float4(phk[0], phk[1], phk[2], rho);
 }
 
 // T stage, one node: row q, T-window column c in [0, w+2), x = x0 - 1 + c.
@@ -279,31 +285,38 @@ __device__ __forceinline__ void stage_density(Smem& s, int q, int c, const RingC
 // B_i tr S) / tau_f at the node itself.
 template <int FORCE>
 __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q, int c, int w) {
-  const float(*pm)[kDW] = s.phi[(q - 1) % 6];
-  const float(*pz)[kDW] = s.phi[q % 6];
-  const float(*pq)[kDW] = s.phi[(q + 1) % 6];
+  const float4* pm = s.phi[(q - 1) % 6];
+  const float4* pz = s.phi[q % 6];
+  const float4* pq = s.phi[(q + 1) % 6];
   const int cc = c + 1;  // phi-window column of this node
-  float ph[3], gx[3], gy[3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const float W = pz[k][cc - 1], E = pz[k][cc + 1];
-    const float SW = pm[k][cc - 1], S = pm[k][cc], SE = pm[k][cc + 1];
-    const float NW = pq[k][cc - 1], Nn = pq[k][cc], NE = pq[k][cc + 1];
-    ph[k] = pz[k][cc];
-    // Eq. fd1 with 1/c_s^2 = 3: 3 (1/9) = 1/3 on the axes, 3 (1/36) = 1/12 on the diagonals
-    gx[k] = (1.0f / 3.0f) * (E - W) + (1.0f / 12.0f) * ((NE - NW) + (SE - SW));
-    gy[k] = (1.0f / 3.0f) * (Nn - S) + (1.0f / 12.0f) * ((NE + NW) - (SE + SW));
-  }
-  const float rho2 = pz[3][cc] * pz[3][cc];
+  // the nine (phi_1, phi_2, phi_3, rho) of the stencil, one vector load each;
+  // the gradients run on the packed pairs (phi_1, phi_2) and (phi_3, rho)
+  // (the rho lane is computed and dropped)
+  const float4 C = pz[cc], W = pz[cc - 1], E = pz[cc + 1];
+  const float4 SW = pm[cc - 1], S = pm[cc], SE = pm[cc + 1];
+  const float4 NW = pq[cc - 1], Nn = pq[cc], NE = pq[cc + 1];
+  auto lo = [](const float4& v) { return make_float2(v.x, v.y); };
+  auto hi = [](const float4& v) { return make_float2(v.z, v.w); };
+  // Eq. fd1 with 1/c_s^2 = 3: 3 (1/9) = 1/3 on the axes, 3 (1/36) = 1/12 on the diagonals
+  const float2 c3 = bc2(1.0f / 3.0f), c12 = bc2(1.0f / 12.0f);
+  const float2 gx01 = fma2(c12, add2(sub2(lo(NE), lo(NW)), sub2(lo(SE), lo(SW))), mul2(c3, sub2(lo(E), lo(W))));
+  const float2 gy01 = fma2(c12, sub2(add2(lo(NE), lo(NW)), add2(lo(SE), lo(SW))), mul2(c3, sub2(lo(Nn), lo(S))));
+  const float2 gx2r = fma2(c12, add2(sub2(hi(NE), hi(NW)), sub2(hi(SE), hi(SW))), mul2(c3, sub2(hi(E), hi(W))));
+  const float2 gy2r = fma2(c12, sub2(add2(hi(NE), hi(NW)), add2(hi(SE), hi(SW))), mul2(c3, sub2(hi(Nn), hi(S))));
+  const float ph[3] = {C.x, C.y, C.z};
+  const float gx[3] = {gx01.x, gx01.y, gx2r.x};
+  const float gy[3] = {gy01.x, gy01.y, gy2r.x};
+  const float rho2 = C.w * C.w;
   float txx = 0.0f, txy = 0.0f, tyy = 0.0f;
-  float nv[6];
+  float2 nv[3];
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
     const int k = p < 2 ? 0 : 1;
     const int l = p == 0 ? 1 : 2;
     // G_kl = phi_l grad phi_k - phi_k grad phi_l
-    const float Gx = ph[l] * gx[k] - ph[k] * gx[l];
-    const float Gy = ph[l] * gy[k] - ph[k] * gy[l];
+    const float2 G = fma2(bc2(ph[l]), make_float2(gx[k], gy[k]),
+                          neg2(mul2(bc2(ph[k]), make_float2(gx[l], gy[l]))));
+    const float Gx = G.x, Gy = G.y;
     const float g2 = Gx * Gx + Gy * Gy;
     const float pp = ph[k] * ph[l];
     float mag = 0.0f;
@@ -332,17 +345,16 @@ __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q,
     // and 0 at or below the |G| cutoff of the tension (no k-l interface)
     const float den = fmaxf(mag, kNormalDelta * pp);
     const float rden = g2 > 1e-30f ? __fdividef(1.0f, den) : 0.0f;  // |n| <= 1
-    nv[2 * p] = Gx * rden;
-    nv[2 * p + 1] = Gy * rden;
+    nv[p] = mul2(G, bc2(rden));
   }
   float(*Tt)[kTW] = s.T[q & 3];
   Tt[0][c] = txx;
   Tt[1][c] = txy;
   Tt[2][c] = tyy;
   if (c >= 1 && c <= w) {
-    float(*nn)[kTX] = s.nrm[q % 3];
+    float2(*nn)[kTX] = s.nrm[q % 3];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) nn[j][c - 1] = nv[j];
+    for (int p = 0; p < 3; ++p) nn[p][c - 1] = nv[p];
   }
 }
 
@@ -355,43 +367,46 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
   const float(*Tz)[kTW] = s.T[q & 3];
   const float(*Tp)[kTW] = s.T[(q + 1) & 3];
   // colour fractions and density from the D stage (the phi ring keeps six
-  // rows, so the next iteration's D stage writes other slots), and the total
-  // distribution f_i = sum_k f_{i,k} of the pulled populations
-  const float(*ph)[kDW] = s.phi[q % 6];
-  const float phi0 = ph[0][c + 2], phi1 = ph[1][c + 2], phi2 = ph[2][c + 2], rho = ph[3][c + 2];
+  // rows, so the next iteration's D stage writes other slots)
+  const float4 pr = s.phi[q % 6][c + 2];
+  const float phi0 = pr.x, phi1 = pr.y, phi2 = pr.z, rho = pr.w;
   const float phv[3] = {phi0, phi1, phi2};
   const float irho = __frcp_rn(rho);
-  float fi[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const int wc = c + 4 - ex(i);
-    fi[i] = (popv<ST>(pp, 0, i, wc, rc) + popv<ST>(pp, 1, i, wc, rc)) + popv<ST>(pp, 2, i, wc, rc);
-  }
-  // F_s = div T (Eq. 11), T window column of this node is c + 1; none with
-  // the perturbation operator, whose S is read at the node instead
+  // Total distribution f_i = sum_k f_{i,k} of the pulled populations, held
+  // in the packed pairs of directions (1, 2), (3, 4) = -(1, 2), (5, 6) and
+  // (7, 8) = -(5, 6): on these pairs e_i.v is (v_x, v_y), its negation,
+  // (v_x + v_y, v_y - v_x) or its negation, so the collision and the
+  // recolouring below run on pairs.
+  auto pull2 = [&](int k, int i, int j) {
+    return make_float2(popv<ST>(pp, k, i, c + 4 - ex(i), rc), popv<ST>(pp, k, j, c + 4 - ex(j), rc));
+  };
+  auto fsum2 = [&](int i, int j) { return add2(add2(pull2(0, i, j), pull2(1, i, j)), pull2(2, i, j)); };
+  const float f0 = (popv<ST>(pp, 0, 0, c + 4, rc) + popv<ST>(pp, 1, 0, c + 4, rc)) + popv<ST>(pp, 2, 0, c + 4, rc);
+  const float2 f12 = fsum2(1, 2), f34 = fsum2(3, 4), f56 = fsum2(5, 6), f78 = fsum2(7, 8);
+  // F_s = div T (Eq. 11) as the pair (F_x, F_y) = d_x (T_xx, T_xy) + d_y (T_xy, T_yy);
+  // T window column of this node is c + 1.  None with the perturbation
+  // operator, whose S is read at the node instead.
   const int tc = c + 1;
-  float Fx = 0.0f, Fy = 0.0f, Sxx = 0.0f, Sxy = 0.0f, Syy = 0.0f;
+  float2 F = make_float2(0.0f, 0.0f);
+  float Sxx = 0.0f, Sxy = 0.0f, Syy = 0.0f;
   if (FORCE == 1) {
     Sxx = Tz[0][tc];
     Sxy = Tz[1][tc];
     Syy = Tz[2][tc];
   } else {
-    const float xxW = Tz[0][tc - 1], xxE = Tz[0][tc + 1];
-    const float xxSW = Tm[0][tc - 1], xxSE = Tm[0][tc + 1], xxNW = Tp[0][tc - 1], xxNE = Tp[0][tc + 1];
-    const float xyW = Tz[1][tc - 1], xyE = Tz[1][tc + 1], xyS = Tm[1][tc], xyN = Tp[1][tc];
-    const float xySW = Tm[1][tc - 1], xySE = Tm[1][tc + 1], xyNW = Tp[1][tc - 1], xyNE = Tp[1][tc + 1];
-    const float yyS = Tm[2][tc], yyN = Tp[2][tc];
-    const float yySW = Tm[2][tc - 1], yySE = Tm[2][tc + 1], yyNW = Tp[2][tc - 1], yyNE = Tp[2][tc + 1];
-    Fx = (1.0f / 3.0f) * ((xxE - xxW) + (xyN - xyS)) +
-         (1.0f / 12.0f) * (((xxNE - xxNW) + (xxSE - xxSW)) + ((xyNE + xyNW) - (xySE + xySW)));
-    Fy = (1.0f / 3.0f) * ((xyE - xyW) + (yyN - yyS)) +
-         (1.0f / 12.0f) * (((xyNE - xyNW) + (xySE - xySW)) + ((yyNE + yyNW) - (yySE + yySW)));
+    auto A = [](const float (*T)[kTW], int col) { return make_float2(T[0][col], T[1][col]); };
+    auto B = [](const float (*T)[kTW], int col) { return make_float2(T[1][col], T[2][col]); };
+    const float2 axis = add2(sub2(A(Tz, tc + 1), A(Tz, tc - 1)), sub2(B(Tp, tc), B(Tm, tc)));
+    const float2 diag = add2(add2(sub2(A(Tp, tc + 1), A(Tp, tc - 1)), sub2(A(Tm, tc + 1), A(Tm, tc - 1))),
+                             sub2(add2(B(Tp, tc + 1), B(Tp, tc - 1)), add2(B(Tm, tc + 1), B(Tm, tc - 1))));
+    F = fma2(bc2(1.0f / 12.0f), diag, mul2(bc2(1.0f / 3.0f), axis));
   }
-  const float mx = (fi[1] - fi[3]) + (fi[5] - fi[6]) + (fi[8] - fi[7]);
-  const float my = (fi[2] - fi[4]) + (fi[5] - fi[8]) + (fi[6] - fi[7]);
+  // momentum sum_i f_i e_i: (f_1 - f_3, f_2 - f_4) + (f_5 - f_7) (1, 1) + (f_6 - f_8) (-1, 1)
+  const float2 d13 = sub2(f12, f34), d57 = sub2(f56, f78);
+  const float2 m = add2(d13, make_float2(d57.x - d57.y, d57.x + d57.y));
   // Eq. uk1
-  const float ux = fmaf(0.5f, Fx, mx) * irho;
-  const float uy = fmaf(0.5f, Fy, my) * irho;
+  const float2 u = mul2(fma2(bc2(0.5f), F, m), bc2(irho));
+  const float ux = u.x, uy = u.y, Fx = F.x, Fy = F.y;
   const int x = x0 + c, y = y0 - 2 + q;
   if (MODE == MODE_FIELDS) {
     const size_t N = static_cast<size_t>(a.nx) * a.ny;
@@ -424,64 +439,75 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
   const float g9 = 9.0f * g;
   const float gm3uF = -3.0f * g * uF;
   const float omr = om * rho;
-  float fd[9];
   // perturbation operator (FORCE 1): Phi_i = om (w_i e_i.S.e_i - B_i tr S),
   // even in e_i, with Leclaire's B_1-4 = 2/27, B_5-8 = 5/108; Phi_0 is the
   // negated sum of the others (-om B_0 tr S in exact arithmetic, as
   // sum_i B_i = 1/3), so the operator moves no mass in FP32 either
   const float trS = Sxx + Syy;
   float phisum = 0.0f;
+  float2 fd12, fd34, fd56, fd78;
 #pragma unroll
-  for (int i = 1; i <= 6; ++i) {
-    if (i == 3 || i == 4) continue;  // pairs (1,3), (2,4), (5,7), (6,8)
-    const int o = (i == 1) ? 3 : (i == 2) ? 4 : (i == 5) ? 7 : 8;
-    const float eu = ex(i) * ux + ey(i) * uy;
-    const float eF = ex(i) * Fx + ey(i) * Fy;
-    float S = wt(i) * (fmaf(c1 * eu, eu, c0) + fmaf(g9 * eu, eF, gm3uF));
+  for (int d = 0; d < 2; ++d) {  // d = 0: axis pairs (1, 2) / (3, 4); d = 1: diagonal pairs (5, 6) / (7, 8)
+    const float w = wt(d == 0 ? 1 : 5);
+    const float2 eu = d == 0 ? u : make_float2(ux + uy, uy - ux);
+    const float2 eF = d == 0 ? F : make_float2(Fx + Fy, Fy - Fx);
+    float2 S = mul2(bc2(w), add2(fma2(mul2(bc2(c1), eu), eu, bc2(c0)), fma2(mul2(bc2(g9), eu), eF, bc2(gm3uF))));
     if (FORCE == 1) {
-      const float eSe = (ex(i) * ex(i)) * Sxx + (2.0f * ex(i) * ey(i)) * Sxy + (ey(i) * ey(i)) * Syy;
-      const float Bi = i <= 4 ? 2.0f / 27.0f : 5.0f / 108.0f;
-      const float ph = om * fmaf(wt(i), eSe, -Bi * trS);
-      S += ph;
-      phisum += 2.0f * ph;
+      const float2 eSe = d == 0 ? make_float2(Sxx, Syy) : make_float2(trS + 2.0f * Sxy, trS - 2.0f * Sxy);
+      const float Bi = d == 0 ? 2.0f / 27.0f : 5.0f / 108.0f;
+      const float2 ph = mul2(bc2(om), fma2(bc2(w), eSe, bc2(-Bi * trS)));
+      S = add2(S, ph);
+      phisum += 2.0f * ph.x + 2.0f * ph.y;
     }
-    const float A = 3.0f * wt(i) * fmaf(omr, eu, g * eF);
-    const float wr = wt(i) * rho;
-    fd[i] = fi[i] + fmaf(om, wr - fi[i], S + A);
-    fd[o] = fi[o] + fmaf(om, wr - fi[o], S - A);
+    const float2 A = mul2(bc2(3.0f * w), fma2(bc2(omr), eu, mul2(bc2(g), eF)));
+    const float2 wr = bc2(w * rho);
+    const float2 fp = d == 0 ? f12 : f56, fn = d == 0 ? f34 : f78;
+    const float2 dp = add2(fp, fma2(bc2(om), sub2(wr, fp), add2(S, A)));
+    const float2 dn = add2(fn, fma2(bc2(om), sub2(wr, fn), sub2(S, A)));
+    if (d == 0) {
+      fd12 = dp;
+      fd34 = dn;
+    } else {
+      fd56 = dp;
+      fd78 = dn;
+    }
   }
-  fd[0] = fi[0] + fmaf(om, fmaf(wt(0), rho, -fi[0]), wt(0) * (c0 + gm3uF) - phisum);
+  const float fd0 = f0 + fmaf(om, fmaf(wt(0), rho, -f0), wt(0) * (c0 + gm3uF) - phisum);
   // segregation parameters beta_kl (pairs 12, 13, 23); prod = rho_1 rho_2 rho_3 / rho^3
   const float cb = fminf(a.beta_A * (phi0 * phi1 * phi2), 1.0f);
-  const float(*nn)[kTX] = s.nrm[q % 3];
-  float Rx[3], Ry[3];
+  const float2(*nn)[kTX] = s.nrm[q % 3];
+  float2 R[3];
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
     const int k = p < 2 ? 0 : 1;
     const int l = p == 0 ? 1 : 2;
     const float b = a.beta0 * fmaf(cb, a.beta_h[p], 1.0f);
     const float amp = b * (phv[k] * phv[l]) * rho;  // beta_kl rho_k rho_l / rho
-    Rx[p] = amp * nn[2 * p][c];
-    Ry[p] = amp * nn[2 * p + 1][c];
+    R[p] = mul2(bc2(amp), nn[p][c]);
   }
   // V_k = sum_{l != k} beta_kl (rho_k rho_l / rho) n_kl, with n_lk = -n_kl
-  const float Vx[3] = {Rx[0] + Rx[1], Rx[2] - Rx[0], -Rx[1] - Rx[2]};
-  const float Vy[3] = {Ry[0] + Ry[1], Ry[2] - Ry[0], -Ry[1] - Ry[2]};
+  const float2 V[3] = {add2(R[0], R[1]), sub2(R[2], R[0]), neg2(add2(R[1], R[2]))};
   // Eq. 6: f^ddagger_{i,k} = phi_k f^dagger_i + w'_i (e_i . V_k), stored at
   // padded column x + 4 and, for the four columns next to each edge, also in
   // the ghost column on the opposite side
+  const float2 wa = make_float2(a.wrec[1], a.wrec[2]), wd = make_float2(a.wrec[5], a.wrec[6]);
   float val[27];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    val[plane_of(k, 0)] = phv[k] * fd[0];
-#pragma unroll
-    for (int i = 1; i <= 6; ++i) {
-      if (i == 3 || i == 4) continue;
-      const int o = (i == 1) ? 3 : (i == 2) ? 4 : (i == 5) ? 7 : 8;
-      const float t = a.wrec[i] * (ex(i) * Vx[k] + ey(i) * Vy[k]);
-      val[plane_of(k, i)] = fmaf(phv[k], fd[i], t);
-      val[plane_of(k, o)] = fmaf(phv[k], fd[o], -t);
-    }
+    const float2 pk = bc2(phv[k]);
+    const float2 ta = mul2(wa, V[k]);                                          // e_1.V, e_2.V
+    const float2 td = mul2(wd, make_float2(V[k].x + V[k].y, V[k].y - V[k].x));  // e_5.V, e_6.V
+    const float2 v12 = fma2(pk, fd12, ta), v34 = fma2(pk, fd34, neg2(ta));
+    const float2 v56 = fma2(pk, fd56, td), v78 = fma2(pk, fd78, neg2(td));
+    val[plane_of(k, 0)] = phv[k] * fd0;
+    val[plane_of(k, 1)] = v12.x;
+    val[plane_of(k, 2)] = v12.y;
+    val[plane_of(k, 3)] = v34.x;
+    val[plane_of(k, 4)] = v34.y;
+    val[plane_of(k, 5)] = v56.x;
+    val[plane_of(k, 6)] = v56.y;
+    val[plane_of(k, 7)] = v78.x;
+    val[plane_of(k, 8)] = v78.y;
   }
   const size_t PS = static_cast<size_t>(a.ny) * a.pitch;  // plane stride
   const size_t off = static_cast<size_t>(y) * a.pitch + (x + kGhost);
@@ -491,19 +517,27 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
     // per SM (2.6 % faster than storing all 27 at the end)
     // (a node within kGhost columns of both edges, on grids narrower than
     // 2 kGhost, gets both ghost copies)
-    float* out = a.fout + off;
+    // plane stride in bytes: below 2^32 (checked when a context is created),
+    // so each plane's address is one 32 x 32 -> 64-bit multiply-add
+    const unsigned psb = static_cast<unsigned>(a.ny) * static_cast<unsigned>(a.pitch) * 4u;
+    char* out = reinterpret_cast<char*>(a.fout + off);
+    auto st = [psb](char* base, int p, float v) {
+      *reinterpret_cast<float*>(base + static_cast<unsigned long long>(p) * psb) = v;
+    };
     const bool glo = x < kGhost, ghi = x >= a.nx - kGhost;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
 #pragma unroll
-      for (int i = 0; i < 9; ++i) out[plane_of(k, i) * PS] = val[plane_of(k, i)];
+      for (int i = 0; i < 9; ++i) st(out, plane_of(k, i), val[plane_of(k, i)]);
       if (glo) {
+        char* o2 = out + 4 * static_cast<ptrdiff_t>(a.nx);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) out[plane_of(k, i) * PS + a.nx] = val[plane_of(k, i)];
+        for (int i = 0; i < 9; ++i) st(o2, plane_of(k, i), val[plane_of(k, i)]);
       }
       if (ghi) {
+        char* o2 = out - 4 * static_cast<ptrdiff_t>(a.nx);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) out[plane_of(k, i) * PS - a.nx] = val[plane_of(k, i)];
+        for (int i = 0; i < 9; ++i) st(o2, plane_of(k, i), val[plane_of(k, i)]);
       }
     }
   } else {

@@ -47,6 +47,8 @@ def test_params_struct_layout_matches_header():
     dict(nx=8, ny=8, beta0=0.0), dict(nx=8, ny=8, beta0=1.5), dict(nx=8, ny=8, beta_form=7),
     dict(nx=8, ny=8, recolor_form=2), dict(nx=8, ny=8, storage=9), dict(nx=8, ny=8, storage=-1),
     dict(nx=8, ny=8, force_form=2), dict(nx=8, ny=8, force_form=-1), dict(nx=8, ny=8, force_form=1, storage=1),
+    # nx*ny below 2^31, but one padded FP32 plane reaches 4 GiB
+    dict(nx=4, ny=2 ** 28), dict(nx=32768, ny=32768),
 ])
 def test_invalid_params_rejected(lib, kw):
     with pytest.raises(L.Lbm3Error) as e:
@@ -62,6 +64,11 @@ def test_buffer_bytes(lib):
     # 16-bit deviations plus three FP32 rho' planes
     assert L.lbm3_buffer_bytes(L.Params(2048, 2048, storage=1)) == (27 * 2 + 3 * 4) * 2048 * 2056
     assert L.lbm3_buffer_bytes(L.Params(2048, 2048, storage=2)) == (27 * 2 + 3 * 4) * 2048 * 2056
+
+
+def test_largest_plane_accepted(lib):
+    # 32768 x 32760 x 4 bytes per padded plane: just below the 4 GiB plane limit
+    assert L.lbm3_buffer_bytes(L.Params(32760, 32760)) == 27 * 32760 * 32768 * 4
 
 
 def test_null_context_is_einval(lib):

@@ -79,9 +79,13 @@ def test_mass_conserved_by_storage(L, storage):
 
 @pytest.mark.parametrize("storage", [1, 2])
 def test_laplace_pressure_matches_fp32(L, storage):
-    """A relaxing droplet (48^2, R = 10): the pressure jump of the 16-bit
-    run equals the FP32 run's to 1 % after 3000 steps."""
-    n, R, sig = 48, 10.0, 0.01
+    """A droplet relaxed to equilibrium (48^2, R = 12, 6000 steps; its FP32
+    pressure jump changes by < 0.1 % between 3000 and 6000 steps): the 16-bit
+    run's jump equals the FP32 run's within 16 rounding units u of the
+    storage, the per-unit bound of the 512^2 Janus comparison.  (Taken
+    mid-relaxation, the gap follows each run's rounding trajectory: 1.5 % at
+    R = 10 after 3000 steps, while Delta p itself still moved by 7 %.)"""
+    n, R, sig = 48, 12.0, 0.01
     rho = W.compound_droplet(n, n, 0.0, R)
     rho[2] = 0.0
     rho[0] = 1.0 - rho[1]
@@ -92,11 +96,11 @@ def test_laplace_pressure_matches_fp32(L, storage):
     for st in (0, storage):
         sim = L.Simulation(L.Params(n, n, sigma=(sig, sig, sig), storage=st))
         sim.init(rho)
-        sim.step(3000)
+        sim.step(6000)
         pr = sim.fields()["p"]
         sim.close()
         dps[st] = pr[inside].mean() - pr[outside].mean()
-    assert dps[storage] == pytest.approx(dps[0], rel=0.01), dps
+    assert dps[storage] == pytest.approx(dps[0], rel=16 * UNIT[storage]), dps
 
 
 @pytest.mark.parametrize("storage", [1, 2])
