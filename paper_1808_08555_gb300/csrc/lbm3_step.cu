@@ -72,6 +72,13 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+// hardware reciprocal estimate (rcp.approx: at most 1 ulp off; rho is never
+// denormal), one instruction
+__device__ __forceinline__ float rcp_est(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
@@ -111,8 +118,8 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 // Bounded wait for the phase with the given parity.  Returns false (after
 // flagging the error and the CTA abort) if it did not complete in kWaitNs or
 // another thread of the CTA already aborted.
-__device__ bool mbar_wait(unsigned long long* bar, uint32_t parity, volatile int* abort_flag,
-                          unsigned int* err) {
+__device__ __noinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity, volatile int* abort_flag,
+                                       unsigned int* err) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (unsigned it = 1;; ++it) {
@@ -238,11 +245,12 @@ __device__ void produce(Smem& s, const StepArgs& a, const CUtensorMap* map, cons
 // complement of the two others.  With plain products rho_k * (1/rho) a pure
 // node gets 1 +- 1 ulp, always with the same sign for the same density, and
 // the recolouring then creates or destroys that fluid's mass at a steady
-// ~1e-8 relative per step.  Shared by the D and C stages so both see
-// bit-identical fractions.  Returns 1/rho (correctly rounded).
-__device__ __forceinline__ float colour_fractions(float r0, float r1, float r2, float* p, float* rho_out) {
+// ~1e-8 relative per step.  The complement makes the sum exact whatever the
+// rounding of 1/rho, so the hardware estimate serves.  Computed once per
+// node (D stage) and read from the phi ring by the later stages.
+__device__ __forceinline__ void colour_fractions(float r0, float r1, float r2, float* p, float* rho_out) {
   const float rho = (r0 + r1) + r2;
-  const float ir = __frcp_rn(rho);
+  const float ir = rcp_est(rho);
   float p0 = r0 * ir, p1 = r1 * ir, p2 = r2 * ir;
   if (r0 >= r1 && r0 >= r2) {
     p0 = (1.0f - p1) - p2;
@@ -255,7 +263,6 @@ __device__ __forceinline__ float colour_fractions(float r0, float r1, float r2, 
   p[1] = p1;
   p[2] = p2;
   *rho_out = rho;
-  return ir;
 }
 
 // D stage, one node: row q (window slot), density column c in [0, w+4), i.e.
@@ -371,7 +378,7 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
   const float4 pr = s.phi[q % 6][c + 2];
   const float phi0 = pr.x, phi1 = pr.y, phi2 = pr.z, rho = pr.w;
   const float phv[3] = {phi0, phi1, phi2};
-  const float irho = __frcp_rn(rho);
+  const float irho = rcp_est(rho);
   // Total distribution f_i = sum_k f_{i,k} of the pulled populations, held
   // in the packed pairs of directions (1, 2), (3, 4) = -(1, 2), (5, 6) and
   // (7, 8) = -(5, 6): on these pairs e_i.v is (v_x, v_y), its negation,
@@ -529,15 +536,17 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
     for (int k = 0; k < 3; ++k) {
 #pragma unroll
       for (int i = 0; i < 9; ++i) st(out, plane_of(k, i), val[plane_of(k, i)]);
-      if (glo) {
-        char* o2 = out + 4 * static_cast<ptrdiff_t>(a.nx);
+      if (glo || ghi) {
+        if (glo) {
+          char* o2 = out + 4 * static_cast<ptrdiff_t>(a.nx);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) st(o2, plane_of(k, i), val[plane_of(k, i)]);
-      }
-      if (ghi) {
-        char* o2 = out - 4 * static_cast<ptrdiff_t>(a.nx);
+          for (int i = 0; i < 9; ++i) st(o2, plane_of(k, i), val[plane_of(k, i)]);
+        }
+        if (ghi) {
+          char* o2 = out - 4 * static_cast<ptrdiff_t>(a.nx);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) st(o2, plane_of(k, i), val[plane_of(k, i)]);
+          for (int i = 0; i < 9; ++i) st(o2, plane_of(k, i), val[plane_of(k, i)]);
+        }
       }
     }
   } else {
@@ -581,6 +590,10 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
   }
 }
 
+// Every tile is at most kTX columns wide (single grid: strips of kTX and a
+// narrower last one; batches: strip_x0() with ceil(nx / kTX) strips), so each
+// stage has at most 2 (kTX + 4) = 256 nodes per pair of rows: one per
+// consumer thread.
 template <int MODE, int ST, int FORCE>
 __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h, int tid) {
   const int nq = h + 4;  // rows q = 0 .. h+3 <-> y = y0-2 .. y0+h+1
@@ -595,18 +608,13 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
       const int nr = min(2, nq - q0);
       for (int r = 0; r < nr && !dead; ++r) {
         const int q = q0 + r;
-        dead = !mbar_wait(&s.full[q % kSlots], static_cast<uint32_t>((q / kSlots) & 1), abort_flag, a.err);
+        const uint32_t par = static_cast<uint32_t>((q / kSlots) & 1);
+        if (!mbar_try_wait(&s.full[q % kSlots], par)) dead = !mbar_wait(&s.full[q % kSlots], par, abort_flag, a.err);
       }
-      if (!dead && nr > 0) {
+      if (!dead && tid < nr * (w + 4)) {
         const int W = w + 4;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int it = tid + u * kConsumers;
-          if (it < nr * W) {
-            const int r = it >= W ? 1 : 0;
-            stage_density<ST>(s, q0 + r, it - r * W, rc);
-          }
-        }
+        const int r = tid >= W ? 1 : 0;
+        stage_density<ST>(s, q0 + r, tid - r * W, rc);
       }
     }
     consumers_sync();
@@ -614,16 +622,10 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
     if (!dead) {
       const int qa = max(2 * j - 1, 1), qb = min(2 * j, nq - 2);
       const int nr = qb - qa + 1;
-      if (nr > 0) {
+      if (tid < nr * (w + 2)) {  // at most 252 nodes
         const int W = w + 2;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int it = tid + u * kConsumers;
-          if (it < nr * W) {
-            const int r = it >= W ? 1 : 0;
-            stage_tension<FORCE>(s, a, qa + r, it - r * W, w);
-          }
-        }
+        const int r = tid >= W ? 1 : 0;
+        stage_tension<FORCE>(s, a, qa + r, tid - r * W, w);
       }
     }
     consumers_sync();
@@ -631,11 +633,9 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
     if (!dead) {
       const int qa = max(2 * j - 2, 2), qb = min(2 * j - 1, h + 1);
       const int nr = qb - qa + 1;
-      if (nr > 0) {
-        for (int it = tid; it < nr * w; it += kConsumers) {
-          const int r = it >= w ? 1 : 0;
-          stage_collide<MODE, ST, FORCE>(s, a, qa + r, it - r * w, x0, y0, rc);
-        }
+      if (tid < nr * w) {  // at most 248 nodes
+        const int r = tid >= w ? 1 : 0;
+        stage_collide<MODE, ST, FORCE>(s, a, qa + r, tid - r * w, x0, y0, rc);
       }
     }
     // release the population rows the C stage finished with (rows 0 and 1
