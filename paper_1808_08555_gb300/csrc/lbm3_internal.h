@@ -89,7 +89,7 @@ static_assert(3 * kDevGroupHalfs * 2 + 3 * kRhoGroupFloats * 4 <= 3 * kGroupFloa
               "a 16-bit slot must fit in an FP32 slot");
 constexpr int kDW = kTX + 4;      // density/phi window:     x0-2 .. x0+w+2
 constexpr int kTW = kTX + 2;      // tension-tensor window:  x0-1 .. x0+w+1
-constexpr int kSlots = 6;         // population ring depth (rows)
+constexpr int kSlots = 4;         // population ring depth (rows): a row is free again after its D stage
 constexpr int kConsumers = 256;   // 8 compute warps: one C-stage node each per pair of rows
 constexpr int kThreads = kConsumers + 32;  // + 1 copy-issuing warp
 

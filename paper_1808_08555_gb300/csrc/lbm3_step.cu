@@ -20,7 +20,10 @@
 // (cp.async.bulk.tensor + mbarrier complete_tx): per row three boxes of
 // 9 planes x 132 columns, issued by one producer warp into a ring of kSlots
 // rows; eight consumer warps run the stages in lock step (two named barriers
-// per pair of rows).  HBM traffic is one read and one write of
+// per pair of rows).  Only the D stage reads a population row: it also
+// leaves the node's total distribution f_i = sum_k f_{i,k} in a ring of its
+// own for the C stage, so each population row is released as soon as its D
+// stage is done and the loads run almost two iterations ahead.  HBM traffic is one read and one write of
 // the 27 populations per node; halo re-reads of neighbouring strips' columns
 // are served by L2.
 //
@@ -52,6 +55,8 @@ struct Smem {
   // kPW columns, one per direction group, each starting on a 128-byte boundary
   float pop[kSlots][3 * kGroupFloats];
   float4 phi[6][kDW];          // (phi_1, phi_2, phi_3, rho) of row q in slot q % 6
+  float2 fi2[6][4][kTX];       // (f_1, f_2), (f_3, f_4), (f_5, f_6), (f_7, f_8) of row q in slot q % 6
+  float fi0[6][kTX];           // f_0 of row q in slot q % 6
   float T[4][3][kTW];          // T_xx, T_xy, T_yy of row q in slot q % 4
   float2 nrm[3][3][kTX];       // (x, y) of n_12, n_13, n_23 of row q in slot q % 3
   unsigned long long full[kSlots];
@@ -267,22 +272,38 @@ __device__ __forceinline__ void colour_fractions(float r0, float r1, float r2, f
 
 // D stage, one node: row q (window slot), density column c in [0, w+4), i.e.
 // x = x0 - 2 + c.  The pulled value of direction i sits at window column
-// c + 2 - e_ix of row q's slot.
+// c + 2 - e_ix of row q's slot.  The 27 values are held as packed pairs of
+// directions (1, 2), (3, 4), (5, 6), (7, 8) per colour: rho_k sums a colour's
+// pairs, f_i = sum_k f_{i,k} sums the colours of a pair.  Nodes of the
+// strip itself (c in [2, w+2)) leave f_i in the f ring for the C stage.
 template <int ST>
-__device__ __forceinline__ void stage_density(Smem& s, int q, int c, const RingCols& rc) {
+__device__ __forceinline__ void stage_density(Smem& s, int q, int c, int w, const RingCols& rc) {
   const float* pp = s.pop[q % kSlots];
   const int wc = c + 2;
-  // rho_k = sum_i f_{i,k}: colours 1 and 2 as one packed pair, colour 3 alone
-  float2 r01 = make_float2(popv<ST>(pp, 0, 0, wc, rc), popv<ST>(pp, 1, 0, wc, rc));
-  float r2 = popv<ST>(pp, 2, 0, wc, rc);
+  float f0[3], r[3];
+  float2 F[4];  // per pair of directions: sum over the colours so far
 #pragma unroll
-  for (int i = 1; i < 9; ++i) {
-    r01 = add2(r01, make_float2(popv<ST>(pp, 0, i, wc - ex(i), rc), popv<ST>(pp, 1, i, wc - ex(i), rc)));
-    r2 += popv<ST>(pp, 2, i, wc - ex(i), rc);
+  for (int k = 0; k < 3; ++k) {
+    f0[k] = popv<ST>(pp, k, 0, wc, rc);
+    float2 A;  // running sum of this colour's pairs
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int i = 2 * m + 1, j = 2 * m + 2;
+      const float2 P = make_float2(popv<ST>(pp, k, i, wc - ex(i), rc), popv<ST>(pp, k, j, wc - ex(j), rc));
+      A = m == 0 ? P : add2(A, P);
+      F[m] = k == 0 ? P : add2(F[m], P);
+    }
+    r[k] = f0[k] + (A.x + A.y);
   }
   float phk[3], rho;
-  colour_fractions(r01.x, r01.y, r2, phk, &rho);
-  s.phi[q % 6][c] = make_float4(phk[0], phk[1], phk[2], rho);
+  colour_fractions(r[0], r[1], r[2], phk, &rho);
+  const int fs = q % 6;
+  s.phi[fs][c] = make_float4(phk[0], phk[1], phk[2], rho);
+  if (c >= 2 && c < w + 2) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) s.fi2[fs][m][c - 2] = F[m];
+    s.fi0[fs][c - 2] = (f0[0] + f0[1]) + f0[2];
+  }
 }
 
 // T stage, one node: row q, T-window column c in [0, w+2), x = x0 - 1 + c.
@@ -369,27 +390,23 @@ __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q,
 template <int MODE, int ST, int FORCE>
 __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q, int c, int x0, int y0,
                                               const RingCols& rc) {
-  const float* pp = s.pop[q % kSlots];
   const float(*Tm)[kTW] = s.T[(q - 1) & 3];
   const float(*Tz)[kTW] = s.T[q & 3];
   const float(*Tp)[kTW] = s.T[(q + 1) & 3];
-  // colour fractions and density from the D stage (the phi ring keeps six
-  // rows, so the next iteration's D stage writes other slots)
+  // colour fractions and density from the D stage (the phi and f rings keep
+  // six rows, so the next iteration's D stage writes other slots)
   const float4 pr = s.phi[q % 6][c + 2];
   const float phi0 = pr.x, phi1 = pr.y, phi2 = pr.z, rho = pr.w;
   const float phv[3] = {phi0, phi1, phi2};
   const float irho = rcp_est(rho);
-  // Total distribution f_i = sum_k f_{i,k} of the pulled populations, held
-  // in the packed pairs of directions (1, 2), (3, 4) = -(1, 2), (5, 6) and
-  // (7, 8) = -(5, 6): on these pairs e_i.v is (v_x, v_y), its negation,
-  // (v_x + v_y, v_y - v_x) or its negation, so the collision and the
-  // recolouring below run on pairs.
-  auto pull2 = [&](int k, int i, int j) {
-    return make_float2(popv<ST>(pp, k, i, c + 4 - ex(i), rc), popv<ST>(pp, k, j, c + 4 - ex(j), rc));
-  };
-  auto fsum2 = [&](int i, int j) { return add2(add2(pull2(0, i, j), pull2(1, i, j)), pull2(2, i, j)); };
-  const float f0 = (popv<ST>(pp, 0, 0, c + 4, rc) + popv<ST>(pp, 1, 0, c + 4, rc)) + popv<ST>(pp, 2, 0, c + 4, rc);
-  const float2 f12 = fsum2(1, 2), f34 = fsum2(3, 4), f56 = fsum2(5, 6), f78 = fsum2(7, 8);
+  // Total distribution f_i = sum_k f_{i,k} of the pulled populations (D
+  // stage), in the packed pairs of directions (1, 2), (3, 4) = -(1, 2),
+  // (5, 6) and (7, 8) = -(5, 6): on these pairs e_i.v is (v_x, v_y), its
+  // negation, (v_x + v_y, v_y - v_x) or its negation, so the collision and
+  // the recolouring below run on pairs.
+  const int fs = q % 6;
+  const float f0 = s.fi0[fs][c];
+  const float2 f12 = s.fi2[fs][0][c], f34 = s.fi2[fs][1][c], f56 = s.fi2[fs][2][c], f78 = s.fi2[fs][3][c];
   // F_s = div T (Eq. 11) as the pair (F_x, F_y) = d_x (T_xx, T_xy) + d_y (T_xy, T_yy);
   // T window column of this node is c + 1.  None with the perturbation
   // operator, whose S is read at the node instead.
@@ -516,7 +533,6 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
     val[plane_of(k, 7)] = v78.x;
     val[plane_of(k, 8)] = v78.y;
   }
-  const size_t PS = static_cast<size_t>(a.ny) * a.pitch;  // plane stride
   const size_t off = static_cast<size_t>(y) * a.pitch + (x + kGhost);
   if (ST == ST_FP32) {
     // each colour's nine values are stored, with their ghost copies, as soon
@@ -553,39 +569,49 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
     // Encode each colour as rho'_k and 16-bit deviations d_i = f_i - w_i rho_k
     // (rho_k = sum_i f_i): rho'_k absorbs the rounding of the nine d_i, so
     // sum_i (w_i rho'_k + d_i) = rho_k and the colour mass survives storage.
-    unsigned short code[27];
-    float rp[3];
+    // Each colour is encoded and stored (with its ghost copies) as soon as
+    // its nine values exist, as in the FP32 path; plane strides in bytes as
+    // there (a 16-bit plane is half an FP32 plane, below 2 GiB).
+    const unsigned psh = static_cast<unsigned>(a.ny) * static_cast<unsigned>(a.pitch) * 2u;
+    const unsigned psf = 2u * psh;
+    char* dout = reinterpret_cast<char*>(a.dout + off);
+    char* rout = reinterpret_cast<char*>(a.rout + off);
+    auto st16 = [psh](char* base, int p, unsigned short v) {
+      *reinterpret_cast<unsigned short*>(base + static_cast<unsigned long long>(p) * psh) = v;
+    };
+    auto st32 = [psf](char* base, int p, float v) {
+      *reinterpret_cast<float*>(base + static_cast<unsigned long long>(p) * psf) = v;
+    };
+    const bool glo = x < kGhost, ghi = x >= a.nx - kGhost;
+    const ptrdiff_t gh = 2 * static_cast<ptrdiff_t>(a.nx), gf = 4 * static_cast<ptrdiff_t>(a.nx);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       float rt = val[plane_of(k, 0)];
 #pragma unroll
       for (int i = 1; i < 9; ++i) rt += val[plane_of(k, i)];
       float sr = 0.0f;
+      unsigned short code[9];
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
-        const unsigned short b = enc16<ST>(val[plane_of(k, i)] - wt(i) * rt);
-        code[plane_of(k, i)] = b;
-        sr += dec16<ST>(b);
+        code[i] = enc16<ST>(val[plane_of(k, i)] - wt(i) * rt);
+        sr += dec16<ST>(code[i]);
       }
-      rp[k] = rt - sr;
-    }
-    unsigned short* dout = a.dout + off;
-    float* rout = a.rout + off;
+      const float rpk = rt - sr;
 #pragma unroll
-    for (int p = 0; p < 27; ++p) dout[p * PS] = code[p];
+      for (int i = 0; i < 9; ++i) st16(dout, plane_of(k, i), code[i]);
+      st32(rout, k, rpk);
+      if (glo || ghi) {
+        if (glo) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) rout[k * PS] = rp[k];
-    if (x < kGhost) {
+          for (int i = 0; i < 9; ++i) st16(dout + gh, plane_of(k, i), code[i]);
+          st32(rout + gf, k, rpk);
+        }
+        if (ghi) {
 #pragma unroll
-      for (int p = 0; p < 27; ++p) dout[p * PS + a.nx] = code[p];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) rout[k * PS + a.nx] = rp[k];
-    }
-    if (x >= a.nx - kGhost) {
-#pragma unroll
-      for (int p = 0; p < 27; ++p) dout[p * PS - a.nx] = code[p];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) rout[k * PS - a.nx] = rp[k];
+          for (int i = 0; i < 9; ++i) st16(dout - gh, plane_of(k, i), code[i]);
+          st32(rout - gf, k, rpk);
+        }
+      }
     }
   }
 }
@@ -614,8 +640,11 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
       if (!dead && tid < nr * (w + 4)) {
         const int W = w + 4;
         const int r = tid >= W ? 1 : 0;
-        stage_density<ST>(s, q0 + r, tid - r * W, rc);
+        stage_density<ST>(s, q0 + r, tid - r * W, w, rc);
       }
+      // this thread is done with the population rows of this D stage: the
+      // producer may refill their slots (every consumer arrives once per row)
+      for (int r = 0; r < nr; ++r) mbar_arrive(&s.empty[(q0 + r) % kSlots]);
     }
     consumers_sync();
     // ---------------- T stage: rows q = 2j-1, 2j within [1, nq-2], columns x0-1 .. x0+w
@@ -637,12 +666,6 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
         const int r = tid >= w ? 1 : 0;
         stage_collide<MODE, ST, FORCE>(s, a, qa + r, tid - r * w, x0, y0, rc);
       }
-    }
-    // release the population rows the C stage finished with (rows 0 and 1
-    // are D-stage halo rows only and are released here as well)
-    if (j >= 1) {
-      mbar_arrive(&s.empty[(2 * j - 2) % kSlots]);
-      mbar_arrive(&s.empty[(2 * j - 1) % kSlots]);
     }
   }
 }
