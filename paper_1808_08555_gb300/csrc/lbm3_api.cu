@@ -298,20 +298,48 @@ lbm3_status check_device_errors(lbm3_ctx* c) {
   return LBM3_OK;
 }
 
-void tiling(const lbm3_ctx* c, int* rows, int* grid) {
-  const int nstrips = (c->p.nx + lbm3::kTX - 1) / lbm3::kTX;
-  int H = c->rows_override;
+// Row-chunk heights of the single-grid step kernel: H for the full-width
+// strips and H_last for a narrower last strip, sized so that one wave of
+// resident CTAs covers the grid.  The last strip's CTAs take the resident
+// slots the full strips leave free; among the choices the one with the
+// smallest estimated makespan max(H + 4, rho (H_last + 4)) wins, with rho the
+// cost per row of the narrow strip relative to a full one (the work scales
+// with its width, the per-row latency of the row pipeline does not).
+constexpr double kNarrowRowBase = 0.5;  // rho = base + (1 - base) width / kTX
+
+void tiling(const lbm3_ctx* c, StepArgs* a, int* grid) {
+  const int nx = c->p.nx, ny = c->p.ny;
+  const int nfs = nx / lbm3::kTX;
+  const int wl = nx - nfs * lbm3::kTX;
+  auto ceil_div = [](int x, int y) { return (x + y - 1) / y; };
+  auto clamp_rows = [ny](int H) { return H < 4 ? (ny < 4 ? ny : 4) : (H > ny ? ny : H); };
+  int H = c->rows_override, HL = c->rows_override;
   if (H <= 0) {
     const int resident = (c->occ > 0 ? c->occ : 1) * (c->num_sms > 0 ? c->num_sms : 1);
-    int chunks = resident / nstrips;
-    if (chunks < 1) chunks = 1;
-    H = (c->p.ny + chunks - 1) / chunks;
-    if (H < 4) H = 4;  // small grids: short columns keep the pipeline fill short
+    const int nstrips = nfs + (wl > 0 ? 1 : 0);
+    // small grids: short columns keep the pipeline fill short (H >= 4)
+    H = HL = ceil_div(ny, resident / nstrips > 1 ? resident / nstrips : 1);
+    if (wl > 0 && nfs > 0) {
+      const double rho = kNarrowRowBase + (1.0 - kNarrowRowBase) * wl / lbm3::kTX;
+      double best = 1e300;
+      for (int cf = 1; nfs * cf < resident; ++cf) {
+        const int h = ceil_div(ny, cf), hl = ceil_div(ny, resident - nfs * cf);
+        const double t = std::max(h + 4.0, rho * (hl + 4.0));
+        if (t < best) {
+          best = t;
+          H = h;
+          HL = hl;
+        }
+        if (h <= 4) break;
+      }
+    }
   }
-  if (H > c->p.ny) H = c->p.ny;
-  const int chunks = (c->p.ny + H - 1) / H;
-  *rows = H;
-  *grid = nstrips * chunks;
+  H = clamp_rows(H);
+  HL = clamp_rows(HL);
+  a->rows_per_cta = H;
+  a->rows_last = HL;
+  a->full_blocks = nfs * ceil_div(ny, H);
+  *grid = a->full_blocks + (wl > 0 ? ceil_div(ny, HL) : 0);
 }
 
 StepArgs args_for(const lbm3_ctx* c, const float* fin, float* fout, int* grid) {
@@ -325,9 +353,7 @@ StepArgs args_for(const lbm3_ctx* c, const float* fin, float* fout, int* grid) {
     a.rin = fin ? reinterpret_cast<const float*>(a.din + 27 * PS) : nullptr;
     a.rout = fout ? reinterpret_cast<float*>(a.dout + 27 * PS) : nullptr;
   }
-  int rows = 0;
-  tiling(c, &rows, grid);
-  a.rows_per_cta = rows;
+  tiling(c, &a, grid);
   return a;
 }
 

@@ -111,7 +111,9 @@ struct StepArgs {
   const float* rin;
   float* rout;
   int nstrips;        // ceil(nx / kTX)
-  int rows_per_cta;   // H
+  int rows_per_cta;   // H of the full-width strips
+  int rows_last;      // H of the narrower last strip (when kTX does not divide nx)
+  int full_blocks;    // CTAs of the full-width strips, (nx / kTX) * ceil(ny / H); the rest take the last strip
   float inv_nu[3];    // 1/nu_k, nu_k = (tau_k - 1/2)/3 (so 1/nu = sum_k phi_k/nu_k)
   float cpair[3];     // 1e6 / (rho0_k rho0_l) for pairs (12, 13, 23)
   float sigma[3];     // sigma_12, sigma_13, sigma_23

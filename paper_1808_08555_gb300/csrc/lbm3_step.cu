@@ -700,20 +700,31 @@ __device__ __forceinline__ Smem& aligned_smem() {
   return *reinterpret_cast<Smem*>(smem_raw + pad);
 }
 
-// Single grid: CTA b takes strip b % nstrips and row chunk b / nstrips.
-// Full-width strips with a narrower last one measured 4.6 % faster on a
-// 2048^2 grid than equal-width strips (all CTAs of one wave stay busy with
-// 248-node C stages instead of 240).
+// Single grid: full-width strips of kTX columns and, when kTX does not
+// divide nx, a narrower last strip.  CTAs b < full_blocks take full strip
+// b % (nx / kTX) and row chunk b / (nx / kTX) of rows_per_cta rows; the
+// others take chunks of rows_last rows of the last strip, whose height the
+// host picks separately (a narrow CTA costs less per row).  Full-width strips
+// with a narrower last one measured 4.6 % faster on a 2048^2 grid than
+// equal-width strips (248-node C stages instead of 240).
 template <int MODE, int ST, int FORCE>
 __global__ void __launch_bounds__(kThreads, 2)
     fused_step_kernel(StepArgs a, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap1) {
   Smem& s = aligned_smem();
-  const int strip = blockIdx.x % a.nstrips;
-  const int chunk = blockIdx.x / a.nstrips;
+  const int nfs = a.nx / kTX;  // full-width strips
+  const int b = static_cast<int>(blockIdx.x);
+  int strip, y0, h;
+  if (b < a.full_blocks) {
+    strip = b % nfs;
+    y0 = (b / nfs) * a.rows_per_cta;
+    h = min(a.rows_per_cta, a.ny - y0);
+  } else {
+    strip = nfs;
+    y0 = (b - a.full_blocks) * a.rows_last;
+    h = min(a.rows_last, a.ny - y0);
+  }
   const int x0 = strip * kTX;
   const int w = min(kTX, a.nx - x0);
-  const int y0 = chunk * a.rows_per_cta;
-  const int h = min(a.rows_per_cta, a.ny - y0);
   if (w <= 0 || h <= 0) return;
   run_tile<MODE, ST, FORCE>(s, a, &tmap, &tmap1, x0, w, y0, h);
 }

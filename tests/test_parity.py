@@ -93,10 +93,13 @@ def test_random_state_tiny_grids(L, nx, ny, rows):
 
 
 @pytest.mark.parametrize("nx,ny,rows,R", [(200, 37, 8, (4.0, 10.0)), (136, 21, 5, (3.0, 4.0)),
-                                           (260, 40, 0, (4.0, 8.0)), (320, 72, 8, (4.0, 10.0))])
+                                           (260, 40, 0, (4.0, 8.0)), (320, 72, 8, (4.0, 10.0)),
+                                           (264, 1200, 0, (4.0, 10.0))])
 def test_droplets_across_tile_seams(L, nx, ny, rows, R):
     """Droplets scattered over several strips (ragged last strip) and several
-    row chunks (ragged last chunk), ten steps from a relaxed-ish state."""
+    row chunks (ragged last chunk), ten steps from a relaxed-ish state.  With
+    automatic tiling on a 152-SM GB300, 264 x 1200 gets full strips cut into
+    10-row chunks and a 16-column last strip cut into 19-row chunks."""
     rho = W.droplet_field(nx, ny, seed=nx + ny, count=8, rmin=R[0], rmax=R[1], gap=10.0)
     assert rho[1].sum() + rho[2].sum() > 50.0
     p = L.Params(nx, ny, tau=(0.6, 0.9, 1.3), sigma=(0.01, 0.013, 0.007))
@@ -261,7 +264,9 @@ def test_full_size_compound_2048_sampled(L):
     m_gpu, _ = sim.mass()
     sim.close()
     centres = [(1024 + 200, 1024), (1024, 1024 + 400), (1024 - 283, 1024 - 283), (1024 + 141, 1024 + 141),
-               (127, 107), (128, 108), (0, 0), (2047, 2047), (1023, 1620), (1280, 1455)]
+               (127, 107), (128, 108), (0, 0), (2047, 2047), (1023, 1620), (1280, 1455),
+               # seams of 114-row chunks (full strips) and 128-row chunks (last strip)
+               (1984, 114), (1983, 1026), (2000, 128), (2040, 1920)]
     assert _patch_check(L, p, f_t, f_t1, centres) <= 1e-5
     host = f_t1.reshape(3, 9, -1).sum(axis=(1, 2))
     np.testing.assert_allclose(m_gpu, host, rtol=1e-12)
