@@ -549,10 +549,13 @@ def main():
                     help="grid edge (default: 2048 compound, 4096 janus, 256 adjoint); other edges scale the "
                          "droplet radii (profiling and larger cases only)")
     args = ap.parse_args()
+    # default K / W per workload: a step of the adjoint workload is a whole
+    # gradient evaluation (~60-80 ms), of the others one lattice step
+    dflt = {"compound": (5000, 50), "sweep": (2000, 20), "janus": (1000, 20), "adjoint": (10, 3)}[args.workload]
     if args.steps is None:
-        args.steps = 3 if args.impl == "reference" else 5000
+        args.steps = 3 if args.impl == "reference" else dflt[0]
     if args.warmup is None:
-        args.warmup = 3 if args.impl == "reference" else 50
+        args.warmup = 3 if args.impl == "reference" else dflt[1]
     ws, rank, local = dist_env()
     if ws > 1:
         import torch.distributed as dist
