@@ -960,6 +960,9 @@ struct lbm3_batch {
   cudaStream_t cap_stream = nullptr;  // private stream for graph capture
   lbm3::BatchItem* d_items = nullptr;
   lbm3::BatchDesc* d_descs = nullptr;
+  // per parity, the instances' step arguments for the kernel parameter space
+  // (empty for batches of more than kBatchParamInst instances)
+  std::vector<lbm3::BatchArgsBlock> pargs;
   int nitems = 0;
   int rows = 64;
   int device = 0;
@@ -998,8 +1001,12 @@ void destroy_batch(lbm3_batch* b) {
   delete b;
 }
 
+const lbm3::BatchArgsBlock* param_args(const lbm3_batch* b, int parity) {
+  return b->pargs.empty() ? nullptr : &b->pargs[static_cast<size_t>(parity)];
+}
+
 lbm3_status launch_one(lbm3_batch* b, int parity, cudaStream_t st) {
-  const cudaError_t e = lbm3::launch_batch(b->d_items, b->nitems, b->d_descs, parity, st);
+  const cudaError_t e = lbm3::launch_batch(b->d_items, b->nitems, b->d_descs, param_args(b, parity), parity, st);
   if (e != cudaSuccess) return bfail(b, LBM3_ECUDA, "lbm3_batch_step: %s", cudaGetErrorString(e));
   return LBM3_OK;
 }
@@ -1008,8 +1015,10 @@ lbm3_status build_graph(lbm3_batch* b, int parity) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t e1 = lbm3::launch_batch(b->d_items, b->nitems, b->d_descs, parity, b->cap_stream);
-    cudaError_t e2 = lbm3::launch_batch(b->d_items, b->nitems, b->d_descs, parity ^ 1, b->cap_stream);
+    cudaError_t e1 = lbm3::launch_batch(b->d_items, b->nitems, b->d_descs, param_args(b, parity), parity,
+                                        b->cap_stream);
+    cudaError_t e2 = lbm3::launch_batch(b->d_items, b->nitems, b->d_descs, param_args(b, parity ^ 1), parity ^ 1,
+                                        b->cap_stream);
     e = cudaStreamEndCapture(b->cap_stream, &g);
     if (e == cudaSuccess && e1 != cudaSuccess) e = e1;
     if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
@@ -1113,6 +1122,11 @@ lbm3_status lbm3_batch_create(const lbm3_params* params, int32_t count, void* cu
     }
   }
   b->nitems = static_cast<int>(items.size());
+  if (count <= lbm3::kBatchParamInst) {
+    b->pargs.assign(2, lbm3::BatchArgsBlock{});
+    for (int p = 0; p < 2; ++p)
+      for (int i = 0; i < count; ++i) b->pargs[static_cast<size_t>(p)].a[i] = descs[static_cast<size_t>(i)].args[p];
+  }
   cudaError_t e = cudaMalloc(&b->d_items, sizeof(lbm3::BatchItem) * items.size());
   if (e == cudaSuccess) e = cudaMalloc(&b->d_descs, sizeof(lbm3::BatchDesc) * descs.size());
   if (e == cudaSuccess)

@@ -143,6 +143,16 @@ struct alignas(64) BatchDesc {
   StepArgs args[2];
   alignas(64) unsigned char map[2][128];
 };
+// The step arguments of up to kBatchParamInst instances for one parity,
+// passed by value in the kernel parameter space (at most 32,764 bytes on
+// sm_70 and later): each argument is then a read of the constant bank at an
+// index uniform over the CTA, as for the single grid.  Larger batches read
+// them from the BatchDesc array in global memory.
+constexpr int kBatchParamInst = 144;
+struct BatchArgsBlock {
+  StepArgs a[kBatchParamInst];
+};
+static_assert(sizeof(BatchArgsBlock) + 64 <= 32764, "kernel parameter space");
 
 size_t step_smem_bytes();
 cudaError_t step_configure();  // sets the dynamic shared memory attribute
@@ -158,7 +168,10 @@ cudaError_t launch_step(const StepArgs& a, const void* tmaps, int grid, int mode
 cudaError_t encode_population_maps(void* tmaps, const void* buf, int nx, int ny, int storage);
 // bytes of one population buffer
 size_t population_bytes(int nx, int ny, int storage);
-cudaError_t launch_batch(const BatchItem* items, int nitems, const BatchDesc* descs, int parity, cudaStream_t s);
+// args: this parity's arguments of every instance (count <= kBatchParamInst),
+// or nullptr to read them from descs
+cudaError_t launch_batch(const BatchItem* items, int nitems, const BatchDesc* descs, const BatchArgsBlock* args,
+                         int parity, cudaStream_t s);
 int step_occupancy(int* blocks_per_sm);
 
 // ------------------------------------------------------------- aux kernels

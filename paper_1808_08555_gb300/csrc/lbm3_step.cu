@@ -750,6 +750,21 @@ __global__ void __launch_bounds__(kThreads, 2)
   run_tile<MODE_STEP, ST_FP32, 0>(s, d->args[parity], map, map, it.x0, it.w, it.y0, it.h);
 }
 
+// Batch whose step arguments travel in the kernel parameter space: the same
+// work items and tensor maps, the arguments read from the constant bank.
+__global__ void __launch_bounds__(kThreads, 2)
+    fused_batch_param_kernel(const BatchItem* __restrict__ items, const BatchDesc* __restrict__ descs, int parity,
+                             const __grid_constant__ BatchArgsBlock args) {
+  Smem& s = aligned_smem();
+  const BatchItem it = items[blockIdx.x];
+  const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(descs[it.inst].map[parity]);
+  if (threadIdx.x == kConsumers)
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+  __syncthreads();
+  run_tile<MODE_STEP, ST_FP32, 0>(s, args.a[it.inst], map, map, it.x0, it.w, it.y0, it.h);
+}
+
 }  // namespace
 
 size_t step_smem_bytes() { return sizeof(Smem) + 128; }
@@ -775,12 +790,18 @@ cudaError_t step_configure() {
                              bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(fused_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fused_batch_param_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return e;
 }
 
-cudaError_t launch_batch(const BatchItem* items, int nitems, const BatchDesc* descs, int parity, cudaStream_t st) {
+cudaError_t launch_batch(const BatchItem* items, int nitems, const BatchDesc* descs, const BatchArgsBlock* args,
+                         int parity, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
-  fused_batch_kernel<<<nitems, kThreads, step_smem_bytes(), st>>>(items, descs, parity);
+  if (args)
+    fused_batch_param_kernel<<<nitems, kThreads, step_smem_bytes(), st>>>(items, descs, parity, *args);
+  else
+    fused_batch_kernel<<<nitems, kThreads, step_smem_bytes(), st>>>(items, descs, parity);
   return cudaGetLastError();
 }
 
