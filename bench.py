@@ -333,7 +333,8 @@ def run_sweep(args):
                                            "unit": "MLUPS", "ms_per_step": round(ms_seq / args.steps, 5)},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": None, "bytes_per_node": BYTES_PER_NODE,
-                         "kernel": "fused_batch_kernel", "peak_source": peak_kind},
+                         "kernel": "fused_batch_param_kernel" if len(cases) <= 144 else "fused_batch_kernel",
+                         "peak_source": peak_kind},
             "gpu_launches": args.steps}
 
 
