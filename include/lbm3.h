@@ -126,10 +126,12 @@ lbm3_status lbm3_init(lbm3_ctx* ctx, const double* rho, int on_device);
  * for checkpoint restore and for tests from non-equilibrium states. */
 lbm3_status lbm3_set_populations(lbm3_ctx* ctx, const double* f, int on_device);
 
-/* Tuning: rows of the grid each CTA of the fused step kernel marches over
- * (0 = automatic: about one full wave of CTAs over the GPU's SMs; otherwise
- * 1..ny).  Results do not depend on it beyond FP32 rounding being identical
- * (the arithmetic per node is the same); only speed does. */
+/* Tuning: rows of the grid each CTA of the fused step kernel marches over.
+ * 0 = automatic: one wave of CTAs over the GPU's SMs, with the 124-column
+ * strips and a narrower last strip (when 124 does not divide nx) cut into
+ * chunks of separately chosen heights.  Otherwise 1..ny, the same height
+ * for every strip.  Results are bit-identical for every choice (the
+ * arithmetic per node is the same); only speed changes. */
 lbm3_status lbm3_set_rows_per_cta(lbm3_ctx* ctx, int32_t rows);
 
 /* Advance n >= 0 time steps (Sec. 2: collision, recolouring, streaming),

@@ -107,6 +107,24 @@ def test_droplets_across_tile_seams(L, nx, ny, rows, R):
     check_parity(L, p, f0, 10, rows)
 
 
+def test_tiling_does_not_change_results(L):
+    """The arithmetic per node does not depend on the tiling: automatic row
+    chunks (different heights for the 124-column strips and the narrow last
+    strip), a small explicit height and one chunk per strip give
+    bit-identical populations after several steps."""
+    nx, ny = 136, 1200
+    rho = W.droplet_field(nx, ny, seed=5, count=12, rmin=4.0, rmax=10.0, gap=10.0)
+    p = L.Params(nx, ny, tau=(0.6, 0.9, 1.3), sigma=(0.01, 0.013, 0.007))
+    out = []
+    for rows in (0, 5, ny):
+        sim = L.Simulation(p, rows_per_cta=rows)
+        sim.init(rho)
+        sim.step(6)
+        out.append(sim.populations())
+        sim.close()
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+
+
 # ------------------------------------------------------------- long runs
 
 def test_two_droplets_64_1_and_1000_steps(L):
