@@ -169,6 +169,28 @@ def test_checkpoint_recomputation_is_exact(L):
     np.testing.assert_allclose(outs[0][2], rs, rtol=3e-4)
 
 
+@pytest.mark.gpu
+def test_tape_that_does_not_fit_is_enomem_and_context_survives(L):
+    """Recording 10^7 states of a 256^2 grid (about 73 TB) fails with
+    LBM3_ENOMEM before any step runs; the context keeps its state and steps
+    on with its mass conserved."""
+    n = 256
+    rho0, _ = W.case_adjoint(n)
+    p = L.Params(n, n, tau=(1.0, 1.0, 1.0), sigma=(0.01, 0.01, 0.01))
+    sim = L.Simulation(p)
+    sim.init(rho0)
+    m0, _ = sim.mass()
+    with pytest.raises(L.Lbm3Error) as e:
+        sim.tape_forward(10 ** 7, 1)
+    assert e.value.status == L.ENOMEM
+    assert "cannot allocate" in str(e.value)
+    assert sim.t == 0
+    sim.step(20)
+    m1, _ = sim.mass()
+    sim.close()
+    assert np.abs(m1 / m0 - 1).max() <= 1e-6
+
+
 def _fd_case(L, name, every, through_autograd):
     g = json.load(open(os.path.join(HERE, "golden", name)))
     n, steps = g["n"], g["steps"]
