@@ -134,6 +134,18 @@ lbm3_status lbm3_set_populations(lbm3_ctx* ctx, const double* f, int on_device);
  * arithmetic per node is the same); only speed changes. */
 lbm3_status lbm3_set_rows_per_cta(lbm3_ctx* ctx, int32_t rows);
 
+/* Testing hook for the step kernel's bounded waits (FP32 storage with the
+ * body force; ignored otherwise).  In the next lbm3_step launch only, which
+ * then runs a separate instantiation of the kernel, CTA 0 announces march
+ * row `row` (0 = the first halo row of its tile) to its consumers but never
+ * copies it.  Its waits
+ * then run out after 2 s, the CTA stops without writing its tile, and the
+ * next synchronising call (lbm3_mass, lbm3_fields, lbm3_sync) returns
+ * LBM3_ETIMEOUT.  That call also clears the error word, so the context stays
+ * usable once its state is set again.  -1 cancels; other values below -1
+ * are LBM3_EINVAL.  Nothing faults and no wait is unbounded. */
+lbm3_status lbm3_debug_stall_row(lbm3_ctx* ctx, int32_t row);
+
 /* Advance n >= 0 time steps (Sec. 2: collision, recolouring, streaming),
  * asynchronously on the context's stream. */
 lbm3_status lbm3_step(lbm3_ctx* ctx, int64_t n);

@@ -42,6 +42,7 @@ struct lbm3_ctx {
   unsigned int* bad = nullptr;
   int red_blocks = 1;
   int rows_override = 0;
+  int stall_row = -1;  // lbm3_debug_stall_row: applies to the next lbm3_step launch only
   StepArgs base{};
   // TMA descriptors of buf[0] and buf[1]: one (FP32) or two (deviations, rho')
   alignas(64) unsigned char tmap[2][256];
@@ -564,6 +565,7 @@ lbm3_status lbm3_create(const lbm3_params* p, void* cuda_stream, lbm3_ctx** out)
   a.boxw = lbm3::kPW;  // pitch_of() is never below one box
   a.nstrips = (p->nx + lbm3::kTX - 1) / lbm3::kTX;
   a.err = c->err;
+  a.stall_row = -1;
   fill_constants(*p, &a);
   *out = c;
   return LBM3_OK;
@@ -661,6 +663,13 @@ lbm3_status lbm3_set_rows_per_cta(lbm3_ctx* c, int32_t rows) {
   return LBM3_OK;
 }
 
+lbm3_status lbm3_debug_stall_row(lbm3_ctx* c, int32_t row) {
+  if (!c) return LBM3_EINVAL;
+  if (row < -1) return fail(c, LBM3_EINVAL, "lbm3_debug_stall_row: row %d < -1", row);
+  c->stall_row = row;
+  return LBM3_OK;
+}
+
 lbm3_status lbm3_step(lbm3_ctx* c, int64_t n) {
   if (!c) return LBM3_EINVAL;
   if (n < 0) return fail(c, LBM3_EINVAL, "lbm3_step: n = %lld < 0", static_cast<long long>(n));
@@ -670,6 +679,8 @@ lbm3_status lbm3_step(lbm3_ctx* c, int64_t n) {
   for (int64_t s = 0; s < n; ++s) {
     int grid = 0;
     StepArgs a = args_for(c, c->buf[c->cur], c->buf[c->cur ^ 1], &grid);
+    a.stall_row = c->stall_row;
+    c->stall_row = -1;
     LBM3_CUDA(c, lbm3::launch_step(a, c->tmap[c->cur], grid, lbm3::MODE_STEP, c->p.storage, c->p.force_form, c->stream));
     c->cur ^= 1;
     c->t += 1;

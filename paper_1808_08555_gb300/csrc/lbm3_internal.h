@@ -122,6 +122,7 @@ struct StepArgs {
   float beta_h[3];
   float wrec[9];      // recolouring weight per direction: w_i / |e_i|^p
   unsigned int* err;  // device error word (bit 0: a bounded wait timed out)
+  int stall_row;      // testing hook: CTA 0's producer skips the copies of this march row (-1: none)
   // MODE_FIELDS outputs (FP64, [3][N] and [N]); NULL entries are skipped
   double* out_rho;
   double* out_ux;

@@ -195,7 +195,7 @@ __device__ __forceinline__ int wrap(int a, int n) {
 // Row q of the march (y = y0 - 2 + q) needs, for the directions with
 // e_y = 1 - g, the source row y - e_y: three TMA boxes per row, one per group
 // g, each bringing the 9 planes of that group over columns [tma_x, tma_x + boxw).
-template <int ST>
+template <int ST, bool STALL>
 __device__ void produce(Smem& s, const StepArgs& a, const CUtensorMap* map, const CUtensorMap* map1, int x0,
                         int y0, int nq, int lane) {
   const int ny = a.ny;
@@ -218,7 +218,11 @@ __device__ void produce(Smem& s, const StepArgs& a, const CUtensorMap* map, cons
     if (!ok) break;
     if (lane == 0) mbar_arrive_expect_tx(&s.full[slot], row_bytes);
     __syncwarp();
-    if (ST == ST_FP32) {
+    // testing hook (lbm3_debug_stall_row, a separate instantiation): the row
+    // is announced but never copied, so the consumers' bounded waits run out
+    const bool stall = STALL && q == a.stall_row && blockIdx.x == 0;
+    if (stall) {
+    } else if (ST == ST_FP32) {
       if (lane < 3) {
         const int g = lane;  // e_y = 1 - g
         const int src_row = wrap(y0 - 2 + q - (1 - g), ny);
@@ -672,7 +676,7 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
 
 // One tile (strip of w columns starting at x0, rows y0 .. y0+h-1): barrier
 // set-up, then the producer warp and the consumer warps.
-template <int MODE, int ST, int FORCE>
+template <int MODE, int ST, int FORCE, bool STALL = false>
 __device__ __forceinline__ void run_tile(Smem& s, const StepArgs& a, const CUtensorMap* map, const CUtensorMap* map1,
                                          int x0, int w, int y0, int h) {
   const int nq = h + 4;
@@ -687,7 +691,7 @@ __device__ __forceinline__ void run_tile(Smem& s, const StepArgs& a, const CUten
   }
   __syncthreads();
   if (tid >= kConsumers) {
-    produce<ST>(s, a, map, map1, x0, y0, nq, tid - kConsumers);
+    produce<ST, STALL>(s, a, map, map1, x0, y0, nq, tid - kConsumers);
   } else {
     consume<MODE, ST, FORCE>(s, a, x0, w, y0, h, tid);
   }
@@ -707,7 +711,7 @@ __device__ __forceinline__ Smem& aligned_smem() {
 // host picks separately (a narrow CTA costs less per row).  Full-width strips
 // with a narrower last one measured 4.6 % faster on a 2048^2 grid than
 // equal-width strips (248-node C stages instead of 240).
-template <int MODE, int ST, int FORCE>
+template <int MODE, int ST, int FORCE, bool STALL = false>
 __global__ void __launch_bounds__(kThreads, 2)
     fused_step_kernel(StepArgs a, const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap1) {
   Smem& s = aligned_smem();
@@ -726,7 +730,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int x0 = strip * kTX;
   const int w = min(kTX, a.nx - x0);
   if (w <= 0 || h <= 0) return;
-  run_tile<MODE, ST, FORCE>(s, a, &tmap, &tmap1, x0, w, y0, h);
+  run_tile<MODE, ST, FORCE, STALL>(s, a, &tmap, &tmap1, x0, w, y0, h);
 }
 
 // Batch of independent grids: CTA b runs work item b (instance, tile); the
@@ -789,6 +793,9 @@ cudaError_t step_configure() {
     e = cudaFuncSetAttribute(fused_step_kernel<MODE_FIELDS, ST_FP32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              bytes);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fused_step_kernel<MODE_STEP, ST_FP32, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             bytes);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(fused_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(fused_batch_param_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -816,7 +823,10 @@ cudaError_t launch_step(const StepArgs& a, const void* tmaps, int grid, int mode
   memcpy(&m0, tmaps, sizeof m0);
   memcpy(&m1, static_cast<const unsigned char*>(tmaps) + 128, sizeof m1);
   const size_t sm = step_smem_bytes();
-  if (force == 1) {  // perturbation operator: FP32 storage only
+  if (a.stall_row >= 0 && mode == MODE_STEP && storage == ST_FP32 && force == 0) {
+    // testing hook: the instantiation that can withhold a row
+    fused_step_kernel<MODE_STEP, ST_FP32, 0, true><<<grid, kThreads, sm, st>>>(a, m0, m1);
+  } else if (force == 1) {  // perturbation operator: FP32 storage only
     if (storage != ST_FP32) return cudaErrorInvalidValue;
     if (mode == MODE_STEP)
       fused_step_kernel<MODE_STEP, ST_FP32, 1><<<grid, kThreads, sm, st>>>(a, m0, m1);

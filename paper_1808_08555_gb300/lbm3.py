@@ -96,6 +96,7 @@ def load() -> ctypes.CDLL:
         "lbm3_init": (st, [vp, dp, ctypes.c_int]),
         "lbm3_set_populations": (st, [vp, dp, ctypes.c_int]),
         "lbm3_set_rows_per_cta": (st, [vp, ctypes.c_int32]),
+        "lbm3_debug_stall_row": (st, [vp, ctypes.c_int32]),
         "lbm3_step": (st, [vp, ctypes.c_int64]),
         "lbm3_fields": (st, [vp, dp, dp, dp, dp, ctypes.c_int]),
         "lbm3_populations": (st, [vp, dp, ctypes.c_int]),
@@ -185,6 +186,12 @@ def lbm3_set_populations(ctx, f):
 
 def lbm3_set_rows_per_cta(ctx, rows: int):
     _check(ctx, load().lbm3_set_rows_per_cta(ctx, int(rows)))
+
+
+def lbm3_debug_stall_row(ctx, row: int):
+    """Testing hook: the next step's CTA 0 never receives march row `row`,
+    so its bounded waits run out (LBM3_ETIMEOUT at the next sync)."""
+    _check(ctx, load().lbm3_debug_stall_row(ctx, int(row)))
 
 
 def lbm3_step(ctx, n: int = 1):
