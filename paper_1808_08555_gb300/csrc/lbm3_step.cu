@@ -57,7 +57,7 @@ struct Smem {
   float4 phi[6][kDW];          // (phi_1, phi_2, phi_3, rho) of row q in slot q % 6
   float2 fi2[6][4][kTX];       // (f_1, f_2), (f_3, f_4), (f_5, f_6), (f_7, f_8) of row q in slot q % 6
   float fi0[6][kTX];           // f_0 of row q in slot q % 6
-  float T[4][3][kTW];          // T_xx, T_xy, T_yy of row q in slot q % 4
+  float4 T[4][kTW];            // (T_xx, T_xy, T_xy, T_yy) of row q in slot q % 4: the pairs the divergence uses
   float2 nrm[3][3][kTX];       // (x, y) of n_12, n_13, n_23 of row q in slot q % 3
   unsigned long long full[kSlots];
   unsigned long long empty[kSlots];
@@ -379,10 +379,7 @@ __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q,
     const float rden = g2 > 1e-30f ? __fdividef(1.0f, den) : 0.0f;  // |n| <= 1
     nv[p] = mul2(G, bc2(rden));
   }
-  float(*Tt)[kTW] = s.T[q & 3];
-  Tt[0][c] = txx;
-  Tt[1][c] = txy;
-  Tt[2][c] = tyy;
+  s.T[q & 3][c] = make_float4(txx, txy, txy, tyy);
   if (c >= 1 && c <= w) {
     float2(*nn)[kTX] = s.nrm[q % 3];
 #pragma unroll
@@ -394,9 +391,9 @@ __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q,
 template <int MODE, int ST, int FORCE>
 __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q, int c, int x0, int y0,
                                               const RingCols& rc) {
-  const float(*Tm)[kTW] = s.T[(q - 1) & 3];
-  const float(*Tz)[kTW] = s.T[q & 3];
-  const float(*Tp)[kTW] = s.T[(q + 1) & 3];
+  const float4* Tm = s.T[(q - 1) & 3];
+  const float4* Tz = s.T[q & 3];
+  const float4* Tp = s.T[(q + 1) & 3];
   // colour fractions and density from the D stage (the phi and f rings keep
   // six rows, so the next iteration's D stage writes other slots)
   const float4 pr = s.phi[q % 6][c + 2];
@@ -418,15 +415,18 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
   float2 F = make_float2(0.0f, 0.0f);
   float Sxx = 0.0f, Sxy = 0.0f, Syy = 0.0f;
   if (FORCE == 1) {
-    Sxx = Tz[0][tc];
-    Sxy = Tz[1][tc];
-    Syy = Tz[2][tc];
+    const float4 Sc = Tz[tc];
+    Sxx = Sc.x;
+    Sxy = Sc.y;
+    Syy = Sc.w;
   } else {
-    auto A = [](const float (*T)[kTW], int col) { return make_float2(T[0][col], T[1][col]); };
-    auto B = [](const float (*T)[kTW], int col) { return make_float2(T[1][col], T[2][col]); };
-    const float2 axis = add2(sub2(A(Tz, tc + 1), A(Tz, tc - 1)), sub2(B(Tp, tc), B(Tm, tc)));
-    const float2 diag = add2(add2(sub2(A(Tp, tc + 1), A(Tp, tc - 1)), sub2(A(Tm, tc + 1), A(Tm, tc - 1))),
-                             sub2(add2(B(Tp, tc + 1), B(Tp, tc - 1)), add2(B(Tm, tc + 1), B(Tm, tc - 1))));
+    // one vector load per stencil node: A = (T_xx, T_xy), B = (T_xy, T_yy)
+    const float4 E = Tz[tc + 1], W = Tz[tc - 1], Nn = Tp[tc], S = Tm[tc];
+    const float4 NE = Tp[tc + 1], NW = Tp[tc - 1], SE = Tm[tc + 1], SW = Tm[tc - 1];
+    auto A = [](const float4& v) { return make_float2(v.x, v.y); };
+    auto B = [](const float4& v) { return make_float2(v.z, v.w); };
+    const float2 axis = add2(sub2(A(E), A(W)), sub2(B(Nn), B(S)));
+    const float2 diag = add2(add2(sub2(A(NE), A(NW)), sub2(A(SE), A(SW))), sub2(add2(B(NE), B(NW)), add2(B(SE), B(SW))));
     F = fma2(bc2(1.0f / 12.0f), diag, mul2(bc2(1.0f / 3.0f), axis));
   }
   // momentum sum_i f_i e_i: (f_1 - f_3, f_2 - f_4) + (f_5 - f_7) (1, 1) + (f_6 - f_8) (-1, 1)
