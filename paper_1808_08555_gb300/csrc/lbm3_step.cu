@@ -55,10 +55,11 @@ struct Smem {
   // kPW columns, one per direction group, each starting on a 128-byte boundary
   float pop[kSlots][3 * kGroupFloats];
   float4 phi[6][kDW];          // (phi_1, phi_2, phi_3, rho) of row q in slot q % 6
-  float2 fi2[6][4][kTX];       // (f_1, f_2), (f_3, f_4), (f_5, f_6), (f_7, f_8) of row q in slot q % 6
+  float4 fi4[6][2][kTX];       // (f_1, f_2, f_3, f_4), (f_5, f_6, f_7, f_8) of row q in slot q % 6
   float fi0[6][kTX];           // f_0 of row q in slot q % 6
   float4 T[4][kTW];            // (T_xx, T_xy, T_xy, T_yy) of row q in slot q % 4: the pairs the divergence uses
-  float2 nrm[3][3][kTX];       // (x, y) of n_12, n_13, n_23 of row q in slot q % 3
+  float4 nrm01[3][kTX];        // (x, y) of n_12 and n_13 of row q in slot q % 3
+  float2 nrm2[3][kTX];         // (x, y) of n_23
   unsigned long long full[kSlots];
   unsigned long long empty[kSlots];
   int abort_flag;
@@ -305,7 +306,7 @@ __device__ __forceinline__ void stage_density(Smem& s, int q, int c, int w, cons
   s.phi[fs][c] = make_float4(phk[0], phk[1], phk[2], rho);
   if (c >= 2 && c < w + 2) {
 #pragma unroll
-    for (int m = 0; m < 4; ++m) s.fi2[fs][m][c - 2] = F[m];
+    for (int m = 0; m < 2; ++m) s.fi4[fs][m][c - 2] = make_float4(F[2 * m].x, F[2 * m].y, F[2 * m + 1].x, F[2 * m + 1].y);
     s.fi0[fs][c - 2] = (f0[0] + f0[1]) + f0[2];
   }
 }
@@ -381,9 +382,9 @@ __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q,
   }
   s.T[q & 3][c] = make_float4(txx, txy, txy, tyy);
   if (c >= 1 && c <= w) {
-    float2(*nn)[kTX] = s.nrm[q % 3];
-#pragma unroll
-    for (int p = 0; p < 3; ++p) nn[p][c - 1] = nv[p];
+    const int ns = q % 3;
+    s.nrm01[ns][c - 1] = make_float4(nv[0].x, nv[0].y, nv[1].x, nv[1].y);
+    s.nrm2[ns][c - 1] = nv[2];
   }
 }
 
@@ -407,7 +408,9 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
   // the recolouring below run on pairs.
   const int fs = q % 6;
   const float f0 = s.fi0[fs][c];
-  const float2 f12 = s.fi2[fs][0][c], f34 = s.fi2[fs][1][c], f56 = s.fi2[fs][2][c], f78 = s.fi2[fs][3][c];
+  const float4 f1234 = s.fi4[fs][0][c], f5678 = s.fi4[fs][1][c];
+  const float2 f12 = make_float2(f1234.x, f1234.y), f34 = make_float2(f1234.z, f1234.w);
+  const float2 f56 = make_float2(f5678.x, f5678.y), f78 = make_float2(f5678.z, f5678.w);
   // F_s = div T (Eq. 11) as the pair (F_x, F_y) = d_x (T_xx, T_xy) + d_y (T_xy, T_yy);
   // T window column of this node is c + 1.  None with the perturbation
   // operator, whose S is read at the node instead.
@@ -503,7 +506,9 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
   const float fd0 = f0 + fmaf(om, fmaf(wt(0), rho, -f0), wt(0) * (c0 + gm3uF) - phisum);
   // segregation parameters beta_kl (pairs 12, 13, 23); prod = rho_1 rho_2 rho_3 / rho^3
   const float cb = fminf(a.beta_A * (phi0 * phi1 * phi2), 1.0f);
-  const float2(*nn)[kTX] = s.nrm[q % 3];
+  const int ns = q % 3;
+  const float4 n01 = s.nrm01[ns][c];
+  const float2 nn[3] = {make_float2(n01.x, n01.y), make_float2(n01.z, n01.w), s.nrm2[ns][c]};
   float2 R[3];
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
@@ -511,7 +516,7 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
     const int l = p == 0 ? 1 : 2;
     const float b = a.beta0 * fmaf(cb, a.beta_h[p], 1.0f);
     const float amp = b * (phv[k] * phv[l]) * rho;  // beta_kl rho_k rho_l / rho
-    R[p] = mul2(bc2(amp), nn[p][c]);
+    R[p] = mul2(bc2(amp), nn[p]);
   }
   // V_k = sum_{l != k} beta_kl (rho_k rho_l / rho) n_kl, with n_lk = -n_kl
   const float2 V[3] = {add2(R[0], R[1]), sub2(R[2], R[0]), neg2(add2(R[1], R[2]))};
