@@ -94,12 +94,14 @@ def test_random_state_tiny_grids(L, nx, ny, rows):
 
 @pytest.mark.parametrize("nx,ny,rows,R", [(200, 37, 8, (4.0, 10.0)), (136, 21, 5, (3.0, 4.0)),
                                            (260, 40, 0, (4.0, 8.0)), (320, 72, 8, (4.0, 10.0)),
-                                           (264, 1200, 0, (4.0, 10.0))])
+                                           (264, 1200, 0, (4.0, 10.0)), (128, 3000, 0, (4.0, 10.0))])
 def test_droplets_across_tile_seams(L, nx, ny, rows, R):
     """Droplets scattered over several strips (ragged last strip) and several
     row chunks (ragged last chunk), ten steps from a relaxed-ish state.  With
     automatic tiling on a 152-SM GB300, 264 x 1200 gets full strips cut into
-    10-row chunks and a 16-column last strip cut into 19-row chunks."""
+    10-row chunks and a 16-column last strip cut into 19-row chunks, and
+    128 x 3000 a 4-column last strip (8 density columns, 4 output columns)
+    with its own chunk height beside a full strip."""
     rho = W.droplet_field(nx, ny, seed=nx + ny, count=8, rmin=R[0], rmax=R[1], gap=10.0)
     assert rho[1].sum() + rho[2].sum() > 50.0
     p = L.Params(nx, ny, tau=(0.6, 0.9, 1.3), sigma=(0.01, 0.013, 0.007))
