@@ -23,7 +23,10 @@
 // per pair of rows).  Only the D stage reads a population row: it also
 // leaves the node's total distribution f_i = sum_k f_{i,k} in a ring of its
 // own for the C stage, so each population row is released as soon as its D
-// stage is done and the loads run almost two iterations ahead.  HBM traffic is one read and one write of
+// stage is done and the loads run almost two iterations ahead.  The stages
+// hand each other one vector per node and quantity (phi and rho, f_i, the
+// tension tensor, the normals), and the arithmetic runs on packed FP32 pairs
+// (directions e and -e, x and y).  HBM traffic is one read and one write of
 // the 27 populations per node; halo re-reads of neighbouring strips' columns
 // are served by L2.
 //
