@@ -78,7 +78,7 @@ typedef enum {
 /* Problem statement (Sec. 2).  Validation in lbm3_create:
  * nx >= 4 and a multiple of 4, ny >= 1, nx*ny < 2^31; tau[k] > 0.5;
  * rho0[k] > 0; sigma_kl > 0; 0 < beta0 <= 1; forms and storage in range;
- * force_form 1 with FP32 storage only. */
+ * force_form 1 with FP32 storage only; 0 <= normal_delta <= 1. */
 typedef struct {
   int32_t nx, ny;
   double tau[3];      /* per-fluid relaxation time; nu_k = (tau_k - 1/2)/3 (Eq. tau) */
@@ -89,6 +89,13 @@ typedef struct {
   int32_t recolor_form; /* lbm3_recolor_form */
   int32_t storage;    /* lbm3_storage */
   int32_t force_form; /* lbm3_force_form (0 for the paper's model) */
+  double normal_delta; /* recolouring normal of Eq. 6: n_kl = G_kl / max(|G_kl|, normal_delta phi_k phi_l).
+                          0 = the paper's unit normal G_kl/|G_kl| (Sec. 2, after Eq. 11).  A value
+                          d > 0 leaves the unit normal wherever |G_kl| >= d phi_k phi_l (across a
+                          k-l interface |G_kl| is about 1.26 phi_k phi_l) and takes n_kl continuously
+                          to 0 where G_kl vanishes, where the unit normal's direction is decided by
+                          rounding.  The Python binding uses 0.1.  In both forms n_kl = 0 where
+                          |G_kl| <= 1e-15. */
 } lbm3_params;
 
 /* Bytes of ONE population buffer for these parameters, with the row pitch

@@ -39,6 +39,7 @@ class _Params(ctypes.Structure):
         ("beta_form", ctypes.c_int),
         ("recolor_form", ctypes.c_int),
         ("force_form", ctypes.c_int),
+        ("normal_delta", ctypes.c_double),
     ]
 
 
@@ -55,6 +56,9 @@ class Params:
     beta_form: int = 0
     recolor_form: int = 0
     force_form: int = 0  # 0: Eq. 11 force via Eq. 5; 1: perturbation operator (Eqs. phi1, phi_old)
+    # recolouring normal n = G / max(|G|, normal_delta phi_k phi_l) in Eq. 6;
+    # 0 is the paper's unit normal G/|G| (Sec. 2, after Eq. 11)
+    normal_delta: float = 0.1
     extra: dict = field(default_factory=dict)
 
     def _c(self) -> _Params:
@@ -68,18 +72,24 @@ class Params:
         p.beta_form = int(self.beta_form)
         p.recolor_form = int(self.recolor_form)
         p.force_form = int(self.force_form)
+        p.normal_delta = float(self.normal_delta)
         return p
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no vector or host-specific flags)."""
+    """Compile the oracle with gcc (no vector or host-specific flags), with
+    OpenMP over the node loops when the compiler supports it (the results do
+    not depend on the thread count)."""
     with _lock:
         if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
             return _LIB_PATH
         os.makedirs(_BUILD, exist_ok=True)
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-D_DEFAULT_SOURCE",
-                               "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-D_DEFAULT_SOURCE", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB_PATH)
         return _LIB_PATH
 
@@ -104,6 +114,8 @@ def _load():
         lib.orc_step.argtypes = [pp, dp, ctypes.c_int]
         lib.orc_init.argtypes = [pp, dp, dp]
         lib.orc_mass.argtypes = [pp, dp, dp, dp]
+        lib.orc_threads.restype = ctypes.c_int
+        lib.orc_threads.argtypes = [ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -115,6 +127,12 @@ def _ptr(a: np.ndarray):
 
 def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def threads(n: int = 0) -> int:
+    """Host threads of the oracle's node loops: n > 0 sets them, 0 only
+    reads them.  Returns the number in effect (1 for a build without OpenMP)."""
+    return int(_load().orc_threads(int(n)))
 
 
 # ------------------------------------------------------------------ pieces

@@ -23,17 +23,19 @@
  *    interface-thickness result (Eq. 21 with k = 0.1504 from Eq. k, Sec. 3.1)
  *    belongs to the cosine form n_kl . e_i / |e_i|.  Both are provided
  *    (recolor_form 0 = cosine form, the default; 1 = as printed).
- *  - n_kl = G_kl/|G_kl| is undefined where G_kl = 0, and the recolouring
- *    term of Eq. 6 jumps there whenever rho_k rho_l/rho is not negligible
- *    (e.g. at a droplet centre or at the saddle of phi between two nearby
- *    droplets), where rounding noise in G then decides the direction.  The
- *    recolouring uses n_kl = G_kl / max(|G_kl|, 0.1 phi_k phi_l), which
- *    equals the paper's unit normal wherever a k-l interface exists (there
- *    |G_kl| is about 1.26 phi_k phi_l across the whole tanh profile of Eq. 21)
- *    and goes to zero continuously, with a bounded gain, where G_kl
- *    vanishes.  Where |G_kl| <= 1e-15 no k-l interface is taken to exist:
- *    the tension term |G|(I - n n) of Eq. 11, which vanishes with |G|, is 0
- *    there, and so is n_kl in the recolouring.
+ *  - recolouring normal.  Eq. 6 uses the unit normal n_kl = G_kl/|G_kl|
+ *    (Sec. 2, after Eq. 11).  normal_delta = 0 evaluates exactly that.  It is
+ *    undefined where G_kl = 0, and the recolouring term then jumps whenever
+ *    rho_k rho_l/rho is not negligible (e.g. at a droplet centre or at the
+ *    saddle of phi between two nearby droplets), where rounding noise in G
+ *    decides the direction.  normal_delta = d > 0 evaluates
+ *    n_kl = G_kl / max(|G_kl|, d phi_k phi_l) instead: the paper's unit
+ *    normal wherever |G_kl| >= d phi_k phi_l (across the tanh profile of
+ *    Eq. 21 |G_kl| is about 1.26 phi_k phi_l), going to zero continuously,
+ *    with a bounded gain, where G_kl vanishes.  In both forms, where
+ *    |G_kl| <= 1e-15 no k-l interface is taken to exist: the tension term
+ *    |G|(I - n n) of Eq. 11, which vanishes with |G|, is 0 there, and so is
+ *    n_kl in the recolouring.
  *  - the derivatives inside F_s (Eq. 11) are the isotropic stencil of
  *    Eq. fd1 applied to phi_k = rho_k/rho, and then again to each component
  *    of the tensor inside the divergence.
@@ -47,6 +49,17 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* Loops over nodes whose iterations write disjoint outputs run on all host
+ * threads when the oracle is built with OpenMP.  Each output is computed by
+ * the same arithmetic in the same order either way, so the results are
+ * bit-identical for any thread count. */
+#ifdef _OPENMP
+#include <omp.h>
+#define NODE_LOOP _Pragma("omp parallel for schedule(static)")
+#else
+#define NODE_LOOP
+#endif
+
 /* D2Q9 velocities and weights (Sec. 2, after Eq. 3): e0 = 0, e1,3 = (+-1,0),
  * e2,4 = (0,+-1), e5,7 = +-(1,1), e6,8 = +-(-1,1); w0 = 4/9, w1-4 = 1/9,
  * w5-8 = 1/36.  c_s^2 = 1/3. */
@@ -57,7 +70,6 @@ static const double WT[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,
                              1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
 static const double CS2 = 1.0 / 3.0;
 static const double GEPS = 1e-15;   /* |G| at or below which no k-l interface exists */
-static const double NDELTA = 1e-1;  /* recolouring normal: n = G / max(|G|, NDELTA phi_k phi_l) */
 
 typedef struct {
   int nx, ny;
@@ -69,6 +81,8 @@ typedef struct {
   int recolor_form;  /* 0 = n.e_i/|e_i| (cosine form); 1 = n.e_i as printed in Eq. 6 */
   int force_form;    /* 0 = force of Eq. 11 through Guo's scheme (Eq. 5), the paper's;
                         1 = perturbation operator of Eqs. phi1 / phi_old (Leclaire et al.) */
+  double normal_delta; /* recolouring normal n = G / max(|G|, normal_delta phi_k phi_l);
+                          0 = the paper's G/|G| */
 } orc_params;
 
 /* ---------------------------------------------------------------- helpers */
@@ -161,6 +175,7 @@ void orc_perturbation(const double* sig, const double* G, const double* C, doubl
 
 /* Eq. fd1: d_alpha v(x) = (1/cs2) sum_i w_i v(x + e_i) e_i,alpha on a periodic grid. */
 void orc_grad(int nx, int ny, const double* v, double* gx, double* gy) {
+  NODE_LOOP
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       double sx = 0.0, sy = 0.0;
@@ -182,24 +197,27 @@ void orc_colour_gradients(const orc_params* p, const double* rho, double* G, dou
   int nx = p->nx, ny = p->ny, N = nx * ny;
   double* phi = (double*)calloc((size_t)3 * N, sizeof(double));
   double* gphi = (double*)calloc((size_t)6 * N, sizeof(double));
+  NODE_LOOP
   for (int n = 0; n < N; ++n) {
     double r = rho[n] + rho[N + n] + rho[2 * N + n];
     for (int k = 0; k < 3; ++k) phi[k * N + n] = rho[k * N + n] / r;
   }
   for (int k = 0; k < 3; ++k) orc_grad(nx, ny, phi + k * N, gphi + (2 * k) * N, gphi + (2 * k + 1) * N);
-  memset(G, 0, sizeof(double) * 18 * (size_t)N);
-  memset(C, 0, sizeof(double) * 9 * (size_t)N);
-  for (int k = 0; k < 3; ++k)
-    for (int l = 0; l < 3; ++l) {
-      if (l == k) continue;
-      for (int n = 0; n < N; ++n) {
+  NODE_LOOP
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l) {
+        if (l == k) {
+          G[((k * 3 + l) * 2 + 0) * N + n] = G[((k * 3 + l) * 2 + 1) * N + n] = 0.0;
+          C[(k * 3 + l) * N + n] = 0.0;
+          continue;
+        }
         for (int a = 0; a < 2; ++a)
           G[((k * 3 + l) * 2 + a) * N + n] =
               phi[l * N + n] * gphi[(2 * k + a) * N + n] - phi[k * N + n] * gphi[(2 * l + a) * N + n];
         double c = 1e6 * rho[k * N + n] * rho[l * N + n] / (p->rho0[k] * p->rho0[l]);
         C[(k * 3 + l) * N + n] = c < 1.0 ? c : 1.0;
       }
-    }
   free(phi);
   free(gphi);
 }
@@ -222,6 +240,7 @@ void orc_force(const orc_params* p, const double* rho, double* Fx, double* Fy, d
     for (int l = 0; l < 3; ++l) {
       if (l == k) continue;
       double s = sigma_of(p, k, l);
+      NODE_LOOP
       for (int n = 0; n < N; ++n) {
         double gx = G[((k * 3 + l) * 2 + 0) * N + n], gy = G[((k * 3 + l) * 2 + 1) * N + n];
         double mag = sqrt(gx * gx + gy * gy);
@@ -300,15 +319,17 @@ void orc_fields(const orc_params* p, const double* f, double* rho, double* ux, d
   double* rk = (double*)calloc((size_t)3 * N, sizeof(double));
   double* Fx = (double*)malloc(sizeof(double) * (size_t)N);
   double* Fy = (double*)malloc(sizeof(double) * (size_t)N);
-  for (int k = 0; k < 3; ++k)
-    for (int i = 0; i < 9; ++i)
-      for (int n = 0; n < N; ++n) rk[k * N + n] += f[(k * 9 + i) * N + n];
+  NODE_LOOP
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < 3; ++k)
+      for (int i = 0; i < 9; ++i) rk[k * N + n] += f[(k * 9 + i) * N + n];
   if (p->force_form == 1) {
     memset(Fx, 0, sizeof(double) * (size_t)N);
     memset(Fy, 0, sizeof(double) * (size_t)N);
   } else {
     orc_force(p, rk, Fx, Fy, NULL);
   }
+  NODE_LOOP
   for (int n = 0; n < N; ++n) {
     double r = rk[n] + rk[N + n] + rk[2 * N + n];
     double mx = 0.0, my = 0.0;
@@ -340,9 +361,10 @@ static void orc_step_once(const orc_params* p, double* f, double* fn) {
   for (int k = 0; k < 3; ++k) nu[k] = (p->tau[k] - 0.5) * CS2;
 
   /* densities rho_k = sum_i f_{i,k} */
-  for (int k = 0; k < 3; ++k)
-    for (int i = 0; i < 9; ++i)
-      for (int n = 0; n < N; ++n) rk[k * N + n] += f[(k * 9 + i) * N + n];
+  NODE_LOOP
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < 3; ++k)
+      for (int i = 0; i < 9; ++i) rk[k * N + n] += f[(k * 9 + i) * N + n];
   /* interfacial force (Eq. 11; none with the perturbation operator) and
    * colour gradients */
   if (p->force_form == 1) {
@@ -353,6 +375,8 @@ static void orc_step_once(const orc_params* p, double* f, double* fn) {
   }
   orc_colour_gradients(p, rk, G, C);
 
+  /* each source node writes its own 27 destinations (Eq. 30): disjoint */
+  NODE_LOOP
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       int n = y * nx + x;
@@ -396,7 +420,7 @@ static void orc_step_once(const orc_params* p, double* f, double* fn) {
             double gx = G[((k * 3 + l) * 2 + 0) * N + n], gy = G[((k * 3 + l) * 2 + 1) * N + n];
             double mag = sqrt(gx * gx + gy * gy);
             if (mag <= GEPS) continue;  /* no k-l interface: n_kl = 0, as in Eq. 11 */
-            double den = NDELTA * (rloc[k] / r) * (rloc[l] / r);
+            double den = p->normal_delta * (rloc[k] / r) * (rloc[l] / r);
             if (mag > den) den = mag;
             double en = (gx * EX[i] + gy * EY[i]) / den;
             if (p->recolor_form == 0 && i != 0) en /= sqrt((double)(EX[i] * EX[i] + EY[i] * EY[i]));
@@ -416,9 +440,11 @@ static void orc_step_once(const orc_params* p, double* f, double* fn) {
 void orc_step(const orc_params* p, double* f, int nsteps) {
   size_t bytes = sizeof(double) * 27 * (size_t)p->nx * p->ny;
   double* fn = (double*)malloc(bytes);
+  const long total = 27L * p->nx * p->ny;
   for (int s = 0; s < nsteps; ++s) {
     orc_step_once(p, f, fn);
-    memcpy(f, fn, bytes);
+    NODE_LOOP
+    for (long j = 0; j < total; ++j) f[j] = fn[j];
   }
   free(fn);
 }
@@ -446,4 +472,16 @@ void orc_mass(const orc_params* p, const double* f, double* mass, double* mom) {
         mom[0] += v * EX[i];
         mom[1] += v * EY[i];
       }
+}
+
+/* Host threads used by the node loops (OpenMP builds); 0 leaves the current
+ * setting.  Returns the number in effect (1 without OpenMP). */
+int orc_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }

@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE.  It exists to give exact reference gradients (through
 torch.autograd) for the library's hand-written reverse mode; only the tests
 may import it.  It shares nothing with the CUDA library.  Its forward is the
 same computation as ``lbm3_oracle.c`` -- the same readings of the paper (the
-regularised recolouring normal, the 1e-15 tension cutoff, the derivatives of
+recolouring normal G / max(|G|, normal_delta phi_k phi_l), the 1e-15 tension cutoff, the derivatives of
 Eq. fd1 applied twice, the local tau_f in BGK and Guo terms) -- and the tests
 pin it to that oracle and its gradients to central differences of that oracle.
 
@@ -26,7 +26,6 @@ EY = (0, 0, 1, 0, -1, 1, 1, -1, -1)
 WT = (4 / 9, 1 / 9, 1 / 9, 1 / 9, 1 / 9, 1 / 36, 1 / 36, 1 / 36, 1 / 36)
 CS2 = 1.0 / 3.0
 GEPS = 1e-15      # |G| at or below which the tension term is 0
-NDELTA = 0.1      # recolouring normal n = G / max(|G|, NDELTA phi_k phi_l)
 PAIRS = ((0, 1), (0, 2), (1, 2))
 
 
@@ -93,7 +92,8 @@ def beta(prm, sigma, rk):
 def step(prm, f, sigma):
     """One step (Sec. 2): collision with the Guo force, recolouring (Eq. 6),
     streaming (Eq. 30).  prm: dict with tau, rho0, beta0, beta_form,
-    recolor_form."""
+    recolor_form and optionally normal_delta (the recolouring normal
+    G / max(|G|, normal_delta phi_k phi_l); 0.1 if absent, 0 = G/|G|)."""
     rk = f.sum(dim=1)                                   # rho_k = sum_i f_{i,k}
     r = rk.sum(dim=0)
     phi = rk / r
@@ -136,7 +136,7 @@ def step(prm, f, sigma):
         cy = (EY[i] - uy) / CS2 + eu / (CS2 * CS2) * EY[i]
         Phi = WT[i] * (1 - 1 / (2 * tauf)) * (cx * Fx + cy * Fy)                         # Eq. 5
         fdag.append(fi[i] - (fi[i] - feq) / tauf + Phi)                                   # Eqs. 1, 2
-    # Eq. 6 with the regularised normal
+    # Eq. 6 with the normal G / max(|G|, normal_delta phi_k phi_l)
     bq = beta(prm, sigma, rk)
     form = prm.get("recolor_form", 0)
     out = []
@@ -151,7 +151,7 @@ def step(prm, f, sigma):
                 g2 = gx * gx + gy * gy
                 ok = g2 > GEPS * GEPS      # no k-l interface at or below the cutoff: n = 0
                 mag = torch.sqrt(torch.where(ok, g2, torch.ones_like(g2)))
-                den = torch.maximum(mag, NDELTA * phi[k] * phi[l])
+                den = torch.maximum(mag, prm.get("normal_delta", 0.1) * phi[k] * phi[l])
                 dsafe = torch.where(ok, den, torch.ones_like(den))
                 en = (gx * EX[i] + gy * EY[i]) / dsafe
                 if form == 0 and i != 0:

@@ -39,7 +39,6 @@
 namespace lbm3 {
 namespace {
 
-constexpr float kNormalDeltaA = 0.1f;  // recolouring normal G / max(|G|, 0.1 phi_k phi_l)
 constexpr int kAdjThreads = 256;
 
 // Programmatic dependent launch: the adjoint's kernels are launched with
@@ -275,7 +274,7 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adj_node_kernel(const float* _
       if (!(g2 > 1e-30f)) continue;  // no k-l interface: n = 0
       const float mag = sqrtf(g2);
       const float pp = ph[k] * ph[l];
-      const float den = fmaxf(mag, kNormalDeltaA * pp);
+      const float den = fmaxf(mag, a.ndelta * pp);  // recolouring normal G / max(|G|, delta phi_k phi_l)
       const float nxv = Gx / den, nyv = Gy / den;
       const float b = a.beta0 * (1.0f + cb * a.beta_h[p]);
       const float amp = b * pp * rho;  // beta_kl rho_k rho_l / rho
@@ -290,7 +289,7 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adj_node_kernel(const float* _
       lcb += lb * a.beta0 * a.beta_h[p];
       dh[p] = lb * a.beta0 * cb;
       float lGx, lGy;
-      if (mag >= kNormalDeltaA * pp) {  // unit normal G/|G|
+      if (mag >= a.ndelta * pp) {  // unit normal G/|G|
         const float nl = nxv * lnx + nyv * lny;
         lGx = (lnx - nxv * nl) / mag;
         lGy = (lny - nyv * nl) / mag;
@@ -298,8 +297,8 @@ __global__ void __launch_bounds__(kAdjThreads, 3) adj_node_kernel(const float* _
         lGx = lnx / den;
         lGy = lny / den;
         const float lden = -(lnx * nxv + lny * nyv) / den;
-        lph[k] += lden * kNormalDeltaA * ph[l];
-        lph[l] += lden * kNormalDeltaA * ph[k];
+        lph[k] += lden * a.ndelta * ph[l];
+        lph[l] += lden * a.ndelta * ph[k];
       }
       // G = phi_l grad phi_k - phi_k grad phi_l
       lgx[k] += ph[l] * lGx;

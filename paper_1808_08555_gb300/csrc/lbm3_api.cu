@@ -143,6 +143,10 @@ lbm3_status validate(const lbm3_params* p, std::string* why) {
     *why = "lbm3: beta_form, recolor_form, storage or force_form out of range";
     return LBM3_EINVAL;
   }
+  if (!(p->normal_delta >= 0.0 && p->normal_delta <= 1.0)) {
+    *why = "lbm3: normal_delta must be in [0, 1]";
+    return LBM3_EINVAL;
+  }
   if (p->force_form == LBM3_FORCE_PERTURBATION && p->storage != LBM3_FP32) {
     *why = "lbm3: the perturbation-operator force form needs FP32 storage";
     return LBM3_EINVAL;
@@ -210,6 +214,7 @@ void fill_constants(const lbm3_params& p, StepArgs* a) {
   }
   a->beta0 = static_cast<float>(p.beta0);
   a->beta_A = static_cast<float>(A);
+  a->ndelta = static_cast<float>(p.normal_delta);
   for (int i = 0; i < 9; ++i) {
     const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
     const double len = std::sqrt(static_cast<double>(lbm3::ex(i) * lbm3::ex(i) + lbm3::ey(i) * lbm3::ey(i)));

@@ -121,6 +121,7 @@ struct StepArgs {
   float beta_A;       // beta_kl = beta0 (1 + min(beta_A * r g b / rho^3, 1) * beta_h[kl])
   float beta_h[3];
   float wrec[9];      // recolouring weight per direction: w_i / |e_i|^p
+  float ndelta;       // recolouring normal G / max(|G|, ndelta phi_k phi_l); 0 = G/|G|
   unsigned int* err;  // device error word (bit 0: a bounded wait timed out)
   int stall_row;      // testing hook: CTA 0's producer skips the copies of this march row (-1: none)
   // MODE_FIELDS outputs (FP64, [3][N] and [N]); NULL entries are skipped

@@ -7,7 +7,8 @@
 //                               phi_k = rho_k/rho (Eq. 30 read as a pull;
 //                               rho_k as after Eq. 30)
 //   T stage  (rows 2j-1, 2j):   grad phi_k (Eq. fd1) -> G_kl, C_kl (Eq. 15),
-//                               normals n_kl (regularised where G_kl -> 0) and
+//                               normals n_kl (optionally regularised where
+//                               G_kl -> 0) and
 //                               the tension tensor
 //                               T = sum_{k<l} sigma_kl C_kl |G_kl| (I - n n)
 //                               (Eq. 11's double sum, 1/2 folded into k<l)
@@ -47,11 +48,6 @@ namespace lbm3 {
 namespace {
 
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
-// n_kl = G_kl / |G_kl| is undefined where G_kl = 0 and makes the recolouring
-// of Eq. 6 jump there; the normal is regularised as G / max(|G|, 0.1 phi_k
-// phi_l).  Across a k-l interface |G_kl| is about 1.26 phi_k phi_l (tanh
-// profile of Eq. 21), so the regularisation only acts near zeros of G_kl.
-constexpr float kNormalDelta = 1e-1f;
 
 struct Smem {
   // pulled-row ring (row q in slot q % kSlots): three TMA boxes of 9 planes x
@@ -376,10 +372,13 @@ __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q,
         tyy = fmaf(sc * Gy, Gy, tyy);
       }
     }
-    // recolouring normal G / max(|G|, kNormalDelta phi_k phi_l): the unit
-    // normal wherever a k-l interface exists, continuous to 0 where G -> 0,
-    // and 0 at or below the |G| cutoff of the tension (no k-l interface)
-    const float den = fmaxf(mag, kNormalDelta * pp);
+    // recolouring normal G / max(|G|, delta phi_k phi_l): with delta = 0 the
+    // unit normal G/|G| of Eq. 6; with delta > 0 the unit normal wherever
+    // |G| >= delta phi_k phi_l (across a k-l interface |G| is about
+    // 1.26 phi_k phi_l on the tanh profile of Eq. 21), going continuously to
+    // 0 where G -> 0.  0 at or below the |G| cutoff of the tension (no k-l
+    // interface).
+    const float den = fmaxf(mag, a.ndelta * pp);
     const float rden = g2 > 1e-30f ? __fdividef(1.0f, den) : 0.0f;  // |n| <= 1
     nv[p] = mul2(G, bc2(rden));
   }

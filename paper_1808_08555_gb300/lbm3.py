@@ -45,6 +45,7 @@ class lbm3_params(ctypes.Structure):
         ("beta0", ctypes.c_double),
         ("beta_form", ctypes.c_int32), ("recolor_form", ctypes.c_int32),
         ("storage", ctypes.c_int32), ("force_form", ctypes.c_int32),
+        ("normal_delta", ctypes.c_double),
     ]
 
 
@@ -62,6 +63,9 @@ class Params:
     recolor_form: int = RECOLOR_COSINE
     storage: int = FP32
     force_form: int = FORCE_BODY  # 1: perturbation operator (Eqs. phi1 / phi_old)
+    # recolouring normal G / max(|G|, normal_delta phi_k phi_l) in Eq. 6;
+    # 0 is the paper's unit normal G/|G|
+    normal_delta: float = 0.1
 
     def to_c(self) -> lbm3_params:
         p = lbm3_params()
@@ -73,6 +77,7 @@ class Params:
         p.beta0 = float(self.beta0)
         p.beta_form, p.recolor_form = int(self.beta_form), int(self.recolor_form)
         p.storage, p.force_form = int(self.storage), int(self.force_form)
+        p.normal_delta = float(self.normal_delta)
         return p
 
 

@@ -37,8 +37,9 @@ def test_header_symbols_exported(lib):
 
 def test_params_struct_layout_matches_header():
     # int32 nx, ny; 3+3 doubles; 3 sigmas; beta0; 4 int32 (beta, recolour, storage, force
-    # forms) -> 4*2 + 8*10 + 4*4 = 104 bytes
-    assert ctypes.sizeof(L.lbm3_params) == 104
+    # forms); normal_delta -> 4*2 + 8*10 + 4*4 + 8 = 112 bytes
+    assert ctypes.sizeof(L.lbm3_params) == 112
+    assert L.lbm3_params.normal_delta.offset == 104
 
 
 @pytest.mark.parametrize("kw", [
@@ -47,6 +48,8 @@ def test_params_struct_layout_matches_header():
     dict(nx=8, ny=8, beta0=0.0), dict(nx=8, ny=8, beta0=1.5), dict(nx=8, ny=8, beta_form=7),
     dict(nx=8, ny=8, recolor_form=2), dict(nx=8, ny=8, storage=9), dict(nx=8, ny=8, storage=-1),
     dict(nx=8, ny=8, force_form=2), dict(nx=8, ny=8, force_form=-1), dict(nx=8, ny=8, force_form=1, storage=1),
+    dict(nx=8, ny=8, normal_delta=-0.1), dict(nx=8, ny=8, normal_delta=1.5),
+    dict(nx=8, ny=8, normal_delta=float("nan")),
     # nx*ny below 2^31, but one padded FP32 plane reaches 4 GiB
     dict(nx=4, ny=2 ** 28), dict(nx=32768, ny=32768),
 ])

@@ -33,7 +33,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 def _prm(op):
-    return dict(tau=op.tau, rho0=op.rho0, beta0=op.beta0, beta_form=op.beta_form, recolor_form=op.recolor_form)
+    return dict(tau=op.tau, rho0=op.rho0, beta0=op.beta0, beta_form=op.beta_form, recolor_form=op.recolor_form,
+                normal_delta=op.normal_delta)
 
 
 def _loss_c(op, rho, steps, phit):
@@ -46,11 +47,13 @@ def _loss_c(op, rho, steps, phit):
 
 @pytest.mark.parametrize("beta_form", [0, 1, 2, 3])
 @pytest.mark.parametrize("recolor_form", [0, 1])
-def test_torch_restatement_matches_c_oracle(beta_form, recolor_form):
+@pytest.mark.parametrize("normal_delta", [0.1, 0.0])
+def test_torch_restatement_matches_c_oracle(beta_form, recolor_form, normal_delta):
     nx, ny = 40, 24
     rho = W.droplet_field(nx, ny, seed=3, count=4, rmin=3.0, rmax=6.0, gap=4.0)
     sig = (0.01, 0.008, 0.012) if beta_form == 3 else (0.01, 0.013, 0.007)
-    op = O.Params(nx, ny, tau=(0.6, 0.9, 1.3), sigma=sig, beta_form=beta_form, recolor_form=recolor_form)
+    op = O.Params(nx, ny, tau=(0.6, 0.9, 1.3), sigma=sig, beta_form=beta_form, recolor_form=recolor_form,
+                  normal_delta=normal_delta)
     f0 = O.step(op, O.init(op, rho), 2)
     ref = O.step(op, f0.copy(), 3)
     f = torch.from_numpy(f0)
@@ -135,12 +138,14 @@ def _state(nx, ny, op, seed=3):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("beta_form,recolor_form", [(0, 0), (0, 1), (1, 0), (2, 0), (3, 0), (3, 1)])
-def test_one_step_vjp_matches_autograd(L, beta_form, recolor_form):
+@pytest.mark.parametrize("beta_form,recolor_form,delta", [(0, 0, 0.1), (0, 1, 0.1), (1, 0, 0.1), (2, 0, 0.1),
+                                                          (3, 0, 0.1), (3, 1, 0.1), (0, 0, 0.0), (3, 1, 0.0)])
+def test_one_step_vjp_matches_autograd(L, beta_form, recolor_form, delta):
     nx, ny = 64, 40
     sig = (0.01, 0.008, 0.012) if beta_form in (2, 3) else (0.01, 0.013, 0.007)
-    op = O.Params(nx, ny, tau=(0.6, 0.9, 1.3), sigma=sig, beta_form=beta_form, recolor_form=recolor_form)
-    p = L.Params(nx, ny, tau=op.tau, sigma=sig, beta_form=beta_form, recolor_form=recolor_form)
+    op = O.Params(nx, ny, tau=(0.6, 0.9, 1.3), sigma=sig, beta_form=beta_form, recolor_form=recolor_form,
+                  normal_delta=delta)
+    p = L.Params(nx, ny, tau=op.tau, sigma=sig, beta_form=beta_form, recolor_form=recolor_form, normal_delta=delta)
     dphi = np.random.default_rng(7).standard_normal((3, ny, nx))
     f32, dpop, ds = _gpu_vjp(L, p, _state(nx, ny, op), dphi, 1, 1)
     rpop, rs = _ref_vjp(op, f32, dphi, 1)

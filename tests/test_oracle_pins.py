@@ -385,3 +385,25 @@ def test_concentration_factor_values():
     assert C[0, 1] == pytest.approx(0.025, rel=1e-12)
     assert C[0, 2] == pytest.approx(min(1e6 * 5e-5 / 2.0, 1.0))
     assert np.all(G == 0.0)
+
+
+def test_oracle_threads_do_not_change_results():
+    """The oracle's node loops run on several host threads (OpenMP) only where
+    the iterations write disjoint outputs, each with the same arithmetic in
+    the same order: one thread and all threads give bit-identical states."""
+    n = 40
+    rho = W.droplet_field(n, n, seed=9, count=4, rmin=3.0, rmax=7.0, gap=4.0)
+    p = O.Params(n, n, tau=(0.6, 0.9, 1.3), sigma=(0.01, 0.013, 0.007), beta_form=3)
+    all_threads = O.threads()
+    try:
+        O.threads(1)
+        one = O.step(p, O.init(p, rho), 20)
+        f1 = O.fields(p, one)
+        O.threads(max(all_threads, 4))
+        many = O.step(p, O.init(p, rho), 20)
+        fm = O.fields(p, many)
+    finally:
+        O.threads(all_threads)
+    assert np.array_equal(one, many)
+    for k in ("rho", "ux", "uy", "p"):
+        assert np.array_equal(f1[k], fm[k])

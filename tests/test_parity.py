@@ -40,7 +40,8 @@ def f32(a):
 
 def oparams(p):
     return O.Params(p.nx, p.ny, tau=p.tau, rho0=p.rho0, sigma=p.sigma, beta0=p.beta0,
-                    beta_form=p.beta_form, recolor_form=p.recolor_form, force_form=p.force_form)
+                    beta_form=p.beta_form, recolor_form=p.recolor_form, force_form=p.force_form,
+                    normal_delta=p.normal_delta)
 
 
 def fp32_sensitivity(op, f0, steps, seed=0):
@@ -255,7 +256,7 @@ def _patch_check(L, p, f_t, f_t1, centres, half=8, radius=3):
     """Nodes within `radius` of each centre depend on f(t) within 4 nodes, so
     a periodic 2*half patch around them gives the exact one-step result."""
     op_small = O.Params(2 * half, 2 * half, tau=p.tau, rho0=p.rho0, sigma=p.sigma, beta0=p.beta0,
-                        beta_form=p.beta_form, recolor_form=p.recolor_form)
+                        beta_form=p.beta_form, recolor_form=p.recolor_form, normal_delta=p.normal_delta)
     worst = 0.0
     for (cx, cy) in centres:
         ys = (np.arange(cy - half, cy + half)) % p.ny
