@@ -264,9 +264,13 @@ const char* lbm3_batch_last_error(const lbm3_batch* b);
  * allocator, or they run under a fixed device-memory budget).  The paper has
  * no counterpart: this is a service of the library, not part of the method.
  *
- * dev_f: device array [27][ny][nx] of FP32 populations (either layout the
- * library uses; the sums do not depend on the streaming shift), on the
- * current CUDA device.  dev_out: device array of 5 doubles receiving
+ * dev_f: device array of FP32 populations on the current CUDA device, in
+ * the plain layout of the host-side calls: unpadded, [3][9][ny][nx] (plane
+ * k*9 + i holds colour k, direction i; rows of exactly nx values).  This is
+ * NOT the layout of the library's own population buffers (padded rows with
+ * ghost columns, planes grouped by direction), which lbm3_mass reduces
+ * instead.  Whether the values are pre- or post-streaming does not matter:
+ * the sums over all nodes are the same.  dev_out: device array of 5 doubles receiving
  * (mass_r, mass_g, mass_b, mom_x, mom_y) as in lbm3_mass.  Work is enqueued on
  * `cuda_stream` (a cudaStream_t of the current device; NULL = legacy default
  * stream); the call does not synchronise.

@@ -235,7 +235,8 @@ def engulfing_length_eq(sigma_rb: float, R_r: float = 60.0, R_g: float = 80.0, s
 
 
 def near_critical(kind: str, sigma: float, beta_form: int = L.BETA_PAPER, force_form: int = L.FORCE_BODY,
-                  steps: int = 60000, n: int = 300, nu: float = 0.1, recolor_form: int = L.RECOLOR_COSINE) -> dict:
+                  steps: int = 60000, n: int = 300, nu: float = 0.1, recolor_form: int = L.RECOLOR_COSINE,
+                  normal_delta: float = 0.1) -> dict:
     """Sec. 4.3 near-critical states, n x n periodic, viscosities nu.
     kind = "kissing": two droplets R = 60, sigma_rg = 0.01, sigma_gb =
     sigma_rb = `sigma`, centres d_rg (Eq. drg) apart across y = 150.5, the
@@ -243,9 +244,10 @@ def near_critical(kind: str, sigma: float, beta_form: int = L.BETA_PAPER, force_
     droplet R_r = 60 partially engulfed by a green one R_g = 80, sigma_gb =
     sigma_rg = 0.01, sigma_rb = `sigma`, centres d_rg apart (the analytic
     value, R_g - R_r at and above the critical 0.02), the red droplet
-    initially whole.  Returns the interface lengths after `steps` steps and
-    the analytic length of the interface that vanishes at the critical
-    point."""
+    initially whole.  normal_delta selects the recolouring normal of Eq. 6
+    (0 = the paper's G/|G|).  Returns the interface lengths after `steps`
+    steps and the analytic length of the interface that vanishes at the
+    critical point."""
     tau = 3.0 * nu + 0.5
     y, x = np.mgrid[0:n, 0:n].astype(float)
     c = (n + 1) / 2.0 - 1.0
@@ -267,7 +269,7 @@ def near_critical(kind: str, sigma: float, beta_form: int = L.BETA_PAPER, force_
         pg = np.clip(edge(R_g - np.hypot(x - c, y - c)) - pr, 0.0, None)
         want, key = engulfing_length_eq(sigma), "L_rb"
     p = L.Params(n, n, tau=(tau, tau, tau), sigma=sig, beta_form=beta_form, force_form=force_form,
-                 recolor_form=recolor_form)
+                 recolor_form=recolor_form, normal_delta=normal_delta)
     sim = L.Simulation(p)
     sim.init(np.stack([pr, pg, np.clip(1.0 - pr - pg, 0.0, None)]))
     sim.step(steps)
