@@ -53,7 +53,16 @@ typedef enum {
 typedef enum {
   LBM3_FP32 = 0,     /* populations stored as FP32, FP32 arithmetic */
   LBM3_FP16_DEV = 1, /* stored as FP32 rho'_k per node plus FP16 deviations f - w_i rho'_k; FP32 arithmetic */
-  LBM3_BF16_DEV = 2  /* the same with BF16 deviations */
+  LBM3_BF16_DEV = 2, /* the same with BF16 deviations */
+  LBM3_REDUCED = 3   /* reduced state, FP32: per node the colour fractions phi_k, the post-collision total
+                        distribution f^dagger_i and the recolouring vectors V_k = sum_{l != k} beta_kl
+                        (rho_k rho_l / rho) n_kl (18 values instead of 27 populations).  Collision and
+                        recolouring use only the total distribution and the colour densities (Eqs. 1, 6),
+                        so every population f_{i,k} = phi_k f^dagger_i + w'_i e_i . V_k is rebuilt
+                        from its source node in the pull, with the same FP32 operations as the FP32
+                        storage: results are bit-identical to LBM3_FP32.  A state set from populations
+                        (lbm3_init, lbm3_set_populations) is kept as FP32 populations in an extra
+                        buffer until the next step turns it into the reduced state.  Body force only. */
 } lbm3_storage;
 
 typedef enum {
@@ -102,7 +111,8 @@ typedef struct {
  * P = max(nx + 8, 136) rounded up to a multiple of 8 (rows carry four ghost
  * columns on each side that hold the periodic wrap): 27 * ny * P * 4 for FP32
  * storage, 27 * ny * P * 2 + 3 * ny * P * 4 for the 16-bit deviation
- * storages.  Writes *bytes.  No device work. */
+ * storages, 18 * ny * P * 4 for the reduced state.  Writes *bytes.  No
+ * device work. */
 lbm3_status lbm3_buffer_bytes(const lbm3_params* p, size_t* bytes);
 
 /* Validate p and create a context bound to the current CUDA device and to
@@ -114,6 +124,10 @@ lbm3_status lbm3_buffer_bytes(const lbm3_params* p, size_t* bytes);
  * lbm3_populations call, one FP32 buffer (27 * ny * P * 4 bytes) used to
  * convert host data.  *out receives the context (NULL on failure). */
 lbm3_status lbm3_create(const lbm3_params* p, void* cuda_stream, lbm3_ctx** out);
+/* (The reduced storage allocates the same FP32 buffer, 27 * ny * P * 4
+ * bytes, on its first lbm3_init / lbm3_set_populations / lbm3_populations /
+ * lbm3_mass / lbm3_phi call; it holds populations set by the caller until
+ * the next step, and the expanded populations for reads.) */
 
 /* Use caller-owned device memory for the two population buffers (each at
  * least lbm3_buffer_bytes bytes, 256-byte aligned, distinct).  The caller keeps
@@ -174,6 +188,47 @@ lbm3_status lbm3_populations(lbm3_ctx* ctx, double* f, int on_device);
  * Returns LBM3_ENUMERIC if a sum is NaN or Inf. */
 lbm3_status lbm3_mass(lbm3_ctx* ctx, double* mass, double* mom);
 
+/* Interface diagnostics of the current state, measured in FP64 on the device
+ * from the FP64 fields (the paper measures contact angles, Eq. theta_kl, and
+ * Laplace jumps, Eqs. laplace and 22, without giving a procedure).
+ *  - Interface points of a pair (k, l), m the third colour: on every link
+ *    (x, y)-(x+1, y) and (x, y)-(x, y+1) inside the grid (not across the
+ *    periodic edges) with phi_k, phi_l > 0 at both ends, where
+ *    ln(phi_k / phi_l) changes sign (> 0 at exactly one end) and
+ *    phi_m < third_max at both ends, the zero of its linear interpolant
+ *    (exact on the tanh profile of Eq. 21).
+ *  - circle[q] = (cx, cy, R), q = pairs 12, 13, 23: the algebraic
+ *    least-squares circle of the pair's points, min sum (x^2 + y^2 + D x +
+ *    E y + F)^2, in grid coordinates (node (x, y) at (x, y)).
+ *  - junction[j] = (x, y): the two intersections of circles 12 and 13, each
+ *    averaged with the intersections of circles 12/23 and 13/23 nearest to it.
+ *  - varphi_junction[j][q]: at junction j each circle's tangent is a line;
+ *    with one direction per line chosen so that no half-plane holds all
+ *    three, the angle inside fluid m between the interfaces k-m and l-m is
+ *    that between their directions, and varphi_kl = 180 - that angle
+ *    (degrees; the contact angle of Eq. theta_kl).  varphi = their mean.
+ *  - p_bulk[k], n_bulk[k]: mean of p = rho/3 over the n_bulk[k] nodes with
+ *    phi_k > bulk_min (NaN if none): p_bulk[k] - p_bulk[l] is the Laplace
+ *    jump across a k-l interface.
+ *  - flags: bit 0 a pair has fewer than 3 points (its circle and every angle
+ *    are NaN), bit 1 circles 12 and 13 do not meet, bit 2 the interfaces do
+ *    not surround a junction (angles NaN in either case).
+ * Written for a droplet that does not cross the periodic edges.  Uses the
+ * idle population buffer as FP64 staging and, on its first call, allocates
+ * 271 KB of device scratch.  Synchronises the stream.  0 < third_max <= 1,
+ * 0 < bulk_min < 1, else LBM3_EINVAL. */
+typedef struct {
+  double varphi[3];
+  double varphi_junction[2][3];
+  double junction[2][2];
+  double circle[3][3];
+  double points[3];
+  double p_bulk[3];
+  double n_bulk[3];
+  int32_t flags;
+} lbm3_interfaces;
+lbm3_status lbm3_interface_diagnostics(lbm3_ctx* ctx, double third_max, double bulk_min, lbm3_interfaces* out);
+
 /* Replace the physical parameters (tau, rho0, sigma_kl, beta0, beta_form,
  * recolor_form) of a context; nx, ny and storage must stay the same
  * (LBM3_EINVAL otherwise).  The state is kept; a recorded run (below) is
@@ -181,7 +236,7 @@ lbm3_status lbm3_mass(lbm3_ctx* ctx, double* mass, double* mom);
 lbm3_status lbm3_set_params(lbm3_ctx* ctx, const lbm3_params* p);
 
 /* Colour fractions phi_k = rho_k / rho (after Eq. 30) at the current time,
- * phi[3][ny][nx] in FP64 (FP32 storage only, LBM3_EINVAL otherwise).
+ * phi[3][ny][nx] in FP64 (FP32 and reduced storage only, LBM3_EINVAL otherwise).
  * Synchronises the stream when on_device is 0. */
 lbm3_status lbm3_phi(lbm3_ctx* ctx, double* phi, int on_device);
 

@@ -46,7 +46,10 @@ struct lbm3_ctx {
   StepArgs base{};
   // TMA descriptors of buf[0] and buf[1]: one (FP32) or two (deviations, rho')
   alignas(64) unsigned char tmap[2][256];
-  float* shadow = nullptr;  // 16-bit storage: FP32 copy of one buffer for host I/O
+  float* shadow = nullptr;  // 16-bit and reduced storage: FP32 populations for host I/O
+  alignas(64) unsigned char shadow_map[256];  // its TMA descriptors (reduced storage)
+  bool in_shadow = false;   // reduced storage: the state is the FP32 populations in the shadow
+  double* diag = nullptr;   // interface diagnostics: block partial sums and totals (first use)
   // reverse mode: checkpoints S_0, S_K, S_2K, ... of a recorded run, the
   // recomputed states of one segment, the adjoint scratch and accumulator
   unsigned char* ckpt = nullptr;
@@ -139,7 +142,7 @@ lbm3_status validate(const lbm3_params* p, std::string* why) {
     return LBM3_EINVAL;
   }
   if (p->beta_form < 0 || p->beta_form > 3 || p->recolor_form < 0 || p->recolor_form > 1 ||
-      p->storage < LBM3_FP32 || p->storage > LBM3_BF16_DEV || p->force_form < 0 || p->force_form > 1) {
+      p->storage < LBM3_FP32 || p->storage > LBM3_REDUCED || p->force_form < 0 || p->force_form > 1) {
     *why = "lbm3: beta_form, recolor_form, storage or force_form out of range";
     return LBM3_EINVAL;
   }
@@ -260,8 +263,12 @@ lbm3_status ensure_buffers(lbm3_ctx* c) {
   return encode_maps(c);
 }
 
-// FP32 target of host input: the current buffer, or for 16-bit storage the
-// FP32 shadow (allocated on first use) that is then encoded into it.
+// FP32 target of host input: the current buffer, or for the 16-bit and
+// reduced storages the FP32 shadow (allocated on first use).  A 16-bit
+// storage encodes it into the current buffer; the reduced storage keeps the
+// state there until the next step, which reads it as FP32 populations and
+// writes the reduced state (the reduced state holds only populations that a
+// step has produced).
 lbm3_status fp32_target(lbm3_ctx* c, float** out) {
   if (c->p.storage == LBM3_FP32) {
     *out = c->buf[c->cur];
@@ -271,9 +278,13 @@ lbm3_status fp32_target(lbm3_ctx* c, float** out) {
     void* p = nullptr;
     if (cudaMalloc(&p, fp32_bytes(c->p)) != cudaSuccess) {
       cudaGetLastError();
-      return fail(c, LBM3_ENOMEM, "lbm3: cannot allocate the FP32 shadow for 16-bit storage");
+      return fail(c, LBM3_ENOMEM, "lbm3: cannot allocate the FP32 shadow of the populations");
     }
     c->shadow = static_cast<float*>(p);
+    if (c->p.storage == LBM3_REDUCED) {
+      const cudaError_t e = lbm3::encode_population_maps(c->shadow_map, c->shadow, c->p.nx, c->p.ny, LBM3_FP32);
+      if (e != cudaSuccess) return cuda_fail(c, e, "encoding the TMA descriptor of the FP32 shadow");
+    }
   }
   *out = c->shadow;
   return LBM3_OK;
@@ -281,7 +292,43 @@ lbm3_status fp32_target(lbm3_ctx* c, float** out) {
 
 lbm3_status commit_fp32(lbm3_ctx* c) {
   if (c->p.storage == LBM3_FP32) return LBM3_OK;
+  if (c->p.storage == LBM3_REDUCED) {
+    c->in_shadow = true;
+    return LBM3_OK;
+  }
   LBM3_CUDA(c, lbm3::launch_encode(c->shadow, c->buf[c->cur], c->p.nx, c->p.ny, c->p.storage, c->stream));
+  return LBM3_OK;
+}
+
+// The current state as a step's input: buffer, TMA descriptors and storage
+// (the FP32 shadow while a reduced-storage state is still populations).
+struct StateIn {
+  const float* buf;
+  const void* map;
+  int storage;
+};
+StateIn state_in(const lbm3_ctx* c) {
+  if (c->p.storage == LBM3_REDUCED && c->in_shadow) return {c->shadow, c->shadow_map, LBM3_FP32};
+  return {c->buf[c->cur], c->tmap[c->cur], c->p.storage};
+}
+
+// FP32 stored populations of the current state: the current buffer (FP32
+// storage) or the shadow, decoded (16-bit) or expanded (reduced) into it.
+lbm3_status fp32_state(lbm3_ctx* c, const float** out) {
+  if (c->p.storage == LBM3_FP32) {
+    *out = c->buf[c->cur];
+    return LBM3_OK;
+  }
+  float* sh = nullptr;
+  lbm3_status st = fp32_target(c, &sh);
+  if (st != LBM3_OK) return st;
+  if (c->p.storage == LBM3_REDUCED) {
+    if (!c->in_shadow)
+      LBM3_CUDA(c, lbm3::launch_expand_reduced(c->buf[c->cur], sh, c->p.nx, c->p.ny, c->base, c->stream));
+  } else {
+    LBM3_CUDA(c, lbm3::launch_decode(c->buf[c->cur], sh, c->p.nx, c->p.ny, c->p.storage, c->stream));
+  }
+  *out = sh;
   return LBM3_OK;
 }
 
@@ -352,7 +399,7 @@ StepArgs args_for(const lbm3_ctx* c, const float* fin, float* fout, int* grid) {
   StepArgs a = c->base;
   a.fin = fin;
   a.fout = fout;
-  if (c->p.storage != LBM3_FP32) {
+  if (c->p.storage == LBM3_FP16_DEV || c->p.storage == LBM3_BF16_DEV) {
     const size_t PS = static_cast<size_t>(lbm3::pitch_of(c->p.nx)) * c->p.ny;
     a.din = reinterpret_cast<const unsigned short*>(fin);
     a.dout = reinterpret_cast<unsigned short*>(fout);
@@ -683,11 +730,15 @@ lbm3_status lbm3_step(lbm3_ctx* c, int64_t n) {
   if (n > 0) c->tape_valid = false;
   for (int64_t s = 0; s < n; ++s) {
     int grid = 0;
-    StepArgs a = args_for(c, c->buf[c->cur], c->buf[c->cur ^ 1], &grid);
+    const StateIn in = state_in(c);
+    // a reduced-storage state that is still populations: FP32 in, reduced out
+    const int storage = in.storage == c->p.storage ? c->p.storage : lbm3::ST_F2R;
+    StepArgs a = args_for(c, in.buf, c->buf[c->cur ^ 1], &grid);
     a.stall_row = c->stall_row;
     c->stall_row = -1;
-    LBM3_CUDA(c, lbm3::launch_step(a, c->tmap[c->cur], grid, lbm3::MODE_STEP, c->p.storage, c->p.force_form, c->stream));
+    LBM3_CUDA(c, lbm3::launch_step(a, in.map, grid, lbm3::MODE_STEP, storage, c->p.force_form, c->stream));
     c->cur ^= 1;
+    c->in_shadow = false;
     c->t += 1;
   }
   return LBM3_OK;
@@ -699,7 +750,8 @@ lbm3_status lbm3_fields(lbm3_ctx* c, double* rho, double* ux, double* uy, double
   DeviceGuard g(c->device);
   const size_t N = nodes(c->p);
   int grid = 0;
-  StepArgs a = args_for(c, c->buf[c->cur], nullptr, &grid);
+  const StateIn in = state_in(c);
+  StepArgs a = args_for(c, in.buf, nullptr, &grid);
   double* staging = reinterpret_cast<double*>(c->buf[c->cur ^ 1]);
   if (on_device) {
     a.out_rho = rho;
@@ -712,7 +764,7 @@ lbm3_status lbm3_fields(lbm3_ctx* c, double* rho, double* ux, double* uy, double
     a.out_uy = uy ? staging + 4 * N : nullptr;
     a.out_p = pr ? staging + 5 * N : nullptr;
   }
-  LBM3_CUDA(c, lbm3::launch_step(a, c->tmap[c->cur], grid, lbm3::MODE_FIELDS, c->p.storage, c->p.force_form, c->stream));
+  LBM3_CUDA(c, lbm3::launch_step(a, in.map, grid, lbm3::MODE_FIELDS, in.storage, c->p.force_form, c->stream));
   if (!on_device) {
     if (rho) LBM3_CUDA(c, cudaMemcpyAsync(rho, staging, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (ux) LBM3_CUDA(c, cudaMemcpyAsync(ux, staging + 3 * N, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -729,14 +781,9 @@ lbm3_status lbm3_populations(lbm3_ctx* c, double* f, int on_device) {
   if (!c->state_set) return fail(c, LBM3_ESTATE, "lbm3_populations: state not initialised");
   DeviceGuard g(c->device);
   const size_t N = nodes(c->p);
-  const float* src = c->buf[c->cur];
-  if (c->p.storage != LBM3_FP32) {
-    float* sh = nullptr;
-    lbm3_status st = fp32_target(c, &sh);
-    if (st != LBM3_OK) return st;
-    LBM3_CUDA(c, lbm3::launch_decode(c->buf[c->cur], sh, c->p.nx, c->p.ny, c->p.storage, c->stream));
-    src = sh;
-  }
+  const float* src = nullptr;
+  lbm3_status st0 = fp32_state(c, &src);
+  if (st0 != LBM3_OK) return st0;
   if (on_device) {
     LBM3_CUDA(c, lbm3::launch_get_planes(src, f, c->p.nx, c->p.ny, 0, 27, c->stream));
     return LBM3_OK;
@@ -757,10 +804,13 @@ lbm3_status lbm3_mass(lbm3_ctx* c, double* mass, double* mom) {
   if (!c) return LBM3_EINVAL;
   if (!c->state_set) return fail(c, LBM3_ESTATE, "lbm3_mass: state not initialised");
   DeviceGuard g(c->device);
-  if (c->p.storage == LBM3_FP32)
-    LBM3_CUDA(c, lbm3::launch_reduce_padded(c->buf[c->cur], c->p.nx, c->p.ny, c->partial, c->red_blocks,
-                                            c->red_out, c->stream));
-  else
+  if (c->p.storage == LBM3_FP32 || c->p.storage == LBM3_REDUCED) {
+    const float* src = nullptr;
+    lbm3_status st0 = fp32_state(c, &src);
+    if (st0 != LBM3_OK) return st0;
+    LBM3_CUDA(c, lbm3::launch_reduce_padded(src, c->p.nx, c->p.ny, c->partial, c->red_blocks, c->red_out,
+                                            c->stream));
+  } else
     LBM3_CUDA(c, lbm3::launch_reduce_dev(c->buf[c->cur], c->p.nx, c->p.ny, c->p.storage, c->partial,
                                          c->red_blocks, c->red_out, c->stream));
   double h[5];
@@ -775,6 +825,41 @@ lbm3_status lbm3_mass(lbm3_ctx* c, double* mass, double* mom) {
   }
   for (int j = 0; j < 5; ++j)
     if (!std::isfinite(h[j])) return fail(c, LBM3_ENUMERIC, "lbm3_mass: non-finite sum (NaN/Inf in the state)");
+  return LBM3_OK;
+}
+
+lbm3_status lbm3_interface_diagnostics(lbm3_ctx* c, double third_max, double bulk_min, lbm3_interfaces* out) {
+  if (!c) return LBM3_EINVAL;
+  if (!out) return fail(c, LBM3_EINVAL, "lbm3_interface_diagnostics: NULL out");
+  if (!(third_max > 0.0 && third_max <= 1.0) || !(bulk_min > 0.0 && bulk_min < 1.0))
+    return fail(c, LBM3_EINVAL, "lbm3_interface_diagnostics: need 0 < third_max <= 1 and 0 < bulk_min < 1");
+  if (!c->state_set) return fail(c, LBM3_ESTATE, "lbm3_interface_diagnostics: state not initialised");
+  DeviceGuard g(c->device);
+  if (!c->diag) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, lbm3::diag_scratch_doubles() * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, LBM3_ENOMEM, "lbm3_interface_diagnostics: cannot allocate the diagnostic scratch");
+    }
+    c->diag = static_cast<double*>(q);
+  }
+  const size_t N = nodes(c->p);
+  int grid = 0;
+  const StateIn in = state_in(c);
+  StepArgs a = args_for(c, in.buf, nullptr, &grid);
+  // FP64 rho_k and p of the current state in the idle buffer (32 bytes per node)
+  double* staging = reinterpret_cast<double*>(c->buf[c->cur ^ 1]);
+  a.out_rho = staging;
+  a.out_p = staging + 3 * N;
+  LBM3_CUDA(c, lbm3::launch_step(a, in.map, grid, lbm3::MODE_FIELDS, in.storage, c->p.force_form, c->stream));
+  LBM3_CUDA(c, lbm3::launch_diag(staging, staging + 3 * N, c->p.nx, c->p.ny, third_max, bulk_min, c->diag,
+                                 c->stream));
+  double sums[33];
+  LBM3_CUDA(c, cudaMemcpyAsync(sums, c->diag + static_cast<size_t>(lbm3::kDiagMaxBlocks) * 33, sizeof sums,
+                               cudaMemcpyDeviceToHost, c->stream));
+  lbm3_status st = check_device_errors(c);
+  if (st != LBM3_OK) return st;
+  lbm3::diag_geometry(sums, c->p.nx, c->p.ny, out);
   return LBM3_OK;
 }
 
@@ -795,6 +880,7 @@ lbm3_status lbm3_destroy(lbm3_ctx* c) {
     cudaFree(c->buf[1]);
   }
   if (c->shadow) cudaFree(c->shadow);
+  if (c->diag) cudaFree(c->diag);
   if (c->ckpt) cudaFree(c->ckpt);
   if (c->tape) cudaFree(c->tape);
   if (c->adj) cudaFree(c->adj);
@@ -812,6 +898,14 @@ lbm3_status lbm3_set_params(lbm3_ctx* c, const lbm3_params* p) {
   if (validate(p, &why) != LBM3_OK) return fail(c, LBM3_EINVAL, "%s", why.c_str());
   if (p->nx != c->p.nx || p->ny != c->p.ny || p->storage != c->p.storage)
     return fail(c, LBM3_EINVAL, "lbm3_set_params: nx, ny and storage cannot change");
+  if (c->p.storage == LBM3_REDUCED && c->state_set && !c->in_shadow) {
+    // the reduced state's populations are formed with the recolouring
+    // weights of the step that produced them: expand them with those weights
+    const float* sh = nullptr;
+    lbm3_status st = fp32_state(c, &sh);
+    if (st != LBM3_OK) return st;
+    c->in_shadow = true;
+  }
   c->p = *p;
   fill_constants(*p, &c->base);
   c->tape_valid = false;
@@ -822,11 +916,15 @@ lbm3_status lbm3_phi(lbm3_ctx* c, double* phi, int on_device) {
   if (!c) return LBM3_EINVAL;
   if (!phi) return fail(c, LBM3_EINVAL, "lbm3_phi: NULL phi");
   if (!c->state_set) return fail(c, LBM3_ESTATE, "lbm3_phi: state not initialised");
-  if (c->p.storage != LBM3_FP32) return fail(c, LBM3_EINVAL, "lbm3_phi: needs FP32 storage (use lbm3_fields)");
+  if (c->p.storage != LBM3_FP32 && c->p.storage != LBM3_REDUCED)
+    return fail(c, LBM3_EINVAL, "lbm3_phi: needs FP32 or reduced storage (use lbm3_fields)");
   DeviceGuard g(c->device);
   const size_t N = nodes(c->p);
+  const float* src = nullptr;
+  lbm3_status st0 = fp32_state(c, &src);
+  if (st0 != LBM3_OK) return st0;
   double* dst = on_device ? phi : reinterpret_cast<double*>(c->buf[c->cur ^ 1]);
-  LBM3_CUDA(c, lbm3::launch_phi(c->buf[c->cur], dst, c->p.nx, c->p.ny, c->stream));
+  LBM3_CUDA(c, lbm3::launch_phi(src, dst, c->p.nx, c->p.ny, c->stream));
   if (on_device) return LBM3_OK;
   LBM3_CUDA(c, cudaMemcpyAsync(phi, dst, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   return check_device_errors(c);

@@ -126,6 +126,31 @@ __global__ void decode_kernel(const unsigned short* __restrict__ dev, float* __r
   }
 }
 
+// FP32 stored populations (padded, group-ordered layout) of a reduced state:
+// the value of colour k, direction i at node x is Eq. 6 formed from x's own
+// phi_k, f^dagger_i and V_k by red_pop, as the step's C stage forms it for
+// the FP32 storage (so the expansion is bit-identical to that storage).
+// Ghost columns are expanded from the reduced state's ghost columns.
+__global__ void expand_red_kernel(const float* __restrict__ red, float* __restrict__ f, int nx, int ny,
+                                  StepArgs a) {
+  const int P = pitch_of(nx);
+  const size_t PS = static_cast<size_t>(P) * ny;
+  const float4* vec = reinterpret_cast<const float4*>(red);
+  const float* scl = red + 4 * kRedVecPlanes * PS;
+  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < PS;
+       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    if (static_cast<int>(n % P) >= nx + 2 * kGhost) continue;  // columns after the right ghosts are unused
+    const float4 A = vec[n], X = vec[PS + n], Y = vec[2 * PS + n];
+    const float fd[9] = {A.w, X.w, Y.w, scl[n], scl[PS + n], scl[2 * PS + n], scl[3 * PS + n], scl[4 * PS + n],
+                         scl[5 * PS + n]};
+    const float ph[3] = {A.x, A.y, A.z}, vx[3] = {X.x, X.y, X.z}, vy[3] = {Y.x, Y.y, Y.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int i = 0; i < 9; ++i) f[plane_of(k, i) * PS + n] = red_pop(i, ph[k], fd[i], vx[k], vy[k], a.wrec);
+  }
+}
+
 __global__ void check_rho_kernel(const double* __restrict__ rho, int n, unsigned int* bad) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     const double a = rho[j], b = rho[n + j], c = rho[2 * n + j];
@@ -341,6 +366,13 @@ cudaError_t launch_encode(const float* fp32, void* buf, int nx, int ny, int stor
     encode_kernel<ST_FP16><<<g, 256, 0, s>>>(fp32, d, nx, ny);
   else
     encode_kernel<ST_BF16><<<g, 256, 0, s>>>(fp32, d, nx, ny);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_reduced(const float* red, float* fp32, int nx, int ny, const StepArgs& a,
+                                  cudaStream_t s) {
+  const int g = grid_for(static_cast<size_t>(pitch_of(nx)) * ny);
+  expand_red_kernel<<<g, 256, 0, s>>>(red, fp32, nx, ny, a);
   return cudaGetLastError();
 }
 

@@ -9,6 +9,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "../../include/lbm3.h"
+
 namespace lbm3 {
 
 // ---------------------------------------------------------------- lattice
@@ -39,8 +41,12 @@ __host__ __device__ constexpr float wt(int i) {
 //   group 0: e_y = +1 {2, 5, 6}; group 1: e_y = 0 {0, 1, 3}; group 2: e_y = -1 {4, 7, 8}
 //   plane(k, i) = 9 * group(i) + 3 * k + position of i in its group.
 constexpr int kGhost = 4;
-// storage of the populations between steps
-enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2 };
+// storage of the state between steps.  ST_RED is the reduced state (below);
+// ST_F2R is a step that reads FP32 populations and writes the reduced state
+// (the first step after the state was set from populations).
+enum { ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2, ST_RED = 3, ST_F2R = 4 };
+__host__ __device__ constexpr int st_in(int st) { return st == ST_F2R ? ST_FP32 : st; }
+__host__ __device__ constexpr int st_out(int st) { return st == ST_F2R ? ST_RED : st; }
 __host__ __device__ constexpr int dir_group(int i) { return ey(i) > 0 ? 0 : (ey(i) == 0 ? 1 : 2); }
 __host__ __device__ constexpr int dir_pos(int i) {
   return (i == 2 || i == 0 || i == 4) ? 0 : ((i == 5 || i == 1 || i == 7) ? 1 : 2);
@@ -87,9 +93,46 @@ constexpr int kDevGroupHalfs = (9 * kDevBoxCols + 63) / 64 * 64;
 constexpr int kRhoGroupFloats = (3 * kPW + 31) / 32 * 32;
 static_assert(3 * kDevGroupHalfs * 2 + 3 * kRhoGroupFloats * 4 <= 3 * kGroupFloats * 4,
               "a 16-bit slot must fit in an FP32 slot");
+// Reduced state (collision and recolouring use only the total distribution
+// and the colour densities, Eqs. 1 and 6): per node the colour fractions
+// phi_k, the post-collision totals f^dagger_i and the recolouring vectors
+// V_k = sum_{l != k} beta_kl (rho_k rho_l / rho) n_kl, from which a pulled
+// population is f_{i,k}(x) = phi_k f^dagger_i + w'_i e_i . V_k at x - e_i.
+// HBM: three float4 planes A = (phi_1, phi_2, phi_3, fd_0),
+// X = (V_1x, V_2x, V_3x, fd_1), Y = (V_1y, V_2y, V_3y, fd_2), then six float
+// planes fd_3 .. fd_8, in the padded row layout (72 bytes per padded node).
+// A ring slot holds one source row: the three vector planes (one 4D TMA box)
+// then the six scalar planes (one 3D box), each 128-byte aligned.
+constexpr int kRedVecFloats = (3 * kPW * 4 + 31) / 32 * 32;
+constexpr int kRedSclFloats = (6 * kPW + 31) / 32 * 32;
+constexpr int kRedSlotFloats = kRedVecFloats + kRedSclFloats;
+constexpr int kRedSlots = 6;  // a march-row pair needs 4 source rows; 2 more are in flight
+constexpr int kRedVecPlanes = 3, kRedSclPlanes = 6;
+
+// Pulled population of colour k, direction i, from the reduced state of its
+// source node (phk = phi_k, fd = f^dagger_i, (vx, vy) = V_k there): Eq. 6 as
+// the step's C stage forms it for the FP32 storage, the same FP32 operations
+// in the same order, so the reduced state carries the FP32 form's
+// populations bit for bit.  wrec: the recolouring weights w'_i.
+__device__ __forceinline__ float red_pop(int i, float phk, float fd, float vx, float vy, const float* wrec) {
+  switch (i) {
+    case 0: return __fmul_rn(phk, fd);
+    case 1: return __fmaf_rn(phk, fd, __fmul_rn(wrec[1], vx));
+    case 2: return __fmaf_rn(phk, fd, __fmul_rn(wrec[2], vy));
+    case 3: return __fmaf_rn(phk, fd, -__fmul_rn(wrec[1], vx));
+    case 4: return __fmaf_rn(phk, fd, -__fmul_rn(wrec[2], vy));
+    case 5: return __fmaf_rn(phk, fd, __fmul_rn(wrec[5], __fadd_rn(vx, vy)));
+    case 6: return __fmaf_rn(phk, fd, __fmul_rn(wrec[6], __fsub_rn(vy, vx)));
+    case 7: return __fmaf_rn(phk, fd, -__fmul_rn(wrec[5], __fadd_rn(vx, vy)));
+    default: return __fmaf_rn(phk, fd, -__fmul_rn(wrec[6], __fsub_rn(vy, vx)));
+  }
+}
 constexpr int kDW = kTX + 4;      // density/phi window:     x0-2 .. x0+w+2
 constexpr int kTW = kTX + 2;      // tension-tensor window:  x0-1 .. x0+w+1
 constexpr int kSlots = 4;         // population ring depth (rows): a row is free again after its D stage
+constexpr int kMaxSlots = 6;      // barriers per ring (kSlots, or kRedSlots for the reduced state)
+static_assert(kRedSlots <= kMaxSlots && kRedSlots * kRedSlotFloats <= kSlots * 3 * kGroupFloats,
+              "the reduced ring must fit the FP32 ring");
 constexpr int kConsumers = 256;   // 8 compute warps: one C-stage node each per pair of rows
 constexpr int kThreads = kConsumers + 32;  // + 1 copy-issuing warp
 
@@ -186,6 +229,9 @@ cudaError_t launch_check_rho(const double* rho, int n, unsigned int* bad, cudaSt
 // 16-bit storage: FP32 padded stored values <-> deviations + rho'
 cudaError_t launch_encode(const float* fp32, void* buf, int nx, int ny, int storage, cudaStream_t s);
 cudaError_t launch_decode(const void* buf, float* fp32, int nx, int ny, int storage, cudaStream_t s);
+// reduced state -> FP32 stored populations (padded layout); a.wrec are the recolouring weights
+cudaError_t launch_expand_reduced(const float* red, float* fp32, int nx, int ny, const StepArgs& a,
+                                  cudaStream_t s);
 cudaError_t launch_reduce_dev(const void* buf, int nx, int ny, int storage, double* partial, int blocks,
                               double* out, cudaStream_t s);
 // FP64 reductions: partial[blocks][5] then out[5] = (mass_r, mass_g, mass_b, mom_x, mom_y)
@@ -195,5 +241,17 @@ cudaError_t launch_reduce(const float* f, int N, double* partial, int blocks, do
 // the library's padded, group-ordered layout
 cudaError_t launch_reduce_padded(const float* f, int nx, int ny, double* partial, int blocks, double* out,
                                  cudaStream_t s);
+
+// ------------------------------------------------ interface diagnostics
+// FP64 interface points, circle moments and bulk pressure sums of FP64
+// fields rho [3][N], p [N] (lbm3_diag.cu): partial sums of up to
+// kDiagMaxBlocks blocks, then the 33 totals at scratch + kDiagMaxBlocks * 33.
+constexpr int kDiagMaxBlocks = 1024;
+size_t diag_scratch_doubles();
+cudaError_t launch_diag(const double* rho, const double* p, int nx, int ny, double third_max, double bulk_min,
+                        double* scratch, cudaStream_t s);
+// host side: circles, junctions and contact angles from the 33 totals
+using DiagResult = lbm3_interfaces;
+void diag_geometry(const double* sums, int nx, int ny, DiagResult* r);
 
 }  // namespace lbm3

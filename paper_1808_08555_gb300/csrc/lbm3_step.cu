@@ -31,6 +31,14 @@
 // the 27 populations per node; halo re-reads of neighbouring strips' columns
 // are served by L2.
 //
+// Reduced state (ST_RED): the ring holds source rows of the reduced state
+// (phi_k, f^dagger_i, V_k per node; see lbm3_internal.h), two TMA boxes per
+// row into six slots; the D stage rebuilds each pulled population from its
+// source node with the C stage's own FP32 operations (red_pop), so the
+// reduced form's trajectory is the FP32 form's, bit for bit, at 72 instead of
+// 108 bytes per node and direction of the step.  The C stage stores 9 values
+// per node (three float4 and six floats) instead of 27.
+//
 // Every mbarrier wait is bounded in time (kWaitNs).  A wait that gives up
 // sets bit 0 of *err and marks the CTA aborted: the producer stops issuing
 // copies, the consumers skip their arithmetic but keep every barrier, and the
@@ -52,6 +60,7 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait
 struct Smem {
   // pulled-row ring (row q in slot q % kSlots): three TMA boxes of 9 planes x
   // kPW columns, one per direction group, each starting on a 128-byte boundary
+  // (the reduced state uses the same bytes as kRedSlots slots of kRedSlotFloats)
   float pop[kSlots][3 * kGroupFloats];
   float4 phi[6][kDW];          // (phi_1, phi_2, phi_3, rho) of row q in slot q % 6
   float4 fi4[6][2][kTX];       // (f_1, f_2, f_3, f_4), (f_5, f_6, f_7, f_8) of row q in slot q % 6
@@ -59,8 +68,8 @@ struct Smem {
   float4 T[4][kTW];            // (T_xx, T_xy, T_xy, T_yy) of row q in slot q % 4: the pairs the divergence uses
   float4 nrm01[3][kTX];        // (x, y) of n_12 and n_13 of row q in slot q % 3
   float2 nrm2[3][kTX];         // (x, y) of n_23
-  unsigned long long full[kSlots];
-  unsigned long long empty[kSlots];
+  unsigned long long full[kMaxSlots];
+  unsigned long long empty[kMaxSlots];
   int abort_flag;
 };
 
@@ -160,6 +169,22 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// 4D tiled TMA load of one box (4, boxw, 1, planes) at (0, x, y, 0): the
+// float4 planes of the reduced state.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(x), "r"(y), "r"(0), "r"(su32(bar))
+      : "memory");
+}
+
+// Ring slot of the reduced state's source row r.
+__device__ __forceinline__ float* red_slot(Smem& s, int r) {
+  return &s.pop[0][0] + (r % kRedSlots) * kRedSlotFloats;
+}
+
 // Ring columns of window column 0 (padded column x0) in the FP32 /
 // deviation / rho' boxes of a slot.
 struct RingCols {
@@ -198,20 +223,29 @@ __device__ __forceinline__ int wrap(int a, int n) {
 template <int ST, bool STALL>
 __device__ void produce(Smem& s, const StepArgs& a, const CUtensorMap* map, const CUtensorMap* map1, int x0,
                         int y0, int nq, int lane) {
+  constexpr int STI = st_in(ST);
+  constexpr bool RED = STI == ST_RED;
+  constexpr int NS = RED ? kRedSlots : kSlots;
+  // the reduced state is loaded by source row (y0 - 3 + r, r = 0 .. nq + 1);
+  // the other storages by march row (each row's three boxes from its three
+  // source rows)
+  const int nrows = RED ? nq + 2 : nq;
   const int ny = a.ny;
-  const uint32_t row_bytes = ST == ST_FP32 ? 27u * kPW * 4u : 27u * kDevBoxCols * 2u + 9u * kPW * 4u;
+  const uint32_t row_bytes = STI == ST_FP32 ? 27u * kPW * 4u
+                             : RED          ? (kRedVecPlanes * 4u + kRedSclPlanes) * kPW * 4u
+                                            : 27u * kDevBoxCols * 2u + 9u * kPW * 4u;
   const int tma_x = min(x0, a.pitch - kPW);
   const int dev_x = min(x0, a.pitch - kDevBoxCols) & ~7;
   volatile int* abort_flag = &s.abort_flag;
   int issued = 0;
-  for (int q = 0; q < nq; ++q) {
-    const int slot = q % kSlots;
+  for (int q = 0; q < nrows; ++q) {
+    const int slot = q % NS;
     // lane 0 decides for the whole warp, so the warp never diverges around
     // the __syncwarp() calls below
     int ok = 1;
     if (lane == 0) {
-      if (q >= kSlots)
-        ok = mbar_wait(&s.empty[slot], static_cast<uint32_t>((q / kSlots - 1) & 1), abort_flag, a.err) ? 1 : 0;
+      if (q >= NS)
+        ok = mbar_wait(&s.empty[slot], static_cast<uint32_t>((q / NS - 1) & 1), abort_flag, a.err) ? 1 : 0;
       if (ok && *abort_flag) ok = 0;
     }
     ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -222,7 +256,14 @@ __device__ void produce(Smem& s, const StepArgs& a, const CUtensorMap* map, cons
     // is announced but never copied, so the consumers' bounded waits run out
     const bool stall = STALL && q == a.stall_row && blockIdx.x == 0;
     if (stall) {
-    } else if (ST == ST_FP32) {
+    } else if (RED) {
+      const int src_row = wrap(y0 - 3 + q, ny);
+      float* sl = red_slot(s, q);
+      if (lane == 0)
+        tma_load_4d(sl, map, tma_x, src_row, &s.full[slot]);
+      else if (lane == 1)
+        tma_load_3d(sl + kRedVecFloats, map1, tma_x, src_row, 0, &s.full[slot]);
+    } else if (STI == ST_FP32) {
       if (lane < 3) {
         const int g = lane;  // e_y = 1 - g
         const int src_row = wrap(y0 - 2 + q - (1 - g), ny);
@@ -244,8 +285,8 @@ __device__ void produce(Smem& s, const StepArgs& a, const CUtensorMap* map, cons
   // Wait (bounded) until every issued row has landed, so that no copy can
   // target this CTA's shared memory after it exits.  On the normal path the
   // consumers wait for the same phases, so this costs nothing.
-  for (int q = (issued > kSlots ? issued - kSlots : 0); q < issued; ++q)
-    mbar_wait_drain(&s.full[q % kSlots], static_cast<uint32_t>((q / kSlots) & 1));
+  for (int q = (issued > NS ? issued - NS : 0); q < issued; ++q)
+    mbar_wait_drain(&s.full[q % NS], static_cast<uint32_t>((q / NS) & 1));
 }
 
 // ---------------------------------------------------------------- consumers
@@ -299,6 +340,69 @@ __device__ __forceinline__ void stage_density(Smem& s, int q, int c, int w, cons
     }
     r[k] = f0[k] + (A.x + A.y);
   }
+  float phk[3], rho;
+  colour_fractions(r[0], r[1], r[2], phk, &rho);
+  const int fs = q % 6;
+  s.phi[fs][c] = make_float4(phk[0], phk[1], phk[2], rho);
+  if (c >= 2 && c < w + 2) {
+#pragma unroll
+    for (int m = 0; m < 2; ++m) s.fi4[fs][m][c - 2] = make_float4(F[2 * m].x, F[2 * m].y, F[2 * m + 1].x, F[2 * m + 1].y);
+    s.fi0[fs][c - 2] = (f0[0] + f0[1]) + f0[2];
+  }
+}
+
+// The three colours' pulled populations of direction I at the node of
+// density column c (reduced state): from the source node x - e_I, in source
+// row r = q + 1 - e_Iy of the ring and window column c + 2 - e_Ix.
+template <int I>
+__device__ __forceinline__ void pull_red(Smem& s, const StepArgs& a, int q, int wc, float* v) {
+  const float* sl = red_slot(s, q + 1 - ey(I));
+  const float4* vec = reinterpret_cast<const float4*>(sl);
+  const int col = wc - ex(I);
+  const float4 A = vec[col];  // (phi_1, phi_2, phi_3, fd_0)
+  float4 X = make_float4(0.0f, 0.0f, 0.0f, 0.0f), Y = X;
+  if (ex(I) != 0 || I == 1) X = vec[kPW + col];      // (V_1x, V_2x, V_3x, fd_1)
+  if (ey(I) != 0 || I == 2) Y = vec[2 * kPW + col];  // (V_1y, V_2y, V_3y, fd_2)
+  const float fd = I == 0 ? A.w : (I == 1 ? X.w : (I == 2 ? Y.w : sl[kRedVecFloats + (I - 3) * kPW + col]));
+  v[0] = red_pop(I, A.x, fd, X.x, Y.x, a.wrec);
+  v[1] = red_pop(I, A.y, fd, X.y, Y.y, a.wrec);
+  v[2] = red_pop(I, A.z, fd, X.z, Y.z, a.wrec);
+}
+
+// D stage, one node, reduced state: the 27 pulled populations rebuilt from
+// their source nodes, then the sums of stage_density in the same order, so
+// every result equals the FP32 storage's.
+__device__ __forceinline__ void stage_density_red(Smem& s, const StepArgs& a, int q, int c, int w,
+                                                  const RingCols& rc) {
+  const int wc = c + 2 + rc.f;
+  float f0[3], r[3];
+  pull_red<0>(s, a, q, wc, f0);
+  float2 F[4], A[3];
+  float vi[3], vj[3];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    if (m == 0) {
+      pull_red<1>(s, a, q, wc, vi);
+      pull_red<2>(s, a, q, wc, vj);
+    } else if (m == 1) {
+      pull_red<3>(s, a, q, wc, vi);
+      pull_red<4>(s, a, q, wc, vj);
+    } else if (m == 2) {
+      pull_red<5>(s, a, q, wc, vi);
+      pull_red<6>(s, a, q, wc, vj);
+    } else {
+      pull_red<7>(s, a, q, wc, vi);
+      pull_red<8>(s, a, q, wc, vj);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float2 P = make_float2(vi[k], vj[k]);
+      A[k] = m == 0 ? P : add2(A[k], P);
+      F[m] = k == 0 ? P : add2(F[m], P);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) r[k] = f0[k] + (A[k].x + A[k].y);
   float phk[3], rho;
   colour_fractions(r[0], r[1], r[2], phk, &rho);
   const int fs = q % 6;
@@ -545,7 +649,29 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
     val[plane_of(k, 8)] = v78.y;
   }
   const size_t off = static_cast<size_t>(y) * a.pitch + (x + kGhost);
-  if (ST == ST_FP32) {
+  constexpr int STO = st_out(ST);
+  if (STO == ST_RED) {
+    // reduced state: phi_k and f^dagger_0 (A), V_kx and f^dagger_1 (X),
+    // V_ky and f^dagger_2 (Y), f^dagger_3 .. f^dagger_8; with the ghost
+    // copies of the four columns next to each edge as for the populations
+    const size_t PS = static_cast<size_t>(a.ny) * a.pitch;
+    float4* vo = reinterpret_cast<float4*>(a.fout) + off;
+    float* so = a.fout + 4 * kRedVecPlanes * PS + off;
+    const float4 A4 = make_float4(phi0, phi1, phi2, fd0);
+    const float4 X4 = make_float4(V[0].x, V[1].x, V[2].x, fd12.x);
+    const float4 Y4 = make_float4(V[0].y, V[1].y, V[2].y, fd12.y);
+    const float sc[6] = {fd34.x, fd34.y, fd56.x, fd56.y, fd78.x, fd78.y};
+    auto put = [&](ptrdiff_t d) {
+      vo[d] = A4;
+      vo[PS + d] = X4;
+      vo[2 * PS + d] = Y4;
+#pragma unroll
+      for (int t = 0; t < 6; ++t) so[t * PS + d] = sc[t];
+    };
+    put(0);
+    if (x < kGhost) put(a.nx);
+    if (x >= a.nx - kGhost) put(-static_cast<ptrdiff_t>(a.nx));
+  } else if (STO == ST_FP32) {
     // each colour's nine values are stored, with their ghost copies, as soon
     // as they exist: shorter live ranges at the 96-register cap of two CTAs
     // per SM (2.6 % faster than storing all 27 at the end)
@@ -633,6 +759,7 @@ __device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q,
 // consumer thread.
 template <int MODE, int ST, int FORCE>
 __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h, int tid) {
+  constexpr int STI = st_in(ST);
   const int nq = h + 4;  // rows q = 0 .. h+3 <-> y = y0-2 .. y0+h+1
   const RingCols rc = ring_cols(a, x0);
   volatile int* abort_flag = &s.abort_flag;
@@ -643,19 +770,38 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
     {
       const int q0 = 2 * j;
       const int nr = min(2, nq - q0);
-      for (int r = 0; r < nr && !dead; ++r) {
-        const int q = q0 + r;
-        const uint32_t par = static_cast<uint32_t>((q / kSlots) & 1);
-        if (!mbar_try_wait(&s.full[q % kSlots], par)) dead = !mbar_wait(&s.full[q % kSlots], par, abort_flag, a.err);
+      if (STI == ST_RED) {
+        // march rows q0, q0 + 1 pull from source rows q0 .. q0 + nr + 1
+        for (int r = q0; r <= q0 + nr + 1 && !dead; ++r) {
+          const uint32_t par = static_cast<uint32_t>((r / kRedSlots) & 1);
+          if (!mbar_try_wait(&s.full[r % kRedSlots], par))
+            dead = !mbar_wait(&s.full[r % kRedSlots], par, abort_flag, a.err);
+        }
+      } else {
+        for (int r = 0; r < nr && !dead; ++r) {
+          const int q = q0 + r;
+          const uint32_t par = static_cast<uint32_t>((q / kSlots) & 1);
+          if (!mbar_try_wait(&s.full[q % kSlots], par)) dead = !mbar_wait(&s.full[q % kSlots], par, abort_flag, a.err);
+        }
       }
       if (!dead && tid < nr * (w + 4)) {
         const int W = w + 4;
         const int r = tid >= W ? 1 : 0;
-        stage_density<ST>(s, q0 + r, tid - r * W, w, rc);
+        if (STI == ST_RED)
+          stage_density_red(s, a, q0 + r, tid - r * W, w, rc);
+        else
+          stage_density<STI>(s, q0 + r, tid - r * W, w, rc);
       }
-      // this thread is done with the population rows of this D stage: the
-      // producer may refill their slots (every consumer arrives once per row)
-      for (int r = 0; r < nr; ++r) mbar_arrive(&s.empty[(q0 + r) % kSlots]);
+      // this thread is done with the rows of this D stage: the producer may
+      // refill their slots (every consumer arrives once per row).  Source
+      // rows q0 and q0 + 1 of the reduced state have served all three march
+      // rows that pull from them.
+      if (STI == ST_RED) {
+        mbar_arrive(&s.empty[q0 % kRedSlots]);
+        mbar_arrive(&s.empty[(q0 + 1) % kRedSlots]);
+      } else {
+        for (int r = 0; r < nr; ++r) mbar_arrive(&s.empty[(q0 + r) % kSlots]);
+      }
     }
     consumers_sync();
     // ---------------- T stage: rows q = 2j-1, 2j within [1, nq-2], columns x0-1 .. x0+w
@@ -689,7 +835,7 @@ __device__ __forceinline__ void run_tile(Smem& s, const StepArgs& a, const CUten
   const int nq = h + 4;
   const int tid = threadIdx.x;
   if (tid == 0) {
-    for (int j = 0; j < kSlots; ++j) {
+    for (int j = 0; j < kMaxSlots; ++j) {
       mbar_init(&s.full[j], 1);
       mbar_init(&s.empty[j], kConsumers);
     }
@@ -793,6 +939,9 @@ cudaError_t step_configure() {
   if (e == cudaSuccess) e = configure_one<MODE_FIELDS, ST_FP16>(bytes);
   if (e == cudaSuccess) e = configure_one<MODE_STEP, ST_BF16>(bytes);
   if (e == cudaSuccess) e = configure_one<MODE_FIELDS, ST_BF16>(bytes);
+  if (e == cudaSuccess) e = configure_one<MODE_STEP, ST_RED>(bytes);
+  if (e == cudaSuccess) e = configure_one<MODE_FIELDS, ST_RED>(bytes);
+  if (e == cudaSuccess) e = configure_one<MODE_STEP, ST_F2R>(bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(fused_step_kernel<MODE_STEP, ST_FP32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              bytes);
@@ -844,6 +993,14 @@ cudaError_t launch_step(const StepArgs& a, const void* tmaps, int grid, int mode
       fused_step_kernel<MODE_STEP, ST_FP32, 0><<<grid, kThreads, sm, st>>>(a, m0, m1);
     else
       fused_step_kernel<MODE_FIELDS, ST_FP32, 0><<<grid, kThreads, sm, st>>>(a, m0, m1);
+  } else if (storage == ST_RED) {
+    if (mode == MODE_STEP)
+      fused_step_kernel<MODE_STEP, ST_RED, 0><<<grid, kThreads, sm, st>>>(a, m0, m1);
+    else
+      fused_step_kernel<MODE_FIELDS, ST_RED, 0><<<grid, kThreads, sm, st>>>(a, m0, m1);
+  } else if (storage == ST_F2R) {  // FP32 populations in, reduced state out
+    if (mode != MODE_STEP) return cudaErrorInvalidValue;
+    fused_step_kernel<MODE_STEP, ST_F2R, 0><<<grid, kThreads, sm, st>>>(a, m0, m1);
   } else if (storage == ST_FP16) {
     if (mode == MODE_STEP)
       fused_step_kernel<MODE_STEP, ST_FP16, 0><<<grid, kThreads, sm, st>>>(a, m0, m1);
@@ -860,6 +1017,7 @@ cudaError_t launch_step(const StepArgs& a, const void* tmaps, int grid, int mode
 
 size_t population_bytes(int nx, int ny, int storage) {
   const size_t PS = static_cast<size_t>(pitch_of(nx)) * static_cast<size_t>(ny);
+  if (storage == ST_RED) return (4 * kRedVecPlanes + kRedSclPlanes) * PS * 4;
   return storage == ST_FP32 ? 27 * PS * 4 : 27 * PS * 2 + 3 * PS * 4;
 }
 
@@ -906,6 +1064,22 @@ cudaError_t encode_population_maps(void* tmaps, const void* buf, int nx, int ny,
   if (!encode) return e;
   const int P = pitch_of(nx);
   unsigned char* m = static_cast<unsigned char*>(tmaps);
+  if (storage == ST_RED) {
+    // the float4 planes as a (4, P, ny, 3) FP32 tensor, box (4, kPW, 1, 3);
+    // the scalar planes as (P, ny, 6), box (kPW, 1, 6)
+    const cuuint64_t dims[4] = {4, static_cast<cuuint64_t>(P), static_cast<cuuint64_t>(ny), kRedVecPlanes};
+    const cuuint64_t strides[3] = {16, static_cast<cuuint64_t>(P) * 16, static_cast<cuuint64_t>(ny) * P * 16};
+    const cuuint32_t box[4] = {4, static_cast<cuuint32_t>(kPW), 1, kRedVecPlanes};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(reinterpret_cast<CUtensorMap*>(m), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                              const_cast<void*>(buf), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    const float* scl = static_cast<const float*>(buf) + static_cast<size_t>(4 * kRedVecPlanes) * P * ny;
+    return encode_3d(encode, m + 128, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, scl, P, ny, kRedSclPlanes, kPW,
+                     kRedSclPlanes);
+  }
   if (storage == ST_FP32) {
     e = encode_3d(encode, m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, buf, P, ny, 27, kPW, 9);
     if (e == cudaSuccess) memcpy(m + 128, m, 128);  // unused second map

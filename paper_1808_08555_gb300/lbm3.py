@@ -27,7 +27,7 @@ _STATUS = {OK: "LBM3_OK", EINVAL: "LBM3_EINVAL", ENOMEM: "LBM3_ENOMEM", ECUDA: "
            ESTATE: "LBM3_ESTATE", ENUMERIC: "LBM3_ENUMERIC", ETIMEOUT: "LBM3_ETIMEOUT"}
 BETA_PAPER, BETA_FU, BETA_SPENCER, BETA_LECLAIRE = range(4)
 RECOLOR_COSINE, RECOLOR_LITERAL = range(2)
-FP32, FP16_DEV, BF16_DEV = 0, 1, 2
+FP32, FP16_DEV, BF16_DEV, REDUCED = 0, 1, 2, 3
 FORCE_BODY, FORCE_PERTURBATION = 0, 1
 
 
@@ -81,6 +81,15 @@ class Params:
         return p
 
 
+class lbm3_interfaces(ctypes.Structure):
+    _fields_ = [
+        ("varphi", ctypes.c_double * 3), ("varphi_junction", (ctypes.c_double * 3) * 2),
+        ("junction", (ctypes.c_double * 2) * 2), ("circle", (ctypes.c_double * 3) * 3),
+        ("points", ctypes.c_double * 3), ("p_bulk", ctypes.c_double * 3), ("n_bulk", ctypes.c_double * 3),
+        ("flags", ctypes.c_int32),
+    ]
+
+
 _lib = None
 
 
@@ -113,6 +122,8 @@ def load() -> ctypes.CDLL:
         "lbm3_mass_noalloc": (st, [vp, ctypes.c_int32, ctypes.c_int32, vp, vp]),
         "lbm3_set_params": (st, [vp, P]),
         "lbm3_phi": (st, [vp, dp, ctypes.c_int]),
+        "lbm3_interface_diagnostics": (st, [vp, ctypes.c_double, ctypes.c_double,
+                                            ctypes.POINTER(lbm3_interfaces)]),
         "lbm3_tape_forward": (st, [vp, ctypes.c_int64, ctypes.c_int32]),
         "lbm3_tape_backward": (st, [vp, dp, ctypes.c_int, dp, dp, ctypes.c_int, dp]),
         "lbm3_batch_create": (st, [P, ctypes.c_int32, vp, ctypes.c_int32, ctypes.POINTER(vp)]),
@@ -248,6 +259,17 @@ def lbm3_phi(ctx, phi):
     _check(ctx, load().lbm3_phi(ctx, p, dev))
 
 
+def lbm3_interface_diagnostics(ctx, third_max: float = 1e-3, bulk_min: float = 0.99) -> dict:
+    """FP64 device diagnostics of the current state (see include/lbm3.h):
+    contact angles varphi_kl (degrees), junctions, fitted interface circles,
+    bulk pressures per fluid."""
+    r = lbm3_interfaces()
+    _check(ctx, load().lbm3_interface_diagnostics(ctx, float(third_max), float(bulk_min), ctypes.byref(r)))
+    return {"varphi": list(r.varphi), "varphi_junction": [list(v) for v in r.varphi_junction],
+            "junctions": [tuple(v) for v in r.junction], "circles": [tuple(v) for v in r.circle],
+            "points": list(r.points), "p_bulk": list(r.p_bulk), "n_bulk": list(r.n_bulk), "flags": int(r.flags)}
+
+
 def lbm3_tape_forward(ctx, nsteps: int, checkpoint_every: int):
     _check(ctx, load().lbm3_tape_forward(ctx, int(nsteps), int(checkpoint_every)))
 
@@ -339,6 +361,9 @@ class Simulation:
         out = np.empty((3, self.params.ny, self.params.nx))
         lbm3_phi(self.ctx, out)
         return out
+
+    def interfaces(self, third_max: float = 1e-3, bulk_min: float = 0.99) -> dict:
+        return lbm3_interface_diagnostics(self.ctx, third_max, bulk_min)
 
     def set_params(self, params: Params):
         lbm3_set_params(self.ctx, params)

@@ -5,11 +5,13 @@ fluid 3 right half of one circle in fluid 1; sigma_12/13/23 =
 
 Records phi_k at 64 interface nodes (default_rng(3), among nodes with
 0.05 < phi_k < 0.95 at the end for the node's colour k = j mod 3), the three
-colour masses, and the pressure jumps p(inside fluid k) - p(far matrix) for
+colour masses, the pressure jumps p(inside fluid k) - p(far matrix) for
 k = 2, 3 (discs of radius R/2 around the half-circle centroids; matrix:
-distance > R + 10 from the centre).  Calls only ``oracle``.
+distance > R + 10 from the centre), the contact angles varphi_kl at the two
+junctions (Eq. theta_kl, measured by ``oracle.diagnostics``) and the bulk
+pressures of the three fluids.  Calls only ``oracle``.
 
-    python tests/golden/make_janus_512.py [--steps 1000]
+    python tests/golden/make_janus_512.py [--steps 1000] [--out FILE]
 """
 from __future__ import annotations
 
@@ -47,6 +49,7 @@ def main():
     ap.add_argument("--out", default=os.path.join(ROOT, "tests", "golden", "janus_512.json"))
     a = ap.parse_args()
     import oracle as O
+    from oracle import diagnostics as D
     from paper_1808_08555_gb300 import workloads as W
     op = O.Params(N, N, tau=(1.0, 1.0, 1.0), sigma=SIGMA)
     t0 = time.time()
@@ -68,11 +71,14 @@ def main():
            "n": N, "R": R, "sigma": SIGMA, "steps": a.steps,
            "nodes_kyx": nodes, "phi": [float(phi[k, y, x]) for (k, y, x) in nodes],
            "mass": [float(m) for m in rho.sum(axis=(1, 2))],
-           "dp2": float(fl["p"][d2].mean() - pf), "dp3": float(fl["p"][d3].mean() - pf),
-           "seconds": round(time.time() - t0, 1)}
+           "dp2": float(fl["p"][d2].mean() - pf), "dp3": float(fl["p"][d3].mean() - pf)}
+    ang = D.contact_angles(phi)
+    out.update({"varphi": ang["varphi"], "varphi_junction": ang["per_junction"], "circles": ang["circles"],
+                "p_bulk": [D.bulk_pressure(phi, fl["p"], k) for k in range(3)],
+                "seconds": round(time.time() - t0, 1)})
     with open(a.out, "w") as fh:
         json.dump(out, fh, indent=1)
-    print(json.dumps({k: out[k] for k in ("mass", "dp2", "dp3", "seconds")}))
+    print(json.dumps({k: out[k] for k in ("mass", "dp2", "dp3", "varphi", "p_bulk", "seconds")}))
 
 
 if __name__ == "__main__":

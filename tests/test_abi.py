@@ -40,6 +40,8 @@ def test_params_struct_layout_matches_header():
     # forms); normal_delta -> 4*2 + 8*10 + 4*4 + 8 = 112 bytes
     assert ctypes.sizeof(L.lbm3_params) == 112
     assert L.lbm3_params.normal_delta.offset == 104
+    # lbm3_interfaces: 31 doubles and an int32 flag word, padded to 8 bytes
+    assert ctypes.sizeof(L.lbm3_interfaces) == 256 and L.lbm3_interfaces.flags.offset == 248
 
 
 @pytest.mark.parametrize("kw", [
@@ -67,6 +69,12 @@ def test_buffer_bytes(lib):
     # 16-bit deviations plus three FP32 rho' planes
     assert L.lbm3_buffer_bytes(L.Params(2048, 2048, storage=1)) == (27 * 2 + 3 * 4) * 2048 * 2056
     assert L.lbm3_buffer_bytes(L.Params(2048, 2048, storage=2)) == (27 * 2 + 3 * 4) * 2048 * 2056
+    # reduced state: three float4 planes and six float planes
+    assert L.lbm3_buffer_bytes(L.Params(2048, 2048, storage=3)) == 18 * 4 * 2048 * 2056
+    with pytest.raises(L.Lbm3Error):
+        L.lbm3_buffer_bytes(L.Params(8, 8, storage=4))
+    with pytest.raises(L.Lbm3Error):   # the perturbation operator runs on FP32 storage only
+        L.lbm3_buffer_bytes(L.Params(8, 8, storage=3, force_form=1))
 
 
 def test_largest_plane_accepted(lib):
