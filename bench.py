@@ -34,6 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_NODE = 216            # 27 pops x 4 B read + 27 x 4 B written
+BYTES_PER_NODE_REDUCED = 144    # 18 values (phi_k, f^dagger_i, V_k) x 4 B read + written
 FALLBACK_HBM_GBS = 6800.0
 WORKLOAD = ("compound double droplet 2048x2048 periodic, fluid-3 core r=200 in fluid-2 shell r=400, "
             "tau=(0.6,0.7,0.9), sigma12/13/23=0.01/0.012/0.005, beta0=0.7, FP32 populations")
@@ -178,7 +179,8 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     case = make_case(args.size or 2048)
-    p = L.Params(case.nx, case.ny, tau=case.tau, sigma=case.sigma, beta0=case.beta0)
+    storage = {"fp32": L.FP32, "reduced": L.REDUCED}[args.storage]
+    p = L.Params(case.nx, case.ny, tau=case.tau, sigma=case.sigma, beta0=case.beta0, storage=storage)
     nodes = case.nx * case.ny
     sim = L.Simulation(p, device=dev)
     stream = sim.stream
@@ -233,7 +235,8 @@ def run_ours(args, ws, rank, local):
     total_updates = ws * nodes * args.steps
     value = aggregate_mlups(ws, nodes, args.steps, ms / 1e3)
     per_launch_s = ms / 1e3 / args.steps
-    achieved = BYTES_PER_NODE * nodes / per_launch_s / 1e9
+    bpn = BYTES_PER_NODE_REDUCED if args.storage == "reduced" else BYTES_PER_NODE
+    achieved = bpn * nodes / per_launch_s / 1e9
     peak, peak_kind = hbm_peak()
     line = {
         "metric": "ternary D2Q9 MLUPS (fused colour-gradient step, 2048^2 compound droplet)",
@@ -255,9 +258,9 @@ def run_ours(args, ws, rank, local):
                          "inputs smaller than L2 (small profiling case)"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4),
-                     "traffic": recorded_traffic() if case.nx == 2048 else None,
+                     "traffic": recorded_traffic() if case.nx == 2048 and args.storage == "fp32" else None,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                     else "fallback 6.8 TB/s", "bytes_per_node": BYTES_PER_NODE,
+                     else "fallback 6.8 TB/s", "bytes_per_node": bpn,
                      "kernel": STEP_KERNEL},
         "e2e": {"value": round(total_updates / e2e_s / 1e6, 2), "unit": "MLUPS",
                 "h2d_bytes_per_step": round(3 * nodes * 8 / args.steps, 1),
@@ -559,6 +562,8 @@ def main():
                          "adjoint: gradient evaluations of the 256^2 gradient workload")
     ap.add_argument("--horizon", type=int, default=2000,
                     help="adjoint workload: steps of the differentiated run (2000 is the workload; fewer for profiling)")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "reduced"],
+                    help="compound workload: state storage (fp32: 27 populations; reduced: phi_k, f^dagger_i, V_k)")
     ap.add_argument("--size", type=int, default=None,
                     help="grid edge (default: 2048 compound, 4096 janus, 256 adjoint); other edges scale the "
                          "droplet radii (profiling and larger cases only)")

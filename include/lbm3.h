@@ -295,6 +295,20 @@ typedef struct lbm3_batch lbm3_batch;
  * *out receives the batch (NULL on failure). */
 lbm3_status lbm3_batch_create(const lbm3_params* params, int32_t count, void* cuda_stream, int32_t rows_per_cta,
                               lbm3_batch** out);
+/* Empirical tile-height tuning of a batch.  Times `candidates` (1..16) tile
+ * heights -- the best ranked by the batch's makespan model (largest-first
+ * assignment of the work items to the GPU's resident CTA slots), plus 64 and
+ * 128 rows when not among them -- with one warm-up and `steps` >= 1 timed
+ * launches each (CUDA events on the batch's stream), on the current state:
+ * every timed launch reads the current state and writes the idle buffers,
+ * so neither the state nor lbm3_batch_time changes.  Keeps the fastest
+ * height for lbm3_batch_step.  *rows and *ms_per_step (either may be NULL)
+ * receive the winner; table (may be NULL) receives (candidates + 2) pairs
+ * (rows, ms per launch), unused pairs zero.  Every instance must be
+ * initialised (else LBM3_ESTATE).  Synchronises the stream.  Results of
+ * later steps do not depend on the height (same arithmetic per node). */
+lbm3_status lbm3_batch_autotune(lbm3_batch* b, int32_t candidates, int32_t steps, int32_t* rows,
+                                double* ms_per_step, double* table);
 /* Number of instances; number of CTA work items of one step. */
 int32_t lbm3_batch_count(const lbm3_batch* b);
 int32_t lbm3_batch_work_items(const lbm3_batch* b);

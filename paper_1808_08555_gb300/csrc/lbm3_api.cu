@@ -1078,7 +1078,9 @@ struct lbm3_batch {
   // (empty for batches of more than kBatchParamInst instances)
   std::vector<lbm3::BatchArgsBlock> pargs;
   int nitems = 0;
+  size_t items_cap = 0;  // BatchItem slots allocated at d_items
   int rows = 64;
+  std::vector<int> ranked;  // tile heights ranked by the makespan model, best first
   int device = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // two steps, by starting parity
   int64_t t = 0;
@@ -1146,6 +1148,62 @@ lbm3_status build_graph(lbm3_batch* b, int parity) {
   return LBM3_OK;
 }
 
+// Work items of every instance for tile height `rows` (equal-width strips of
+// at most kTX columns, row chunks of `rows`), largest first.
+void batch_items(const lbm3_batch* b, int rows, std::vector<lbm3::BatchItem>* out_items) {
+  out_items->clear();
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    const lbm3_ctx* c = b->ctx[i];
+    const int ns = (c->p.nx + lbm3::kTX - 1) / lbm3::kTX;
+    const int H = std::min(rows, c->p.ny);
+    for (int y0 = 0; y0 < c->p.ny; y0 += H)
+      for (int s = 0; s < ns; ++s) {
+        const int x0 = lbm3::strip_x0(s, ns, c->p.nx);
+        out_items->push_back(
+            {static_cast<int>(i), x0, lbm3::strip_x0(s + 1, ns, c->p.nx) - x0, y0, std::min(H, c->p.ny - y0)});
+      }
+  }
+  std::stable_sort(out_items->begin(), out_items->end(), [](const lbm3::BatchItem& a, const lbm3::BatchItem& c) {
+    return a.w * (a.h + 4) > c.w * (c.h + 4);
+  });
+}
+
+// Estimated step time of a work list: largest-first assignment of the items
+// to the resident CTA slots, item cost ~ (h + 4 halo rows) x (w + 32 columns
+// of per-row overhead).
+double batch_makespan(const lbm3_batch* b, const std::vector<lbm3::BatchItem>& its) {
+  const int slots = std::max(1, b->ctx[0]->occ * b->ctx[0]->num_sms);
+  std::vector<double> load(static_cast<size_t>(slots), 0.0);
+  for (const lbm3::BatchItem& it : its) {
+    auto m = std::min_element(load.begin(), load.end());
+    *m += static_cast<double>(it.h + 4) * (it.w + 32);
+  }
+  return *std::max_element(load.begin(), load.end());
+}
+
+// Upload a work list (growing the device array when needed).
+lbm3_status batch_upload(lbm3_batch* b, const std::vector<lbm3::BatchItem>& items) {
+  if (b->d_items) {  // launches in flight may still read the current list
+    const cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, LBM3_ECUDA, "lbm3: batch work list: %s", cudaGetErrorString(e));
+  }
+  if (items.size() > b->items_cap) {
+    if (b->d_items) cudaFree(b->d_items);
+    b->d_items = nullptr;
+    b->items_cap = 0;
+    if (cudaMalloc(&b->d_items, sizeof(lbm3::BatchItem) * items.size()) != cudaSuccess) {
+      cudaGetLastError();
+      return bfail(b, LBM3_ENOMEM, "lbm3: cannot allocate the batch work list");
+    }
+    b->items_cap = items.size();
+  }
+  const cudaError_t e =
+      cudaMemcpy(b->d_items, items.data(), sizeof(lbm3::BatchItem) * items.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return bfail(b, LBM3_ECUDA, "lbm3: batch work list upload: %s", cudaGetErrorString(e));
+  b->nitems = static_cast<int>(items.size());
+  return LBM3_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1193,58 +1251,32 @@ lbm3_status lbm3_batch_create(const lbm3_params* params, int32_t count, void* cu
     }
   }
   // Tile height: given, or the one whose largest-first assignment of the work
-  // items to the resident CTA slots gives the shortest estimated step (item
-  // cost ~ (h + 4 halo rows) x (w + 32 columns of per-row overhead)).
-  auto make_items = [&](int rows, std::vector<lbm3::BatchItem>* out_items) {
-    out_items->clear();
-    for (int i = 0; i < count; ++i) {
-      lbm3_ctx* c = b->ctx[i];
-      const int ns = (c->p.nx + lbm3::kTX - 1) / lbm3::kTX;
-      const int H = std::min(rows, c->p.ny);
-      for (int y0 = 0; y0 < c->p.ny; y0 += H)
-        for (int s = 0; s < ns; ++s) {
-          const int x0 = lbm3::strip_x0(s, ns, c->p.nx);
-          out_items->push_back({i, x0, lbm3::strip_x0(s + 1, ns, c->p.nx) - x0, y0, std::min(H, c->p.ny - y0)});
-        }
-    }
-    std::stable_sort(out_items->begin(), out_items->end(), [](const lbm3::BatchItem& a, const lbm3::BatchItem& c) {
-      return a.w * (a.h + 4) > c.w * (c.h + 4);
-    });
-  };
-  const int slots = std::max(1, b->ctx[0]->occ * b->ctx[0]->num_sms);
-  auto makespan = [&](const std::vector<lbm3::BatchItem>& its) {
-    std::vector<double> load(static_cast<size_t>(slots), 0.0);
-    for (const lbm3::BatchItem& it : its) {
-      auto m = std::min_element(load.begin(), load.end());
-      *m += static_cast<double>(it.h + 4) * (it.w + 32);
-    }
-    return *std::max_element(load.begin(), load.end());
-  };
-  if (rows_per_cta > 0) {
-    make_items(rows_per_cta, &items);
-  } else {
-    double best = 0.0;
+  // items to the resident CTA slots gives the shortest estimated step.  The
+  // heights are kept ranked by that estimate for lbm3_batch_autotune.
+  {
+    std::vector<std::pair<double, int>> est;
     for (int rows = 16; rows <= 512; rows += 8) {
       std::vector<lbm3::BatchItem> cand;
-      make_items(rows, &cand);
-      const double t = makespan(cand);
-      if (items.empty() || t < best) {
-        best = t;
-        items.swap(cand);
-        b->rows = rows;
-      }
+      batch_items(b, rows, &cand);
+      est.push_back({batch_makespan(b, cand), rows});
     }
+    std::stable_sort(est.begin(), est.end(),
+                     [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x.first < y.first; });
+    for (const auto& e : est) b->ranked.push_back(e.second);
   }
-  b->nitems = static_cast<int>(items.size());
+  if (rows_per_cta <= 0) b->rows = b->ranked[0];
+  batch_items(b, b->rows, &items);
   if (count <= lbm3::kBatchParamInst) {
     b->pargs.assign(2, lbm3::BatchArgsBlock{});
     for (int p = 0; p < 2; ++p)
       for (int i = 0; i < count; ++i) b->pargs[static_cast<size_t>(p)].a[i] = descs[static_cast<size_t>(i)].args[p];
   }
-  cudaError_t e = cudaMalloc(&b->d_items, sizeof(lbm3::BatchItem) * items.size());
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_descs, sizeof(lbm3::BatchDesc) * descs.size());
-  if (e == cudaSuccess)
-    e = cudaMemcpy(b->d_items, items.data(), sizeof(lbm3::BatchItem) * items.size(), cudaMemcpyHostToDevice);
+  if (batch_upload(b, items) != LBM3_OK) {
+    std::fprintf(stderr, "lbm3_batch_create: %s\n", b->msg.c_str());
+    destroy_batch(b);
+    return LBM3_ENOMEM;
+  }
+  cudaError_t e = cudaMalloc(&b->d_descs, sizeof(lbm3::BatchDesc) * descs.size());
   if (e == cudaSuccess)
     e = cudaMemcpy(b->d_descs, descs.data(), sizeof(lbm3::BatchDesc) * descs.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
@@ -1259,6 +1291,83 @@ lbm3_status lbm3_batch_create(const lbm3_params* params, int32_t count, void* cu
 }
 
 int32_t lbm3_batch_count(const lbm3_batch* b) { return b ? static_cast<int32_t>(b->ctx.size()) : -1; }
+
+lbm3_status lbm3_batch_autotune(lbm3_batch* b, int32_t candidates, int32_t steps, int32_t* rows_out,
+                                double* ms_out, double* table) {
+  if (!b) return LBM3_EINVAL;
+  if (candidates < 1 || candidates > 16 || steps < 1)
+    return bfail(b, LBM3_EINVAL, "lbm3_batch_autotune: need 1 <= candidates <= 16 and steps >= 1");
+  for (size_t i = 0; i < b->ctx.size(); ++i)
+    if (!b->ctx[i]->state_set) return bfail(b, LBM3_ESTATE, "lbm3_batch_autotune: instance %zu not initialised", i);
+  DeviceGuard g(b->device);
+  // candidates: the model's best-ranked heights, then 64 and 128 if absent
+  std::vector<int> cand(b->ranked.begin(), b->ranked.begin() + std::min<size_t>(candidates, b->ranked.size()));
+  for (int extra : {64, 128})
+    if (std::find(cand.begin(), cand.end(), extra) == cand.end()) cand.push_back(extra);
+  // every timed launch reads the current state and writes the idle buffers,
+  // so neither the state nor the time changes
+  const int parity = b->ctx[0]->cur;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    return bfail(b, LBM3_ECUDA, "lbm3_batch_autotune: cannot create events");
+  }
+  int best_rows = b->rows;
+  double best_ms = 1e300;
+  lbm3_status st = LBM3_OK;
+  for (size_t k = 0; k < cand.size() && st == LBM3_OK; ++k) {
+    std::vector<lbm3::BatchItem> items;
+    batch_items(b, cand[k], &items);
+    st = batch_upload(b, items);
+    if (st != LBM3_OK) break;
+    st = launch_one(b, parity, b->stream);  // warm-up launch
+    if (st != LBM3_OK) break;
+    cudaEventRecord(e0, b->stream);
+    for (int s = 0; s < steps && st == LBM3_OK; ++s) st = launch_one(b, parity, b->stream);
+    cudaEventRecord(e1, b->stream);
+    if (st != LBM3_OK) break;
+    float ms = 0.0f;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      st = bfail(b, LBM3_ECUDA, "lbm3_batch_autotune: %s", cudaGetErrorString(e));
+      break;
+    }
+    const double per = static_cast<double>(ms) / steps;
+    if (table) {
+      table[2 * k] = cand[k];
+      table[2 * k + 1] = per;
+    }
+    if (per < best_ms) {
+      best_ms = per;
+      best_rows = cand[k];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (table)
+    for (size_t k = cand.size(); k < static_cast<size_t>(candidates) + 2; ++k) table[2 * k] = table[2 * k + 1] = 0.0;
+  // keep the winner; the step graphs are captured again for its work list
+  std::vector<lbm3::BatchItem> items;
+  batch_items(b, best_rows, &items);
+  const lbm3_status st2 = batch_upload(b, items);
+  if (st == LBM3_OK) st = st2;
+  b->rows = best_rows;
+  for (int p = 0; p < 2; ++p)
+    if (b->graph[p]) {
+      cudaGraphExecDestroy(b->graph[p]);
+      b->graph[p] = nullptr;
+    }
+  if (rows_out) *rows_out = best_rows;
+  if (ms_out) *ms_out = best_ms;
+  if (st != LBM3_OK) return st;
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    st = check_device_errors(b->ctx[i]);
+    if (st != LBM3_OK) return bcheck(b, st, static_cast<int>(i));
+  }
+  return LBM3_OK;
+}
 
 int32_t lbm3_batch_work_items(const lbm3_batch* b) { return b ? b->nitems : -1; }
 

@@ -128,6 +128,8 @@ def load() -> ctypes.CDLL:
         "lbm3_tape_backward": (st, [vp, dp, ctypes.c_int, dp, dp, ctypes.c_int, dp]),
         "lbm3_batch_create": (st, [P, ctypes.c_int32, vp, ctypes.c_int32, ctypes.POINTER(vp)]),
         "lbm3_batch_count": (ctypes.c_int32, [vp]),
+        "lbm3_batch_autotune": (st, [vp, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_double), dp]),
         "lbm3_batch_work_items": (ctypes.c_int32, [vp]),
         "lbm3_batch_init": (st, [vp, ctypes.c_int32, dp, ctypes.c_int]),
         "lbm3_batch_set_populations": (st, [vp, ctypes.c_int32, dp, ctypes.c_int]),
@@ -461,6 +463,20 @@ def lbm3_batch_destroy(b):
     load().lbm3_batch_destroy(b)
 
 
+def lbm3_batch_autotune(b, candidates: int = 5, steps: int = 20) -> dict:
+    """Time candidate tile heights on the current state (see include/lbm3.h)
+    and keep the fastest.  Returns the winner and every candidate's time."""
+    rows = ctypes.c_int32()
+    ms = ctypes.c_double()
+    table = np.zeros(2 * (candidates + 2))
+    s = load().lbm3_batch_autotune(b, int(candidates), int(steps), ctypes.byref(rows), ctypes.byref(ms),
+                                   ctypes.c_void_p(table.ctypes.data))
+    if s != OK:
+        raise Lbm3Error(s, load().lbm3_batch_last_error(b).decode())
+    cands = [(int(r), float(t)) for r, t in table.reshape(-1, 2) if r > 0]
+    return {"rows": int(rows.value), "ms_per_step": float(ms.value), "candidates": cands}
+
+
 class Batch:
     """Independent simulations advanced together on the current device and
     torch's current stream (one launch per step, replayed from a CUDA graph)."""
@@ -494,6 +510,9 @@ class Batch:
     def step(self, n: int = 1):
         lbm3_batch_step(self.b, n)
         return self
+
+    def autotune(self, candidates: int = 5, steps: int = 20) -> dict:
+        return lbm3_batch_autotune(self.b, candidates, steps)
 
     def populations(self, i) -> np.ndarray:
         p = self.params[i]

@@ -91,3 +91,33 @@ def test_batch_errors(L):
     bad = [L.Params(8, 8), L.Params(6, 8)]
     with pytest.raises(L.Lbm3Error):
         L.Batch(bad)
+
+
+def test_autotune_keeps_state_and_results(L):
+    """Empirical tile-height tuning: the timed candidates leave the state and
+    the time unchanged, the winner is one of the candidates, and steps after
+    tuning (also through the step graphs, which are captured again) equal
+    single-instance runs bit for bit."""
+    params, fields = _instances(L)
+    batch = L.Batch(params)
+    for i, rho in enumerate(fields):
+        batch.init(i, rho)
+    batch.step(3)
+    before = [batch.populations(i) for i in range(len(params))]
+    res = batch.autotune(candidates=4, steps=3)
+    assert batch.t == 3
+    assert res["rows"] in [r for r, _ in res["candidates"]]
+    assert len(res["candidates"]) >= 4 and all(t > 0 for _, t in res["candidates"])
+    assert res["ms_per_step"] == min(t for _, t in res["candidates"])
+    for i in range(len(params)):
+        np.testing.assert_array_equal(batch.populations(i), before[i])
+    batch.step(5)
+    for i, (p, rho) in enumerate(zip(params, fields)):
+        sim = L.Simulation(p)
+        sim.init(rho)
+        sim.step(8)
+        np.testing.assert_array_equal(batch.populations(i), sim.populations(), err_msg=f"instance {i}")
+        sim.close()
+    with pytest.raises(L.Lbm3Error):
+        batch.autotune(candidates=0)
+    batch.close()
