@@ -185,6 +185,22 @@ __device__ __forceinline__ float* red_slot(Smem& s, int r) {
   return &s.pop[0][0] + (r % kRedSlots) * kRedSlotFloats;
 }
 
+// Slots of the three source rows q, q + 1, q + 2 that march row q pulls from
+// (one modulo instead of three).
+struct RedRows {
+  const float* row[3];
+};
+__device__ __forceinline__ RedRows red_rows(Smem& s, int q) {
+  int j = q % kRedSlots;
+  RedRows r;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    r.row[t] = &s.pop[0][0] + j * kRedSlotFloats;
+    j = j + 1 == kRedSlots ? 0 : j + 1;
+  }
+  return r;
+}
+
 // Ring columns of window column 0 (padded column x0) in the FP32 /
 // deviation / rho' boxes of a slot.
 struct RingCols {
@@ -352,11 +368,13 @@ __device__ __forceinline__ void stage_density(Smem& s, int q, int c, int w, cons
 }
 
 // The three colours' pulled populations of direction I at the node of
-// density column c (reduced state): from the source node x - e_I, in source
-// row r = q + 1 - e_Iy of the ring and window column c + 2 - e_Ix.
+// window column wc (reduced state): from the source node x - e_I, in source
+// row q + 1 - e_Iy and window column wc - e_Ix, formed by red_pop.  (Packing
+// colours 1 and 2 into FP32 pairs here spills registers at the 96-register
+// cap of two CTAs per SM.)
 template <int I>
-__device__ __forceinline__ void pull_red(Smem& s, const StepArgs& a, int q, int wc, float* v) {
-  const float* sl = red_slot(s, q + 1 - ey(I));
+__device__ __forceinline__ void pull_red(const RedRows& rr, const StepArgs& a, int wc, float* v) {
+  const float* sl = rr.row[1 - ey(I)];
   const float4* vec = reinterpret_cast<const float4*>(sl);
   const int col = wc - ex(I);
   const float4 A = vec[col];  // (phi_1, phi_2, phi_3, fd_0)
@@ -370,46 +388,49 @@ __device__ __forceinline__ void pull_red(Smem& s, const StepArgs& a, int q, int 
 }
 
 // D stage, one node, reduced state: the 27 pulled populations rebuilt from
-// their source nodes, then the sums of stage_density in the same order, so
-// every result equals the FP32 storage's.
+// their source nodes, one direction at a time, summed as stage_density sums
+// them (each lane of its packed pairs is the same scalar addition, in the
+// same order), so every result equals the FP32 storage's.  Directions are
+// taken one by one so that only one source node's values are live at a time.
 __device__ __forceinline__ void stage_density_red(Smem& s, const StepArgs& a, int q, int c, int w,
                                                   const RingCols& rc) {
   const int wc = c + 2 + rc.f;
-  float f0[3], r[3];
-  pull_red<0>(s, a, q, wc, f0);
-  float2 F[4], A[3];
-  float vi[3], vj[3];
+  const RedRows rr = red_rows(s, q);
+  float f0[3], v[3];
+  float Ax[3], Ay[3], Fx[4], Fy[4];  // lanes of the per-colour pair sums A and the pair totals F
+  pull_red<0>(rr, a, wc, f0);
+  auto take = [&](int lane, int m) {  // lane 0: direction 2m+1, lane 1: 2m+2
+    float* Acc = lane == 0 ? Ax : Ay;
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    if (m == 0) {
-      pull_red<1>(s, a, q, wc, vi);
-      pull_red<2>(s, a, q, wc, vj);
-    } else if (m == 1) {
-      pull_red<3>(s, a, q, wc, vi);
-      pull_red<4>(s, a, q, wc, vj);
-    } else if (m == 2) {
-      pull_red<5>(s, a, q, wc, vi);
-      pull_red<6>(s, a, q, wc, vj);
-    } else {
-      pull_red<7>(s, a, q, wc, vi);
-      pull_red<8>(s, a, q, wc, vj);
-    }
+    for (int k = 0; k < 3; ++k) Acc[k] = m == 0 ? v[k] : Acc[k] + v[k];
+    (lane == 0 ? Fx : Fy)[m] = (v[0] + v[1]) + v[2];
+  };
+  pull_red<1>(rr, a, wc, v);
+  take(0, 0);
+  pull_red<2>(rr, a, wc, v);
+  take(1, 0);
+  pull_red<3>(rr, a, wc, v);
+  take(0, 1);
+  pull_red<4>(rr, a, wc, v);
+  take(1, 1);
+  pull_red<5>(rr, a, wc, v);
+  take(0, 2);
+  pull_red<6>(rr, a, wc, v);
+  take(1, 2);
+  pull_red<7>(rr, a, wc, v);
+  take(0, 3);
+  pull_red<8>(rr, a, wc, v);
+  take(1, 3);
+  float r[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const float2 P = make_float2(vi[k], vj[k]);
-      A[k] = m == 0 ? P : add2(A[k], P);
-      F[m] = k == 0 ? P : add2(F[m], P);
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < 3; ++k) r[k] = f0[k] + (A[k].x + A[k].y);
+  for (int k = 0; k < 3; ++k) r[k] = f0[k] + (Ax[k] + Ay[k]);
   float phk[3], rho;
   colour_fractions(r[0], r[1], r[2], phk, &rho);
   const int fs = q % 6;
   s.phi[fs][c] = make_float4(phk[0], phk[1], phk[2], rho);
   if (c >= 2 && c < w + 2) {
 #pragma unroll
-    for (int m = 0; m < 2; ++m) s.fi4[fs][m][c - 2] = make_float4(F[2 * m].x, F[2 * m].y, F[2 * m + 1].x, F[2 * m + 1].y);
+    for (int m = 0; m < 2; ++m) s.fi4[fs][m][c - 2] = make_float4(Fx[2 * m], Fy[2 * m], Fx[2 * m + 1], Fy[2 * m + 1]);
     s.fi0[fs][c - 2] = (f0[0] + f0[1]) + f0[2];
   }
 }
@@ -771,8 +792,9 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
       const int q0 = 2 * j;
       const int nr = min(2, nq - q0);
       if (STI == ST_RED) {
-        // march rows q0, q0 + 1 pull from source rows q0 .. q0 + nr + 1
-        for (int r = q0; r <= q0 + nr + 1 && !dead; ++r) {
+        // march rows q0, q0 + 1 pull from source rows q0 .. q0 + nr + 1; all
+        // but the last two were waited for in the previous iteration
+        for (int r = j == 0 ? q0 : q0 + 2; r <= q0 + nr + 1 && !dead; ++r) {
           const uint32_t par = static_cast<uint32_t>((r / kRedSlots) & 1);
           if (!mbar_try_wait(&s.full[r % kRedSlots], par))
             dead = !mbar_wait(&s.full[r % kRedSlots], par, abort_flag, a.err);
