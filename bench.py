@@ -3,10 +3,13 @@
 Workload: the 2048x2048 periodic compound double droplet (fluid-3 core radius
 200 inside a fluid-2 shell radius 400 in a fluid-1 matrix, tau = (0.6, 0.7,
 0.9) for viscosity ratio 1:2:4, sigma_12/13/23 = 0.01/0.012/0.005,
-beta^0 = 0.7), FP32 plain storage.  A "step" is one lattice time step of the
+beta^0 = 0.7), FP32 arithmetic.  A "step" is one lattice time step of the
 whole grid (one launch of the fused kernel).  The metric is MLUPS (million
-lattice-node updates per second), reported with the HBM roofline fraction
-(216 algorithmic bytes per node update: 27 FP32 populations read and written).
+lattice-node updates per second), reported with the HBM roofline fraction.
+Two forms of the state are timed: the chosen form, the reduced state (phi_k,
+f^dagger_i and V_k per node; 144 algorithmic bytes per node update), which is
+the headline, and the plain FP32 form (27 populations; 216 bytes); both give
+bit-identical states, so they are compared at equal error.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -37,7 +40,7 @@ BYTES_PER_NODE = 216            # 27 pops x 4 B read + 27 x 4 B written
 BYTES_PER_NODE_REDUCED = 144    # 18 values (phi_k, f^dagger_i, V_k) x 4 B read + written
 FALLBACK_HBM_GBS = 6800.0
 WORKLOAD = ("compound double droplet 2048x2048 periodic, fluid-3 core r=200 in fluid-2 shell r=400, "
-            "tau=(0.6,0.7,0.9), sigma12/13/23=0.01/0.012/0.005, beta0=0.7, FP32 populations")
+            "tau=(0.6,0.7,0.9), sigma12/13/23=0.01/0.012/0.005, beta0=0.7, FP32 arithmetic")
 STEP_KERNEL = "fused_step_kernel"
 
 
@@ -65,10 +68,12 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """Per-launch DRAM bytes of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "fused_step_compound_2048_traffic.json")
+def recorded_traffic(form: str = "fp32"):
+    """Per-launch DRAM bytes of the step kernel in the given form from the
+    committed ncu summary, if it was taken on the current kernel source (else
+    None)."""
+    name = "fused_step_compound_2048_traffic.json" if form == "fp32" else f"fused_step_{form}_compound_2048_traffic.json"
+    path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as fh:
             d = json.load(fh)
@@ -162,10 +167,14 @@ def workload_name(size: int) -> str:
     if size == 2048:
         return WORKLOAD
     return (f"compound double droplet {size}x{size} periodic (the 2048^2 workload with radii scaled by "
-            f"{size}/2048), tau=(0.6,0.7,0.9), sigma12/13/23=0.01/0.012/0.005, beta0=0.7, FP32 populations")
+            f"{size}/2048), tau=(0.6,0.7,0.9), sigma12/13/23=0.01/0.012/0.005, beta0=0.7, FP32 arithmetic")
 
 
 def run_ours(args, ws, rank, local):
+    """The compound-droplet workload in the chosen form (reduced state) and the
+    plain FP32 form; `value` is the chosen form's throughput (both give
+    bit-identical states, so the error is equal by construction), the plain
+    form is reported beside it.  --storage restricts the run to one form."""
     import torch
 
     from paper_1808_08555_gb300 import build as B
@@ -179,14 +188,9 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     case = make_case(args.size or 2048)
-    storage = {"fp32": L.FP32, "reduced": L.REDUCED}[args.storage]
-    p = L.Params(case.nx, case.ny, tau=case.tau, sigma=case.sigma, beta0=case.beta0, storage=storage)
     nodes = case.nx * case.ny
-    sim = L.Simulation(p, device=dev)
-    stream = sim.stream
-    sim.init(case.rho)
-    sim.step(args.warmup)
-    sim.sync()
+    forms = {"reduced": L.REDUCED, "fp32": L.FP32}
+    order = ["reduced", "fp32"] if args.storage == "both" else [args.storage]
 
     def barrier():
         if ws > 1:
@@ -197,79 +201,101 @@ def run_ours(args, ws, rank, local):
     def max_over_ranks(x: float) -> float:
         return reduce_max(x, ws, dev)
 
-    # ---------------- device-resident throughput (inputs already in HBM)
-    clocks = ClockSampler(local)
-    barrier()
-    clocks.start()
-    time.sleep(0.3)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sim.step(args.steps)
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
-    sim.sync()
-    barrier()
-    ms = max_over_ranks(ms)
-    m, mom = sim.mass()
-
-    # ---------------- end to end through the C ABI with host buffers
-    host_rho = torch.from_numpy(case.rho).pin_memory()
-    outs = {k: torch.empty(sh, dtype=torch.float64).pin_memory() for k, sh in
-            (("rho", (3, case.ny, case.nx)), ("ux", (case.ny, case.nx)), ("uy", (case.ny, case.nx)),
-             ("p", (case.ny, case.nx)))}
-    barrier()
-    t0 = time.perf_counter()
-    L.lbm3_init(sim.ctx, host_rho)
-    L.lbm3_step(sim.ctx, args.steps)
-    L.lbm3_fields(sim.ctx, outs["rho"], outs["ux"], outs["uy"], outs["p"])
-    e2e_s = time.perf_counter() - t0
-    barrier()
-    e2e_s = max_over_ranks(e2e_s)
-    sim.close()
+    peak, peak_kind = hbm_peak()
+    res = {}
+    for name in order:
+        p = L.Params(case.nx, case.ny, tau=case.tau, sigma=case.sigma, beta0=case.beta0, storage=forms[name])
+        sim = L.Simulation(p, device=dev)
+        stream = sim.stream
+        sim.init(case.rho)
+        sim.step(args.warmup)
+        sim.sync()
+        # ---------------- device-resident throughput (inputs already in HBM)
+        clocks = ClockSampler(local)
+        barrier()
+        clocks.start()
+        time.sleep(0.3)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        clk = clocks.stop()
+        sim.sync()
+        barrier()
+        ms = max_over_ranks(ms)
+        m, mom = sim.mass()
+        # ---------------- end to end through the C ABI with host buffers
+        host_rho = torch.from_numpy(case.rho).pin_memory()
+        outs = {k: torch.empty(sh, dtype=torch.float64).pin_memory() for k, sh in
+                (("rho", (3, case.ny, case.nx)), ("ux", (case.ny, case.nx)), ("uy", (case.ny, case.nx)),
+                 ("p", (case.ny, case.nx)))}
+        barrier()
+        t0 = time.perf_counter()
+        L.lbm3_init(sim.ctx, host_rho)
+        L.lbm3_step(sim.ctx, args.steps)
+        L.lbm3_fields(sim.ctx, outs["rho"], outs["ux"], outs["uy"], outs["p"])
+        e2e_s = time.perf_counter() - t0
+        barrier()
+        e2e_s = max_over_ranks(e2e_s)
+        sim.close()
+        bpn = BYTES_PER_NODE_REDUCED if name == "reduced" else BYTES_PER_NODE
+        per_launch_s = ms / 1e3 / args.steps
+        achieved = bpn * nodes / per_launch_s / 1e9
+        res[name] = {
+            "value": aggregate_mlups(ws, nodes, args.steps, ms / 1e3), "ms": ms, "clocks": clk,
+            "mass": [float(x) for x in m], "momentum": [float(x) for x in mom],
+            "e2e": ws * nodes * args.steps / e2e_s / 1e6,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4),
+                         "traffic": recorded_traffic(name) if case.nx == 2048 else None,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                         else "fallback 6.8 TB/s", "bytes_per_node": bpn,
+                         "kernel": f"{STEP_KERNEL}<{'reduced state' if name == 'reduced' else 'FP32 populations'}>"},
+        }
 
     if rank != 0:
         return None
+    head = order[0]
+    h = res[head]
     total_updates = ws * nodes * args.steps
-    value = aggregate_mlups(ws, nodes, args.steps, ms / 1e3)
-    per_launch_s = ms / 1e3 / args.steps
-    bpn = BYTES_PER_NODE_REDUCED if args.storage == "reduced" else BYTES_PER_NODE
-    achieved = bpn * nodes / per_launch_s / 1e9
-    peak, peak_kind = hbm_peak()
     line = {
         "metric": "ternary D2Q9 MLUPS (fused colour-gradient step, 2048^2 compound droplet)",
-        "value": round(value, 2),
+        "value": round(h["value"], 2),
         "unit": "MLUPS",
         "n_gpus": ws,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": round(ms / args.steps, 5),
+        "ms_per_step": round(h["ms"] / args.steps, 5),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic (seedless analytic droplet fields, Eq. 21 tanh edges)",
         "config": {"workload": workload_name(case.nx), "nx": case.nx, "ny": case.ny, "nodes_per_step": nodes,
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                   "l2": (f"inputs larger than L2: two {27 * 4 * case.ny * (case.nx + 8) / 1e6:.0f} MB "
-                          "population buffers vs 129 MB L2") if case.nx >= 1024 else
+                   "form": head, "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": (f"inputs larger than L2: two {h['roofline']['bytes_per_node'] / 2 * case.ny * (case.nx + 8) / 1e6:.0f} MB "
+                          "state buffers vs 129 MB L2") if case.nx >= 1024 else
                          "inputs smaller than L2 (small profiling case)"},
-        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4),
-                     "traffic": recorded_traffic() if case.nx == 2048 and args.storage == "fp32" else None,
-                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                     else "fallback 6.8 TB/s", "bytes_per_node": bpn,
-                     "kernel": STEP_KERNEL},
-        "e2e": {"value": round(total_updates / e2e_s / 1e6, 2), "unit": "MLUPS",
+        "roofline": h["roofline"],
+        "e2e": {"value": round(h["e2e"], 2), "unit": "MLUPS",
                 "h2d_bytes_per_step": round(3 * nodes * 8 / args.steps, 1),
                 "d2h_bytes_per_step": round(6 * nodes * 8 / args.steps, 1),
                 "note": "lbm3_init from pinned host rho, K steps, lbm3_fields to pinned host; bytes amortised over K"},
         "gpu_launches": args.steps,
-        "clocks": clk,
-        "checks": {"mass": [float(x) for x in m], "momentum": [float(x) for x in mom]},
+        "clocks": h["clocks"],
+        "checks": {"mass": h["mass"], "momentum": h["momentum"]},
     }
+    if len(order) > 1:
+        line["forms"] = {n: {"MLUPS": round(r["value"], 2), "ms_per_step": round(r["ms"] / args.steps, 5),
+                             "e2e_MLUPS": round(r["e2e"], 2), "roofline": r["roofline"], "clocks": r["clocks"]}
+                         for n, r in res.items()}
+        line["forms"]["equal_error"] = ("the reduced state rebuilds every population with the FP32 form's own "
+                                        "operations: states and masses are bit-identical "
+                                        f"(masses equal here: {res['reduced']['mass'] == res['fp32']['mass']})")
+        line["speedup_vs_plain_fp32"] = round(res["reduced"]["value"] / res["fp32"]["value"], 4)
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(case, args.cpu_steps)
     return line
@@ -562,8 +588,9 @@ def main():
                          "adjoint: gradient evaluations of the 256^2 gradient workload")
     ap.add_argument("--horizon", type=int, default=2000,
                     help="adjoint workload: steps of the differentiated run (2000 is the workload; fewer for profiling)")
-    ap.add_argument("--storage", default="fp32", choices=["fp32", "reduced"],
-                    help="compound workload: state storage (fp32: 27 populations; reduced: phi_k, f^dagger_i, V_k)")
+    ap.add_argument("--storage", default="both", choices=["both", "fp32", "reduced"],
+                    help="compound workload: state storage (both: the reduced form as the headline and the plain "
+                         "FP32 form beside it; fp32: 27 populations only; reduced: phi_k, f^dagger_i, V_k only)")
     ap.add_argument("--size", type=int, default=None,
                     help="grid edge (default: 2048 compound, 4096 janus, 256 adjoint); other edges scale the "
                          "droplet radii (profiling and larger cases only)")

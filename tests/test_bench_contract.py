@@ -62,3 +62,11 @@ def test_library_arm_contract():
         assert k in d["clocks"], k
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["value"] == pytest.approx(256 * 256 * d["steps"] / (d["ms_per_step"] * d["steps"] / 1e3) / 1e6, rel=1e-3)
+    # both forms: the reduced state is the headline, the plain FP32 form beside it, at equal error
+    f = d["forms"]
+    assert d["config"]["form"] == "reduced" and set(f) >= {"reduced", "fp32", "equal_error"}
+    assert f["reduced"]["MLUPS"] == d["value"] and f["reduced"]["roofline"]["bytes_per_node"] == 144
+    assert f["fp32"]["roofline"]["bytes_per_node"] == 216
+    assert "True" in f["equal_error"]
+    assert d["speedup_vs_plain_fp32"] == pytest.approx(f["reduced"]["MLUPS"] / f["fp32"]["MLUPS"], rel=1e-3)
+    assert d["cpu_baseline"]["single_core"]["cores"] == 1
