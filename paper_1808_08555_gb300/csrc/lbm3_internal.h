@@ -107,6 +107,7 @@ constexpr int kRedVecFloats = (3 * kPW * 4 + 31) / 32 * 32;
 constexpr int kRedSclFloats = (6 * kPW + 31) / 32 * 32;
 constexpr int kRedSlotFloats = kRedVecFloats + kRedSclFloats;
 constexpr int kRedSlots = 6;  // a march-row pair needs 4 source rows; 2 more are in flight
+static_assert(kPW % 4 == 0, "the reduced state's vector box moves four columns per innermost run");
 constexpr int kRedVecPlanes = 3, kRedSclPlanes = 6;
 
 // Pulled population of colour k, direction i, from the reduced state of its

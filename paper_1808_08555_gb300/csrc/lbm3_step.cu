@@ -169,8 +169,8 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// 4D tiled TMA load of one box (4, boxw, 1, planes) at (0, x, y, 0): the
-// float4 planes of the reduced state.
+// 4D tiled TMA load of one box (16, boxw/4, 1, planes) at (0, x, y, 0): the
+// float4 planes of the reduced state, four columns per innermost run.
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int x, int y,
                                             unsigned long long* bar) {
   asm volatile(
@@ -276,7 +276,7 @@ __device__ void produce(Smem& s, const StepArgs& a, const CUtensorMap* map, cons
       const int src_row = wrap(y0 - 3 + q, ny);
       float* sl = red_slot(s, q);
       if (lane == 0)
-        tma_load_4d(sl, map, tma_x, src_row, &s.full[slot]);
+        tma_load_4d(sl, map, tma_x / 4, src_row, &s.full[slot]);
       else if (lane == 1)
         tma_load_3d(sl + kRedVecFloats, map1, tma_x, src_row, 0, &s.full[slot]);
     } else if (STI == ST_FP32) {
@@ -1087,11 +1087,13 @@ cudaError_t encode_population_maps(void* tmaps, const void* buf, int nx, int ny,
   const int P = pitch_of(nx);
   unsigned char* m = static_cast<unsigned char*>(tmaps);
   if (storage == ST_RED) {
-    // the float4 planes as a (4, P, ny, 3) FP32 tensor, box (4, kPW, 1, 3);
-    // the scalar planes as (P, ny, 6), box (kPW, 1, 6)
-    const cuuint64_t dims[4] = {4, static_cast<cuuint64_t>(P), static_cast<cuuint64_t>(ny), kRedVecPlanes};
-    const cuuint64_t strides[3] = {16, static_cast<cuuint64_t>(P) * 16, static_cast<cuuint64_t>(ny) * P * 16};
-    const cuuint32_t box[4] = {4, static_cast<cuuint32_t>(kPW), 1, kRedVecPlanes};
+    // the float4 planes as a (16, P/4, ny, 3) FP32 tensor (four columns of
+    // float4 innermost: 64-byte inner runs rather than 16-byte ones), box
+    // (16, kPW/4, 1, 3) at column tma_x/4; the scalar planes as (P, ny, 6),
+    // box (kPW, 1, 6).  P and tma_x are multiples of 4.
+    const cuuint64_t dims[4] = {16, static_cast<cuuint64_t>(P / 4), static_cast<cuuint64_t>(ny), kRedVecPlanes};
+    const cuuint64_t strides[3] = {64, static_cast<cuuint64_t>(P) * 16, static_cast<cuuint64_t>(ny) * P * 16};
+    const cuuint32_t box[4] = {16, static_cast<cuuint32_t>(kPW / 4), 1, kRedVecPlanes};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUresult r = encode(reinterpret_cast<CUtensorMap*>(m), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
                               const_cast<void*>(buf), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
