@@ -306,8 +306,10 @@ def run_sweep(args):
     {128,192,256,384,512} with seed 0, two touching droplets of radius N/6,
     sigma_12/sigma_23 and sigma_13/sigma_23 on an 8x8 grid of
     {0.2,...,2.0}), advanced together by one launch per step replayed from a
-    CUDA graph; compared with the same instances stepped one after another
-    with the single-grid kernel."""
+    CUDA graph, in the reduced state (headline) and with FP32 populations
+    (bit-identical); the tile height is first the makespan model's, then the
+    empirical tuner's.  Compared with the same instances stepped one after
+    another with the single-grid kernel (FP32 populations)."""
     import torch
 
     from paper_1808_08555_gb300 import build as B
@@ -316,40 +318,45 @@ def run_sweep(args):
     from paper_1808_08555_gb300 import workloads as W
 
     cases = W.sweep_instances(seed=0)
-    params = [L.Params(c.nx, c.ny, tau=c.tau, sigma=c.sigma, beta0=c.beta0) for c in cases]
     nodes = sum(c.nx * c.ny for c in cases)
-    batch = L.Batch(params)
-    work_items = batch.work_items
-    for i, c in enumerate(cases):
-        batch.init(i, W.touching_droplets(c.nx))
-    batch.step(args.warmup)
-    batch.sync()
-    s = batch.stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # the makespan model's tile height, then the empirical tuner's choice
-    torch.cuda.synchronize()
-    e0.record(s)
-    batch.step(args.steps)
-    e1.record(s)
-    e1.synchronize()
-    ms_model = e0.elapsed_time(e1)
-    tune = batch.autotune(candidates=5, steps=20)
-    work_items_tuned = batch.work_items
-    batch.step(2)
-    torch.cuda.synchronize()
-    e0.record(s)
-    batch.step(args.steps)
-    e1.record(s)
-    e1.synchronize()
-    ms_batch = e0.elapsed_time(e1)
-    batch.close()
+
+    def timed(batch):
+        s = batch.stream
+        torch.cuda.synchronize()
+        e0.record(s)
+        batch.step(args.steps)
+        e1.record(s)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    forms = {}
+    for name, storage in (("reduced", L.REDUCED), ("fp32", L.FP32)):
+        params = [L.Params(c.nx, c.ny, tau=c.tau, sigma=c.sigma, beta0=c.beta0, storage=storage) for c in cases]
+        batch = L.Batch(params)
+        items_model = batch.work_items
+        for i, c in enumerate(cases):
+            batch.init(i, W.touching_droplets(c.nx))
+        batch.step(args.warmup)
+        batch.sync()
+        ms_model = timed(batch)
+        tune = batch.autotune(candidates=5, steps=20)
+        batch.step(2)
+        ms = timed(batch)
+        forms[name] = {"MLUPS": nodes * args.steps / (ms / 1e3) / 1e6, "ms": ms, "work_items": batch.work_items,
+                       "model": {"work_items": items_model,
+                                 "MLUPS": round(nodes * args.steps / (ms_model / 1e3) / 1e6, 2)},
+                       "autotuned": {"rows": tune["rows"], "candidates_ms_per_step": tune["candidates"]},
+                       "mass_instance0": [float(v) for v in batch.mass(0)[0]]}
+        batch.close()
     # the same instances one after another with the single-grid kernel
     sims = []
-    for c, p in zip(cases, params):
-        sim = L.Simulation(p)
+    for c in cases:
+        sim = L.Simulation(L.Params(c.nx, c.ny, tau=c.tau, sigma=c.sigma, beta0=c.beta0))
         sim.init(W.touching_droplets(c.nx))
         sim.step(args.warmup)
         sims.append(sim)
+    s = sims[0].stream
     torch.cuda.synchronize()
     e0.record(s)
     for sim in sims:
@@ -359,24 +366,28 @@ def run_sweep(args):
     ms_seq = e0.elapsed_time(e1)
     for sim in sims:
         sim.close()
-    v = nodes * args.steps / (ms_batch / 1e3) / 1e6
     peak, peak_kind = hbm_peak()
-    achieved = BYTES_PER_NODE * nodes / (ms_batch / 1e3 / args.steps) / 1e9
-    return {"metric": "ternary D2Q9 MLUPS, batched morphology sweep (64 instances)", "value": round(v, 2),
+    out = {}
+    for name, f in forms.items():
+        bpn = BYTES_PER_NODE_REDUCED if name == "reduced" else BYTES_PER_NODE
+        ach = bpn * nodes / (f["ms"] / 1e3 / args.steps) / 1e9
+        out[name] = {"MLUPS": round(f["MLUPS"], 2), "ms_per_step": round(f["ms"] / args.steps, 5),
+                     "work_items": f["work_items"], "tile_height": {"model": f["model"], "autotuned": f["autotuned"]},
+                     "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                                  "frac": round(ach / peak, 4), "traffic": None, "bytes_per_node": bpn,
+                                  "kernel": f"fused_batch_param_kernel<{name}>", "peak_source": peak_kind}}
+    h = out["reduced"]
+    return {"metric": "ternary D2Q9 MLUPS, batched morphology sweep (64 instances)", "value": h["MLUPS"],
             "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(ms_batch / args.steps, 5), "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "sweep of 64 instances, edges {128..512} seed 0, touching droplets R=N/6",
-                       "nodes_per_step": nodes, "work_items": work_items_tuned},
-            "tile_height": {"model": {"work_items": work_items,
-                                      "MLUPS": round(nodes * args.steps / (ms_model / 1e3) / 1e6, 2)},
-                            "autotuned": {"rows": tune["rows"], "candidates_ms_per_step": tune["candidates"]}},
+                       "nodes_per_step": nodes, "form": "reduced (headline); fp32 beside it"},
+            "forms": out,
+            "equal_error": forms["reduced"]["mass_instance0"] == forms["fp32"]["mass_instance0"],
             "sequential_single_instance": {"value": round(nodes * args.steps / (ms_seq / 1e3) / 1e6, 2),
                                            "unit": "MLUPS", "ms_per_step": round(ms_seq / args.steps, 5)},
-            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": None, "bytes_per_node": BYTES_PER_NODE,
-                         "kernel": "fused_batch_param_kernel" if len(cases) <= 144 else "fused_batch_kernel",
-                         "peak_source": peak_kind},
+            "roofline": h["roofline"],
             "gpu_launches": args.steps}
 
 
@@ -565,13 +576,26 @@ def run_reference(args, ws, rank):
         op = O.Params(n, n, tau=case.tau, sigma=case.sigma, beta0=case.beta0)
         return op, O.init(op, rho)
 
-    n_probe = min(256, case.nx, case.ny)
-    op, f = window(n_probe)
-    t0 = time.perf_counter()
-    O.step(op, f, 2)
-    rate = 2 * n_probe * n_probe / (time.perf_counter() - t0)          # node updates per second
-    n = int(math.sqrt(args.ref_seconds * rate / max(1, args.steps))) // 4 * 4
-    n = max(16, min(n, case.nx, case.ny))
+    # size the window from the oracle's speed, then re-measure at that size
+    # (small windows pay the threads' start-up per loop; at most one thread
+    # per 16384 nodes)
+    def use_threads(n):
+        return O.threads(max(1, min(cores, n * n // 16384)))
+
+    n = min(256, case.nx, case.ny)
+    for _ in range(3):
+        used = use_threads(n)
+        op, f = window(n)
+        t0 = time.perf_counter()
+        O.step(op, f, 2)
+        rate = 2 * n * n / (time.perf_counter() - t0)          # node updates per second
+        n_new = int(math.sqrt(args.ref_seconds * rate / max(1, args.steps))) // 4 * 4
+        n_new = max(16, min(n_new, case.nx, case.ny))
+        if abs(n_new - n) <= max(4, n // 8):
+            n = n_new
+            break
+        n = n_new
+    used = use_threads(n)
     op, f = window(n)
     for _ in range(min(args.warmup, 1)):
         f = O.step(op, f, 1)
@@ -590,7 +614,7 @@ def run_reference(args, ws, rank):
         "ms_per_step": round(total / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(case.nx), "nx": case.nx, "ny": case.ny, "sample_window": n},
-        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": used, "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 

@@ -288,8 +288,13 @@ lbm3_status lbm3_tape_backward(lbm3_ctx* ctx, const double* dphi, int dphi_on_de
 typedef struct lbm3_batch lbm3_batch;
 
 /* Create `count` instances from params[0..count-1] (each validated as in
- * lbm3_create) on the current device and `cuda_stream`.  All population
- * buffers are allocated here.  rows_per_cta: rows per work item (0 =
+ * lbm3_create; every instance with the body force and the same storage,
+ * LBM3_FP32 or LBM3_REDUCED, else LBM3_EINVAL) on the current device and
+ * `cuda_stream`.  All state buffers (and, for the reduced state, each
+ * instance's FP32 population buffer) are allocated here.  With the reduced
+ * state, the first step after instances were set (lbm3_batch_init /
+ * _set_populations) reads their populations; if only some were set, that
+ * step runs as two launches (the set instances, the others).  rows_per_cta: rows per work item (0 =
  * automatic: the tile height whose largest-first assignment of work items to
  * the GPU's resident CTA slots gives the shortest estimated step).
  * *out receives the batch (NULL on failure). */
@@ -305,7 +310,8 @@ lbm3_status lbm3_batch_create(const lbm3_params* params, int32_t count, void* cu
  * height for lbm3_batch_step.  *rows and *ms_per_step (either may be NULL)
  * receive the winner; table (may be NULL) receives (candidates + 2) pairs
  * (rows, ms per launch), unused pairs zero.  Every instance must be
- * initialised (else LBM3_ESTATE).  Synchronises the stream.  Results of
+ * initialised, and with the reduced state have stepped since it was last set
+ * (else LBM3_ESTATE).  Synchronises the stream.  Results of
  * later steps do not depend on the height (same arithmetic per node). */
 lbm3_status lbm3_batch_autotune(lbm3_batch* b, int32_t candidates, int32_t steps, int32_t* rows,
                                 double* ms_per_step, double* table);

@@ -1079,6 +1079,9 @@ struct lbm3_batch {
   std::vector<lbm3::BatchArgsBlock> pargs;
   int nitems = 0;
   size_t items_cap = 0;  // BatchItem slots allocated at d_items
+  std::vector<lbm3::BatchItem> items;  // host copy of the work list
+  lbm3::BatchItem* d_items2 = nullptr;  // reduced state: work lists of a split first step
+  int storage = LBM3_FP32;
   int rows = 64;
   std::vector<int> ranked;  // tile heights ranked by the makespan model, best first
   int device = 0;
@@ -1111,6 +1114,7 @@ void destroy_batch(lbm3_batch* b) {
     if (b->graph[p]) cudaGraphExecDestroy(b->graph[p]);
   for (lbm3_ctx* c : b->ctx) lbm3_destroy(c);
   if (b->d_items) cudaFree(b->d_items);
+  if (b->d_items2) cudaFree(b->d_items2);
   if (b->d_descs) cudaFree(b->d_descs);
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   cudaGetLastError();
@@ -1122,7 +1126,8 @@ const lbm3::BatchArgsBlock* param_args(const lbm3_batch* b, int parity) {
 }
 
 lbm3_status launch_one(lbm3_batch* b, int parity, cudaStream_t st) {
-  const cudaError_t e = lbm3::launch_batch(b->d_items, b->nitems, b->d_descs, param_args(b, parity), parity, st);
+  const cudaError_t e =
+      lbm3::launch_batch(b->d_items, b->nitems, b->d_descs, param_args(b, parity), parity, b->storage, st);
   if (e != cudaSuccess) return bfail(b, LBM3_ECUDA, "lbm3_batch_step: %s", cudaGetErrorString(e));
   return LBM3_OK;
 }
@@ -1132,9 +1137,9 @@ lbm3_status build_graph(lbm3_batch* b, int parity) {
   cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaError_t e1 = lbm3::launch_batch(b->d_items, b->nitems, b->d_descs, param_args(b, parity), parity,
-                                        b->cap_stream);
+                                        b->storage, b->cap_stream);
     cudaError_t e2 = lbm3::launch_batch(b->d_items, b->nitems, b->d_descs, param_args(b, parity ^ 1), parity ^ 1,
-                                        b->cap_stream);
+                                        b->storage, b->cap_stream);
     e = cudaStreamEndCapture(b->cap_stream, &g);
     if (e == cudaSuccess && e1 != cudaSuccess) e = e1;
     if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
@@ -1201,6 +1206,47 @@ lbm3_status batch_upload(lbm3_batch* b, const std::vector<lbm3::BatchItem>& item
       cudaMemcpy(b->d_items, items.data(), sizeof(lbm3::BatchItem) * items.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bfail(b, LBM3_ECUDA, "lbm3: batch work list upload: %s", cudaGetErrorString(e));
   b->nitems = static_cast<int>(items.size());
+  b->items = items;
+  return LBM3_OK;
+}
+
+// Reduced state: the first step of instances whose state is still FP32
+// populations (set since the last step) reads them and writes the reduced
+// state; the other instances take an ordinary reduced step in a second
+// launch of the same step.
+lbm3_status batch_first_reduced_step(lbm3_batch* b, int parity) {
+  std::vector<char> pop(b->ctx.size());
+  size_t npop = 0;
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    pop[i] = b->ctx[i]->in_shadow ? 1 : 0;
+    npop += pop[i];
+  }
+  if (npop == 0) return LBM3_OK;
+  cudaError_t e;
+  if (npop == b->ctx.size()) {
+    e = lbm3::launch_batch(b->d_items, b->nitems, b->d_descs, nullptr, parity, lbm3::ST_F2R, b->stream);
+  } else {
+    std::vector<lbm3::BatchItem> split;
+    for (const lbm3::BatchItem& it : b->items)
+      if (pop[static_cast<size_t>(it.inst)]) split.push_back(it);
+    const int nf = static_cast<int>(split.size());
+    for (const lbm3::BatchItem& it : b->items)
+      if (!pop[static_cast<size_t>(it.inst)]) split.push_back(it);
+    e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess && !b->d_items2) e = cudaMalloc(&b->d_items2, sizeof(lbm3::BatchItem) * b->items_cap);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->d_items2, split.data(), sizeof(lbm3::BatchItem) * split.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = lbm3::launch_batch(b->d_items2, nf, b->d_descs, nullptr, parity, lbm3::ST_F2R, b->stream);
+    if (e == cudaSuccess)
+      e = lbm3::launch_batch(b->d_items2 + nf, static_cast<int>(split.size()) - nf, b->d_descs, param_args(b, parity),
+                             parity, lbm3::ST_RED, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // d_items2 is rewritten by the next split
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, LBM3_ECUDA, "lbm3_batch_step: %s", cudaGetErrorString(e));
+  }
+  for (lbm3_ctx* c : b->ctx) c->in_shadow = false;
   return LBM3_OK;
 }
 
@@ -1227,12 +1273,20 @@ lbm3_status lbm3_batch_create(const lbm3_params* params, int32_t count, void* cu
       return st;
     }
     b->ctx.push_back(c);
-    if (c->p.storage != LBM3_FP32 || c->p.force_form != LBM3_FORCE_BODY) {
-      std::fprintf(stderr, "lbm3_batch_create: instance %d: batches use FP32 storage and the body force\n", i);
+    if ((c->p.storage != LBM3_FP32 && c->p.storage != LBM3_REDUCED) || c->p.storage != params[0].storage ||
+        c->p.force_form != LBM3_FORCE_BODY) {
+      std::fprintf(stderr,
+                   "lbm3_batch_create: instance %d: batches use the body force and one storage for every instance, "
+                   "FP32 or the reduced state\n",
+                   i);
       destroy_batch(b);
       return LBM3_EINVAL;
     }
     st = ensure_buffers(c);
+    if (st == LBM3_OK && c->p.storage == LBM3_REDUCED) {
+      float* sh = nullptr;  // the FP32 populations a state is set to, and their descriptors
+      st = fp32_target(c, &sh);
+    }
     if (st != LBM3_OK) {
       std::fprintf(stderr, "lbm3_batch_create: instance %d: %s\n", i, c->msg.c_str());
       destroy_batch(b);
@@ -1242,13 +1296,16 @@ lbm3_status lbm3_batch_create(const lbm3_params* params, int32_t count, void* cu
   // per-instance descriptors and the work list (largest tiles first)
   std::vector<lbm3::BatchDesc> descs(count);
   std::vector<lbm3::BatchItem> items;
+  b->storage = params[0].storage;
   for (int i = 0; i < count; ++i) {
     lbm3_ctx* c = b->ctx[i];
     for (int p = 0; p < 2; ++p) {
       int grid = 0;
       descs[i].args[p] = args_for(c, c->buf[p], c->buf[p ^ 1], &grid);
-      std::memcpy(descs[i].map[p], c->tmap[p], 128);
+      std::memcpy(descs[i].map[p], c->tmap[p], 256);
+      if (b->storage == LBM3_REDUCED) descs[i].args_f2r[p] = args_for(c, c->shadow, c->buf[p ^ 1], &grid);
     }
+    if (b->storage == LBM3_REDUCED) std::memcpy(descs[i].map_f2r, c->shadow_map, 256);
   }
   // Tile height: given, or the one whose largest-first assignment of the work
   // items to the resident CTA slots gives the shortest estimated step.  The
@@ -1297,8 +1354,12 @@ lbm3_status lbm3_batch_autotune(lbm3_batch* b, int32_t candidates, int32_t steps
   if (!b) return LBM3_EINVAL;
   if (candidates < 1 || candidates > 16 || steps < 1)
     return bfail(b, LBM3_EINVAL, "lbm3_batch_autotune: need 1 <= candidates <= 16 and steps >= 1");
-  for (size_t i = 0; i < b->ctx.size(); ++i)
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
     if (!b->ctx[i]->state_set) return bfail(b, LBM3_ESTATE, "lbm3_batch_autotune: instance %zu not initialised", i);
+    if (b->ctx[i]->in_shadow)
+      return bfail(b, LBM3_ESTATE, "lbm3_batch_autotune: instance %zu holds populations set since the last step; "
+                   "a reduced-state batch is tuned after a step", i);
+  }
   DeviceGuard g(b->device);
   // candidates: the model's best-ranked heights, then 64 and 128 if absent
   std::vector<int> cand(b->ranked.begin(), b->ranked.begin() + std::min<size_t>(candidates, b->ranked.size()));
@@ -1390,7 +1451,6 @@ lbm3_status lbm3_batch_step(lbm3_batch* b, int64_t n) {
   for (size_t i = 0; i < b->ctx.size(); ++i)
     if (!b->ctx[i]->state_set) return bfail(b, LBM3_ESTATE, "lbm3_batch_step: instance %zu not initialised", i);
   DeviceGuard g(b->device);
-  const int parity = b->ctx[0]->cur;
   auto advance = [&](int64_t k) {
     for (lbm3_ctx* c : b->ctx) {
       if (k & 1) c->cur ^= 1;
@@ -1398,6 +1458,17 @@ lbm3_status lbm3_batch_step(lbm3_batch* b, int64_t n) {
     }
     b->t += k;
   };
+  if (b->storage == LBM3_REDUCED && n > 0) {
+    bool any = false;
+    for (const lbm3_ctx* c : b->ctx) any = any || c->in_shadow;
+    if (any) {
+      lbm3_status st = batch_first_reduced_step(b, b->ctx[0]->cur);
+      if (st != LBM3_OK) return st;
+      advance(1);
+      n -= 1;
+    }
+  }
+  const int parity = b->ctx[0]->cur;
   if (n >= 2) {
     if (!b->graph[parity]) {
       lbm3_status st = build_graph(b, parity);

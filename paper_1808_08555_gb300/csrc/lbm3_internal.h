@@ -185,9 +185,15 @@ struct BatchItem {
 };
 // Per instance: step arguments and TMA descriptor for each buffer parity
 // (parity p reads buffer p and writes buffer 1 - p).
+// map[p] holds the input buffer's TMA descriptors (two for the reduced
+// state: vector and scalar planes).  A reduced-state instance whose state is
+// still FP32 populations (after it was set) steps once with args_f2r[p]
+// (its FP32 populations in, the reduced state out) and map_f2r.
 struct alignas(64) BatchDesc {
   StepArgs args[2];
-  alignas(64) unsigned char map[2][128];
+  StepArgs args_f2r[2];
+  alignas(64) unsigned char map[2][256];
+  alignas(64) unsigned char map_f2r[256];
 };
 // The step arguments of up to kBatchParamInst instances for one parity,
 // passed by value in the kernel parameter space (at most 32,764 bytes on
@@ -216,8 +222,11 @@ cudaError_t encode_population_maps(void* tmaps, const void* buf, int nx, int ny,
 size_t population_bytes(int nx, int ny, int storage);
 // args: this parity's arguments of every instance (count <= kBatchParamInst),
 // or nullptr to read them from descs
+// storage: ST_FP32 or ST_RED for the steps of the batch; ST_F2R for the
+// first step of reduced-state instances set from populations (descs' F2R
+// arguments, read from global memory)
 cudaError_t launch_batch(const BatchItem* items, int nitems, const BatchDesc* descs, const BatchArgsBlock* args,
-                         int parity, cudaStream_t s);
+                         int parity, int storage, cudaStream_t s);
 int step_occupancy(int* blocks_per_sm);
 
 // ------------------------------------------------------------- aux kernels

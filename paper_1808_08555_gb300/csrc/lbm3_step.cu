@@ -909,39 +909,53 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 // Batch of independent grids: CTA b runs work item b (instance, tile); the
-// instance's arguments for this step's buffer parity and its tensor map are
+// instance's arguments for this step's buffer parity and its tensor maps are
 // read from the descriptor in global memory (read-only during the launch).
 // The arguments stay there rather than in a shared-memory copy: read from
 // shared memory, the compiler keeps the per-instance constants live in
 // registers and spills at the 96-register cap of two 288-thread CTAs per
 // SM; read from the read-only path they are reloaded at use, as the single
 // grid's kernel-parameter constants are (64 % more batch throughput).
+// ST: ST_FP32 or ST_RED; ST_F2R takes the descriptors' F2R arguments.
+template <int ST>
 __global__ void __launch_bounds__(kThreads, 2)
     fused_batch_kernel(const BatchItem* __restrict__ items, const BatchDesc* __restrict__ descs, int parity) {
   Smem& s = aligned_smem();
   const BatchItem it = items[blockIdx.x];
   const BatchDesc* d = descs + it.inst;
-  const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(d->map[parity]);
-  if (threadIdx.x == kConsumers)
+  const unsigned char* mp = ST == ST_F2R ? d->map_f2r : d->map[parity];
+  const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(mp);
+  const CUtensorMap* map1 = reinterpret_cast<const CUtensorMap*>(mp + 128);
+  if (threadIdx.x == kConsumers) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
                  : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map1))
+                 : "memory");
+  }
   __syncthreads();
-  run_tile<MODE_STEP, ST_FP32, 0>(s, d->args[parity], map, map, it.x0, it.w, it.y0, it.h);
+  run_tile<MODE_STEP, ST, 0>(s, ST == ST_F2R ? d->args_f2r[parity] : d->args[parity], map, map1, it.x0, it.w, it.y0,
+                             it.h);
 }
 
 // Batch whose step arguments travel in the kernel parameter space: the same
 // work items and tensor maps, the arguments read from the constant bank.
+template <int ST>
 __global__ void __launch_bounds__(kThreads, 2)
     fused_batch_param_kernel(const BatchItem* __restrict__ items, const BatchDesc* __restrict__ descs, int parity,
                              const __grid_constant__ BatchArgsBlock args) {
   Smem& s = aligned_smem();
   const BatchItem it = items[blockIdx.x];
-  const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(descs[it.inst].map[parity]);
-  if (threadIdx.x == kConsumers)
+  const unsigned char* mp = descs[it.inst].map[parity];
+  const CUtensorMap* map = reinterpret_cast<const CUtensorMap*>(mp);
+  const CUtensorMap* map1 = reinterpret_cast<const CUtensorMap*>(mp + 128);
+  if (threadIdx.x == kConsumers) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
                  : "memory");
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map1))
+                 : "memory");
+  }
   __syncthreads();
-  run_tile<MODE_STEP, ST_FP32, 0>(s, args.a[it.inst], map, map, it.x0, it.w, it.y0, it.h);
+  run_tile<MODE_STEP, ST, 0>(s, args.a[it.inst], map, map1, it.x0, it.w, it.y0, it.h);
 }
 
 }  // namespace
@@ -974,19 +988,38 @@ cudaError_t step_configure() {
     e = cudaFuncSetAttribute(fused_step_kernel<MODE_STEP, ST_FP32, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fused_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    e = cudaFuncSetAttribute(fused_batch_kernel<ST_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(fused_batch_param_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    e = cudaFuncSetAttribute(fused_batch_kernel<ST_RED>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fused_batch_kernel<ST_F2R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fused_batch_param_kernel<ST_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fused_batch_param_kernel<ST_RED>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return e;
 }
 
 cudaError_t launch_batch(const BatchItem* items, int nitems, const BatchDesc* descs, const BatchArgsBlock* args,
-                         int parity, cudaStream_t st) {
+                         int parity, int storage, cudaStream_t st) {
   if (nitems <= 0) return cudaSuccess;
-  if (args)
-    fused_batch_param_kernel<<<nitems, kThreads, step_smem_bytes(), st>>>(items, descs, parity, *args);
-  else
-    fused_batch_kernel<<<nitems, kThreads, step_smem_bytes(), st>>>(items, descs, parity);
+  const size_t sm = step_smem_bytes();
+  if (storage == ST_F2R) {
+    fused_batch_kernel<ST_F2R><<<nitems, kThreads, sm, st>>>(items, descs, parity);
+  } else if (storage == ST_RED) {
+    if (args)
+      fused_batch_param_kernel<ST_RED><<<nitems, kThreads, sm, st>>>(items, descs, parity, *args);
+    else
+      fused_batch_kernel<ST_RED><<<nitems, kThreads, sm, st>>>(items, descs, parity);
+  } else if (storage == ST_FP32) {
+    if (args)
+      fused_batch_param_kernel<ST_FP32><<<nitems, kThreads, sm, st>>>(items, descs, parity, *args);
+    else
+      fused_batch_kernel<ST_FP32><<<nitems, kThreads, sm, st>>>(items, descs, parity);
+  } else {
+    return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -121,3 +121,53 @@ def test_autotune_keeps_state_and_results(L):
     with pytest.raises(L.Lbm3Error):
         batch.autotune(candidates=0)
     batch.close()
+
+
+def _reduced(L, params):
+    return [L.Params(**{**p.__dict__, "storage": L.REDUCED}) for p in params]
+
+
+@pytest.mark.parametrize("steps", [1, 6, 7])
+def test_reduced_batch_equals_single_fp32_instances(L, steps):
+    """A batch in the reduced state (the first step from the set
+    populations, then reduced steps through the step graphs) gives every
+    instance's FP32 single-grid populations bit for bit."""
+    params, fields = _instances(L)
+    batch = L.Batch(_reduced(L, params), rows_per_cta=24)
+    for i, rho in enumerate(fields):
+        batch.init(i, rho)
+    batch.step(steps)
+    for i, (p, rho) in enumerate(zip(params, fields)):
+        sim = L.Simulation(p)
+        sim.init(rho)
+        sim.step(steps)
+        np.testing.assert_array_equal(batch.populations(i), sim.populations(), err_msg=f"instance {i}")
+        sim.close()
+    batch.close()
+
+
+def test_reduced_batch_one_instance_reset_midway(L):
+    """Setting one instance's populations mid-run splits the next step into
+    a populations-in launch for it and a reduced launch for the others; the
+    instance is set to its own populations, so every trajectory is unchanged.
+    Tuning a batch that holds set populations is refused until it steps."""
+    params, fields = _instances(L)
+    batch = L.Batch(_reduced(L, params))
+    for i, rho in enumerate(fields):
+        batch.init(i, rho)
+    batch.step(3)
+    batch.set_populations(1, batch.populations(1))
+    with pytest.raises(L.Lbm3Error) as e:
+        batch.autotune(candidates=2, steps=1)
+    assert e.value.status == L.ESTATE
+    batch.step(4)
+    res = batch.autotune(candidates=2, steps=2)
+    assert res["rows"] > 0
+    batch.step(1)
+    for i, (p, rho) in enumerate(zip(params, fields)):
+        sim = L.Simulation(p)
+        sim.init(rho)
+        sim.step(8)
+        np.testing.assert_array_equal(batch.populations(i), sim.populations(), err_msg=f"instance {i}")
+        sim.close()
+    batch.close()
