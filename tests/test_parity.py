@@ -291,3 +291,20 @@ def test_full_size_compound_2048_sampled(L):
     assert _patch_check(L, p, f_t, f_t1, centres) <= 1e-5
     host = f_t1.reshape(3, 9, -1).sum(axis=(1, 2))
     np.testing.assert_allclose(m_gpu, host, rtol=1e-12)
+
+
+@pytest.mark.parametrize("storage", [0, 3])
+def test_three_phase_junctions_element_by_element(L, storage):
+    """Three-phase junctions at scale, element by element: a Janus droplet
+    (96^2, R = 24, tensions 0.010/0.008/0.012) relaxed 600 steps by the
+    oracle, so that both junctions are diffuse three-fluid regions where the
+    junction factor of Eq. 19 is active, then 20 steps on both sides.  The
+    input passes the same FP32-conditioning check as every parity case."""
+    n = 96
+    p = L.Params(n, n, sigma=(0.010, 0.008, 0.012), storage=storage)
+    op = oparams(p)
+    f0 = f32(O.step(op, O.init(op, W.janus_droplet(n, 24.0)), 600))
+    rho = f0.sum(axis=1)
+    ph = rho / rho.sum(axis=0)
+    assert (np.minimum(np.minimum(ph[0], ph[1]), ph[2]) > 0.05).sum() >= 4   # nodes with all three fluids
+    check_parity(L, p, f0, 20)
