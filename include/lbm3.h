@@ -363,6 +363,46 @@ const char* lbm3_batch_last_error(const lbm3_batch* b);
  * needed between calls. */
 lbm3_status lbm3_mass_noalloc(const float* dev_f, int32_t nx, int32_t ny, void* cuda_stream, double* dev_out);
 
+/* ------------------------------------------------------------------------
+ * N fluids (2 <= nfluids <= 6).  The paper writes the interfacial force
+ * (Eq. 11) and the recolouring (Eq. 6) for any number of fluids and simulates
+ * three.  This context runs the same step (Eq. fd1 gradients, Eq. 11 force
+ * through Guo's term, BGK with the harmonic-mean viscosity, recolouring,
+ * streaming) for N fluids, as three kernels per step over global-memory
+ * intermediates (a first path: not the fused, TMA-fed kernel of lbm3_step).
+ * beta_kl for N fluids, which the paper does not give beyond three:
+ *   beta_kl = beta0 [1 + sum_{m != k, l} min(35 rho_k rho_l rho_m / rho^3, 1) g(X_kl^m)]
+ * with X_kl^m of Eq. 18 for the third fluid m and g of Eq. 20: Eq. 19
+ * exactly for N = 3, one junction term per third fluid beyond (beta_form 1:
+ * the constant beta0 of Eq. fu).  Arrays: sigma[nfluids][nfluids] symmetric
+ * with a zero diagonal and positive entries off it; tau, rho0 [nfluids];
+ * host densities rho[N][ny][nx] and populations f[N][9][ny][nx] (FP64,
+ * post-streaming) as for the three-fluid calls; the state is FP32.  Any
+ * invalid parameter gives LBM3_EINVAL from lbm3n_create.  The context
+ * allocates its two population buffers, the intermediates
+ * ((N + 13 + N (N - 1)) nx ny floats) and an FP64 staging area. */
+typedef struct lbm3n_ctx lbm3n_ctx;
+typedef struct {
+  int32_t nx, ny, nfluids;
+  const double* tau;    /* [nfluids], each > 0.5 */
+  const double* rho0;   /* [nfluids], each > 0 (Eq. 15) */
+  const double* sigma;  /* [nfluids][nfluids] */
+  double beta0;         /* (0, 1] */
+  int32_t beta_form;    /* 0: the N-fluid form above; 1: Eq. fu */
+  int32_t recolor_form; /* as lbm3_recolor_form */
+  double normal_delta;  /* as lbm3_params.normal_delta */
+} lbm3n_params;
+lbm3_status lbm3n_create(const lbm3n_params* p, void* cuda_stream, lbm3n_ctx** out);
+/* rest equilibrium per colour from host densities (rho_k >= 0) */
+lbm3_status lbm3n_init(lbm3n_ctx* ctx, const double* rho, int on_device);
+lbm3_status lbm3n_set_populations(lbm3n_ctx* ctx, const double* f, int on_device);
+lbm3_status lbm3n_step(lbm3n_ctx* ctx, int64_t n);  /* asynchronous */
+lbm3_status lbm3n_populations(lbm3n_ctx* ctx, double* f, int on_device);  /* synchronises */
+/* FP64 per-fluid mass[nfluids] and lattice momentum mom[2] (synchronises) */
+lbm3_status lbm3n_mass(lbm3n_ctx* ctx, double* mass, double* mom);
+lbm3_status lbm3n_destroy(lbm3n_ctx* ctx);
+const char* lbm3n_last_error(const lbm3n_ctx* ctx);
+
 /* Wait for the context's stream and report device-side errors (timed-out
  * waits) recorded since the last check. */
 lbm3_status lbm3_sync(lbm3_ctx* ctx);

@@ -19,7 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblbm3.so")
-SOURCES = ["lbm3_api.cu", "lbm3_step.cu", "lbm3_aux.cu", "lbm3_static.cu", "lbm3_adjoint.cu", "lbm3_diag.cu"]
+SOURCES = ["lbm3_api.cu", "lbm3_step.cu", "lbm3_aux.cu", "lbm3_static.cu", "lbm3_adjoint.cu", "lbm3_diag.cu",
+           "lbm3_nphase.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -1,0 +1,554 @@
+// N-fluid colour-gradient step on D2Q9 (arXiv 1808.08555: Eq. 11 and the
+// recolouring of Eq. 6 are written for any number of fluids; the paper
+// simulates three).  A first CUDA path for 2 <= N <= kMaxFluids, as three
+// kernels per step over global-memory intermediates, one node per thread:
+//   densities:  pull the 9N populations (Eq. 30), rho_k, rho, phi_k (the
+//               largest fraction as the complement of the others, so they
+//               sum to 1 exactly), the total distribution f_i
+//   tension:    grad phi_k (Eq. fd1), G_kl and C_kl (Eq. 15) for the
+//               N(N-1)/2 pairs, the tension tensor of Eq. 11 summed over the
+//               pairs, the recolouring normals n_kl = G / max(|G|, delta phi_k phi_l)
+//   collide:    F_s = div T (Eq. fd1), u (Eq. uk1), tau_f (Eqs. vis_1, tau),
+//               BGK with Guo's forcing (Eqs. 1-3, 5), beta_kl, recolouring
+//               (Eq. 6); f^ddagger stored at the node that produced it
+// beta_kl for N fluids (the paper gives Eqs. 18-20 for three):
+//   beta_kl = beta^0 [1 + sum_{m != k,l} min(35 rho_k rho_l rho_m / rho^3, 1) g(X_kl^m)],
+// with g(X_kl^m) of Eqs. 18 and 20 precomputed on the host; it is Eq. 19
+// exactly for N = 3.  The fluid count is a template parameter, so every
+// per-node array stays in registers.
+//
+// Layout: populations [N][9][ny][nx] FP32, unpadded, periodic by index
+// arithmetic; intermediates phi [N][ny][nx], rho [ny][nx], f_i [9][ny][nx],
+// T [3][ny][nx], normals [P][2][ny][nx] with P = N(N-1)/2.
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm3.h"
+#include "lbm3_internal.h"
+
+namespace lbm3 {
+namespace {
+
+constexpr int kMaxFluids = 6;
+constexpr int kMaxPairs = kMaxFluids * (kMaxFluids - 1) / 2;
+constexpr int kNThreads = 256;
+
+struct NArgs {
+  int nx, ny;
+  float inv_nu[kMaxFluids];                   // 1/nu_k
+  float sigma[kMaxPairs];                     // sigma_kl for pairs k < l in row order
+  float cpair[kMaxPairs];                     // 1e6 / (rho0_k rho0_l)
+  float gjunc[kMaxPairs][kMaxFluids];         // g(X_kl^m) (0 for m = k, l)
+  float beta0, beta_A;                        // beta_A = 35 (0: Eq. fu, constant beta)
+  float wrec[9];                              // recolouring weights w_i / |e_i|^p
+  float ndelta;
+};
+
+__host__ __device__ constexpr int pair_index(int k, int l, int n) {  // k < l
+  return k * n - k * (k + 1) / 2 + (l - k - 1);
+}
+
+__device__ __forceinline__ int wrapn(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+template <int N>
+__global__ void __launch_bounds__(kNThreads) n_density_kernel(const float* __restrict__ f, float* __restrict__ phi,
+                                                              float* __restrict__ rho_out, float* __restrict__ fi,
+                                                              NArgs a) {
+  const int nx = a.nx, ny = a.ny;
+  const size_t NN = static_cast<size_t>(nx) * ny;
+  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < NN;
+       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
+    float r[N];
+    float tot[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) tot[i] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      float s = 0.0f;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const size_t src = static_cast<size_t>(wrapn(y - ey(i), ny)) * nx + wrapn(x - ex(i), nx);
+        const float v = f[(static_cast<size_t>(k) * 9 + i) * NN + src];  // Eq. 30 as a pull
+        s += v;
+        tot[i] += v;
+      }
+      r[k] = s;
+    }
+    float rho = 0.0f, rmax = -1.0f;
+    int kmax = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      rho += r[k];
+      if (r[k] > rmax) {
+        rmax = r[k];
+        kmax = k;
+      }
+    }
+    const float ir = 1.0f / rho;
+    float rest = 1.0f;
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      if (k != kmax) {
+        const float p = r[k] * ir;
+        phi[static_cast<size_t>(k) * NN + n] = p;
+        rest -= p;
+      }
+    phi[static_cast<size_t>(kmax) * NN + n] = rest;  // the fractions sum to 1 exactly
+    rho_out[n] = rho;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fi[static_cast<size_t>(i) * NN + n] = tot[i];
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kNThreads) n_tension_kernel(const float* __restrict__ phi,
+                                                              const float* __restrict__ rho_in, float* __restrict__ T,
+                                                              float* __restrict__ nrm, NArgs a) {
+  const int nx = a.nx, ny = a.ny;
+  const size_t NN = static_cast<size_t>(nx) * ny;
+  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < NN;
+       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
+    float ph[N], gx[N], gy[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      ph[k] = phi[static_cast<size_t>(k) * NN + n];
+      float sx = 0.0f, sy = 0.0f;  // Eq. fd1: (1/cs2) sum_i w_i phi(x + e_i) e_i
+#pragma unroll
+      for (int i = 1; i < 9; ++i) {
+        const float v = phi[static_cast<size_t>(k) * NN + static_cast<size_t>(wrapn(y + ey(i), ny)) * nx +
+                            wrapn(x + ex(i), nx)];
+        const float w3 = 3.0f * (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+        sx += w3 * ex(i) * v;
+        sy += w3 * ey(i) * v;
+      }
+      gx[k] = sx;
+      gy[k] = sy;
+    }
+    const float rho = rho_in[n];
+    float txx = 0.0f, txy = 0.0f, tyy = 0.0f;
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+#pragma unroll
+      for (int l = k + 1; l < N; ++l, ++q) {
+        const float Gx = ph[l] * gx[k] - ph[k] * gx[l];  // G_kl = phi_l grad phi_k - phi_k grad phi_l
+        const float Gy = ph[l] * gy[k] - ph[k] * gy[l];
+        const float g2 = Gx * Gx + Gy * Gy;
+        float nxv = 0.0f, nyv = 0.0f;
+        if (g2 > 1e-30f) {
+          const float mag = sqrtf(g2);
+          const float pp = ph[k] * ph[l];
+          const float ck = fminf(a.cpair[q] * pp * rho * rho, 1.0f);  // Eq. 15
+          const float sc = a.sigma[q] * ck / mag;                     // sigma C |G| (I - n n) = sigma C (|G|^2 I - G G)/|G|
+          txx += sc * Gy * Gy;
+          txy -= sc * Gx * Gy;
+          tyy += sc * Gx * Gx;
+          const float den = fmaxf(mag, a.ndelta * pp);
+          nxv = Gx / den;
+          nyv = Gy / den;
+        }
+        nrm[(static_cast<size_t>(q) * 2) * NN + n] = nxv;
+        nrm[(static_cast<size_t>(q) * 2 + 1) * NN + n] = nyv;
+      }
+    T[n] = txx;
+    T[NN + n] = txy;
+    T[2 * NN + n] = tyy;
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kNThreads) n_collide_kernel(const float* __restrict__ phi,
+                                                              const float* __restrict__ rho_in,
+                                                              const float* __restrict__ fi,
+                                                              const float* __restrict__ T,
+                                                              const float* __restrict__ nrm, float* __restrict__ fout,
+                                                              NArgs a) {
+  const int nx = a.nx, ny = a.ny;
+  const size_t NN = static_cast<size_t>(nx) * ny;
+  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < NN;
+       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
+    // F_s = div T (Eq. 11), each component by Eq. fd1
+    float Fx = 0.0f, Fy = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+      const size_t m = static_cast<size_t>(wrapn(y + ey(i), ny)) * nx + wrapn(x + ex(i), nx);
+      const float w3 = 3.0f * (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+      const float txx = T[m], txy = T[NN + m], tyy = T[2 * NN + m];
+      Fx += w3 * (ex(i) * txx + ey(i) * txy);
+      Fy += w3 * (ex(i) * txy + ey(i) * tyy);
+    }
+    const float rho = rho_in[n];
+    float ph[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) ph[k] = phi[static_cast<size_t>(k) * NN + n];
+    float f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = fi[static_cast<size_t>(i) * NN + n];
+    float mx = 0.0f, my = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+      mx += ex(i) * f[i];
+      my += ey(i) * f[i];
+    }
+    const float irho = 1.0f / rho;
+    const float ux = (mx + 0.5f * Fx) * irho, uy = (my + 0.5f * Fy) * irho;  // Eq. uk1
+    float inu = 0.0f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) inu += ph[k] * a.inv_nu[k];  // rho/nu = sum_k rho_k/nu_k
+    const float om = inu / (3.0f + 0.5f * inu);               // 1/tau_f, tau_f = 3 nu + 1/2
+    const float g = 1.0f - 0.5f * om;                         // Guo prefactor 1 - 1/(2 tau_f)
+    const float uu = ux * ux + uy * uy;
+    float fd[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const float eu = ex(i) * ux + ey(i) * uy;
+      const float feq = wt(i) * rho * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);  // Eq. 3
+      const float cx = 3.0f * (ex(i) - ux) + 9.0f * eu * ex(i);
+      const float cy = 3.0f * (ey(i) - uy) + 9.0f * eu * ey(i);
+      const float Phi = wt(i) * g * (cx * Fx + cy * Fy);                               // Eq. 5
+      fd[i] = f[i] + om * (feq - f[i]) + Phi;                                          // Eqs. 1, 2
+    }
+    // segregation parameters and the recolouring vectors
+    // V_k = sum_{l != k} beta_kl (rho_k rho_l / rho) n_kl, n_lk = -n_kl
+    float Vx[N], Vy[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) Vx[k] = Vy[k] = 0.0f;
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+#pragma unroll
+      for (int l = k + 1; l < N; ++l, ++q) {
+        float b = 1.0f;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          if (m == k || m == l) continue;
+          b += fminf(a.beta_A * ph[k] * ph[l] * ph[m], 1.0f) * a.gjunc[q][m];
+        }
+        const float amp = a.beta0 * b * ph[k] * ph[l] * rho;
+        const float nxv = nrm[(static_cast<size_t>(q) * 2) * NN + n];
+        const float nyv = nrm[(static_cast<size_t>(q) * 2 + 1) * NN + n];
+        Vx[k] += amp * nxv;
+        Vy[k] += amp * nyv;
+        Vx[l] -= amp * nxv;
+        Vy[l] -= amp * nyv;
+      }
+    // Eq. 6, stored at the node (the next step's pull streams it, Eq. 30)
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+        fout[(static_cast<size_t>(k) * 9 + i) * NN + n] =
+            ph[k] * fd[i] + a.wrec[i] * (ex(i) * Vx[k] + ey(i) * Vy[k]);
+  }
+}
+
+int grid_of(size_t NN) {
+  size_t g = (NN + kNThreads - 1) / kNThreads;
+  return static_cast<int>(g > 4096 ? 4096 : (g < 1 ? 1 : g));
+}
+
+template <int N>
+cudaError_t n_step(const float* fin, float* fout, float* work, const NArgs& a, cudaStream_t s) {
+  const size_t NN = static_cast<size_t>(a.nx) * a.ny;
+  float* phi = work;
+  float* rho = phi + N * NN;
+  float* fi = rho + NN;
+  float* T = fi + 9 * NN;
+  float* nrm = T + 3 * NN;
+  const int g = grid_of(NN);
+  n_density_kernel<N><<<g, kNThreads, 0, s>>>(fin, phi, rho, fi, a);
+  n_tension_kernel<N><<<g, kNThreads, 0, s>>>(phi, rho, T, nrm, a);
+  n_collide_kernel<N><<<g, kNThreads, 0, s>>>(phi, rho, fi, T, nrm, fout, a);
+  return cudaGetLastError();
+}
+
+cudaError_t n_step_any(int N, const float* fin, float* fout, float* work, const NArgs& a, cudaStream_t s) {
+  switch (N) {
+    case 2: return n_step<2>(fin, fout, work, a, s);
+    case 3: return n_step<3>(fin, fout, work, a, s);
+    case 4: return n_step<4>(fin, fout, work, a, s);
+    case 5: return n_step<5>(fin, fout, work, a, s);
+    case 6: return n_step<6>(fin, fout, work, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t work_floats(int N, size_t NN) { return (N + 1 + 9 + 3 + static_cast<size_t>(N) * (N - 1)) * NN; }
+
+// stored (post-collision, at the producing node) <-> post-streaming populations
+__global__ void n_set_kernel(const double* __restrict__ fpost, float* __restrict__ f, int nx, int ny, int planes) {
+  const size_t NN = static_cast<size_t>(nx) * ny;
+  const int p = blockIdx.y;  // k*9 + i
+  const int i = p % 9;
+  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < NN;
+       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
+    // stored(x) = post-streaming(x + e_i)
+    const size_t src = static_cast<size_t>(wrapn(y + ey(i), ny)) * nx + wrapn(x + ex(i), nx);
+    f[static_cast<size_t>(p) * NN + n] = static_cast<float>(fpost[static_cast<size_t>(p) * NN + src]);
+  }
+  (void)planes;
+}
+
+__global__ void n_get_kernel(const float* __restrict__ f, double* __restrict__ fpost, int nx, int ny) {
+  const size_t NN = static_cast<size_t>(nx) * ny;
+  const int p = blockIdx.y;
+  const int i = p % 9;
+  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < NN;
+       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
+    const size_t src = static_cast<size_t>(wrapn(y - ey(i), ny)) * nx + wrapn(x - ex(i), nx);
+    fpost[static_cast<size_t>(p) * NN + n] = static_cast<double>(f[static_cast<size_t>(p) * NN + src]);
+  }
+}
+
+// FP64 per-colour mass and lattice momentum: one block per colour x direction
+// plane, a fixed-order tree per block, then a fixed-order sum on the host
+__global__ void n_plane_sum_kernel(const float* __restrict__ f, int NNi, double* __restrict__ out) {
+  const size_t NN = static_cast<size_t>(NNi);
+  const int p = blockIdx.x;
+  double s = 0.0;
+  for (size_t n = threadIdx.x; n < NN; n += blockDim.x) s += static_cast<double>(f[static_cast<size_t>(p) * NN + n]);
+  __shared__ double sh[kNThreads];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kNThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[p] = sh[0];
+}
+
+double g_of(double X) {  // Eq. 20
+  if (X < -1.0) return 1.0;
+  if (X < 0.0) return 1.0 - std::sqrt(1.0 - X * X);
+  if (X <= 1.0) return std::sqrt(1.0 - X * X) - 1.0;
+  return -1.0;
+}
+
+}  // namespace
+}  // namespace lbm3
+
+struct lbm3n_ctx {
+  int N = 0, nx = 0, ny = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  float* buf[2] = {nullptr, nullptr};
+  float* work = nullptr;
+  double* sums = nullptr;
+  int cur = 0;
+  bool state_set = false;
+  int64_t t = 0;
+  lbm3::NArgs args{};
+  std::string msg;
+};
+
+namespace {
+
+lbm3_status nfail(lbm3n_ctx* c, lbm3_status st, const std::string& m) {
+  if (c) c->msg = m;
+  return st;
+}
+
+lbm3_status ncuda(lbm3n_ctx* c, cudaError_t e, const char* where) {
+  return nfail(c, LBM3_ECUDA, std::string("lbm3n: ") + where + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm3_status lbm3n_create(const lbm3n_params* p, void* cuda_stream, lbm3n_ctx** out) {
+  if (!out) return LBM3_EINVAL;
+  *out = nullptr;
+  if (!p || !p->tau || !p->rho0 || !p->sigma) return LBM3_EINVAL;
+  const int N = p->nfluids;
+  if (N < 2 || N > lbm3::kMaxFluids || p->nx < 1 || p->ny < 1) return LBM3_EINVAL;
+  if (static_cast<double>(p->nx) * p->ny * 9 * N >= 2147483648.0) return LBM3_EINVAL;
+  if (!(p->beta0 > 0.0 && p->beta0 <= 1.0) || p->beta_form < 0 || p->beta_form > 1 || p->recolor_form < 0 ||
+      p->recolor_form > 1 || !(p->normal_delta >= 0.0 && p->normal_delta <= 1.0))
+    return LBM3_EINVAL;
+  for (int k = 0; k < N; ++k) {
+    if (!(p->tau[k] > 0.5) || !(p->rho0[k] > 0.0)) return LBM3_EINVAL;
+    for (int l = 0; l < N; ++l) {
+      const double s = p->sigma[k * N + l], t = p->sigma[l * N + k];
+      if (k == l ? s != 0.0 : !(s > 0.0 && s == t)) return LBM3_EINVAL;
+    }
+  }
+  lbm3n_ctx* c = new (std::nothrow) lbm3n_ctx();
+  if (!c) return LBM3_ENOMEM;
+  c->N = N;
+  c->nx = p->nx;
+  c->ny = p->ny;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&c->device);
+  lbm3::NArgs& a = c->args;
+  a.nx = p->nx;
+  a.ny = p->ny;
+  for (int k = 0; k < N; ++k) a.inv_nu[k] = static_cast<float>(3.0 / (p->tau[k] - 0.5));
+  for (int k = 0; k < N; ++k)
+    for (int l = k + 1; l < N; ++l) {
+      const int q = lbm3::pair_index(k, l, N);
+      a.sigma[q] = static_cast<float>(p->sigma[k * N + l]);
+      a.cpair[q] = static_cast<float>(1e6 / (p->rho0[k] * p->rho0[l]));
+      for (int m = 0; m < N; ++m) {
+        double gv = 0.0;
+        if (m != k && m != l) {
+          const double smk = p->sigma[m * N + k], sml = p->sigma[m * N + l], skl = p->sigma[k * N + l];
+          gv = lbm3::g_of((smk * smk + sml * sml - skl * skl) / (2.0 * smk * sml));  // Eqs. 18, 20
+        }
+        a.gjunc[q][m] = static_cast<float>(gv);
+      }
+    }
+  a.beta0 = static_cast<float>(p->beta0);
+  a.beta_A = p->beta_form == 0 ? 35.0f : 0.0f;
+  for (int i = 0; i < 9; ++i) {
+    const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    const double len = std::sqrt(static_cast<double>(lbm3::ex(i) * lbm3::ex(i) + lbm3::ey(i) * lbm3::ey(i)));
+    a.wrec[i] = static_cast<float>((p->recolor_form == 0 && i != 0) ? w / len : w);
+  }
+  a.ndelta = static_cast<float>(p->normal_delta);
+  const size_t NN = static_cast<size_t>(p->nx) * p->ny;
+  const size_t pop = static_cast<size_t>(9) * N * NN * sizeof(float);
+  void *b0 = nullptr, *b1 = nullptr, *w = nullptr, *sm = nullptr;
+  if (cudaMalloc(&b0, pop) != cudaSuccess || cudaMalloc(&b1, pop) != cudaSuccess ||
+      cudaMalloc(&w, lbm3::work_floats(N, NN) * sizeof(float) + 9 * N * NN * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&sm, 9 * N * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    if (b0) cudaFree(b0);
+    if (b1) cudaFree(b1);
+    if (w) cudaFree(w);
+    delete c;
+    return LBM3_ENOMEM;
+  }
+  c->buf[0] = static_cast<float*>(b0);
+  c->buf[1] = static_cast<float*>(b1);
+  c->work = static_cast<float*>(w);
+  c->sums = static_cast<double*>(sm);
+  *out = c;
+  return LBM3_OK;
+}
+
+lbm3_status lbm3n_set_populations(lbm3n_ctx* c, const double* f, int on_device) {
+  if (!c) return LBM3_EINVAL;
+  if (!f) return nfail(c, LBM3_EINVAL, "lbm3n_set_populations: NULL f");
+  const size_t NN = static_cast<size_t>(c->nx) * c->ny;
+  const size_t bytes = static_cast<size_t>(9) * c->N * NN * sizeof(double);
+  const double* src = f;
+  // FP64 staging behind the intermediates in the work allocation
+  double* staging = reinterpret_cast<double*>(c->work + lbm3::work_floats(c->N, NN));
+  if (!on_device) {
+    cudaError_t e = cudaMemcpyAsync(staging, f, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return ncuda(c, e, "copy to the device");
+    src = staging;
+  }
+  dim3 grid(lbm3::grid_of(NN), 9 * c->N);
+  lbm3::n_set_kernel<<<grid, lbm3::kNThreads, 0, c->stream>>>(src, c->buf[c->cur], c->nx, c->ny, 9 * c->N);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return ncuda(c, e, "lbm3n_set_populations");
+  c->state_set = true;
+  c->t = 0;
+  return LBM3_OK;
+}
+
+lbm3_status lbm3n_init(lbm3n_ctx* c, const double* rho, int on_device) {
+  if (!c) return LBM3_EINVAL;
+  if (!rho || on_device) return nfail(c, LBM3_EINVAL, "lbm3n_init: host densities rho[N][ny][nx] required");
+  const size_t NN = static_cast<size_t>(c->nx) * c->ny;
+  std::vector<double> f(static_cast<size_t>(9) * c->N * NN);
+  for (int k = 0; k < c->N; ++k)
+    for (size_t n = 0; n < NN; ++n) {
+      const double v = rho[k * NN + n];
+      if (!(v >= 0.0)) return nfail(c, LBM3_EINVAL, "lbm3n_init: rho_k must be >= 0");
+      for (int i = 0; i < 9; ++i) {
+        const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+        f[(static_cast<size_t>(k) * 9 + i) * NN + n] = w * v;  // rest equilibrium per colour
+      }
+    }
+  return lbm3n_set_populations(c, f.data(), 0);
+}
+
+lbm3_status lbm3n_step(lbm3n_ctx* c, int64_t n) {
+  if (!c) return LBM3_EINVAL;
+  if (n < 0) return nfail(c, LBM3_EINVAL, "lbm3n_step: n < 0");
+  if (!c->state_set) return nfail(c, LBM3_ESTATE, "lbm3n_step: state not set");
+  for (int64_t s = 0; s < n; ++s) {
+    const cudaError_t e = lbm3::n_step_any(c->N, c->buf[c->cur], c->buf[c->cur ^ 1], c->work, c->args, c->stream);
+    if (e != cudaSuccess) return ncuda(c, e, "lbm3n_step");
+    c->cur ^= 1;
+    c->t += 1;
+  }
+  return LBM3_OK;
+}
+
+lbm3_status lbm3n_populations(lbm3n_ctx* c, double* f, int on_device) {
+  if (!c) return LBM3_EINVAL;
+  if (!f) return nfail(c, LBM3_EINVAL, "lbm3n_populations: NULL f");
+  if (!c->state_set) return nfail(c, LBM3_ESTATE, "lbm3n_populations: state not set");
+  const size_t NN = static_cast<size_t>(c->nx) * c->ny;
+  double* dst = on_device ? f : reinterpret_cast<double*>(c->work + lbm3::work_floats(c->N, NN));
+  dim3 grid(lbm3::grid_of(NN), 9 * c->N);
+  lbm3::n_get_kernel<<<grid, lbm3::kNThreads, 0, c->stream>>>(c->buf[c->cur], dst, c->nx, c->ny);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && !on_device)
+    e = cudaMemcpyAsync(f, dst, static_cast<size_t>(9) * c->N * NN * sizeof(double), cudaMemcpyDeviceToHost,
+                        c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return ncuda(c, e, "lbm3n_populations");
+  return LBM3_OK;
+}
+
+lbm3_status lbm3n_mass(lbm3n_ctx* c, double* mass, double* mom) {
+  if (!c) return LBM3_EINVAL;
+  if (!c->state_set) return nfail(c, LBM3_ESTATE, "lbm3n_mass: state not set");
+  const size_t NN = static_cast<size_t>(c->nx) * c->ny;
+  lbm3::n_plane_sum_kernel<<<9 * c->N, lbm3::kNThreads, 0, c->stream>>>(c->buf[c->cur], static_cast<int>(NN),
+                                                                          c->sums);
+  std::vector<double> h(static_cast<size_t>(9) * c->N);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.data(), c->sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return ncuda(c, e, "lbm3n_mass");
+  double mx = 0.0, my = 0.0;
+  for (int k = 0; k < c->N; ++k) {
+    double m = 0.0;
+    for (int i = 0; i < 9; ++i) {
+      const double v = h[static_cast<size_t>(k) * 9 + i];
+      m += v;
+      mx += lbm3::ex(i) * v;
+      my += lbm3::ey(i) * v;
+    }
+    if (mass) mass[k] = m;
+  }
+  if (mom) {
+    mom[0] = mx;
+    mom[1] = my;
+  }
+  return LBM3_OK;
+}
+
+lbm3_status lbm3n_destroy(lbm3n_ctx* c) {
+  if (!c) return LBM3_OK;
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->buf[0]);
+  cudaFree(c->buf[1]);
+  cudaFree(c->work);
+  cudaFree(c->sums);
+  cudaGetLastError();
+  delete c;
+  return LBM3_OK;
+}
+
+const char* lbm3n_last_error(const lbm3n_ctx* c) { return c ? c->msg.c_str() : "lbm3n: NULL context"; }
+
+}  // extern "C"

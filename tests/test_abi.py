@@ -42,6 +42,9 @@ def test_params_struct_layout_matches_header():
     assert L.lbm3_params.normal_delta.offset == 104
     # lbm3_interfaces: 31 doubles and an int32 flag word, padded to 8 bytes
     assert ctypes.sizeof(L.lbm3_interfaces) == 256 and L.lbm3_interfaces.flags.offset == 248
+    # lbm3n_params: 3 int32, 3 pointers, beta0, 2 int32, normal_delta
+    assert ctypes.sizeof(L.lbm3n_params) == 64 and L.lbm3n_params.tau.offset == 16
+    assert L.lbm3n_params.normal_delta.offset == 56
 
 
 @pytest.mark.parametrize("kw", [
