@@ -281,7 +281,11 @@ cudaError_t n_step_any(int N, const float* fin, float* fout, float* work, const 
   }
 }
 
-size_t work_floats(int N, size_t NN) { return (N + 1 + 9 + 3 + static_cast<size_t>(N) * (N - 1)) * NN; }
+// intermediates, rounded up to 64 floats so that the FP64 staging behind them
+// is aligned
+size_t work_floats(int N, size_t NN) {
+  return ((N + 1 + 9 + 3 + static_cast<size_t>(N) * (N - 1)) * NN + 63) / 64 * 64;
+}
 
 // stored (post-collision, at the producing node) <-> post-streaming populations
 __global__ void n_set_kernel(const double* __restrict__ fpost, float* __restrict__ f, int nx, int ny, int planes) {
