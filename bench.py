@@ -448,6 +448,57 @@ def run_janus(args):
             "gpu_launches": args.steps}
 
 
+def run_nphase(args):
+    """N fluids (the first N-fluid path, three kernels per step): four fluids
+    in a nested droplet on an n x n grid (default 2048^2; radii 3n/8, n/4,
+    n/8), tensions 0.01 / 0.008 / 0.006 between neighbouring layers and 0.012
+    otherwise, tau = (1.0, 0.8, 0.9, 1.2).  Algorithmic bytes per node update
+    are the state's, 2 x 9N x 4 (288 B at N = 4); the three kernels also move
+    their intermediates through HBM (written once, read by the next kernel;
+    the stencil reads from L2)."""
+    import torch
+
+    from paper_1808_08555_gb300 import build as B
+    B.build()
+    from paper_1808_08555_gb300 import lbm3 as L
+    from paper_1808_08555_gb300 import workloads as W
+
+    n = args.size or 2048
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    r = np.hypot(x - n / 2, y - n / 2)
+    disc = [0.5 + 0.5 * np.tanh((R - r) / W.XI) for R in (3 * n / 8, n / 4, n / 8)]
+    rho = np.stack([np.clip(1 - disc[0], 0, None), np.clip(disc[0] - disc[1], 0, None),
+                    np.clip(disc[1] - disc[2], 0, None), disc[2]])
+    sig = np.full((4, 4), 0.012)
+    np.fill_diagonal(sig, 0.0)
+    for (k, l, v) in ((0, 1, 0.01), (1, 2, 0.008), (2, 3, 0.006)):
+        sig[k, l] = sig[l, k] = v
+    sim = L.NSimulation(n, n, sig, tau=(1.0, 0.8, 0.9, 1.2))
+    sim.init(rho)
+    sim.step(args.warmup)
+    s = sim.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    sim.step(args.steps)
+    e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    m, _ = sim.mass()
+    sim.close()
+    mlups = n * n / ms / 1e3
+    peak, peak_kind = hbm_peak()
+    bpn = 2 * 9 * 4 * 4
+    return {"metric": "D2Q9 MLUPS, four fluids (N-fluid path)", "value": round(mlups, 1), "unit": "MLUPS",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"four-fluid nested droplet {n}x{n}, radii {3 * n // 8}/{n // 4}/{n // 8}"},
+            "roofline": {"bound": "hbm", "achieved": round(bpn * mlups / 1e3, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(bpn * mlups * 1e6 / (peak * 1e9), 4), "traffic": None, "bytes_per_node": bpn,
+                         "kernel": "n_density + n_tension + n_collide kernels (N = 4)", "peak_source": peak_kind},
+            "checks": {"mass": [float(v) for v in m]}, "gpu_launches": 3 * args.steps}
+
+
 def run_adjoint(args):
     """Reverse mode on the gradient workload: 256^2 touching discs (sigma =
     0.01 each, tau = 1), J = sum (phi - phi_target)^2 after 2000 steps, the
@@ -629,7 +680,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=120.0,
                     help="--impl reference: time budget of the timed steps (sets the sampled window)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="compound", choices=["compound", "sweep", "janus", "adjoint"],
+    ap.add_argument("--workload", default="compound", choices=["compound", "sweep", "janus", "adjoint", "nphase"],
                     help="compound: the 2048^2 compound droplet (default); sweep: the 64-instance batch; "
                          "janus: the 4096^2 Janus droplet with FP32 / FP16 / BF16 storage; "
                          "adjoint: gradient evaluations of the 256^2 gradient workload")
@@ -644,7 +695,8 @@ def main():
     args = ap.parse_args()
     # default K / W per workload: a step of the adjoint workload is a whole
     # gradient evaluation (~60-80 ms), of the others one lattice step
-    dflt = {"compound": (5000, 50), "sweep": (2000, 20), "janus": (1000, 20), "adjoint": (10, 3)}[args.workload]
+    dflt = {"compound": (5000, 50), "sweep": (2000, 20), "janus": (1000, 20), "adjoint": (10, 3),
+            "nphase": (500, 10)}[args.workload]
     if args.steps is None:
         args.steps = 3 if args.impl == "reference" else dflt[0]
     if args.warmup is None:
@@ -666,6 +718,8 @@ def main():
             line = run_janus(args) if rank == 0 else None
         elif args.workload == "adjoint":
             line = run_adjoint(args) if rank == 0 else None
+        elif args.workload == "nphase":
+            line = run_nphase(args) if rank == 0 else None
         else:
             line = run_ours(args, ws, rank, local)
         if line is not None:
