@@ -20,6 +20,12 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
+# Threads of the oracle's node loops wait passively between loops, so that a
+# busy host (other processes, a second threaded library) does not turn each
+# loop's barrier into spinning threads that starve the working ones (read by
+# the OpenMP runtime when the oracle's library first loads it).
+os.environ.setdefault("OMP_WAIT_POLICY", "PASSIVE")
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm3_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")

@@ -228,3 +228,40 @@ def test_normal_delta_on_paper_observables():
         ph = fl["rho"] / fl["rho"].sum(0)
         dps.append(D.bulk_pressure(ph, fl["p"], 1) - D.bulk_pressure(ph, fl["p"], 0))
     assert dps[0] == pytest.approx(dps[1], rel=1e-4)
+
+
+def test_critical_engulfing_paper_beta_against_constant_beta():
+    """Sec. 4.3: at the critical tension sigma_rb = sigma_rg + sigma_gb the
+    equilibrium is complete engulfing (no red-blue interface), which the
+    paper's beta of Eqs. 19-20 reaches and the constant beta of Eq. fu does
+    not.  Red droplet (R = 19.2) half inside a green one (R = 25.6) in blue,
+    96^2, sigma = (0.01, 0.02, 0.01), tau = 0.8, from the analytic critical
+    geometry: the red-blue interface length sum(phi_r phi_b)/(xi/2) must
+    shrink at every 1000 steps with Eqs. 19-20 and grow with Eq. fu, ending
+    more than twice as long.  Mistakes planted in the oracle's Eq. 19 fail
+    this: the sign of g flipped or the junction factor set to 0 make the
+    interface grow, the factor set to 1 everywhere makes the run diverge."""
+    n = 96
+    s = n / 300.0
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    c = (n + 1) / 2.0 - 1.0
+    edge = lambda d: 0.5 + 0.5 * np.tanh(d / W.XI)
+    R_r, R_g = 60.0 * s, 80.0 * s
+    pr = edge(R_r - np.hypot(x - c, y - (c + R_g - R_r)))
+    pg = np.clip(edge(R_g - np.hypot(x - c, y - c)) - pr, 0.0, None)
+    rho = np.stack([pr, pg, np.clip(1.0 - pr - pg, 0.0, None)])
+    lengths = {}
+    for form in (0, 1):
+        op = O.Params(n, n, tau=(0.8, 0.8, 0.8), sigma=(0.01, 0.02, 0.01), beta_form=form)
+        f = O.init(op, rho)
+        L = []
+        for _ in range(4):
+            f = O.step(op, f, 1000)
+            r = f.sum(axis=1)
+            ph = r / r.sum(axis=0)
+            L.append(float((ph[0] * ph[2]).sum() / (W.XI / 2)))
+        lengths[form] = L
+    paper, fu = lengths[0], lengths[1]
+    assert all(b < a for a, b in zip(paper, paper[1:])), paper
+    assert all(b > a for a, b in zip(fu, fu[1:])), fu
+    assert fu[-1] > 2.0 * paper[-1], (paper, fu)
