@@ -30,19 +30,18 @@ __device__ __forceinline__ int dir_ey(int i) { return ey(i); }
 // stored_{i,k}(x) = w_i rho_k(x + e_i): the rest equilibrium w_i rho_k after
 // the pull of the next step.
 __global__ void init_from_rho_kernel(const double* __restrict__ rho, float* __restrict__ f, int nx, int ny) {
-  const int plane = blockIdx.y;  // k*9 + i (input numbering)
+  const int plane = blockIdx.z;  // k*9 + i (input numbering)
   const int k = plane / 9, i = plane % 9;
   const int P = pitch_of(nx);
   const size_t N = static_cast<size_t>(nx) * ny;
-  const size_t NP = static_cast<size_t>(P) * ny;
-  float* dst = f + static_cast<size_t>(plane_of(k, i)) * NP;
+  float* dst = f + static_cast<size_t>(plane_of(k, i)) * P * ny;
   const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
-  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < NP;
-       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int xp = static_cast<int>(n % P), y = static_cast<int>(n / P);
-    const int x = wrapi(xp - kGhost, nx);
-    const size_t src = static_cast<size_t>(wrapi(y + dir_ey(i), ny)) * nx + wrapi(x + dir_ex(i), nx);
-    dst[n] = static_cast<float>(w * rho[k * N + src]);
+  for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+    const size_t row = static_cast<size_t>(wrapi(y + dir_ey(i), ny)) * nx;
+    for (int xp = blockIdx.x * blockDim.x + threadIdx.x; xp < P; xp += gridDim.x * blockDim.x) {
+      const int x = wrapi(xp - kGhost, nx);
+      dst[static_cast<size_t>(y) * P + xp] = static_cast<float>(w * rho[k * N + row + wrapi(x + dir_ex(i), nx)]);
+    }
   }
 }
 
@@ -50,34 +49,32 @@ __global__ void init_from_rho_kernel(const double* __restrict__ rho, float* __re
 // (fpost numbered k*9 + i, unpadded).
 __global__ void set_planes_kernel(const double* __restrict__ fpost, float* __restrict__ f, int nx, int ny,
                                   int plane0) {
-  const int pl = blockIdx.y;
+  const int pl = blockIdx.z;
   const int plane = plane0 + pl, k = plane / 9, i = plane % 9;
   const int P = pitch_of(nx);
   const size_t N = static_cast<size_t>(nx) * ny;
-  const size_t NP = static_cast<size_t>(P) * ny;
-  float* dst = f + static_cast<size_t>(plane_of(k, i)) * NP;
-  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < NP;
-       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int xp = static_cast<int>(n % P), y = static_cast<int>(n / P);
-    const int x = wrapi(xp - kGhost, nx);
-    const size_t src = static_cast<size_t>(wrapi(y + dir_ey(i), ny)) * nx + wrapi(x + dir_ex(i), nx);
-    dst[n] = static_cast<float>(fpost[pl * N + src]);
+  float* dst = f + static_cast<size_t>(plane_of(k, i)) * P * ny;
+  for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+    const size_t row = static_cast<size_t>(wrapi(y + dir_ey(i), ny)) * nx;
+    for (int xp = blockIdx.x * blockDim.x + threadIdx.x; xp < P; xp += gridDim.x * blockDim.x) {
+      const int x = wrapi(xp - kGhost, nx);
+      dst[static_cast<size_t>(y) * P + xp] = static_cast<float>(fpost[pl * N + row + wrapi(x + dir_ex(i), nx)]);
+    }
   }
 }
 
 // fpost(x) = stored(x - e_i), written unpadded with numbering k*9 + i.
 __global__ void get_planes_kernel(const float* __restrict__ f, double* __restrict__ fpost, int nx, int ny,
                                   int plane0) {
-  const int pl = blockIdx.y;
+  const int pl = blockIdx.z;
   const int plane = plane0 + pl, k = plane / 9, i = plane % 9;
   const int P = pitch_of(nx);
   const size_t N = static_cast<size_t>(nx) * ny;
   const float* src = f + static_cast<size_t>(plane_of(k, i)) * static_cast<size_t>(P) * ny;
-  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < N;
-       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
-    const size_t s = static_cast<size_t>(wrapi(y - dir_ey(i), ny)) * P + (wrapi(x - dir_ex(i), nx) + kGhost);
-    fpost[pl * N + n] = static_cast<double>(src[s]);
+  for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+    const size_t srow = static_cast<size_t>(wrapi(y - dir_ey(i), ny)) * P;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x)
+      fpost[pl * N + static_cast<size_t>(y) * nx + x] = static_cast<double>(src[srow + wrapi(x - dir_ex(i), nx) + kGhost]);
   }
 }
 
@@ -310,25 +307,29 @@ int grid_for(size_t N) {
   return static_cast<int>(b < 65535 ? (b > 0 ? b : 1) : 65535);
 }
 
+// Plane kernels: 256 threads along a row's columns, rows by blockIdx.y (at
+// most 1024 per grid stride), one plane per blockIdx.z.
+dim3 plane_grid(int cols, int ny, int planes) {
+  return dim3(static_cast<unsigned>((cols + 255) / 256), static_cast<unsigned>(ny < 1024 ? ny : 1024),
+              static_cast<unsigned>(planes));
+}
+
 }  // namespace
 
 cudaError_t launch_init_from_rho(const double* rho, float* f, int nx, int ny, cudaStream_t s) {
-  dim3 grid(grid_for(static_cast<size_t>(pitch_of(nx)) * ny), 27);
-  init_from_rho_kernel<<<grid, 256, 0, s>>>(rho, f, nx, ny);
+  init_from_rho_kernel<<<plane_grid(pitch_of(nx), ny, 27), 256, 0, s>>>(rho, f, nx, ny);
   return cudaGetLastError();
 }
 
 cudaError_t launch_set_planes(const double* fpost, float* f, int nx, int ny, int plane0, int nplanes,
                               cudaStream_t s) {
-  dim3 grid(grid_for(static_cast<size_t>(pitch_of(nx)) * ny), nplanes);
-  set_planes_kernel<<<grid, 256, 0, s>>>(fpost, f, nx, ny, plane0);
+  set_planes_kernel<<<plane_grid(pitch_of(nx), ny, nplanes), 256, 0, s>>>(fpost, f, nx, ny, plane0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_get_planes(const float* f, double* fpost, int nx, int ny, int plane0, int nplanes,
                               cudaStream_t s) {
-  dim3 grid(grid_for(static_cast<size_t>(nx) * ny), nplanes);
-  get_planes_kernel<<<grid, 256, 0, s>>>(f, fpost, nx, ny, plane0);
+  get_planes_kernel<<<plane_grid(nx, ny, nplanes), 256, 0, s>>>(f, fpost, nx, ny, plane0);
   return cudaGetLastError();
 }
 
