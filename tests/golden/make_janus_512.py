@@ -12,6 +12,11 @@ junctions (Eq. theta_kl, measured by ``oracle.diagnostics``) and the bulk
 pressures of the three fluids.  Calls only ``oracle``.
 
     python tests/golden/make_janus_512.py [--steps 1000] [--out FILE]
+
+janus_512.json is the default run (1000 steps, the junctions still moving);
+janus_512_eq.json is the same workload at equilibrium:
+
+    python tests/golden/make_janus_512.py --steps 80000 --out tests/golden/janus_512_eq.json
 """
 from __future__ import annotations
 
