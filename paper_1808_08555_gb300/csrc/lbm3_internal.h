@@ -35,7 +35,7 @@ __host__ __device__ constexpr float wt(int i) {
 // Populations are stored as 27 planes of ny rows with a padded pitch
 // P = max(nx + 8, 132): column xp = x + 4 holds node x, and the four ghost
 // columns on each side hold copies of the opposite edge (periodic wrap), so
-// that every strip's halo window is one contiguous, in-bounds span of a row.  Planes are
+// that every strip's halo window is one contiguous span of a row.  Planes are
 // ordered by the y-component of their direction so that the nine planes a
 // pulled row needs from one source row are consecutive:
 //   group 0: e_y = +1 {2, 5, 6}; group 1: e_y = 0 {0, 1, 3}; group 2: e_y = -1 {4, 7, 8}

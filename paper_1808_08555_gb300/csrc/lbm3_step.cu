@@ -201,16 +201,19 @@ __device__ __forceinline__ RedRows red_rows(Smem& s, int q) {
   return r;
 }
 
-// Ring columns of window column 0 (padded column x0) in the FP32 /
-// deviation / rho' boxes of a slot.
+// Ring column of window column 0 (padded column x0) in the 16-bit deviation
+// box of a slot; the FP32, rho' and reduced-state boxes start at x0 itself.
+// (Every box starts at the strip's own window, the last strip's box running
+// past the end of the row where it is narrower than the box: TMA fills those
+// columns with zeros without reading memory, and no stage reads them.  A box
+// shifted left to stay inside the row re-read up to kPW - w - 8 columns of
+// the previous strip from DRAM for every row.)
 struct RingCols {
-  int f, d, r;
+  int d;
 };
-__device__ __forceinline__ RingCols ring_cols(const StepArgs& a, int x0) {
+__device__ __forceinline__ RingCols ring_cols(int x0) {
   RingCols c;
-  c.f = x0 - min(x0, a.pitch - kPW);
-  c.d = x0 - (min(x0, a.pitch - kDevBoxCols) & ~7);
-  c.r = c.f;
+  c.d = x0 & 7;
   return c;
 }
 
@@ -218,10 +221,10 @@ __device__ __forceinline__ RingCols ring_cols(const StepArgs& a, int x0) {
 // read directly (FP32), or rebuilt as w_i rho'_k + d (16-bit deviations).
 template <int ST>
 __device__ __forceinline__ float popv(const float* slot, int k, int i, int wc, const RingCols& rc) {
-  if (ST == ST_FP32) return slot[dir_group(i) * kGroupFloats + (3 * k + dir_pos(i)) * kPW + wc + rc.f];
+  if (ST == ST_FP32) return slot[dir_group(i) * kGroupFloats + (3 * k + dir_pos(i)) * kPW + wc];
   const unsigned short* dv = reinterpret_cast<const unsigned short*>(slot);
   const float* rr = reinterpret_cast<const float*>(dv + 3 * kDevGroupHalfs);
-  return fmaf(wt(i), rr[dir_group(i) * kRhoGroupFloats + k * kPW + wc + rc.r],
+  return fmaf(wt(i), rr[dir_group(i) * kRhoGroupFloats + k * kPW + wc],
               dec16<ST>(dv[dir_group(i) * kDevGroupHalfs + (3 * k + dir_pos(i)) * kDevBoxCols + wc + rc.d]));
 }
 
@@ -250,8 +253,8 @@ __device__ void produce(Smem& s, const StepArgs& a, const CUtensorMap* map, cons
   const uint32_t row_bytes = STI == ST_FP32 ? 27u * kPW * 4u
                              : RED          ? (kRedVecPlanes * 4u + kRedSclPlanes) * kPW * 4u
                                             : 27u * kDevBoxCols * 2u + 9u * kPW * 4u;
-  const int tma_x = min(x0, a.pitch - kPW);
-  const int dev_x = min(x0, a.pitch - kDevBoxCols) & ~7;
+  const int tma_x = x0;
+  const int dev_x = x0 & ~7;
   volatile int* abort_flag = &s.abort_flag;
   int issued = 0;
   for (int q = 0; q < nrows; ++q) {
@@ -392,9 +395,8 @@ __device__ __forceinline__ void pull_red(const RedRows& rr, const StepArgs& a, i
 // them (each lane of its packed pairs is the same scalar addition, in the
 // same order), so every result equals the FP32 storage's.  Directions are
 // taken one by one so that only one source node's values are live at a time.
-__device__ __forceinline__ void stage_density_red(Smem& s, const StepArgs& a, int q, int c, int w,
-                                                  const RingCols& rc) {
-  const int wc = c + 2 + rc.f;
+__device__ __forceinline__ void stage_density_red(Smem& s, const StepArgs& a, int q, int c, int w) {
+  const int wc = c + 2;
   const RedRows rr = red_rows(s, q);
   float f0[3], v[3];
   float Ax[3], Ay[3], Fx[4], Fy[4];  // lanes of the per-colour pair sums A and the pair totals F
@@ -517,8 +519,7 @@ __device__ __forceinline__ void stage_tension(Smem& s, const StepArgs& a, int q,
 
 // C stage, one node: row q (output row y0 - 2 + q), column c in [0, w).
 template <int MODE, int ST, int FORCE>
-__device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q, int c, int x0, int y0,
-                                              const RingCols& rc) {
+__device__ __forceinline__ void stage_collide(Smem& s, const StepArgs& a, int q, int c, int x0, int y0) {
   const float4* Tm = s.T[(q - 1) & 3];
   const float4* Tz = s.T[q & 3];
   const float4* Tp = s.T[(q + 1) & 3];
@@ -782,7 +783,7 @@ template <int MODE, int ST, int FORCE>
 __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h, int tid) {
   constexpr int STI = st_in(ST);
   const int nq = h + 4;  // rows q = 0 .. h+3 <-> y = y0-2 .. y0+h+1
-  const RingCols rc = ring_cols(a, x0);
+  const RingCols rc = ring_cols(x0);
   volatile int* abort_flag = &s.abort_flag;
   bool dead = false;
   const int J = (h + 3) / 2 + 1;
@@ -810,7 +811,7 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
         const int W = w + 4;
         const int r = tid >= W ? 1 : 0;
         if (STI == ST_RED)
-          stage_density_red(s, a, q0 + r, tid - r * W, w, rc);
+          stage_density_red(s, a, q0 + r, tid - r * W, w);
         else
           stage_density<STI>(s, q0 + r, tid - r * W, w, rc);
       }
@@ -843,7 +844,7 @@ __device__ void consume(Smem& s, const StepArgs& a, int x0, int w, int y0, int h
       const int nr = qb - qa + 1;
       if (tid < nr * w) {  // at most 248 nodes
         const int r = tid >= w ? 1 : 0;
-        stage_collide<MODE, ST, FORCE>(s, a, qa + r, tid - r * w, x0, y0, rc);
+        stage_collide<MODE, ST, FORCE>(s, a, qa + r, tid - r * w, x0, y0);
       }
     }
   }

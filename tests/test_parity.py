@@ -114,7 +114,8 @@ def test_tiling_does_not_change_results(L):
     """The arithmetic per node does not depend on the tiling: automatic row
     chunks (different heights for the 124-column strips and the narrow last
     strip), a small explicit height and one chunk per strip give
-    bit-identical populations after several steps."""
+    bit-identical populations after several steps.  The narrow last strip's
+    copy box (12 of its columns in the row) runs past the end of the row."""
     nx, ny = 136, 1200
     rho = W.droplet_field(nx, ny, seed=5, count=12, rmin=4.0, rmax=10.0, gap=10.0)
     p = L.Params(nx, ny, tau=(0.6, 0.9, 1.3), sigma=(0.01, 0.013, 0.007))
