@@ -499,6 +499,50 @@ def run_nphase(args):
             "checks": {"mass": [float(v) for v in m]}, "gpu_launches": 3 * args.steps}
 
 
+def run_d3q19(args):
+    """Three fluids on the D3Q19 lattice (the first 3D path, three kernels per
+    step): two spheres, fluid 2 (R = 3n/16 at x = n/4) and fluid 3 (R = 5n/32
+    at x = 3n/4), in fluid 1 on an n^3 grid (default 256^3), sigma_12 / 13 /
+    23 = 0.01 / 0.013 / 0.007, tau = (0.6, 0.9, 1.3).  Algorithmic bytes per
+    node update are the state's, 2 x 19N x 4 (456 B at N = 3); the kernels
+    also move their intermediates through HBM."""
+    import torch
+
+    from paper_1808_08555_gb300 import build as B
+    B.build()
+    from paper_1808_08555_gb300 import lbm3 as L
+    from paper_1808_08555_gb300 import workloads as W
+
+    n = args.size or 256
+    rho = W.spheres_3d(n, n, n, [(1, (n / 4, n / 2, n / 2), 3 * n / 16), (2, (3 * n / 4, n / 2, n / 2), 5 * n / 32)])
+    sig = np.array([[0.0, 0.01, 0.013], [0.01, 0.0, 0.007], [0.013, 0.007, 0.0]])
+    sim = L.D3Q19Simulation(n, n, n, sig, tau=(0.6, 0.9, 1.3))
+    sim.init(rho)
+    del rho
+    sim.step(args.warmup)
+    s = sim.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    sim.step(args.steps)
+    e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    m, _ = sim.mass()
+    sim.close()
+    mlups = n ** 3 / ms / 1e3
+    peak, peak_kind = hbm_peak()
+    bpn = 2 * 19 * 3 * 4
+    return {"metric": "D3Q19 MLUPS, three fluids (3D path)", "value": round(mlups, 1), "unit": "MLUPS",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"two spheres of fluids 2 and 3 in fluid 1, {n}^3, R {3 * n // 16}/{5 * n // 32}"},
+            "roofline": {"bound": "hbm", "achieved": round(bpn * mlups / 1e3, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(bpn * mlups * 1e6 / (peak * 1e9), 4), "traffic": None, "bytes_per_node": bpn,
+                         "kernel": "d_density + d_tension + d_collide kernels (N = 3)", "peak_source": peak_kind},
+            "checks": {"mass": [float(v) for v in m]}, "gpu_launches": 3 * args.steps}
+
+
 def run_adjoint(args):
     """Reverse mode on the gradient workload: 256^2 touching discs (sigma =
     0.01 each, tau = 1), J = sum (phi - phi_target)^2 after 2000 steps, the
@@ -680,10 +724,11 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=120.0,
                     help="--impl reference: time budget of the timed steps (sets the sampled window)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="compound", choices=["compound", "sweep", "janus", "adjoint", "nphase"],
+    ap.add_argument("--workload", default="compound", choices=["compound", "sweep", "janus", "adjoint", "nphase", "d3q19"],
                     help="compound: the 2048^2 compound droplet (default); sweep: the 64-instance batch; "
                          "janus: the 4096^2 Janus droplet with FP32 / FP16 / BF16 storage; "
-                         "adjoint: gradient evaluations of the 256^2 gradient workload")
+                         "adjoint: gradient evaluations of the 256^2 gradient workload; nphase: four fluids, "
+                         "2048^2; d3q19: three fluids on the D3Q19 lattice, 256^3")
     ap.add_argument("--horizon", type=int, default=2000,
                     help="adjoint workload: steps of the differentiated run (2000 is the workload; fewer for profiling)")
     ap.add_argument("--storage", default="both", choices=["both", "fp32", "reduced"],
@@ -696,7 +741,7 @@ def main():
     # default K / W per workload: a step of the adjoint workload is a whole
     # gradient evaluation (~60-80 ms), of the others one lattice step
     dflt = {"compound": (5000, 50), "sweep": (2000, 20), "janus": (1000, 20), "adjoint": (10, 3),
-            "nphase": (500, 10)}[args.workload]
+            "nphase": (500, 10), "d3q19": (200, 5)}[args.workload]
     if args.steps is None:
         args.steps = 3 if args.impl == "reference" else dflt[0]
     if args.warmup is None:
@@ -720,6 +765,8 @@ def main():
             line = run_adjoint(args) if rank == 0 else None
         elif args.workload == "nphase":
             line = run_nphase(args) if rank == 0 else None
+        elif args.workload == "d3q19":
+            line = run_d3q19(args) if rank == 0 else None
         else:
             line = run_ours(args, ws, rank, local)
         if line is not None:

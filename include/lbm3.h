@@ -403,6 +403,52 @@ lbm3_status lbm3n_mass(lbm3n_ctx* ctx, double* mass, double* mom);
 lbm3_status lbm3n_destroy(lbm3n_ctx* ctx);
 const char* lbm3n_last_error(const lbm3n_ctx* ctx);
 
+/* ------------------------------------------------------------------------
+ * N fluids on the D3Q19 lattice (2 <= nfluids <= 4).  The paper writes the
+ * model in vector form (Eq. fd1, the interfacial force of Eq. 11, the
+ * recolouring of Eq. 6) and simulates two dimensions on D2Q9.  This context
+ * runs the same step in three dimensions: Eq. fd1 gradients with the D3Q19
+ * weights (1/3 rest, 1/18 axis, 1/36 edge diagonals, c_s^2 = 1/3), the 3x3
+ * tension tensor of Eq. 11, Guo's forcing, BGK with the harmonic-mean
+ * viscosity, recolouring (w'_i = w_i / |e_i|, or w_i with recolor_form 1),
+ * pull streaming; beta_kl as for lbm3n.  Three kernels per step over
+ * global-memory intermediates (a first path).  Directions, opposite pairs
+ * adjacent:
+ *   0 (0,0,0)  1 (1,0,0)  2 (-1,0,0)  3 (0,1,0)  4 (0,-1,0)  5 (0,0,1)
+ *   6 (0,0,-1)  7 (1,1,0)  8 (-1,-1,0)  9 (1,-1,0)  10 (-1,1,0)  11 (1,0,1)
+ *   12 (-1,0,-1)  13 (1,0,-1)  14 (-1,0,1)  15 (0,1,1)  16 (0,-1,-1)
+ *   17 (0,1,-1)  18 (0,-1,1)
+ * Arrays: sigma[nfluids][nfluids] symmetric with a zero diagonal and
+ * positive entries off it; tau, rho0 [nfluids]; host densities
+ * rho[N][nz][ny][nx] and populations f[N][19][nz][ny][nx] (FP64,
+ * post-streaming: the populations whose densities are the state at time t);
+ * the state is FP32, periodic in all three directions.  ny, nz <= 65535.
+ * Any invalid parameter gives LBM3_EINVAL from lbm3d_create.  The context
+ * allocates its two population buffers (19 N nx ny nz floats each), the
+ * intermediates ((N + 26 + 3 N (N - 1) / 2) nx ny nz floats) and an FP64
+ * staging area of one population state. */
+typedef struct lbm3d_ctx lbm3d_ctx;
+typedef struct {
+  int32_t nx, ny, nz, nfluids;
+  const double* tau;    /* [nfluids], each > 0.5 */
+  const double* rho0;   /* [nfluids], each > 0 (Eq. 15) */
+  const double* sigma;  /* [nfluids][nfluids] */
+  double beta0;         /* (0, 1] */
+  int32_t beta_form;    /* 0: Eq. 19 with one junction term per third fluid; 1: Eq. fu */
+  int32_t recolor_form; /* as lbm3_recolor_form */
+  double normal_delta;  /* as lbm3_params.normal_delta */
+} lbm3d_params;
+lbm3_status lbm3d_create(const lbm3d_params* p, void* cuda_stream, lbm3d_ctx** out);
+/* rest equilibrium per colour from host densities (rho_k >= 0) */
+lbm3_status lbm3d_init(lbm3d_ctx* ctx, const double* rho, int on_device);
+lbm3_status lbm3d_set_populations(lbm3d_ctx* ctx, const double* f, int on_device);
+lbm3_status lbm3d_step(lbm3d_ctx* ctx, int64_t n);  /* asynchronous */
+lbm3_status lbm3d_populations(lbm3d_ctx* ctx, double* f, int on_device);  /* synchronises */
+/* FP64 per-fluid mass[nfluids] and lattice momentum mom[3] (synchronises) */
+lbm3_status lbm3d_mass(lbm3d_ctx* ctx, double* mass, double* mom);
+lbm3_status lbm3d_destroy(lbm3d_ctx* ctx);
+const char* lbm3d_last_error(const lbm3d_ctx* ctx);
+
 /* Wait for the context's stream and report device-side errors (timed-out
  * waits) recorded since the last check. */
 lbm3_status lbm3_sync(lbm3_ctx* ctx);

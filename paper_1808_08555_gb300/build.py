@@ -20,7 +20,7 @@ OBJ = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "liblbm3.so")
 SOURCES = ["lbm3_api.cu", "lbm3_step.cu", "lbm3_aux.cu", "lbm3_static.cu", "lbm3_adjoint.cu", "lbm3_diag.cu",
-           "lbm3_nphase.cu"]
+           "lbm3_nphase.cu", "lbm3_d3q19.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

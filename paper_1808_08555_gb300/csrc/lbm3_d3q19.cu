@@ -1,0 +1,595 @@
+// N-fluid colour-gradient step on the D3Q19 lattice (arXiv 1808.08555: the
+// model of Sec. 2 is written in vector form, Eq. fd1, Eq. 11 and the
+// recolouring of Eq. 6 hold in any dimension; the paper simulates two
+// dimensions).  A first CUDA path for 2 <= N <= kMaxFluids3, three kernels
+// per step over global-memory intermediates, one node per thread, on
+// (x-block, y, z) grids:
+//   densities:  pull the 19N populations (Eq. 30), rho_k, rho, phi_k (the
+//               largest fraction as the complement of the others), the total
+//               distribution f_i
+//   tension:    grad phi_k (Eq. fd1 on D3Q19), G_kl and C_kl (Eq. 15) for the
+//               N(N-1)/2 pairs, the 3x3 tension tensor of Eq. 11 summed over
+//               the pairs, the recolouring normals G / max(|G|, delta phi_k phi_l)
+//   collide:    F_s = div T (Eq. fd1), u (Eq. uk1), tau_f (Eqs. vis_1, tau),
+//               BGK with Guo's forcing (Eqs. 1-3, 5), beta_kl, recolouring
+//               (Eq. 6); f^ddagger stored at the node that produced it
+// beta_kl as for the two-dimensional N-fluid path (Eq. 19 for N = 3, one
+// junction term per third fluid beyond), g(X_kl^m) precomputed on the host.
+//
+// Lattice: rest (weight 1/3), the six axis vectors (1/18), the twelve edge
+// diagonals (1/36), c_s^2 = 1/3, opposite directions adjacent:
+//   0 (0,0,0)  1 (1,0,0)  2 (-1,0,0)  3 (0,1,0)  4 (0,-1,0)  5 (0,0,1)  6 (0,0,-1)
+//   7 (1,1,0)  8 (-1,-1,0)  9 (1,-1,0)  10 (-1,1,0)  11 (1,0,1)  12 (-1,0,-1)
+//   13 (1,0,-1)  14 (-1,0,1)  15 (0,1,1)  16 (0,-1,-1)  17 (0,1,-1)  18 (0,-1,1)
+// Layout: populations [N][19][nz][ny][nx] FP32, unpadded, periodic by index
+// arithmetic; intermediates phi [N], rho, f_i [19], T [6] (xx, xy, xz, yy,
+// yz, zz), normals [P][3] with P = N(N-1)/2, each a [nz][ny][nx] plane.
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm3.h"
+#include "lbm3_internal.h"
+
+namespace lbm3 {
+namespace {
+
+constexpr int kMaxFluids3 = 4;
+constexpr int kMaxPairs3 = kMaxFluids3 * (kMaxFluids3 - 1) / 2;
+constexpr int Q3 = 19;
+constexpr int kBX = 128;  // threads per block, along x
+
+__host__ __device__ constexpr int cx(int i) {
+  return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1 : ((i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int i) {
+  return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1 : ((i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0);
+}
+__host__ __device__ constexpr int cz(int i) {
+  return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1 : ((i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0);
+}
+__host__ __device__ constexpr double w3d(int i) { return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+// FP32 weights whose exact sum is 1 (1/36 rounded down to an even multiple of
+// its ulp, 1/18 twice that, 1/3 the remainder, within 2 ulp of each): with
+// the nearest floats the sum is 1 + 1.5e-8 and every collision would create
+// that fraction of mass (2.5e-8 per step at tau = 0.6)
+__host__ __device__ constexpr float w3f(int i) {
+  return i == 0 ? 0x1.555558p-2f : (i < 7 ? 0x1.c71c70p-5f : 0x1.c71c70p-6f);
+}
+
+struct DArgs {
+  int nx, ny, nz;
+  float inv_nu[kMaxFluids3];            // 1/nu_k
+  float sigma[kMaxPairs3];              // sigma_kl for pairs k < l in row order
+  float cpair[kMaxPairs3];              // 1e6 / (rho0_k rho0_l)
+  float gjunc[kMaxPairs3][kMaxFluids3];  // g(X_kl^m) (0 for m = k, l)
+  float beta0, beta_A;                  // beta_A = 35 (0: Eq. fu, constant beta)
+  float wrec[Q3];                       // recolouring weights w_i / |e_i| or w_i
+  float ndelta;
+};
+
+__host__ __device__ constexpr int pair3(int k, int l, int n) {  // k < l
+  return k * n - k * (k + 1) / 2 + (l - k - 1);
+}
+
+__device__ __forceinline__ int wrap3(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// the node of this thread and the strides of the [nz][ny][nx] planes
+struct Node {
+  int x, y, z;
+  size_t n, NN;
+};
+__device__ __forceinline__ bool node_of(const DArgs& a, Node* o) {
+  o->x = static_cast<int>(blockIdx.x) * kBX + static_cast<int>(threadIdx.x);
+  o->y = static_cast<int>(blockIdx.y);
+  o->z = static_cast<int>(blockIdx.z);
+  o->NN = static_cast<size_t>(a.nx) * a.ny * a.nz;
+  o->n = (static_cast<size_t>(o->z) * a.ny + o->y) * a.nx + o->x;
+  return o->x < a.nx;
+}
+// index of the node at offset (dx, dy, dz), periodic
+__device__ __forceinline__ size_t at(const DArgs& a, const Node& p, int dx, int dy, int dz) {
+  return (static_cast<size_t>(wrap3(p.z + dz, a.nz)) * a.ny + wrap3(p.y + dy, a.ny)) * a.nx + wrap3(p.x + dx, a.nx);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kBX) d_density_kernel(const float* __restrict__ f, float* __restrict__ phi,
+                                                        float* __restrict__ rho_out, float* __restrict__ fi, DArgs a) {
+  Node p;
+  if (!node_of(a, &p)) return;
+  const size_t NN = p.NN;
+  float r[N];
+  float tot[Q3];
+#pragma unroll
+  for (int i = 0; i < Q3; ++i) tot[i] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    float s = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Q3; ++i) {
+      const float v = f[(static_cast<size_t>(k) * Q3 + i) * NN + at(a, p, -cx(i), -cy(i), -cz(i))];  // Eq. 30, pull
+      s += v;
+      tot[i] += v;
+    }
+    r[k] = s;
+  }
+  float rho = 0.0f, rmax = -1.0f;
+  int kmax = 0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    rho += r[k];
+    if (r[k] > rmax) {
+      rmax = r[k];
+      kmax = k;
+    }
+  }
+  const float ir = 1.0f / rho;
+  float rest = 1.0f;
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    if (k != kmax) {
+      const float v = r[k] * ir;
+      phi[static_cast<size_t>(k) * NN + p.n] = v;
+      rest -= v;
+    }
+  phi[static_cast<size_t>(kmax) * NN + p.n] = rest;  // the fractions sum to 1 exactly
+  rho_out[p.n] = rho;
+#pragma unroll
+  for (int i = 0; i < Q3; ++i) fi[static_cast<size_t>(i) * NN + p.n] = tot[i];
+}
+
+template <int N>
+__global__ void __launch_bounds__(kBX) d_tension_kernel(const float* __restrict__ phi, const float* __restrict__ rho_in,
+                                                        float* __restrict__ T, float* __restrict__ nrm, DArgs a) {
+  Node p;
+  if (!node_of(a, &p)) return;
+  const size_t NN = p.NN;
+  float ph[N], g[N][3];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    ph[k] = phi[static_cast<size_t>(k) * NN + p.n];
+    float sx = 0.0f, sy = 0.0f, sz = 0.0f;  // Eq. fd1: (1/cs2) sum_i w_i phi(x + e_i) e_i
+#pragma unroll
+    for (int i = 1; i < Q3; ++i) {
+      const float v = phi[static_cast<size_t>(k) * NN + at(a, p, cx(i), cy(i), cz(i))];
+      const float w3 = 3.0f * w3f(i);
+      sx += w3 * cx(i) * v;
+      sy += w3 * cy(i) * v;
+      sz += w3 * cz(i) * v;
+    }
+    g[k][0] = sx;
+    g[k][1] = sy;
+    g[k][2] = sz;
+  }
+  const float rho = rho_in[p.n];
+  float txx = 0.0f, txy = 0.0f, txz = 0.0f, tyy = 0.0f, tyz = 0.0f, tzz = 0.0f;
+  int q = 0;
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+#pragma unroll
+    for (int l = k + 1; l < N; ++l, ++q) {
+      // G_kl = phi_l grad phi_k - phi_k grad phi_l
+      const float Gx = ph[l] * g[k][0] - ph[k] * g[l][0];
+      const float Gy = ph[l] * g[k][1] - ph[k] * g[l][1];
+      const float Gz = ph[l] * g[k][2] - ph[k] * g[l][2];
+      const float g2 = Gx * Gx + Gy * Gy + Gz * Gz;
+      float nv[3] = {0.0f, 0.0f, 0.0f};
+      if (g2 > 1e-30f) {
+        const float mag = sqrtf(g2);
+        const float pp = ph[k] * ph[l];
+        const float ck = fminf(a.cpair[q] * pp * rho * rho, 1.0f);  // Eq. 15
+        // sigma C |G| (I - n n) = sigma C (|G|^2 I - G G) / |G|
+        const float sc = a.sigma[q] * ck / mag;
+        txx += sc * (Gy * Gy + Gz * Gz);
+        tyy += sc * (Gx * Gx + Gz * Gz);
+        tzz += sc * (Gx * Gx + Gy * Gy);
+        txy -= sc * Gx * Gy;
+        txz -= sc * Gx * Gz;
+        tyz -= sc * Gy * Gz;
+        const float den = fmaxf(mag, a.ndelta * pp);
+        nv[0] = Gx / den;
+        nv[1] = Gy / den;
+        nv[2] = Gz / den;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) nrm[(static_cast<size_t>(q) * 3 + c) * NN + p.n] = nv[c];
+    }
+  T[p.n] = txx;
+  T[NN + p.n] = txy;
+  T[2 * NN + p.n] = txz;
+  T[3 * NN + p.n] = tyy;
+  T[4 * NN + p.n] = tyz;
+  T[5 * NN + p.n] = tzz;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kBX) d_collide_kernel(const float* __restrict__ phi, const float* __restrict__ rho_in,
+                                                        const float* __restrict__ fi, const float* __restrict__ T,
+                                                        const float* __restrict__ nrm, float* __restrict__ fout,
+                                                        DArgs a) {
+  Node p;
+  if (!node_of(a, &p)) return;
+  const size_t NN = p.NN;
+  // F_s = div T (Eq. 11): F_a = (1/cs2) sum_i w_i sum_b e_ib T_ab(x + e_i)
+  float F[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int i = 1; i < Q3; ++i) {
+    const size_t m = at(a, p, cx(i), cy(i), cz(i));
+    const float w3 = 3.0f * w3f(i);
+    const float txx = T[m], txy = T[NN + m], txz = T[2 * NN + m], tyy = T[3 * NN + m], tyz = T[4 * NN + m],
+                tzz = T[5 * NN + m];
+    F[0] += w3 * (cx(i) * txx + cy(i) * txy + cz(i) * txz);
+    F[1] += w3 * (cx(i) * txy + cy(i) * tyy + cz(i) * tyz);
+    F[2] += w3 * (cx(i) * txz + cy(i) * tyz + cz(i) * tzz);
+  }
+  const float rho = rho_in[p.n];
+  float ph[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) ph[k] = phi[static_cast<size_t>(k) * NN + p.n];
+  float f[Q3];
+#pragma unroll
+  for (int i = 0; i < Q3; ++i) f[i] = fi[static_cast<size_t>(i) * NN + p.n];
+  float m[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int i = 1; i < Q3; ++i) {
+    m[0] += cx(i) * f[i];
+    m[1] += cy(i) * f[i];
+    m[2] += cz(i) * f[i];
+  }
+  const float irho = 1.0f / rho;
+  float u[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) u[c] = (m[c] + 0.5f * F[c]) * irho;  // Eq. uk1
+  float inu = 0.0f;
+#pragma unroll
+  for (int k = 0; k < N; ++k) inu += ph[k] * a.inv_nu[k];  // rho/nu = sum_k rho_k/nu_k
+  const float om = inu / (3.0f + 0.5f * inu);               // 1/tau_f, tau_f = 3 nu + 1/2
+  const float gg = 1.0f - 0.5f * om;                        // Guo prefactor 1 - 1/(2 tau_f)
+  const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  float fd[Q3];
+#pragma unroll
+  for (int i = 0; i < Q3; ++i) {
+    const float eu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
+    const float feq = w3f(i) * rho * (1.0f + 3.0f * eu + 4.5f * eu * eu - 1.5f * uu);  // Eq. 3
+    const float c0 = 3.0f * (cx(i) - u[0]) + 9.0f * eu * cx(i);
+    const float c1 = 3.0f * (cy(i) - u[1]) + 9.0f * eu * cy(i);
+    const float c2 = 3.0f * (cz(i) - u[2]) + 9.0f * eu * cz(i);
+    const float Phi = w3f(i) * gg * (c0 * F[0] + c1 * F[1] + c2 * F[2]);               // Eq. 5
+    fd[i] = f[i] + om * (feq - f[i]) + Phi;                                            // Eqs. 1, 2
+  }
+  // V_k = sum_{l != k} beta_kl (rho_k rho_l / rho) n_kl, with n_lk = -n_kl
+  float V[N][3];
+#pragma unroll
+  for (int k = 0; k < N; ++k) V[k][0] = V[k][1] = V[k][2] = 0.0f;
+  int q = 0;
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+#pragma unroll
+    for (int l = k + 1; l < N; ++l, ++q) {
+      float b = 1.0f;
+#pragma unroll
+      for (int mm = 0; mm < N; ++mm) {
+        if (mm == k || mm == l) continue;
+        b += fminf(a.beta_A * ph[k] * ph[l] * ph[mm], 1.0f) * a.gjunc[q][mm];
+      }
+      const float amp = a.beta0 * b * ph[k] * ph[l] * rho;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float nc = nrm[(static_cast<size_t>(q) * 3 + c) * NN + p.n];
+        V[k][c] += amp * nc;
+        V[l][c] -= amp * nc;
+      }
+    }
+  // Eq. 6, stored at the node (the next step's pull streams it, Eq. 30)
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+#pragma unroll
+    for (int i = 0; i < Q3; ++i)
+      fout[(static_cast<size_t>(k) * Q3 + i) * NN + p.n] =
+          ph[k] * fd[i] + a.wrec[i] * (cx(i) * V[k][0] + cy(i) * V[k][1] + cz(i) * V[k][2]);
+}
+
+dim3 grid3(const DArgs& a) { return dim3((a.nx + kBX - 1) / kBX, a.ny, a.nz); }
+
+template <int N>
+cudaError_t d_step(const float* fin, float* fout, float* work, const DArgs& a, cudaStream_t s) {
+  const size_t NN = static_cast<size_t>(a.nx) * a.ny * a.nz;
+  float* phi = work;
+  float* rho = phi + N * NN;
+  float* fi = rho + NN;
+  float* T = fi + Q3 * NN;
+  float* nrm = T + 6 * NN;
+  const dim3 g = grid3(a);
+  d_density_kernel<N><<<g, kBX, 0, s>>>(fin, phi, rho, fi, a);
+  d_tension_kernel<N><<<g, kBX, 0, s>>>(phi, rho, T, nrm, a);
+  d_collide_kernel<N><<<g, kBX, 0, s>>>(phi, rho, fi, T, nrm, fout, a);
+  return cudaGetLastError();
+}
+
+cudaError_t d_step_any(int N, const float* fin, float* fout, float* work, const DArgs& a, cudaStream_t s) {
+  switch (N) {
+    case 2: return d_step<2>(fin, fout, work, a, s);
+    case 3: return d_step<3>(fin, fout, work, a, s);
+    case 4: return d_step<4>(fin, fout, work, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// intermediates (N + 1 + 19 + 6 + 3P planes), rounded up to 64 floats so that
+// the FP64 staging behind them is aligned
+size_t work_floats3(int N, size_t NN) {
+  return ((N + 1 + Q3 + 6 + static_cast<size_t>(3) * N * (N - 1) / 2) * NN + 63) / 64 * 64;
+}
+
+// stored (post-collision, at the producing node) <-> post-streaming
+// populations, all 19N planes of one node per thread
+__global__ void __launch_bounds__(kBX) d_set_kernel(const double* __restrict__ fpost, float* __restrict__ f, DArgs a,
+                                                    int planes) {
+  Node p;
+  if (!node_of(a, &p)) return;
+  for (int pl = 0; pl < planes; ++pl) {
+    const int i = pl % Q3;
+    // stored(x) = post-streaming(x + e_i)
+    f[static_cast<size_t>(pl) * p.NN + p.n] =
+        static_cast<float>(fpost[static_cast<size_t>(pl) * p.NN + at(a, p, cx(i), cy(i), cz(i))]);
+  }
+}
+
+__global__ void __launch_bounds__(kBX) d_get_kernel(const float* __restrict__ f, double* __restrict__ fpost, DArgs a,
+                                                    int planes) {
+  Node p;
+  if (!node_of(a, &p)) return;
+  for (int pl = 0; pl < planes; ++pl) {
+    const int i = pl % Q3;
+    fpost[static_cast<size_t>(pl) * p.NN + p.n] =
+        static_cast<double>(f[static_cast<size_t>(pl) * p.NN + at(a, p, -cx(i), -cy(i), -cz(i))]);
+  }
+}
+
+// FP64 per-plane sums: block (b, plane) sums a fixed stride-class of the
+// plane in a fixed-order tree; the host adds the kSumBlocks partials of a
+// plane in order, so the result does not depend on scheduling
+constexpr int kSumBlocks = 64;
+constexpr int kSumThreads = 256;
+__global__ void __launch_bounds__(kSumThreads) d_plane_sum_kernel(const float* __restrict__ f, size_t NN,
+                                                                  double* __restrict__ out) {
+  const int pl = blockIdx.y;
+  double s = 0.0;
+  for (size_t n = static_cast<size_t>(blockIdx.x) * kSumThreads + threadIdx.x; n < NN;
+       n += static_cast<size_t>(kSumBlocks) * kSumThreads)
+    s += static_cast<double>(f[static_cast<size_t>(pl) * NN + n]);
+  __shared__ double sh[kSumThreads];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = kSumThreads / 2; o > 0; o >>= 1) {
+    if (static_cast<int>(threadIdx.x) < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[static_cast<size_t>(pl) * kSumBlocks + blockIdx.x] = sh[0];
+}
+
+double g_of3(double X) {  // Eq. 20
+  if (X < -1.0) return 1.0;
+  if (X < 0.0) return 1.0 - std::sqrt(1.0 - X * X);
+  if (X <= 1.0) return std::sqrt(1.0 - X * X) - 1.0;
+  return -1.0;
+}
+
+}  // namespace
+}  // namespace lbm3
+
+struct lbm3d_ctx {
+  int N = 0, nx = 0, ny = 0, nz = 0;
+  cudaStream_t stream = nullptr;
+  float* buf[2] = {nullptr, nullptr};
+  float* work = nullptr;
+  double* sums = nullptr;
+  int cur = 0;
+  bool state_set = false;
+  lbm3::DArgs args{};
+  std::string msg;
+};
+
+namespace {
+
+lbm3_status dfail(lbm3d_ctx* c, lbm3_status st, const std::string& m) {
+  if (c) c->msg = m;
+  return st;
+}
+
+lbm3_status dcuda(lbm3d_ctx* c, cudaError_t e, const char* where) {
+  return dfail(c, LBM3_ECUDA, std::string("lbm3d: ") + where + ": " + cudaGetErrorString(e));
+}
+
+size_t nodes(const lbm3d_ctx* c) { return static_cast<size_t>(c->nx) * c->ny * c->nz; }
+
+}  // namespace
+
+extern "C" {
+
+lbm3_status lbm3d_create(const lbm3d_params* p, void* cuda_stream, lbm3d_ctx** out) {
+  if (!out) return LBM3_EINVAL;
+  *out = nullptr;
+  if (!p || !p->tau || !p->rho0 || !p->sigma) return LBM3_EINVAL;
+  const int N = p->nfluids;
+  if (N < 2 || N > lbm3::kMaxFluids3 || p->nx < 1 || p->ny < 1 || p->nz < 1 || p->ny > 65535 || p->nz > 65535)
+    return LBM3_EINVAL;
+  if (static_cast<double>(p->nx) * p->ny * p->nz * lbm3::Q3 * N >= 4294967296.0) return LBM3_EINVAL;
+  if (!(p->beta0 > 0.0 && p->beta0 <= 1.0) || p->beta_form < 0 || p->beta_form > 1 || p->recolor_form < 0 ||
+      p->recolor_form > 1 || !(p->normal_delta >= 0.0 && p->normal_delta <= 1.0))
+    return LBM3_EINVAL;
+  for (int k = 0; k < N; ++k) {
+    if (!(p->tau[k] > 0.5) || !(p->rho0[k] > 0.0)) return LBM3_EINVAL;
+    for (int l = 0; l < N; ++l) {
+      const double s = p->sigma[k * N + l], t = p->sigma[l * N + k];
+      if (k == l ? s != 0.0 : !(s > 0.0 && s == t)) return LBM3_EINVAL;
+    }
+  }
+  lbm3d_ctx* c = new (std::nothrow) lbm3d_ctx();
+  if (!c) return LBM3_ENOMEM;
+  c->N = N;
+  c->nx = p->nx;
+  c->ny = p->ny;
+  c->nz = p->nz;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  lbm3::DArgs& a = c->args;
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = p->nz;
+  for (int k = 0; k < N; ++k) a.inv_nu[k] = static_cast<float>(3.0 / (p->tau[k] - 0.5));
+  for (int k = 0; k < N; ++k)
+    for (int l = k + 1; l < N; ++l) {
+      const int q = lbm3::pair3(k, l, N);
+      a.sigma[q] = static_cast<float>(p->sigma[k * N + l]);
+      a.cpair[q] = static_cast<float>(1e6 / (p->rho0[k] * p->rho0[l]));
+      for (int m = 0; m < N; ++m) {
+        double gv = 0.0;
+        if (m != k && m != l) {
+          const double smk = p->sigma[m * N + k], sml = p->sigma[m * N + l], skl = p->sigma[k * N + l];
+          gv = lbm3::g_of3((smk * smk + sml * sml - skl * skl) / (2.0 * smk * sml));  // Eqs. 18, 20
+        }
+        a.gjunc[q][m] = static_cast<float>(gv);
+      }
+    }
+  a.beta0 = static_cast<float>(p->beta0);
+  a.beta_A = p->beta_form == 0 ? 35.0f : 0.0f;
+  for (int i = 0; i < lbm3::Q3; ++i) {
+    const double len =
+        std::sqrt(static_cast<double>(lbm3::cx(i) * lbm3::cx(i) + lbm3::cy(i) * lbm3::cy(i) + lbm3::cz(i) * lbm3::cz(i)));
+    a.wrec[i] = static_cast<float>((p->recolor_form == 0 && i != 0) ? lbm3::w3d(i) / len : lbm3::w3d(i));
+  }
+  a.ndelta = static_cast<float>(p->normal_delta);
+  const size_t NN = nodes(c);
+  const size_t pop = static_cast<size_t>(lbm3::Q3) * N * NN * sizeof(float);
+  void *b0 = nullptr, *b1 = nullptr, *w = nullptr, *sm = nullptr;
+  if (cudaMalloc(&b0, pop) != cudaSuccess || cudaMalloc(&b1, pop) != cudaSuccess ||
+      cudaMalloc(&w, lbm3::work_floats3(N, NN) * sizeof(float) + lbm3::Q3 * N * NN * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&sm, static_cast<size_t>(lbm3::Q3) * N * lbm3::kSumBlocks * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    if (b0) cudaFree(b0);
+    if (b1) cudaFree(b1);
+    if (w) cudaFree(w);
+    delete c;
+    return LBM3_ENOMEM;
+  }
+  c->buf[0] = static_cast<float*>(b0);
+  c->buf[1] = static_cast<float*>(b1);
+  c->work = static_cast<float*>(w);
+  c->sums = static_cast<double*>(sm);
+  *out = c;
+  return LBM3_OK;
+}
+
+lbm3_status lbm3d_set_populations(lbm3d_ctx* c, const double* f, int on_device) {
+  if (!c) return LBM3_EINVAL;
+  if (!f) return dfail(c, LBM3_EINVAL, "lbm3d_set_populations: NULL f");
+  const size_t NN = nodes(c);
+  const int planes = lbm3::Q3 * c->N;
+  const double* src = f;
+  // FP64 staging behind the intermediates in the work allocation
+  double* staging = reinterpret_cast<double*>(c->work + lbm3::work_floats3(c->N, NN));
+  if (!on_device) {
+    cudaError_t e = cudaMemcpyAsync(staging, f, planes * NN * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return dcuda(c, e, "copy to the device");
+    src = staging;
+  }
+  lbm3::d_set_kernel<<<lbm3::grid3(c->args), lbm3::kBX, 0, c->stream>>>(src, c->buf[c->cur], c->args, planes);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return dcuda(c, e, "lbm3d_set_populations");
+  c->state_set = true;
+  return LBM3_OK;
+}
+
+lbm3_status lbm3d_init(lbm3d_ctx* c, const double* rho, int on_device) {
+  if (!c) return LBM3_EINVAL;
+  if (!rho || on_device) return dfail(c, LBM3_EINVAL, "lbm3d_init: host densities rho[N][nz][ny][nx] required");
+  const size_t NN = nodes(c);
+  std::vector<double> f(static_cast<size_t>(lbm3::Q3) * c->N * NN);
+  for (int k = 0; k < c->N; ++k)
+    for (size_t n = 0; n < NN; ++n) {
+      const double v = rho[k * NN + n];
+      if (!(v >= 0.0)) return dfail(c, LBM3_EINVAL, "lbm3d_init: rho_k must be >= 0");
+      for (int i = 0; i < lbm3::Q3; ++i)
+        f[(static_cast<size_t>(k) * lbm3::Q3 + i) * NN + n] = lbm3::w3d(i) * v;  // rest equilibrium per colour
+    }
+  return lbm3d_set_populations(c, f.data(), 0);
+}
+
+lbm3_status lbm3d_step(lbm3d_ctx* c, int64_t n) {
+  if (!c) return LBM3_EINVAL;
+  if (n < 0) return dfail(c, LBM3_EINVAL, "lbm3d_step: n < 0");
+  if (!c->state_set) return dfail(c, LBM3_ESTATE, "lbm3d_step: state not set");
+  for (int64_t s = 0; s < n; ++s) {
+    const cudaError_t e = lbm3::d_step_any(c->N, c->buf[c->cur], c->buf[c->cur ^ 1], c->work, c->args, c->stream);
+    if (e != cudaSuccess) return dcuda(c, e, "lbm3d_step");
+    c->cur ^= 1;
+  }
+  return LBM3_OK;
+}
+
+lbm3_status lbm3d_populations(lbm3d_ctx* c, double* f, int on_device) {
+  if (!c) return LBM3_EINVAL;
+  if (!f) return dfail(c, LBM3_EINVAL, "lbm3d_populations: NULL f");
+  if (!c->state_set) return dfail(c, LBM3_ESTATE, "lbm3d_populations: state not set");
+  const size_t NN = nodes(c);
+  const int planes = lbm3::Q3 * c->N;
+  double* dst = on_device ? f : reinterpret_cast<double*>(c->work + lbm3::work_floats3(c->N, NN));
+  lbm3::d_get_kernel<<<lbm3::grid3(c->args), lbm3::kBX, 0, c->stream>>>(c->buf[c->cur], dst, c->args, planes);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && !on_device)
+    e = cudaMemcpyAsync(f, dst, planes * NN * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return dcuda(c, e, "lbm3d_populations");
+  return LBM3_OK;
+}
+
+lbm3_status lbm3d_mass(lbm3d_ctx* c, double* mass, double* mom) {
+  if (!c) return LBM3_EINVAL;
+  if (!c->state_set) return dfail(c, LBM3_ESTATE, "lbm3d_mass: state not set");
+  const int planes = lbm3::Q3 * c->N;
+  lbm3::d_plane_sum_kernel<<<dim3(lbm3::kSumBlocks, planes), lbm3::kSumThreads, 0, c->stream>>>(
+      c->buf[c->cur], nodes(c), c->sums);
+  std::vector<double> h(static_cast<size_t>(planes) * lbm3::kSumBlocks);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.data(), c->sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return dcuda(c, e, "lbm3d_mass");
+  double mo[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < c->N; ++k) {
+    double m = 0.0;
+    for (int i = 0; i < lbm3::Q3; ++i) {
+      double v = 0.0;
+      for (int b = 0; b < lbm3::kSumBlocks; ++b) v += h[(static_cast<size_t>(k) * lbm3::Q3 + i) * lbm3::kSumBlocks + b];
+      m += v;
+      mo[0] += lbm3::cx(i) * v;
+      mo[1] += lbm3::cy(i) * v;
+      mo[2] += lbm3::cz(i) * v;
+    }
+    if (mass) mass[k] = m;
+  }
+  if (mom)
+    for (int d = 0; d < 3; ++d) mom[d] = mo[d];
+  return LBM3_OK;
+}
+
+lbm3_status lbm3d_destroy(lbm3d_ctx* c) {
+  if (!c) return LBM3_OK;
+  cudaStreamSynchronize(c->stream);
+  cudaFree(c->buf[0]);
+  cudaFree(c->buf[1]);
+  cudaFree(c->work);
+  cudaFree(c->sums);
+  cudaGetLastError();
+  delete c;
+  return LBM3_OK;
+}
+
+const char* lbm3d_last_error(const lbm3d_ctx* c) { return c ? c->msg.c_str() : "lbm3d: NULL context"; }
+
+}  // extern "C"

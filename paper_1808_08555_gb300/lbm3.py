@@ -675,3 +675,102 @@ class NSimulation:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------- D3Q19
+
+class lbm3d_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("nfluids", ctypes.c_int32),
+        ("tau", ctypes.c_void_p), ("rho0", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
+        ("beta0", ctypes.c_double), ("beta_form", ctypes.c_int32), ("recolor_form", ctypes.c_int32),
+        ("normal_delta", ctypes.c_double),
+    ]
+
+
+def _load_d():
+    lib = load()
+    if not hasattr(lib, "_d_bound"):
+        vp, dp, st = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int
+        sig = {
+            "lbm3d_create": (st, [ctypes.POINTER(lbm3d_params), vp, ctypes.POINTER(vp)]),
+            "lbm3d_init": (st, [vp, dp, ctypes.c_int]),
+            "lbm3d_set_populations": (st, [vp, dp, ctypes.c_int]),
+            "lbm3d_step": (st, [vp, ctypes.c_int64]),
+            "lbm3d_populations": (st, [vp, dp, ctypes.c_int]),
+            "lbm3d_mass": (st, [vp, dp, dp]),
+            "lbm3d_destroy": (st, [vp]),
+            "lbm3d_last_error": (ctypes.c_char_p, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype, fn.argtypes = res, args
+        lib._d_bound = True
+    return lib
+
+
+class D3Q19Simulation:
+    """N-fluid simulation on the D3Q19 lattice (include/lbm3.h, lbm3d_*) on
+    the current device and torch's current stream.  sigma: (N, N) symmetric
+    tension matrix with a zero diagonal; tau, rho0: length N.  Densities are
+    (N, nz, ny, nx), populations (N, 19, nz, ny, nx), post-streaming."""
+
+    def __init__(self, nx: int, ny: int, nz: int, sigma, tau, rho0=None, beta0: float = 0.7, beta_form: int = 0,
+                 recolor_form: int = RECOLOR_COSINE, normal_delta: float = 0.1):
+        import torch
+
+        self.sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        n = self.sigma.shape[0]
+        self.tau = np.ascontiguousarray(tau, dtype=np.float64)
+        self.rho0 = np.ascontiguousarray(rho0 if rho0 is not None else np.ones(n), dtype=np.float64)
+        self.nx, self.ny, self.nz, self.n = int(nx), int(ny), int(nz), n
+        p = lbm3d_params()
+        p.nx, p.ny, p.nz, p.nfluids = self.nx, self.ny, self.nz, n
+        p.tau, p.rho0, p.sigma = self.tau.ctypes.data, self.rho0.ctypes.data, self.sigma.ctypes.data
+        p.beta0, p.beta_form, p.recolor_form, p.normal_delta = float(beta0), int(beta_form), int(recolor_form), \
+            float(normal_delta)
+        self.ctx = ctypes.c_void_p()
+        self.stream = torch.cuda.current_stream()
+        s = _load_d().lbm3d_create(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.ctx))
+        if s != OK:
+            raise Lbm3Error(s, "lbm3d_create failed (parameters invalid or CUDA unavailable)")
+
+    def _check(self, s):
+        if s != OK:
+            raise Lbm3Error(s, _load_d().lbm3d_last_error(self.ctx).decode())
+
+    def init(self, rho):
+        q, dev = _ptr(np.ascontiguousarray(rho, dtype=np.float64))
+        self._check(_load_d().lbm3d_init(self.ctx, q, dev))
+        return self
+
+    def set_populations(self, f):
+        q, dev = _ptr(f if not isinstance(f, np.ndarray) else np.ascontiguousarray(f, dtype=np.float64))
+        self._check(_load_d().lbm3d_set_populations(self.ctx, q, dev))
+        return self
+
+    def step(self, n: int = 1):
+        self._check(_load_d().lbm3d_step(self.ctx, int(n)))
+        return self
+
+    def populations(self) -> np.ndarray:
+        f = np.empty((self.n, 19, self.nz, self.ny, self.nx))
+        self._check(_load_d().lbm3d_populations(self.ctx, ctypes.c_void_p(f.ctypes.data), 0))
+        return f
+
+    def mass(self):
+        m = np.zeros(self.n)
+        mo = np.zeros(3)
+        self._check(_load_d().lbm3d_mass(self.ctx, ctypes.c_void_p(m.ctypes.data), ctypes.c_void_p(mo.ctypes.data)))
+        return m, mo
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            _load_d().lbm3d_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

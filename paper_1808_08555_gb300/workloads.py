@@ -173,6 +173,40 @@ def random_populations(nx: int, ny: int, seed: int, amp: float = 0.1) -> np.ndar
     return f * (1.0 + amp * rng.uniform(-1.0, 1.0, size=f.shape))
 
 
+# ------------------------------------------------------ three dimensions
+# Fields of the D3Q19 path: shape (N, nz, ny, nx), x fastest.
+
+def spheres_3d(nx: int, ny: int, nz: int, spheres, n_fluids: int = 3, xi: float = XI) -> np.ndarray:
+    """Spheres ((fluid k >= 1, (cx, cy, cz), R), ...) with tanh edges in a
+    fluid-0 matrix (N, nz, ny, nx); overlapping spheres are not intended."""
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx].astype(np.float64)
+    p = np.zeros((n_fluids, nz, ny, nx))
+    for k, (cx, cy, cz), R in spheres:
+        p[k] = p[k] + _edge(R - np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2), xi)
+    p[0] = np.clip(1.0 - p[1:].sum(axis=0), 0.0, None)
+    return p
+
+
+def compound_sphere(n: int, r_core: float, r_shell: float, xi: float = XI) -> np.ndarray:
+    """Fluid-3 core inside a fluid-2 shell in a fluid-1 matrix on an n^3 grid
+    (the compound droplet of Sec. 3.2 in three dimensions), (3, n, n, n)."""
+    z, y, x = np.mgrid[0:n, 0:n, 0:n].astype(np.float64)
+    r = np.sqrt((x - n / 2.0) ** 2 + (y - n / 2.0) ** 2 + (z - n / 2.0) ** 2)
+    core = _edge(r_core - r, xi)
+    outer = _edge(r_shell - r, xi)
+    return _stack(np.clip(outer - core, 0.0, None), core)
+
+
+def random_populations_3d(nx: int, ny: int, nz: int, seed: int, n_fluids: int = 3, amp: float = 0.1) -> np.ndarray:
+    """Random post-streaming D3Q19 populations (N, 19, nz, ny, nx): rest
+    equilibrium of random colour densities times (1 + amp * U(-1, 1))."""
+    rng = np.random.default_rng(seed)
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    rho = rng.uniform(0.05, 1.0, size=(n_fluids, nz, ny, nx))
+    f = w[None, :, None, None, None] * rho[:, None]
+    return f * (1.0 + amp * rng.uniform(-1.0, 1.0, size=f.shape))
+
+
 # ----------------------------------------------------------------- configs
 
 @dataclass

@@ -24,13 +24,14 @@ def _declared():
         if h.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", h)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names |= set(re.findall(r"\b(lbm3_\w+)\s*\(", txt))
+            names |= set(re.findall(r"\b(lbm3[nd]?_\w+)\s*\(", txt))
     return names
 
 
 def test_header_symbols_exported(lib):
     names = _declared()
     assert "lbm3_step" in names and "lbm3_create" in names
+    assert "lbm3n_step" in names and "lbm3d_step" in names
     for n in sorted(names):
         assert hasattr(lib, n), f"{n} declared in include/ but not exported"
 
@@ -45,6 +46,9 @@ def test_params_struct_layout_matches_header():
     # lbm3n_params: 3 int32, 3 pointers, beta0, 2 int32, normal_delta
     assert ctypes.sizeof(L.lbm3n_params) == 64 and L.lbm3n_params.tau.offset == 16
     assert L.lbm3n_params.normal_delta.offset == 56
+    # lbm3d_params: 4 int32, 3 pointers, beta0, 2 int32, normal_delta
+    assert ctypes.sizeof(L.lbm3d_params) == 64 and L.lbm3d_params.tau.offset == 16
+    assert L.lbm3d_params.beta0.offset == 40 and L.lbm3d_params.normal_delta.offset == 56
 
 
 @pytest.mark.parametrize("kw", [
