@@ -865,6 +865,13 @@ __device__ __forceinline__ void run_tile(Smem& s, const StepArgs& a, const CUten
     s.abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // Launched as a programmatic dependent of the previous step (single grid):
+  // the next step may be scheduled onto SMs this grid frees, and every CTA
+  // waits here, after its set-up, until the previous grid has completed and
+  // its writes are visible, before it touches global memory.  Both are no-ops
+  // for a launch without that attribute.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __syncthreads();
   if (tid >= kConsumers) {
     produce<ST, STALL>(s, a, map, map1, x0, y0, nq, tid - kConsumers);
@@ -1029,12 +1036,36 @@ int step_occupancy(int* blocks_per_sm) {
       blocks_per_sm, fused_step_kernel<MODE_STEP, ST_FP32, 0>, kThreads, step_smem_bytes()));
 }
 
+// A step of the single grid as a programmatic dependent launch: the grid may
+// be scheduled while the previous kernel in the stream finishes, and waits in
+// run_tile (griddepcontrol.wait) for it to complete.
+template <typename... Args>
+cudaError_t launch_dependent(void (*kernel)(Args...), int grid, size_t sm, cudaStream_t st, const StepArgs& a,
+                             const CUtensorMap& m0, const CUtensorMap& m1) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(grid));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, a, m0, m1);
+}
+
 cudaError_t launch_step(const StepArgs& a, const void* tmaps, int grid, int mode, int storage, int force,
                         cudaStream_t st) {
   CUtensorMap m0, m1;
   memcpy(&m0, tmaps, sizeof m0);
   memcpy(&m1, static_cast<const unsigned char*>(tmaps) + 128, sizeof m1);
   const size_t sm = step_smem_bytes();
+  if (a.stall_row < 0 && mode == MODE_STEP && force == 0 && (storage == ST_FP32 || storage == ST_RED)) {
+    const cudaError_t e = storage == ST_FP32 ? launch_dependent(fused_step_kernel<MODE_STEP, ST_FP32, 0>, grid, sm, st, a, m0, m1)
+                                             : launch_dependent(fused_step_kernel<MODE_STEP, ST_RED, 0>, grid, sm, st, a, m0, m1);
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
   if (a.stall_row >= 0 && mode == MODE_STEP && storage == ST_FP32 && force == 0) {
     // testing hook: the instantiation that can withhold a row
     fused_step_kernel<MODE_STEP, ST_FP32, 0, true><<<grid, kThreads, sm, st>>>(a, m0, m1);
