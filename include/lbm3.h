@@ -425,8 +425,9 @@ const char* lbm3n_last_error(const lbm3n_ctx* ctx);
  * the state is FP32, periodic in all three directions.  ny, nz <= 65535.
  * Any invalid parameter gives LBM3_EINVAL from lbm3d_create.  The context
  * allocates its two population buffers (19 N nx ny nz floats each), the
- * intermediates ((N + 26 + 3 N (N - 1) / 2) nx ny nz floats) and an FP64
- * staging area of one population state. */
+ * intermediates ((4 + 25 + 3 N (N - 1) / 2) nx ny nz floats for N <= 3,
+ * 4 more per node for N = 4) and an FP64 staging area of one population
+ * state. */
 typedef struct lbm3d_ctx lbm3d_ctx;
 typedef struct {
   int32_t nx, ny, nz, nfluids;

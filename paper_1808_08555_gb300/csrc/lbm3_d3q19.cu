@@ -22,8 +22,12 @@
 //   7 (1,1,0)  8 (-1,-1,0)  9 (1,-1,0)  10 (-1,1,0)  11 (1,0,1)  12 (-1,0,-1)
 //   13 (1,0,-1)  14 (-1,0,1)  15 (0,1,1)  16 (0,-1,-1)  17 (0,1,-1)  18 (0,-1,1)
 // Layout: populations [N][19][nz][ny][nx] FP32, unpadded, periodic by index
-// arithmetic; intermediates phi [N], rho, f_i [19], T [6] (xx, xy, xz, yy,
-// yz, zz), normals [P][3] with P = N(N-1)/2, each a [nz][ny][nx] plane.
+// arithmetic.  Intermediates, node-major where a stencil gathers them (one
+// vector load per neighbour): the colour fractions and density as one float4
+// per node (phi_1, phi_2, phi_3 or 0, rho) for N <= 3, two for N = 4
+// ((phi_1 .. phi_4), (rho, 0, 0, 0)); the tension tensor as a float4 (xx, xy,
+// xz, yy) and a float2 (yz, zz) per node; then planes f_i [19] and normals
+// [P][3] with P = N(N-1)/2, each [nz][ny][nx].
 
 #include <cmath>
 #include <cstdio>
@@ -96,9 +100,39 @@ __device__ __forceinline__ size_t at(const DArgs& a, const Node& p, int dx, int 
   return (static_cast<size_t>(wrap3(p.z + dz, a.nz)) * a.ny + wrap3(p.y + dy, a.ny)) * a.nx + wrap3(p.x + dx, a.nx);
 }
 
+// float4 per node of the (phi_k, rho) array
 template <int N>
-__global__ void __launch_bounds__(kBX) d_density_kernel(const float* __restrict__ f, float* __restrict__ phi,
-                                                        float* __restrict__ rho_out, float* __restrict__ fi, DArgs a) {
+constexpr int kPRV = N <= 3 ? 1 : 2;
+
+template <int N>
+__device__ __forceinline__ void pr_store(float4* __restrict__ pr, size_t n, const float (&ph)[N], float rho) {
+  if constexpr (N == 2) {
+    pr[n] = make_float4(ph[0], ph[1], 0.0f, rho);
+  } else if constexpr (N == 3) {
+    pr[n] = make_float4(ph[0], ph[1], ph[2], rho);
+  } else {
+    pr[2 * n] = make_float4(ph[0], ph[1], ph[2], ph[3]);
+    pr[2 * n + 1] = make_float4(rho, 0.0f, 0.0f, 0.0f);
+  }
+}
+// the N colour fractions of node n (one vector load for any N <= 4)
+template <int N>
+__device__ __forceinline__ void pr_phi(const float4* __restrict__ pr, size_t n, float (&ph)[N]) {
+  const float4 v = pr[n * kPRV<N>];
+  ph[0] = v.x;
+  ph[1] = v.y;
+  if constexpr (N >= 3) ph[2] = v.z;
+  if constexpr (N >= 4) ph[3] = v.w;
+}
+template <int N>
+__device__ __forceinline__ float pr_rho(const float4* __restrict__ pr, size_t n) {
+  if constexpr (N <= 3) return pr[n].w;
+  return pr[2 * n + 1].x;
+}
+
+template <int N>
+__global__ void __launch_bounds__(kBX) d_density_kernel(const float* __restrict__ f, float4* __restrict__ pr,
+                                                        float* __restrict__ fi, DArgs a) {
   Node p;
   if (!node_of(a, &p)) return;
   const size_t NN = p.NN;
@@ -129,43 +163,46 @@ __global__ void __launch_bounds__(kBX) d_density_kernel(const float* __restrict_
   }
   const float ir = 1.0f / rho;
   float rest = 1.0f;
+  float ph[N];
 #pragma unroll
   for (int k = 0; k < N; ++k)
     if (k != kmax) {
-      const float v = r[k] * ir;
-      phi[static_cast<size_t>(k) * NN + p.n] = v;
-      rest -= v;
+      ph[k] = r[k] * ir;
+      rest -= ph[k];
     }
-  phi[static_cast<size_t>(kmax) * NN + p.n] = rest;  // the fractions sum to 1 exactly
-  rho_out[p.n] = rho;
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    if (k == kmax) ph[k] = rest;  // the fractions sum to 1 exactly
+  pr_store<N>(pr, p.n, ph, rho);
 #pragma unroll
   for (int i = 0; i < Q3; ++i) fi[static_cast<size_t>(i) * NN + p.n] = tot[i];
 }
 
 template <int N>
-__global__ void __launch_bounds__(kBX) d_tension_kernel(const float* __restrict__ phi, const float* __restrict__ rho_in,
-                                                        float* __restrict__ T, float* __restrict__ nrm, DArgs a) {
+__global__ void __launch_bounds__(kBX) d_tension_kernel(const float4* __restrict__ pr, float4* __restrict__ T4,
+                                                        float2* __restrict__ T2, float* __restrict__ nrm, DArgs a) {
   Node p;
   if (!node_of(a, &p)) return;
   const size_t NN = p.NN;
   float ph[N], g[N][3];
+  pr_phi<N>(pr, p.n, ph);
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    ph[k] = phi[static_cast<size_t>(k) * NN + p.n];
-    float sx = 0.0f, sy = 0.0f, sz = 0.0f;  // Eq. fd1: (1/cs2) sum_i w_i phi(x + e_i) e_i
+  for (int k = 0; k < N; ++k) g[k][0] = g[k][1] = g[k][2] = 0.0f;
+  // Eq. fd1: (1/cs2) sum_i w_i phi(x + e_i) e_i, all colours from one vector
+  // load per neighbour
 #pragma unroll
-    for (int i = 1; i < Q3; ++i) {
-      const float v = phi[static_cast<size_t>(k) * NN + at(a, p, cx(i), cy(i), cz(i))];
-      const float w3 = 3.0f * w3f(i);
-      sx += w3 * cx(i) * v;
-      sy += w3 * cy(i) * v;
-      sz += w3 * cz(i) * v;
+  for (int i = 1; i < Q3; ++i) {
+    float v[N];
+    pr_phi<N>(pr, at(a, p, cx(i), cy(i), cz(i)), v);
+    const float w3 = 3.0f * w3f(i);
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      g[k][0] += w3 * cx(i) * v[k];
+      g[k][1] += w3 * cy(i) * v[k];
+      g[k][2] += w3 * cz(i) * v[k];
     }
-    g[k][0] = sx;
-    g[k][1] = sy;
-    g[k][2] = sz;
   }
-  const float rho = rho_in[p.n];
+  const float rho = pr_rho<N>(pr, p.n);
   float txx = 0.0f, txy = 0.0f, txz = 0.0f, tyy = 0.0f, tyz = 0.0f, tzz = 0.0f;
   int q = 0;
 #pragma unroll
@@ -198,17 +235,13 @@ __global__ void __launch_bounds__(kBX) d_tension_kernel(const float* __restrict_
 #pragma unroll
       for (int c = 0; c < 3; ++c) nrm[(static_cast<size_t>(q) * 3 + c) * NN + p.n] = nv[c];
     }
-  T[p.n] = txx;
-  T[NN + p.n] = txy;
-  T[2 * NN + p.n] = txz;
-  T[3 * NN + p.n] = tyy;
-  T[4 * NN + p.n] = tyz;
-  T[5 * NN + p.n] = tzz;
+  T4[p.n] = make_float4(txx, txy, txz, tyy);
+  T2[p.n] = make_float2(tyz, tzz);
 }
 
 template <int N>
-__global__ void __launch_bounds__(kBX) d_collide_kernel(const float* __restrict__ phi, const float* __restrict__ rho_in,
-                                                        const float* __restrict__ fi, const float* __restrict__ T,
+__global__ void __launch_bounds__(kBX) d_collide_kernel(const float4* __restrict__ pr, const float* __restrict__ fi,
+                                                        const float4* __restrict__ T4, const float2* __restrict__ T2,
                                                         const float* __restrict__ nrm, float* __restrict__ fout,
                                                         DArgs a) {
   Node p;
@@ -220,16 +253,16 @@ __global__ void __launch_bounds__(kBX) d_collide_kernel(const float* __restrict_
   for (int i = 1; i < Q3; ++i) {
     const size_t m = at(a, p, cx(i), cy(i), cz(i));
     const float w3 = 3.0f * w3f(i);
-    const float txx = T[m], txy = T[NN + m], txz = T[2 * NN + m], tyy = T[3 * NN + m], tyz = T[4 * NN + m],
-                tzz = T[5 * NN + m];
+    const float4 ta = T4[m];
+    const float2 tb = T2[m];
+    const float txx = ta.x, txy = ta.y, txz = ta.z, tyy = ta.w, tyz = tb.x, tzz = tb.y;
     F[0] += w3 * (cx(i) * txx + cy(i) * txy + cz(i) * txz);
     F[1] += w3 * (cx(i) * txy + cy(i) * tyy + cz(i) * tyz);
     F[2] += w3 * (cx(i) * txz + cy(i) * tyz + cz(i) * tzz);
   }
-  const float rho = rho_in[p.n];
+  const float rho = pr_rho<N>(pr, p.n);
   float ph[N];
-#pragma unroll
-  for (int k = 0; k < N; ++k) ph[k] = phi[static_cast<size_t>(k) * NN + p.n];
+  pr_phi<N>(pr, p.n, ph);
   float f[Q3];
 #pragma unroll
   for (int i = 0; i < Q3; ++i) f[i] = fi[static_cast<size_t>(i) * NN + p.n];
@@ -298,15 +331,16 @@ dim3 grid3(const DArgs& a) { return dim3((a.nx + kBX - 1) / kBX, a.ny, a.nz); }
 template <int N>
 cudaError_t d_step(const float* fin, float* fout, float* work, const DArgs& a, cudaStream_t s) {
   const size_t NN = static_cast<size_t>(a.nx) * a.ny * a.nz;
-  float* phi = work;
-  float* rho = phi + N * NN;
-  float* fi = rho + NN;
-  float* T = fi + Q3 * NN;
-  float* nrm = T + 6 * NN;
+  // vector arrays first (16-byte aligned offsets), then the planes
+  float4* pr = reinterpret_cast<float4*>(work);
+  float4* T4 = pr + kPRV<N> * NN;
+  float2* T2 = reinterpret_cast<float2*>(T4 + NN);
+  float* fi = reinterpret_cast<float*>(T2 + NN);
+  float* nrm = fi + Q3 * NN;
   const dim3 g = grid3(a);
-  d_density_kernel<N><<<g, kBX, 0, s>>>(fin, phi, rho, fi, a);
-  d_tension_kernel<N><<<g, kBX, 0, s>>>(phi, rho, T, nrm, a);
-  d_collide_kernel<N><<<g, kBX, 0, s>>>(phi, rho, fi, T, nrm, fout, a);
+  d_density_kernel<N><<<g, kBX, 0, s>>>(fin, pr, fi, a);
+  d_tension_kernel<N><<<g, kBX, 0, s>>>(pr, T4, T2, nrm, a);
+  d_collide_kernel<N><<<g, kBX, 0, s>>>(pr, fi, T4, T2, nrm, fout, a);
   return cudaGetLastError();
 }
 
@@ -319,10 +353,11 @@ cudaError_t d_step_any(int N, const float* fin, float* fout, float* work, const 
   }
 }
 
-// intermediates (N + 1 + 19 + 6 + 3P planes), rounded up to 64 floats so that
-// the FP64 staging behind them is aligned
+// intermediates (4 or 8 floats of (phi_k, rho), 6 of T, 19 f_i and 3P normal
+// components per node), rounded up to 64 floats so that the FP64 staging
+// behind them is aligned
 size_t work_floats3(int N, size_t NN) {
-  return ((N + 1 + Q3 + 6 + static_cast<size_t>(3) * N * (N - 1) / 2) * NN + 63) / 64 * 64;
+  return (((N <= 3 ? 4 : 8) + 6 + Q3 + static_cast<size_t>(3) * N * (N - 1) / 2) * NN + 63) / 64 * 64;
 }
 
 // stored (post-collision, at the producing node) <-> post-streaming
