@@ -103,3 +103,47 @@ def test_create_without_gpu_fails_cleanly(lib):
     with pytest.raises(L.Lbm3Error) as e:
         L.lbm3_create(L.Params(8, 8))
     assert e.value.status in (L.ECUDA, L.ENOMEM)
+
+
+def _params_nd(cls, dims, n=3, **kw):
+    """An lbm3n_params / lbm3d_params with valid defaults, then kw applied;
+    the arrays it points to are returned too (they must outlive the call)."""
+    import numpy as np
+
+    sig = np.full((n, n), 0.01)
+    np.fill_diagonal(sig, 0.0)
+    if kw.pop("asym", False):
+        sig[0, 1] += 0.001
+    tau = np.full(n, kw.pop("tau0", 1.0))
+    rho0 = np.ones(n)
+    p = cls()
+    for name, v in dims.items():
+        setattr(p, name, v)
+    p.nfluids = kw.pop("nfluids", n)
+    p.tau, p.rho0, p.sigma = tau.ctypes.data, rho0.ctypes.data, sig.ctypes.data
+    p.beta0, p.beta_form, p.recolor_form, p.normal_delta = 0.7, 0, 0, 0.1
+    for name, v in kw.items():
+        setattr(p, name, v)
+    return p, (sig, tau, rho0)
+
+
+@pytest.mark.parametrize("kw", [dict(nfluids=1), dict(nfluids=5), dict(nz=0), dict(ny=70000), dict(nz=70000),
+                                dict(asym=True), dict(tau0=0.5), dict(beta0=0.0), dict(beta_form=2),
+                                dict(recolor_form=-1), dict(normal_delta=2.0)])
+def test_d3q19_create_validates_on_the_host(lib, kw):
+    """lbm3d_create rejects invalid parameters before any CUDA call."""
+    n = 3 if kw.get("nfluids", 3) in (1, 5) else kw.get("nfluids", 3)
+    p, keep = _params_nd(L.lbm3d_params, {"nx": 8, "ny": 8, "nz": 8}, n=n, **kw)
+    ctx = ctypes.c_void_p()
+    assert L._load_d().lbm3d_create(ctypes.byref(p), None, ctypes.byref(ctx)) == L.EINVAL
+    assert not ctx.value
+
+
+@pytest.mark.parametrize("kw", [dict(nfluids=1), dict(nfluids=7), dict(ny=0), dict(asym=True), dict(tau0=0.5),
+                                dict(beta_form=2), dict(normal_delta=-0.1)])
+def test_nfluid_create_validates_on_the_host(lib, kw):
+    """lbm3n_create rejects invalid parameters before any CUDA call."""
+    p, keep = _params_nd(L.lbm3n_params, {"nx": 8, "ny": 8}, n=3, **kw)
+    ctx = ctypes.c_void_p()
+    assert L._load_n().lbm3n_create(ctypes.byref(p), None, ctypes.byref(ctx)) == L.EINVAL
+    assert not ctx.value
