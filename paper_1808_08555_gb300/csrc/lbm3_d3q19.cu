@@ -374,6 +374,19 @@ __global__ void __launch_bounds__(kBX) d_set_kernel(const double* __restrict__ f
   }
 }
 
+// rest equilibrium per colour from the densities, in the stored form:
+// stored(x) = post-streaming(x + e_i) = w_i rho_k(x + e_i)
+__global__ void __launch_bounds__(kBX) d_init_kernel(const double* __restrict__ rho, float* __restrict__ f, DArgs a,
+                                                     int nfluids) {
+  Node p;
+  if (!node_of(a, &p)) return;
+  for (int k = 0; k < nfluids; ++k)
+#pragma unroll
+    for (int i = 0; i < Q3; ++i)
+      f[(static_cast<size_t>(k) * Q3 + i) * p.NN + p.n] =
+          static_cast<float>(w3d(i) * rho[static_cast<size_t>(k) * p.NN + at(a, p, cx(i), cy(i), cz(i))]);
+}
+
 __global__ void __launch_bounds__(kBX) d_get_kernel(const float* __restrict__ f, double* __restrict__ fpost, DArgs a,
                                                     int planes) {
   Node p;
@@ -544,15 +557,20 @@ lbm3_status lbm3d_init(lbm3d_ctx* c, const double* rho, int on_device) {
   if (!c) return LBM3_EINVAL;
   if (!rho || on_device) return dfail(c, LBM3_EINVAL, "lbm3d_init: host densities rho[N][nz][ny][nx] required");
   const size_t NN = nodes(c);
-  std::vector<double> f(static_cast<size_t>(lbm3::Q3) * c->N * NN);
-  for (int k = 0; k < c->N; ++k)
-    for (size_t n = 0; n < NN; ++n) {
-      const double v = rho[k * NN + n];
-      if (!(v >= 0.0)) return dfail(c, LBM3_EINVAL, "lbm3d_init: rho_k must be >= 0");
-      for (int i = 0; i < lbm3::Q3; ++i)
-        f[(static_cast<size_t>(k) * lbm3::Q3 + i) * NN + n] = lbm3::w3d(i) * v;  // rest equilibrium per colour
-    }
-  return lbm3d_set_populations(c, f.data(), 0);
+  for (size_t n = 0; n < static_cast<size_t>(c->N) * NN; ++n)
+    if (!(rho[n] >= 0.0)) return dfail(c, LBM3_EINVAL, "lbm3d_init: rho_k must be >= 0");
+  // the densities go through the FP64 staging area (N of its 19 N planes)
+  double* staging = reinterpret_cast<double*>(c->work + lbm3::work_floats3(c->N, NN));
+  cudaError_t e = cudaMemcpyAsync(staging, rho, static_cast<size_t>(c->N) * NN * sizeof(double),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) {
+    lbm3::d_init_kernel<<<lbm3::grid3(c->args), lbm3::kBX, 0, c->stream>>>(staging, c->buf[c->cur], c->args, c->N);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return dcuda(c, e, "lbm3d_init");
+  c->state_set = true;
+  return LBM3_OK;
 }
 
 lbm3_status lbm3d_step(lbm3d_ctx* c, int64_t n) {

@@ -302,6 +302,22 @@ __global__ void n_set_kernel(const double* __restrict__ fpost, float* __restrict
   (void)planes;
 }
 
+// rest equilibrium per colour from the densities, in the stored form:
+// stored(x) = post-streaming(x + e_i) = w_i rho_k(x + e_i); one block row
+// per colour x direction plane
+__global__ void n_init_kernel(const double* __restrict__ rho, float* __restrict__ f, int nx, int ny) {
+  const size_t NN = static_cast<size_t>(nx) * ny;
+  const int p = blockIdx.y;  // k*9 + i
+  const int k = p / 9, i = p % 9;
+  const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < NN;
+       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
+    const size_t src = static_cast<size_t>(wrapn(y + ey(i), ny)) * nx + wrapn(x + ex(i), nx);
+    f[static_cast<size_t>(p) * NN + n] = static_cast<float>(w * rho[static_cast<size_t>(k) * NN + src]);
+  }
+}
+
 __global__ void n_get_kernel(const float* __restrict__ f, double* __restrict__ fpost, int nx, int ny) {
   const size_t NN = static_cast<size_t>(nx) * ny;
   const int p = blockIdx.y;
@@ -468,17 +484,22 @@ lbm3_status lbm3n_init(lbm3n_ctx* c, const double* rho, int on_device) {
   if (!c) return LBM3_EINVAL;
   if (!rho || on_device) return nfail(c, LBM3_EINVAL, "lbm3n_init: host densities rho[N][ny][nx] required");
   const size_t NN = static_cast<size_t>(c->nx) * c->ny;
-  std::vector<double> f(static_cast<size_t>(9) * c->N * NN);
-  for (int k = 0; k < c->N; ++k)
-    for (size_t n = 0; n < NN; ++n) {
-      const double v = rho[k * NN + n];
-      if (!(v >= 0.0)) return nfail(c, LBM3_EINVAL, "lbm3n_init: rho_k must be >= 0");
-      for (int i = 0; i < 9; ++i) {
-        const double w = i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
-        f[(static_cast<size_t>(k) * 9 + i) * NN + n] = w * v;  // rest equilibrium per colour
-      }
-    }
-  return lbm3n_set_populations(c, f.data(), 0);
+  for (size_t n = 0; n < static_cast<size_t>(c->N) * NN; ++n)
+    if (!(rho[n] >= 0.0)) return nfail(c, LBM3_EINVAL, "lbm3n_init: rho_k must be >= 0");
+  // the densities go through the FP64 staging area (N of its 9 N planes)
+  double* staging = reinterpret_cast<double*>(c->work + lbm3::work_floats(c->N, NN));
+  cudaError_t e = cudaMemcpyAsync(staging, rho, static_cast<size_t>(c->N) * NN * sizeof(double),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) {
+    lbm3::n_init_kernel<<<dim3(lbm3::grid_of(NN), 9 * c->N), lbm3::kNThreads, 0, c->stream>>>(
+        staging, c->buf[c->cur], c->nx, c->ny);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return ncuda(c, e, "lbm3n_init");
+  c->state_set = true;
+  c->t = 0;
+  return LBM3_OK;
 }
 
 lbm3_status lbm3n_step(lbm3n_ctx* c, int64_t n) {
