@@ -85,7 +85,9 @@ def recorded_traffic(form: str = "fp32"):
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    """nvidia-smi samples of SM clock and throttle reasons while running, each
+    stamped with the host time it arrived, so that the samples taken inside
+    the timed region can be told from those just before and after it."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -110,9 +112,18 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def stop(self):
+    def wait_first(self, timeout: float = 2.0):
+        """Return once the first sample has arrived (nvidia-smi is running)."""
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.01)
+
+    def stop(self, region=None):
+        """Median SM clock and the throttle reasons seen; region = (t0, t1)
+        host times of the timed region: its samples are used when there are
+        any, else every sample (a region shorter than the sampling interval)."""
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -122,24 +133,26 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        rows = []
+        for t_recv, ln in self.lines:
             parts = [x.strip() for x in ln.split(",")]
             if len(parts) < 8:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
+                sm_v, mx_v = float(parts[0]), float(parts[1])
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[4:8]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
+            rows.append((t_recv, sm_v, mx_v, {nm for nm, v in zip(names, parts[4:8]) if v.lower().startswith("active")}))
+        if not rows:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        # a sample's line arrives just after it was taken: within the region
+        # when received between its start and its end plus one interval
+        inside = [r for r in rows if region is not None and region[0] <= r[0] <= region[1] + 0.1]
+        use = inside or rows
+        return {"sm_mhz": statistics.median(r[1] for r in use), "sm_max_mhz": max(r[2] for r in rows),
+                "reasons": sorted(set().union(*(r[3] for r in use))), "samples": len(rows),
+                "samples_in_timed_region": len(inside)}
 
 
 def reduce_max(x: float, ws: int, device) -> float:
@@ -214,15 +227,17 @@ def run_ours(args, ws, rank, local):
         clocks = ClockSampler(local)
         barrier()
         clocks.start()
-        time.sleep(0.3)
+        clocks.wait_first()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        t_region = time.time()
         e0.record(stream)
         sim.step(args.steps)
         e1.record(stream)
         e1.synchronize()
+        region = (t_region, time.time())
         ms = e0.elapsed_time(e1)
-        clk = clocks.stop()
+        clk = clocks.stop(region)
         sim.sync()
         barrier()
         ms = max_over_ranks(ms)

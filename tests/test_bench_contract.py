@@ -70,3 +70,25 @@ def test_library_arm_contract():
     assert "True" in f["equal_error"]
     assert d["speedup_vs_plain_fp32"] == pytest.approx(f["reduced"]["MLUPS"] / f["fp32"]["MLUPS"], rel=1e-3)
     assert d["cpu_baseline"]["single_core"]["cores"] == 1
+
+
+def test_clock_sampler_uses_the_samples_inside_the_timed_region():
+    """The clocks key is the median of the samples that arrived during the
+    timed region (all samples when the region is shorter than the sampling
+    interval), and counts them."""
+    import time
+
+    import bench
+
+    c = bench.ClockSampler(0)
+    c.proc = type("P", (), {"terminate": lambda self: None, "wait": lambda self, timeout=None: 0,
+                            "kill": lambda self: None})()
+    now = time.time()
+    c.lines = [(now - 0.2, "1500, 2070, 300.0, 0x0, Not Active, Not Active, Not Active, Not Active"),
+               (now + 0.05, "2070, 2070, 900.0, 0x4, Not Active, Not Active, Not Active, Active"),
+               (now + 0.5, "1600, 2070, 200.0, 0x0, Not Active, Not Active, Not Active, Not Active")]
+    inside = c.stop((now, now + 0.1))
+    assert inside["sm_mhz"] == 2070.0 and inside["samples_in_timed_region"] == 1
+    assert inside["reasons"] == ["sw_power_cap"] and inside["samples"] == 3
+    none_inside = c.stop((now + 1.0, now + 1.01))
+    assert none_inside["samples_in_timed_region"] == 0 and none_inside["sm_mhz"] == 1600.0
