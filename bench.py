@@ -729,6 +729,32 @@ def run_reference(args, ws, rank):
     }
 
 
+def other_workloads(args):
+    """The other configurations, shortened so that together they add about a
+    minute: the batched sweep, the storage forms on the 4096^2 Janus droplet,
+    gradient evaluations, four fluids on D2Q9 and three on D3Q19.  Each entry
+    is that workload's own line without its bulky fields, or its error."""
+    import copy
+
+    import torch
+
+    plan = [("sweep", run_sweep, 500, 20), ("janus", run_janus, 300, 10), ("adjoint", run_adjoint, 3, 1),
+            ("nphase", run_nphase, 200, 10), ("d3q19", run_d3q19, 50, 3)]
+    out = {}
+    for name, fn, steps, warmup in plan:
+        a = copy.copy(args)
+        a.steps, a.warmup, a.size, a.workload = steps, warmup, None, name
+        try:
+            d = fn(a)
+            keep = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "config", "roofline", "forms",
+                    "storages", "sequential_single_instance", "equal_error", "checks", "gpu_launches")
+            out[name] = {k: d[k] for k in keep if k in d}
+        except Exception as e:  # reported, never fatal to the headline
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -739,6 +765,9 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=120.0,
                     help="--impl reference: time budget of the timed steps (sets the sampled window)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="default run: skip the shortened runs of the other configurations (sweep, Janus storage "
+                         "forms, gradient, N fluids, D3Q19) that are added to the line under other_workloads")
     ap.add_argument("--workload", default="compound", choices=["compound", "sweep", "janus", "adjoint", "nphase", "d3q19"],
                     help="compound: the 2048^2 compound droplet (default); sweep: the 64-instance batch; "
                          "janus: the 4096^2 Janus droplet with FP32 / FP16 / BF16 storage; "
@@ -784,6 +813,10 @@ def main():
             line = run_d3q19(args) if rank == 0 else None
         else:
             line = run_ours(args, ws, rank, local)
+            # one GPU, the default workload: the other configurations as well,
+            # after the timed headline
+            if line is not None and ws == 1 and args.size is None and not args.no_other_workloads:
+                line["other_workloads"] = other_workloads(args)
         if line is not None:
             print(json.dumps(line), flush=True)
     finally:
