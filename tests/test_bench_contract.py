@@ -92,3 +92,19 @@ def test_clock_sampler_uses_the_samples_inside_the_timed_region():
     assert inside["reasons"] == ["sw_power_cap"] and inside["samples"] == 3
     none_inside = c.stop((now + 1.0, now + 1.01))
     assert none_inside["samples_in_timed_region"] == 0 and none_inside["sm_mhz"] == 1600.0
+
+
+@pytest.mark.gpu
+def test_default_line_carries_the_other_workloads():
+    """The default one-GPU run (the round-end form, with a short timed region)
+    adds the other configurations under other_workloads, each with its own
+    metric, value and roofline, and none failing."""
+    d = _run(["--steps", "20", "--warmup", "3", "--no-cpu-baseline"])
+    _common(d)
+    o = d["other_workloads"]
+    assert set(o) == {"sweep", "janus", "adjoint", "nphase", "d3q19"}
+    for name, v in o.items():
+        assert "error" not in v, (name, v)
+        assert v["value"] > 0 and v["unit"] == "MLUPS" and "roofline" in v and "metric" in v, name
+    assert set(o["janus"]["storages"]) >= {"fp32", "fp16_dev", "bf16_dev", "reduced"}
+    assert set(o["sweep"]["forms"]) >= {"reduced", "fp32"}
