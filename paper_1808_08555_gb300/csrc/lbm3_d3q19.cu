@@ -142,12 +142,15 @@ __global__ void __launch_bounds__(kBX) d_density_kernel(const float* __restrict_
   for (int i = 0; i < Q3; ++i) tot[i] = 0.0f;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
+    // a colour's 19 pulled values (Eq. 30) loaded together, then summed
+    float v[Q3];
+#pragma unroll
+    for (int i = 0; i < Q3; ++i) v[i] = f[(static_cast<size_t>(k) * Q3 + i) * NN + at(a, p, -cx(i), -cy(i), -cz(i))];
     float s = 0.0f;
 #pragma unroll
     for (int i = 0; i < Q3; ++i) {
-      const float v = f[(static_cast<size_t>(k) * Q3 + i) * NN + at(a, p, -cx(i), -cy(i), -cz(i))];  // Eq. 30, pull
-      s += v;
-      tot[i] += v;
+      s += v[i];
+      tot[i] += v[i];
     }
     r[k] = s;
   }
