@@ -61,9 +61,12 @@ __global__ void __launch_bounds__(kNThreads) n_density_kernel(const float* __res
                                                               NArgs a) {
   const int nx = a.nx, ny = a.ny;
   const size_t NN = static_cast<size_t>(nx) * ny;
-  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < NN;
-       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
+  {
+    // one row per block row of the grid: no division for the node's coordinates
+    const int y = static_cast<int>(blockIdx.x);
+    const int x = static_cast<int>(blockIdx.y) * kNThreads + static_cast<int>(threadIdx.x);
+    if (x >= nx) return;
+    const size_t n = static_cast<size_t>(y) * nx + x;
     float r[N];
     float tot[9];
 #pragma unroll
@@ -112,9 +115,12 @@ __global__ void __launch_bounds__(kNThreads) n_tension_kernel(const float* __res
                                                               float* __restrict__ nrm, NArgs a) {
   const int nx = a.nx, ny = a.ny;
   const size_t NN = static_cast<size_t>(nx) * ny;
-  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < NN;
-       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
+  {
+    // one row per block row of the grid: no division for the node's coordinates
+    const int y = static_cast<int>(blockIdx.x);
+    const int x = static_cast<int>(blockIdx.y) * kNThreads + static_cast<int>(threadIdx.x);
+    if (x >= nx) return;
+    const size_t n = static_cast<size_t>(y) * nx + x;
     float ph[N], gx[N], gy[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -172,9 +178,12 @@ __global__ void __launch_bounds__(kNThreads) n_collide_kernel(const float* __res
                                                               NArgs a) {
   const int nx = a.nx, ny = a.ny;
   const size_t NN = static_cast<size_t>(nx) * ny;
-  for (size_t n = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; n < NN;
-       n += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int x = static_cast<int>(n % nx), y = static_cast<int>(n / nx);
+  {
+    // one row per block row of the grid: no division for the node's coordinates
+    const int y = static_cast<int>(blockIdx.x);
+    const int x = static_cast<int>(blockIdx.y) * kNThreads + static_cast<int>(threadIdx.x);
+    if (x >= nx) return;
+    const size_t n = static_cast<size_t>(y) * nx + x;
     // F_s = div T (Eq. 11), each component by Eq. fd1
     float Fx = 0.0f, Fy = 0.0f;
 #pragma unroll
@@ -263,7 +272,7 @@ cudaError_t n_step(const float* fin, float* fout, float* work, const NArgs& a, c
   float* fi = rho + NN;
   float* T = fi + 9 * NN;
   float* nrm = T + 3 * NN;
-  const int g = grid_of(NN);
+  const dim3 g(static_cast<unsigned>(a.ny), static_cast<unsigned>((a.nx + kNThreads - 1) / kNThreads));
   n_density_kernel<N><<<g, kNThreads, 0, s>>>(fin, phi, rho, fi, a);
   n_tension_kernel<N><<<g, kNThreads, 0, s>>>(phi, rho, T, nrm, a);
   n_collide_kernel<N><<<g, kNThreads, 0, s>>>(phi, rho, fi, T, nrm, fout, a);
