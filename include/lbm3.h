@@ -447,6 +447,12 @@ lbm3_status lbm3d_step(lbm3d_ctx* ctx, int64_t n);  /* asynchronous */
 lbm3_status lbm3d_populations(lbm3d_ctx* ctx, double* f, int on_device);  /* synchronises */
 /* FP64 per-fluid mass[nfluids] and lattice momentum mom[3] (synchronises) */
 lbm3_status lbm3d_mass(lbm3d_ctx* ctx, double* mass, double* mom);
+/* Observables of the current state (Eq. uk1, as lbm3_fields): rho_k
+ * [N][nz][ny][nx], u [3][nz][ny][nx] = (sum_i f_i e_i + F/2) / rho with the
+ * interfacial force F of Eq. 11, p [nz][ny][nx] = rho / 3, FP64; host pointers
+ * or, with on_device, device pointers; any of the three may be NULL.
+ * Synchronises. */
+lbm3_status lbm3d_fields(lbm3d_ctx* ctx, double* rho, double* u, double* p, int on_device);
 lbm3_status lbm3d_destroy(lbm3d_ctx* ctx);
 const char* lbm3d_last_error(const lbm3d_ctx* ctx);
 

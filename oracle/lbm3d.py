@@ -142,10 +142,10 @@ def guo(tau, u, F):
     return np.stack(out)
 
 
-def step(p: Params3D, f: np.ndarray) -> np.ndarray:
-    """One time step of N colour populations f (N, 19, nz, ny, nx)."""
+def colour_gradients_and_force(p: Params3D, rho: np.ndarray):
+    """G_kl for the ordered pairs and the interfacial force F = div T of
+    Eq. 11, from the colour densities rho (N, nz, ny, nx)."""
     N = p.n
-    rho = f.sum(axis=1)
     r = rho.sum(axis=0)
     phi = rho / r
     gp = [grad(phi[k]) for k in range(N)]
@@ -172,6 +172,16 @@ def step(p: Params3D, f: np.ndarray) -> np.ndarray:
         for b in range(3):
             Fa = Fa + grad(T[a][b])[b]
         F.append(Fa)
+    return G, F
+
+
+def step(p: Params3D, f: np.ndarray) -> np.ndarray:
+    """One time step of N colour populations f (N, 19, nz, ny, nx)."""
+    N = p.n
+    rho = f.sum(axis=1)
+    r = rho.sum(axis=0)
+    phi = rho / r
+    G, F = colour_gradients_and_force(p, rho)
     fi = f.sum(axis=0)
     m = [(fi * E[:, a, None, None, None]).sum(axis=0) for a in range(3)]
     u = [(m[a] + 0.5 * F[a]) / r for a in range(3)]
@@ -214,3 +224,14 @@ def init(rho: np.ndarray) -> np.ndarray:
 def pressure(f: np.ndarray) -> np.ndarray:
     """Lattice pressure c_s^2 rho per node."""
     return CS2 * f.sum(axis=(0, 1))
+
+
+def fields(p: Params3D, f: np.ndarray) -> dict:
+    """rho_k (N, nz, ny, nx), u (3, nz, ny, nx) with the F/2 correction of
+    Eq. uk1, and p = c_s^2 rho, of the post-streaming populations f."""
+    rho = f.sum(axis=1)
+    r = rho.sum(axis=0)
+    _, F = colour_gradients_and_force(p, rho)
+    fi = f.sum(axis=0)
+    u = np.stack([((fi * E[:, a, None, None, None]).sum(axis=0) + 0.5 * F[a]) / r for a in range(3)])
+    return {"rho": rho, "u": u, "p": CS2 * r}

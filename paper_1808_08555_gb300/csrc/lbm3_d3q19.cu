@@ -242,16 +242,10 @@ __global__ void __launch_bounds__(kBX) d_tension_kernel(const float4* __restrict
   T2[p.n] = make_float2(tyz, tzz);
 }
 
-template <int N>
-__global__ void __launch_bounds__(kBX) d_collide_kernel(const float4* __restrict__ pr, const float* __restrict__ fi,
-                                                        const float4* __restrict__ T4, const float2* __restrict__ T2,
-                                                        const float* __restrict__ nrm, float* __restrict__ fout,
-                                                        DArgs a) {
-  Node p;
-  if (!node_of(a, &p)) return;
-  const size_t NN = p.NN;
-  // F_s = div T (Eq. 11): F_a = (1/cs2) sum_i w_i sum_b e_ib T_ab(x + e_i)
-  float F[3] = {0.0f, 0.0f, 0.0f};
+// F_s = div T (Eq. 11): F_a = (1/cs2) sum_i w_i sum_b e_ib T_ab(x + e_i)
+__device__ __forceinline__ void divergence(const float4* __restrict__ T4, const float2* __restrict__ T2,
+                                           const DArgs& a, const Node& p, float (&F)[3]) {
+  F[0] = F[1] = F[2] = 0.0f;
 #pragma unroll
   for (int i = 1; i < Q3; ++i) {
     const size_t m = at(a, p, cx(i), cy(i), cz(i));
@@ -263,19 +257,37 @@ __global__ void __launch_bounds__(kBX) d_collide_kernel(const float4* __restrict
     F[1] += w3 * (cx(i) * txy + cy(i) * tyy + cz(i) * tyz);
     F[2] += w3 * (cx(i) * txz + cy(i) * tyz + cz(i) * tzz);
   }
-  const float rho = pr_rho<N>(pr, p.n);
-  float ph[N];
-  pr_phi<N>(pr, p.n, ph);
-  float f[Q3];
+}
+
+// momentum sum_i f_i e_i of the total distribution
+__device__ __forceinline__ void momentum(const float* __restrict__ fi, size_t n, size_t NN, float (&f)[Q3],
+                                         float (&m)[3]) {
 #pragma unroll
-  for (int i = 0; i < Q3; ++i) f[i] = fi[static_cast<size_t>(i) * NN + p.n];
-  float m[3] = {0.0f, 0.0f, 0.0f};
+  for (int i = 0; i < Q3; ++i) f[i] = fi[static_cast<size_t>(i) * NN + n];
+  m[0] = m[1] = m[2] = 0.0f;
 #pragma unroll
   for (int i = 1; i < Q3; ++i) {
     m[0] += cx(i) * f[i];
     m[1] += cy(i) * f[i];
     m[2] += cz(i) * f[i];
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kBX) d_collide_kernel(const float4* __restrict__ pr, const float* __restrict__ fi,
+                                                        const float4* __restrict__ T4, const float2* __restrict__ T2,
+                                                        const float* __restrict__ nrm, float* __restrict__ fout,
+                                                        DArgs a) {
+  Node p;
+  if (!node_of(a, &p)) return;
+  const size_t NN = p.NN;
+  float F[3];
+  divergence(T4, T2, a, p, F);
+  const float rho = pr_rho<N>(pr, p.n);
+  float ph[N];
+  pr_phi<N>(pr, p.n, ph);
+  float f[Q3], m[3];
+  momentum(fi, p.n, NN, f, m);
   const float irho = 1.0f / rho;
   float u[3];
 #pragma unroll
@@ -329,21 +341,85 @@ __global__ void __launch_bounds__(kBX) d_collide_kernel(const float4* __restrict
           ph[k] * fd[i] + a.wrec[i] * (cx(i) * V[k][0] + cy(i) * V[k][1] + cz(i) * V[k][2]);
 }
 
+// Observables of the state the density and tension kernels have just
+// processed: rho_k = phi_k rho, u = (sum_i f_i e_i + F/2) / rho (Eq. uk1),
+// p = rho / 3, in FP64 (any output may be null)
+template <int N>
+__global__ void __launch_bounds__(kBX) d_fields_kernel(const float4* __restrict__ pr, const float* __restrict__ fi,
+                                                       const float4* __restrict__ T4, const float2* __restrict__ T2,
+                                                       double* __restrict__ rho_out, double* __restrict__ u_out,
+                                                       double* __restrict__ p_out, DArgs a) {
+  Node p;
+  if (!node_of(a, &p)) return;
+  const size_t NN = p.NN;
+  const float rho = pr_rho<N>(pr, p.n);
+  if (rho_out) {
+    float ph[N];
+    pr_phi<N>(pr, p.n, ph);
+#pragma unroll
+    for (int k = 0; k < N; ++k) rho_out[static_cast<size_t>(k) * NN + p.n] = static_cast<double>(ph[k] * rho);
+  }
+  if (u_out) {
+    float F[3], f[Q3], m[3];
+    divergence(T4, T2, a, p, F);
+    momentum(fi, p.n, NN, f, m);
+    const float irho = 1.0f / rho;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u_out[static_cast<size_t>(c) * NN + p.n] = static_cast<double>((m[c] + 0.5f * F[c]) * irho);
+  }
+  if (p_out) p_out[p.n] = static_cast<double>(rho) / 3.0;
+}
+
 dim3 grid3(const DArgs& a) { return dim3((a.nx + kBX - 1) / kBX, a.ny, a.nz); }
+
+// the intermediates' places in the work area
+template <int N>
+struct Work {
+  float4* pr;
+  float4* T4;
+  float2* T2;
+  float* fi;
+  float* nrm;
+  Work(float* work, size_t NN) {
+    // vector arrays first (16-byte aligned offsets), then the planes
+    pr = reinterpret_cast<float4*>(work);
+    T4 = pr + kPRV<N> * NN;
+    T2 = reinterpret_cast<float2*>(T4 + NN);
+    fi = reinterpret_cast<float*>(T2 + NN);
+    nrm = fi + Q3 * NN;
+  }
+};
+
+template <int N>
+cudaError_t d_fields(const float* fin, float* work, double* rho, double* u, double* pr_out, const DArgs& a,
+                     cudaStream_t s) {
+  const size_t NN = static_cast<size_t>(a.nx) * a.ny * a.nz;
+  const Work<N> w(work, NN);
+  const dim3 g = grid3(a);
+  d_density_kernel<N><<<g, kBX, 0, s>>>(fin, w.pr, w.fi, a);
+  d_tension_kernel<N><<<g, kBX, 0, s>>>(w.pr, w.T4, w.T2, w.nrm, a);
+  d_fields_kernel<N><<<g, kBX, 0, s>>>(w.pr, w.fi, w.T4, w.T2, rho, u, pr_out, a);
+  return cudaGetLastError();
+}
+
+cudaError_t d_fields_any(int N, const float* fin, float* work, double* rho, double* u, double* p, const DArgs& a,
+                         cudaStream_t s) {
+  switch (N) {
+    case 2: return d_fields<2>(fin, work, rho, u, p, a, s);
+    case 3: return d_fields<3>(fin, work, rho, u, p, a, s);
+    case 4: return d_fields<4>(fin, work, rho, u, p, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 template <int N>
 cudaError_t d_step(const float* fin, float* fout, float* work, const DArgs& a, cudaStream_t s) {
   const size_t NN = static_cast<size_t>(a.nx) * a.ny * a.nz;
-  // vector arrays first (16-byte aligned offsets), then the planes
-  float4* pr = reinterpret_cast<float4*>(work);
-  float4* T4 = pr + kPRV<N> * NN;
-  float2* T2 = reinterpret_cast<float2*>(T4 + NN);
-  float* fi = reinterpret_cast<float*>(T2 + NN);
-  float* nrm = fi + Q3 * NN;
+  const Work<N> w(work, NN);
   const dim3 g = grid3(a);
-  d_density_kernel<N><<<g, kBX, 0, s>>>(fin, pr, fi, a);
-  d_tension_kernel<N><<<g, kBX, 0, s>>>(pr, T4, T2, nrm, a);
-  d_collide_kernel<N><<<g, kBX, 0, s>>>(pr, fi, T4, T2, nrm, fout, a);
+  d_density_kernel<N><<<g, kBX, 0, s>>>(fin, w.pr, w.fi, a);
+  d_tension_kernel<N><<<g, kBX, 0, s>>>(w.pr, w.T4, w.T2, w.nrm, a);
+  d_collide_kernel<N><<<g, kBX, 0, s>>>(w.pr, w.fi, w.T4, w.T2, w.nrm, fout, a);
   return cudaGetLastError();
 }
 
@@ -601,6 +677,29 @@ lbm3_status lbm3d_populations(lbm3d_ctx* c, double* f, int on_device) {
     e = cudaMemcpyAsync(f, dst, planes * NN * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return dcuda(c, e, "lbm3d_populations");
+  return LBM3_OK;
+}
+
+lbm3_status lbm3d_fields(lbm3d_ctx* c, double* rho, double* u, double* p, int on_device) {
+  if (!c) return LBM3_EINVAL;
+  if (!c->state_set) return dfail(c, LBM3_ESTATE, "lbm3d_fields: state not set");
+  const size_t NN = nodes(c);
+  // the FP64 staging area holds the host case's outputs: N + 3 + 1 of its 19 N planes
+  double* staging = reinterpret_cast<double*>(c->work + lbm3::work_floats3(c->N, NN));
+  double* d_rho = rho ? (on_device ? rho : staging) : nullptr;
+  double* d_u = u ? (on_device ? u : staging + static_cast<size_t>(c->N) * NN) : nullptr;
+  double* d_p = p ? (on_device ? p : staging + static_cast<size_t>(c->N + 3) * NN) : nullptr;
+  cudaError_t e = lbm3::d_fields_any(c->N, c->buf[c->cur], c->work, d_rho, d_u, d_p, c->args, c->stream);
+  if (e == cudaSuccess && !on_device) {
+    if (rho)
+      e = cudaMemcpyAsync(rho, d_rho, static_cast<size_t>(c->N) * NN * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream);
+    if (e == cudaSuccess && u)
+      e = cudaMemcpyAsync(u, d_u, 3 * NN * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && p) e = cudaMemcpyAsync(p, d_p, NN * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return dcuda(c, e, "lbm3d_fields");
   return LBM3_OK;
 }
 

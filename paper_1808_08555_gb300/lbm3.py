@@ -699,6 +699,7 @@ def _load_d():
             "lbm3d_step": (st, [vp, ctypes.c_int64]),
             "lbm3d_populations": (st, [vp, dp, ctypes.c_int]),
             "lbm3d_mass": (st, [vp, dp, dp]),
+            "lbm3d_fields": (st, [vp, dp, dp, dp, ctypes.c_int]),
             "lbm3d_destroy": (st, [vp]),
             "lbm3d_last_error": (ctypes.c_char_p, [vp]),
         }
@@ -763,6 +764,15 @@ class D3Q19Simulation:
         mo = np.zeros(3)
         self._check(_load_d().lbm3d_mass(self.ctx, ctypes.c_void_p(m.ctypes.data), ctypes.c_void_p(mo.ctypes.data)))
         return m, mo
+
+    def fields(self) -> dict:
+        """rho (N, nz, ny, nx), u (3, nz, ny, nx) and p (nz, ny, nx), FP64."""
+        rho = np.empty((self.n, self.nz, self.ny, self.nx))
+        u = np.empty((3, self.nz, self.ny, self.nx))
+        p = np.empty((self.nz, self.ny, self.nx))
+        self._check(_load_d().lbm3d_fields(self.ctx, ctypes.c_void_p(rho.ctypes.data), ctypes.c_void_p(u.ctypes.data),
+                                           ctypes.c_void_p(p.ctypes.data), 0))
+        return {"rho": rho, "u": u, "p": p}
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -230,3 +230,24 @@ def test_invalid_params(L, kw):
                           beta_form=kw.get("beta_form", 0), recolor_form=kw.get("recolor_form", 0),
                           normal_delta=kw.get("normal_delta", 0.1))
     assert e.value.status == L.EINVAL
+
+
+def test_fields_against_oracle(L):
+    """lbm3d_fields after 10 steps of the two-sphere case: colour densities to
+    1e-5 relative, the velocity of Eq. uk1 (with F/2) to 5e-7 absolute (the
+    spurious currents are ~1e-5; FP32 momentum sums resolve ~1e-7), the
+    pressure to 1e-6 relative."""
+    nx, ny, nz = 48, 32, 32
+    p = D.Params3D(nx, ny, nz, sigma=sig({(0, 1): 0.01, (0, 2): 0.013, (1, 2): 0.007}, 3), tau=(0.6, 0.9, 1.3),
+                   rho0=(1.0, 1.0, 1.0))
+    f0 = f32(D.init(_three_fluid_spheres(nx, ny, nz)))
+    sim = sim_of(L, p)
+    sim.set_populations(f0)
+    sim.step(10)
+    got = sim.fields()
+    sim.close()
+    ref = D.fields(p, D.run(p, f0.copy(), 10))
+    assert np.abs(got["rho"] - ref["rho"]).max() <= 1e-5 * np.abs(ref["rho"]).max()
+    assert np.abs(got["u"] - ref["u"]).max() <= 5e-7
+    assert np.abs(ref["u"]).max() > 1e-6   # the comparison is not of zeros
+    assert np.abs(got["p"] / ref["p"] - 1).max() <= 1e-6

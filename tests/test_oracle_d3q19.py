@@ -237,3 +237,29 @@ def test_absent_fourth_fluid_changes_nothing():
     a = D.run(_p3(nx, ny, nz), f3.copy(), 4)
     b = D.run(p4, f4, 4)
     assert np.array_equal(a, b[:3]) and not b[3].any()
+
+
+@pytest.mark.parametrize("plane", sorted(PLANES))
+def test_fields_of_a_uniform_state_project_onto_c_oracle(plane):
+    """The fields (rho_k, u with the F/2 correction of Eq. uk1, p) of a state
+    uniform along one axis are the C oracle's fields of its projection, with
+    no velocity along the uniform axis."""
+    na, nb = 14, 10
+    f2 = O.step(O.Params(na, nb, tau=TAU3, sigma=SIG3), W.random_populations(na, nb, seed=9), 2)
+    ref = O.fields(O.Params(na, nb, tau=TAU3, sigma=SIG3), f2)
+    f3 = _lift(f2, plane, 2)
+    nz, ny, nx = f3.shape[2:]
+    got = D.fields(_p3(nx, ny, nz), f3)
+    a, b, c = PLANES[plane]
+
+    def plane_of(v):   # a (z, y, x) field uniform along c, as the D2Q9 (n_b, n_a) field
+        g = np.take(v, 0, axis=-3 + (2 - c))
+        rem = [ax for ax in (2, 1, 0) if ax != c]
+        return g if rem == [b, a] else g.T
+
+    for k in range(3):
+        assert np.allclose(plane_of(got["rho"][k]), ref["rho"][k], rtol=1e-13, atol=0)
+    assert np.allclose(plane_of(got["u"][a]), ref["ux"], rtol=0, atol=1e-15)
+    assert np.allclose(plane_of(got["u"][b]), ref["uy"], rtol=0, atol=1e-15)
+    assert np.abs(got["u"][c]).max() <= 1e-15
+    assert np.allclose(plane_of(got["p"]), ref["p"], rtol=1e-13, atol=0)
