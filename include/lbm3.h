@@ -400,6 +400,11 @@ lbm3_status lbm3n_step(lbm3n_ctx* ctx, int64_t n);  /* asynchronous */
 lbm3_status lbm3n_populations(lbm3n_ctx* ctx, double* f, int on_device);  /* synchronises */
 /* FP64 per-fluid mass[nfluids] and lattice momentum mom[2] (synchronises) */
 lbm3_status lbm3n_mass(lbm3n_ctx* ctx, double* mass, double* mom);
+/* Observables of the current state, as lbm3_fields: rho_k [N][ny][nx], ux,
+ * uy [ny][nx] = (sum_i f_i e_i + F/2) / rho with the force of Eq. 11,
+ * p = rho / 3; FP64 host pointers or, with on_device, device pointers; any
+ * may be NULL.  Synchronises. */
+lbm3_status lbm3n_fields(lbm3n_ctx* ctx, double* rho, double* ux, double* uy, double* p, int on_device);
 lbm3_status lbm3n_destroy(lbm3n_ctx* ctx);
 const char* lbm3n_last_error(const lbm3n_ctx* ctx);
 

@@ -135,10 +135,10 @@ def guo(tau, ux, uy, Fx, Fy):
     return np.stack(out)
 
 
-def step(p: NParams, f: np.ndarray) -> np.ndarray:
-    """One time step of N colour populations f (N, 9, ny, nx)."""
+def gradients_and_force(p: NParams, rho: np.ndarray):
+    """G_kl for the ordered pairs and the interfacial force (F_x, F_y) = div T
+    of Eq. 11, from the colour densities rho (N, ny, nx)."""
     N = p.n
-    rho = f.sum(axis=1)
     r = rho.sum(axis=0)
     phi = rho / r
     gp = [grad(phi[k]) for k in range(N)]
@@ -164,7 +164,16 @@ def step(p: NParams, f: np.ndarray) -> np.ndarray:
     dxx, _ = grad(Txx)
     dxy, dyx = grad(Txy)
     _, dyy = grad(Tyy)
-    Fx, Fy = dxx + dyx, dxy + dyy
+    return G, dxx + dyx, dxy + dyy
+
+
+def step(p: NParams, f: np.ndarray) -> np.ndarray:
+    """One time step of N colour populations f (N, 9, ny, nx)."""
+    N = p.n
+    rho = f.sum(axis=1)
+    r = rho.sum(axis=0)
+    phi = rho / r
+    G, Fx, Fy = gradients_and_force(p, rho)
     fi = f.sum(axis=0)
     mx = (fi * EX[:, None, None]).sum(axis=0)
     my = (fi * EY[:, None, None]).sum(axis=0)
@@ -198,6 +207,18 @@ def run(p: NParams, f: np.ndarray, nsteps: int) -> np.ndarray:
     for _ in range(nsteps):
         f = step(p, f)
     return f
+
+
+def fields(p: NParams, f: np.ndarray) -> dict:
+    """rho_k (N, ny, nx), u = (sum_i f_i e_i + F/2) / rho (Eq. uk1) and
+    p = rho/3 of the post-streaming populations f."""
+    rho = f.sum(axis=1)
+    r = rho.sum(axis=0)
+    _, Fx, Fy = gradients_and_force(p, rho)
+    fi = f.sum(axis=0)
+    mx = (fi * EX[:, None, None]).sum(axis=0)
+    my = (fi * EY[:, None, None]).sum(axis=0)
+    return {"rho": rho, "ux": (mx + 0.5 * Fx) / r, "uy": (my + 0.5 * Fy) / r, "p": r * CS2}
 
 
 def init(rho: np.ndarray) -> np.ndarray:

@@ -259,6 +259,52 @@ __global__ void __launch_bounds__(kNThreads) n_collide_kernel(const float* __res
   }
 }
 
+// Observables of the state the density and tension kernels have just
+// processed: rho_k = phi_k rho, u = (sum_i f_i e_i + F/2) / rho (Eq. uk1, F
+// by Eq. fd1 from the tension tensor), p = rho / 3, FP64 (any may be null)
+template <int N>
+__global__ void __launch_bounds__(kNThreads) n_fields_kernel(const float* __restrict__ phi,
+                                                             const float* __restrict__ rho_in,
+                                                             const float* __restrict__ fi,
+                                                             const float* __restrict__ T, double* __restrict__ rho_out,
+                                                             double* __restrict__ ux_out, double* __restrict__ uy_out,
+                                                             double* __restrict__ p_out, NArgs a) {
+  const int nx = a.nx, ny = a.ny;
+  const size_t NN = static_cast<size_t>(nx) * ny;
+  const int y = static_cast<int>(blockIdx.x);
+  const int x = static_cast<int>(blockIdx.y) * kNThreads + static_cast<int>(threadIdx.x);
+  if (x >= nx) return;
+  const size_t n = static_cast<size_t>(y) * nx + x;
+  const float rho = rho_in[n];
+  if (rho_out) {
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      rho_out[static_cast<size_t>(k) * NN + n] = static_cast<double>(phi[static_cast<size_t>(k) * NN + n] * rho);
+  }
+  if (ux_out || uy_out) {
+    float Fx = 0.0f, Fy = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+      const size_t m = static_cast<size_t>(wrapn(y + ey(i), ny)) * nx + wrapn(x + ex(i), nx);
+      const float w3 = 3.0f * (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+      const float txx = T[m], txy = T[NN + m], tyy = T[2 * NN + m];
+      Fx += w3 * (ex(i) * txx + ey(i) * txy);
+      Fy += w3 * (ex(i) * txy + ey(i) * tyy);
+    }
+    float mx = 0.0f, my = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+      const float fv = fi[static_cast<size_t>(i) * NN + n];
+      mx += ex(i) * fv;
+      my += ey(i) * fv;
+    }
+    const float irho = 1.0f / rho;
+    if (ux_out) ux_out[n] = static_cast<double>((mx + 0.5f * Fx) * irho);
+    if (uy_out) uy_out[n] = static_cast<double>((my + 0.5f * Fy) * irho);
+  }
+  if (p_out) p_out[n] = static_cast<double>(rho) / 3.0;
+}
+
 int grid_of(size_t NN) {
   size_t g = (NN + kNThreads - 1) / kNThreads;
   return static_cast<int>(g > 4096 ? 4096 : (g < 1 ? 1 : g));
@@ -277,6 +323,34 @@ cudaError_t n_step(const float* fin, float* fout, float* work, const NArgs& a, c
   n_tension_kernel<N><<<g, kNThreads, 0, s>>>(phi, rho, T, nrm, a);
   n_collide_kernel<N><<<g, kNThreads, 0, s>>>(phi, rho, fi, T, nrm, fout, a);
   return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t n_fields(const float* fin, float* work, double* rho, double* ux, double* uy, double* p, const NArgs& a,
+                     cudaStream_t s) {
+  const size_t NN = static_cast<size_t>(a.nx) * a.ny;
+  float* phi = work;
+  float* rh = phi + N * NN;
+  float* fi = rh + NN;
+  float* T = fi + 9 * NN;
+  float* nrm = T + 3 * NN;
+  const dim3 g(static_cast<unsigned>(a.ny), static_cast<unsigned>((a.nx + kNThreads - 1) / kNThreads));
+  n_density_kernel<N><<<g, kNThreads, 0, s>>>(fin, phi, rh, fi, a);
+  n_tension_kernel<N><<<g, kNThreads, 0, s>>>(phi, rh, T, nrm, a);
+  n_fields_kernel<N><<<g, kNThreads, 0, s>>>(phi, rh, fi, T, rho, ux, uy, p, a);
+  return cudaGetLastError();
+}
+
+cudaError_t n_fields_any(int N, const float* fin, float* work, double* rho, double* ux, double* uy, double* p,
+                         const NArgs& a, cudaStream_t s) {
+  switch (N) {
+    case 2: return n_fields<2>(fin, work, rho, ux, uy, p, a, s);
+    case 3: return n_fields<3>(fin, work, rho, ux, uy, p, a, s);
+    case 4: return n_fields<4>(fin, work, rho, ux, uy, p, a, s);
+    case 5: return n_fields<5>(fin, work, rho, ux, uy, p, a, s);
+    case 6: return n_fields<6>(fin, work, rho, ux, uy, p, a, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t n_step_any(int N, const float* fin, float* fout, float* work, const NArgs& a, cudaStream_t s) {
@@ -538,6 +612,30 @@ lbm3_status lbm3n_populations(lbm3n_ctx* c, double* f, int on_device) {
                         c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return ncuda(c, e, "lbm3n_populations");
+  return LBM3_OK;
+}
+
+lbm3_status lbm3n_fields(lbm3n_ctx* c, double* rho, double* ux, double* uy, double* p, int on_device) {
+  if (!c) return LBM3_EINVAL;
+  if (!c->state_set) return nfail(c, LBM3_ESTATE, "lbm3n_fields: state not set");
+  const size_t NN = static_cast<size_t>(c->nx) * c->ny;
+  // the FP64 staging area holds the host case's outputs: N + 3 of its 9 N planes
+  double* staging = reinterpret_cast<double*>(c->work + lbm3::work_floats(c->N, NN));
+  double* d_rho = rho ? (on_device ? rho : staging) : nullptr;
+  double* d_ux = ux ? (on_device ? ux : staging + static_cast<size_t>(c->N) * NN) : nullptr;
+  double* d_uy = uy ? (on_device ? uy : staging + static_cast<size_t>(c->N + 1) * NN) : nullptr;
+  double* d_p = p ? (on_device ? p : staging + static_cast<size_t>(c->N + 2) * NN) : nullptr;
+  cudaError_t e = lbm3::n_fields_any(c->N, c->buf[c->cur], c->work, d_rho, d_ux, d_uy, d_p, c->args, c->stream);
+  if (e == cudaSuccess && !on_device) {
+    if (rho)
+      e = cudaMemcpyAsync(rho, d_rho, static_cast<size_t>(c->N) * NN * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream);
+    if (e == cudaSuccess && ux) e = cudaMemcpyAsync(ux, d_ux, NN * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && uy) e = cudaMemcpyAsync(uy, d_uy, NN * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && p) e = cudaMemcpyAsync(p, d_p, NN * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return ncuda(c, e, "lbm3n_fields");
   return LBM3_OK;
 }
 

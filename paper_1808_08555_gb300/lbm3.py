@@ -601,6 +601,7 @@ def _load_n():
             "lbm3n_step": (st, [vp, ctypes.c_int64]),
             "lbm3n_populations": (st, [vp, dp, ctypes.c_int]),
             "lbm3n_mass": (st, [vp, dp, dp]),
+            "lbm3n_fields": (st, [vp, dp, dp, dp, dp, ctypes.c_int]),
             "lbm3n_destroy": (st, [vp]),
             "lbm3n_last_error": (ctypes.c_char_p, [vp]),
         }
@@ -664,6 +665,14 @@ class NSimulation:
         mo = np.zeros(2)
         self._check(_load_n().lbm3n_mass(self.ctx, ctypes.c_void_p(m.ctypes.data), ctypes.c_void_p(mo.ctypes.data)))
         return m, mo
+
+    def fields(self) -> dict:
+        """rho (N, ny, nx), ux, uy, p (ny, nx), FP64."""
+        rho = np.empty((self.n, self.ny, self.nx))
+        ux, uy, p = (np.empty((self.ny, self.nx)) for _ in range(3))
+        ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
+        self._check(_load_n().lbm3n_fields(self.ctx, ptr(rho), ptr(ux), ptr(uy), ptr(p), 0))
+        return {"rho": rho, "ux": ux, "uy": uy, "p": p}
 
     def close(self):
         if getattr(self, "ctx", None):

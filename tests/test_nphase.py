@@ -162,3 +162,25 @@ def test_invalid_parameters(L):
         L.NSimulation(8, 8, bad, tau=(1.0,) * 3)
     with pytest.raises(L.Lbm3Error):
         L.NSimulation(8, 8, sigma_of(3), tau=(1.0, 0.5, 1.0))      # tau must exceed 1/2
+
+
+def test_fields_against_oracle(L):
+    """lbm3n_fields after 10 steps of four fluids, against the oracle's fields
+    of the same GPU populations (only the readout's own FP32 arithmetic is
+    compared): colour densities to 1e-6 relative, the velocity of Eq. uk1 to
+    5e-7 absolute, the pressure to 1e-6 relative."""
+    n = 4
+    p = N.NParams(24, 20, sigma=sigma_of(n), tau=tuple(0.6 + 0.15 * k for k in range(n)), rho0=(1.0,) * n)
+    f0 = random_state(n, 24, 20, seed=n + 20)
+    sim = L.NSimulation(p.nx, p.ny, p.sigma, p.tau, p.rho0, beta0=p.beta0)
+    sim.set_populations(f0)
+    sim.step(10)
+    got = sim.fields()
+    fg = sim.populations()
+    sim.close()
+    ref = N.fields(p, fg)
+    assert np.abs(got["rho"] - ref["rho"]).max() <= 1e-6 * np.abs(ref["rho"]).max()
+    for k in ("ux", "uy"):
+        assert np.abs(got[k] - ref[k]).max() <= 5e-7, k
+    assert np.abs(ref["ux"]).max() > 1e-6
+    assert np.abs(got["p"] / ref["p"] - 1).max() <= 1e-6

@@ -89,3 +89,17 @@ def test_four_fluid_nested_droplet_laplace_jumps():
         R = math.sqrt(ph[j + 1:].sum() / math.pi)
         jump = pr[ph[j + 1] > 0.99].mean() - pr[ph[j] > 0.99].mean()
         assert jump * R / s[j, j + 1] == pytest.approx(1.0, abs=0.06), j
+
+
+def test_three_fluid_fields_equal_c_oracle():
+    """rho_k, u with the F/2 correction of Eq. uk1, and p of the N-phase
+    restatement equal the C oracle's fields at N = 3."""
+    nx, ny = 16, 12
+    op = O.Params(nx, ny, tau=(0.6, 0.9, 1.3), sigma=SIG3)
+    f = O.step(op, W.random_populations(nx, ny, seed=6), 3)
+    a = O.fields(op, f)
+    b = N.fields(_p3(nx, ny), f)
+    assert np.allclose(b["rho"], a["rho"], rtol=1e-13, atol=0)
+    for k in ("ux", "uy"):
+        assert np.abs(b[k] - a[k]).max() <= 1e-15
+    assert np.allclose(b["p"], a["p"], rtol=1e-13, atol=0)
