@@ -347,6 +347,8 @@ def run_sweep(args):
 
     forms = {}
     for name, storage in (("reduced", L.REDUCED), ("fp32", L.FP32)):
+        if getattr(args, "storage", "both") not in ("both", name):
+            continue
         params = [L.Params(c.nx, c.ny, tau=c.tau, sigma=c.sigma, beta0=c.beta0, storage=storage) for c in cases]
         batch = L.Batch(params)
         items_model = batch.work_items
@@ -391,15 +393,18 @@ def run_sweep(args):
                      "roofline": {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                                   "frac": round(ach / peak, 4), "traffic": None, "bytes_per_node": bpn,
                                   "kernel": f"fused_batch_param_kernel<{name}>", "peak_source": peak_kind}}
-    h = out["reduced"]
+    head = "reduced" if "reduced" in out else "fp32"
+    h = out[head]
     return {"metric": "ternary D2Q9 MLUPS, batched morphology sweep (64 instances)", "value": h["MLUPS"],
             "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "sweep of 64 instances, edges {128..512} seed 0, touching droplets R=N/6",
-                       "nodes_per_step": nodes, "form": "reduced (headline); fp32 beside it"},
+                       "nodes_per_step": nodes,
+                       "form": "reduced (headline); fp32 beside it" if len(out) == 2 else head},
             "forms": out,
-            "equal_error": forms["reduced"]["mass_instance0"] == forms["fp32"]["mass_instance0"],
+            "equal_error": (forms["reduced"]["mass_instance0"] == forms["fp32"]["mass_instance0"]
+                            if len(forms) == 2 else None),
             "sequential_single_instance": {"value": round(nodes * args.steps / (ms_seq / 1e3) / 1e6, 2),
                                            "unit": "MLUPS", "ms_per_step": round(ms_seq / args.steps, 5)},
             "roofline": h["roofline"],
@@ -776,8 +781,8 @@ def main():
     ap.add_argument("--horizon", type=int, default=2000,
                     help="adjoint workload: steps of the differentiated run (2000 is the workload; fewer for profiling)")
     ap.add_argument("--storage", default="both", choices=["both", "fp32", "reduced"],
-                    help="compound workload: state storage (both: the reduced form as the headline and the plain "
-                         "FP32 form beside it; fp32: 27 populations only; reduced: phi_k, f^dagger_i, V_k only)")
+                    help="compound and sweep workloads: state storage (both: the reduced form as the headline and the "
+                         "plain FP32 form beside it; fp32: 27 populations only; reduced: phi_k, f^dagger_i, V_k only)")
     ap.add_argument("--size", type=int, default=None,
                     help="grid edge (default: 2048 compound, 4096 janus, 256 adjoint); other edges scale the "
                          "droplet radii (profiling and larger cases only)")
