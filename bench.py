@@ -520,12 +520,15 @@ def run_nphase(args):
 
 
 def run_d3q19(args):
-    """Three fluids on the D3Q19 lattice (the first 3D path, three kernels per
-    step): two spheres, fluid 2 (R = 3n/16 at x = n/4) and fluid 3 (R = 5n/32
-    at x = 3n/4), in fluid 1 on an n^3 grid (default 256^3), sigma_12 / 13 /
-    23 = 0.01 / 0.013 / 0.007, tau = (0.6, 0.9, 1.3).  Algorithmic bytes per
-    node update are the state's, 2 x 19N x 4 (456 B at N = 3); the kernels
-    also move their intermediates through HBM."""
+    """Three fluids on the D3Q19 lattice (three kernels per step): two spheres,
+    fluid 2 (R = 3n/16 at x = n/4) and fluid 3 (R = 5n/32 at x = 3n/4), in
+    fluid 1 on an n^3 grid (default 256^3), sigma_12 / 13 / 23 = 0.01 / 0.013
+    / 0.007, tau = (0.6, 0.9, 1.3), in the reduced state (the headline) and
+    with FP32 populations (bit-identical trajectories); --storage restricts
+    the run to one form.  Algorithmic bytes per node update are the state's:
+    2 x 19N x 4 = 456 B for the populations, 2 x (19 + 4N) x 4 = 248 B for
+    the reduced state at N = 3; the kernels also move their intermediates
+    through HBM."""
     import torch
 
     from paper_1808_08555_gb300 import build as B
@@ -536,31 +539,45 @@ def run_d3q19(args):
     n = args.size or 256
     rho = W.spheres_3d(n, n, n, [(1, (n / 4, n / 2, n / 2), 3 * n / 16), (2, (3 * n / 4, n / 2, n / 2), 5 * n / 32)])
     sig = np.array([[0.0, 0.01, 0.013], [0.01, 0.0, 0.007], [0.013, 0.007, 0.0]])
-    sim = L.D3Q19Simulation(n, n, n, sig, tau=(0.6, 0.9, 1.3))
-    sim.init(rho)
-    del rho
-    sim.step(args.warmup)
-    s = sim.stream
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(s)
-    sim.step(args.steps)
-    e1.record(s)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    m, _ = sim.mass()
-    sim.close()
-    mlups = n ** 3 / ms / 1e3
+    storage = getattr(args, "storage", "both")
+    order = ["reduced", "fp32"] if storage == "both" else [storage]
     peak, peak_kind = hbm_peak()
-    bpn = 2 * 19 * 3 * 4
-    return {"metric": "D3Q19 MLUPS, three fluids (3D path)", "value": round(mlups, 1), "unit": "MLUPS",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
+    forms, masses = {}, {}
+    for name in order:
+        sim = L.D3Q19Simulation(n, n, n, sig, tau=(0.6, 0.9, 1.3),
+                                storage=L.REDUCED if name == "reduced" else L.FP32)
+        sim.init(rho)
+        sim.step(args.warmup)
+        s = sim.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        sim.step(args.steps)
+        e1.record(s)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        masses[name] = [float(v) for v in sim.mass()[0]]
+        sim.close()
+        torch.cuda.empty_cache()
+        mlups = n ** 3 / ms / 1e3
+        bpn = 2 * (19 + 4 * 3) * 4 if name == "reduced" else 2 * 19 * 3 * 4
+        forms[name] = {"MLUPS": round(mlups, 1), "ms_per_step": round(ms, 5), "bytes_per_node": bpn,
+                       "achieved_GBs": round(bpn * mlups / 1e3, 1),
+                       "frac": round(bpn * mlups * 1e6 / (peak * 1e9), 4)}
+    del rho
+    head = forms[order[0]]
+    checks = {"mass": masses[order[0]]}
+    if len(masses) == 2:
+        checks["same_masses_both_forms"] = masses["reduced"] == masses["fp32"]
+    return {"metric": "D3Q19 MLUPS, three fluids (3D path)", "value": head["MLUPS"], "unit": "MLUPS",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"two spheres of fluids 2 and 3 in fluid 1, {n}^3, R {3 * n // 16}/{5 * n // 32}"},
-            "roofline": {"bound": "hbm", "achieved": round(bpn * mlups / 1e3, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(bpn * mlups * 1e6 / (peak * 1e9), 4), "traffic": None, "bytes_per_node": bpn,
+            "config": {"workload": f"two spheres of fluids 2 and 3 in fluid 1, {n}^3, R {3 * n // 16}/{5 * n // 32}",
+                       "form": order[0] + (" (headline); fp32 populations in 'forms'" if len(order) == 2 else "")},
+            "roofline": {"bound": "hbm", "achieved": head["achieved_GBs"], "peak": peak, "unit": "GB/s",
+                         "frac": head["frac"], "traffic": None, "bytes_per_node": head["bytes_per_node"],
                          "kernel": "d_density + d_tension + d_collide kernels (N = 3)", "peak_source": peak_kind},
-            "checks": {"mass": [float(v) for v in m]}, "gpu_launches": 3 * args.steps}
+            "forms": forms, "checks": checks, "gpu_launches": 3 * args.steps * len(order)}
 
 
 def run_adjoint(args):
@@ -781,7 +798,7 @@ def main():
     ap.add_argument("--horizon", type=int, default=2000,
                     help="adjoint workload: steps of the differentiated run (2000 is the workload; fewer for profiling)")
     ap.add_argument("--storage", default="both", choices=["both", "fp32", "reduced"],
-                    help="compound and sweep workloads: state storage (both: the reduced form as the headline and the "
+                    help="compound, sweep and d3q19 workloads: state storage (both: the reduced form as the headline and the "
                          "plain FP32 form beside it; fp32: 27 populations only; reduced: phi_k, f^dagger_i, V_k only)")
     ap.add_argument("--size", type=int, default=None,
                     help="grid edge (default: 2048 compound, 4096 janus, 256 adjoint); other edges scale the "

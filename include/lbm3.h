@@ -432,7 +432,15 @@ const char* lbm3n_last_error(const lbm3n_ctx* ctx);
  * allocates its two population buffers (19 N nx ny nz floats each), the
  * intermediates ((4 + 25 + 3 N (N - 1) / 2) nx ny nz floats for N <= 3,
  * 4 more per node for N = 4) and an FP64 staging area of one population
- * state. */
+ * state.
+ * storage LBM3_REDUCED keeps, per node, the colour fractions phi_k, the
+ * post-collision total distribution f^dagger_i and the recolouring vectors
+ * V_k (19 + 4 N floats instead of 19 N, in the same buffers), as LBM3_REDUCED
+ * does for lbm3_ctx; every population is rebuilt from its source node with
+ * the FP32 operations of the population form, so results are bit-identical
+ * to LBM3_FP32.  A state set by lbm3d_init / lbm3d_set_populations is held as
+ * populations until the next step; lbm3d_populations and lbm3d_mass expand
+ * the reduced state into the idle buffer first. */
 typedef struct lbm3d_ctx lbm3d_ctx;
 typedef struct {
   int32_t nx, ny, nz, nfluids;
@@ -443,6 +451,7 @@ typedef struct {
   int32_t beta_form;    /* 0: Eq. 19 with one junction term per third fluid; 1: Eq. fu */
   int32_t recolor_form; /* as lbm3_recolor_form */
   double normal_delta;  /* as lbm3_params.normal_delta */
+  int32_t storage;      /* LBM3_FP32 or LBM3_REDUCED (below) */
 } lbm3d_params;
 lbm3_status lbm3d_create(const lbm3d_params* p, void* cuda_stream, lbm3d_ctx** out);
 /* rest equilibrium per colour from host densities (rho_k >= 0) */

@@ -130,19 +130,50 @@ __device__ __forceinline__ float pr_rho(const float4* __restrict__ pr, size_t n)
   return pr[2 * n + 1].x;
 }
 
+// ------------------------------------------------------------ node level
+// The arithmetic of one node, the neighbours' intermediates through
+// accessors.
+
+// colour fractions from the colour densities r_k (the largest as the
+// complement of the others, so that they sum to 1 exactly) and the density
 template <int N>
-__global__ void __launch_bounds__(kBX) d_density_kernel(const float* __restrict__ f, float4* __restrict__ pr,
-                                                        float* __restrict__ fi, DArgs a) {
-  Node p;
-  if (!node_of(a, &p)) return;
+__device__ __forceinline__ void fractions(const float (&r)[N], float (&ph)[N], float& rho) {
+  float rmax = -1.0f;
+  int kmax = 0;
+  rho = 0.0f;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    rho += r[k];
+    if (r[k] > rmax) {
+      rmax = r[k];
+      kmax = k;
+    }
+  }
+  const float ir = 1.0f / rho;
+  float rest = 1.0f;
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    if (k != kmax) {
+      ph[k] = r[k] * ir;
+      rest -= ph[k];
+    }
+#pragma unroll
+  for (int k = 0; k < N; ++k)
+    if (k == kmax) ph[k] = rest;
+}
+
+// The pull (Eq. 30) at node p from stored populations: colour fractions,
+// density, and the total distribution f_i = sum_k f_{i,k}
+template <int N>
+__device__ __forceinline__ void density_node(const float* __restrict__ f, const DArgs& a, const Node& p,
+                                             float (&ph)[N], float& rho, float (&tot)[Q3]) {
   const size_t NN = p.NN;
   float r[N];
-  float tot[Q3];
 #pragma unroll
   for (int i = 0; i < Q3; ++i) tot[i] = 0.0f;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    // a colour's 19 pulled values (Eq. 30) loaded together, then summed
+    // a colour's 19 pulled values loaded together, then summed
     float v[Q3];
 #pragma unroll
     for (int i = 0; i < Q3; ++i) v[i] = f[(static_cast<size_t>(k) * Q3 + i) * NN + at(a, p, -cx(i), -cy(i), -cz(i))];
@@ -154,49 +185,129 @@ __global__ void __launch_bounds__(kBX) d_density_kernel(const float* __restrict_
     }
     r[k] = s;
   }
-  float rho = 0.0f, rmax = -1.0f;
-  int kmax = 0;
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    rho += r[k];
-    if (r[k] > rmax) {
-      rmax = r[k];
-      kmax = k;
-    }
-  }
-  const float ir = 1.0f / rho;
-  float rest = 1.0f;
-  float ph[N];
-#pragma unroll
-  for (int k = 0; k < N; ++k)
-    if (k != kmax) {
-      ph[k] = r[k] * ir;
-      rest -= ph[k];
-    }
-#pragma unroll
-  for (int k = 0; k < N; ++k)
-    if (k == kmax) ph[k] = rest;  // the fractions sum to 1 exactly
-  pr_store<N>(pr, p.n, ph, rho);
-#pragma unroll
-  for (int i = 0; i < Q3; ++i) fi[static_cast<size_t>(i) * NN + p.n] = tot[i];
+  fractions<N>(r, ph, rho);
+}
+
+// ---------------------------------------------------------- reduced state
+// Collision (Eqs. 1-3, 5) uses only the total distribution and the colour
+// densities, and the recolouring of Eq. 6 writes
+//   f^ddagger_{i,k} = phi_k f^dagger_i + w'_i e_i . V_k,
+//   V_k = sum_{l != k} beta_kl (rho_k rho_l / rho) n_kl,
+// so a node's 19 N outputs are fixed by phi_k, f^dagger_i and V_k: 19 + 4 N
+// values (31 instead of 57 for three fluids).  Layout inside a population
+// buffer: N float4 planes [nz][ny][nx] holding (phi_1 .. phi_N, V_1x, V_1y,
+// V_1z, .., V_Nz) in that order, then 19 float planes f^dagger_i.  All N
+// vectors V_k are kept although they sum to zero, so that every population is
+// rebuilt from exactly the values the collision used.
+
+// e_i . V over the nonzero components of e_i (at most two on D3Q19)
+__device__ __forceinline__ float edot(int i, float vx, float vy, float vz) {
+  const float a = cx(i) > 0 ? vx : -vx;
+  const float b = cy(i) > 0 ? vy : -vy;
+  const float c = cz(i) > 0 ? vz : -vz;
+  if (cx(i) != 0) return cy(i) != 0 ? __fadd_rn(a, b) : (cz(i) != 0 ? __fadd_rn(a, c) : a);
+  if (cy(i) != 0) return cz(i) != 0 ? __fadd_rn(b, c) : b;
+  return cz(i) != 0 ? c : 0.0f;
+}
+
+// Eq. 6 for one population, f^ddagger = phi_k f^dagger_i + w'_i (e_i . V_k),
+// in explicitly rounded operations: the collision's store and the reduced
+// state's rebuild give the same bits
+__device__ __forceinline__ float recolour(float phk, float fdi, float wr, float ev) {
+  return __fmaf_rn(wr, ev, __fmul_rn(phk, fdi));
 }
 
 template <int N>
-__global__ void __launch_bounds__(kBX) d_tension_kernel(const float4* __restrict__ pr, float4* __restrict__ T4,
-                                                        float2* __restrict__ T2, float* __restrict__ nrm, DArgs a) {
-  Node p;
-  if (!node_of(a, &p)) return;
+__device__ __forceinline__ void rec_store(float4* __restrict__ R, size_t n, size_t NN, const float (&ph)[N],
+                                          const float (&V)[N][3]) {
+  float r[4 * N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    r[k] = ph[k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) r[N + 3 * k + c] = V[k][c];
+  }
+#pragma unroll
+  for (int j = 0; j < N; ++j) R[static_cast<size_t>(j) * NN + n] = make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+}
+
+template <int N>
+__device__ __forceinline__ void rec_load(const float4* __restrict__ R, size_t n, size_t NN, float (&ph)[N],
+                                         float (&V)[N][3]) {
+  float r[4 * N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    const float4 v = R[static_cast<size_t>(j) * NN + n];
+    r[4 * j] = v.x;
+    r[4 * j + 1] = v.y;
+    r[4 * j + 2] = v.z;
+    r[4 * j + 3] = v.w;
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    ph[k] = r[k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) V[k][c] = r[N + 3 * k + c];
+  }
+}
+
+// The pull (Eq. 30) at node p from the reduced state: each population
+// rebuilt from its source node x - e_i, then the sums of density_node in the
+// same order (so that both state forms give the same bits)
+template <int N>
+__device__ __forceinline__ void density_node_red(const float* __restrict__ g, const DArgs& a, const Node& p,
+                                                 float (&ph)[N], float& rho, float (&tot)[Q3]) {
   const size_t NN = p.NN;
-  float ph[N], g[N][3];
-  pr_phi<N>(pr, p.n, ph);
+  const float4* __restrict__ R = reinterpret_cast<const float4*>(g);
+  const float* __restrict__ fd = g + static_cast<size_t>(4 * N) * NN;
+  float r[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) r[k] = 0.0f;
+  // the 19 pulled f^dagger_i loaded together first, then one source record
+  // per direction (loading several directions' records together was slower)
+  float fdv[Q3];
+#pragma unroll
+  for (int i = 0; i < Q3; ++i) fdv[i] = fd[static_cast<size_t>(i) * NN + at(a, p, -cx(i), -cy(i), -cz(i))];
+#pragma unroll
+  for (int i = 0; i < Q3; ++i) {
+    float sp[N], sv[N][3];
+    rec_load<N>(R, at(a, p, -cx(i), -cy(i), -cz(i)), NN, sp, sv);
+    float t = 0.0f;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const float v = recolour(sp[k], fdv[i], a.wrec[i], edot(i, sv[k][0], sv[k][1], sv[k][2]));
+      r[k] += v;
+      t += v;
+    }
+    tot[i] = t;
+  }
+  fractions<N>(r, ph, rho);
+}
+
+template <int N, bool RED>
+__device__ __forceinline__ void density_any(const float* __restrict__ f, const DArgs& a, const Node& p,
+                                            float (&ph)[N], float& rho, float (&tot)[Q3]) {
+  if constexpr (RED)
+    density_node_red<N>(f, a, p, ph, rho, tot);
+  else
+    density_node<N>(f, a, p, ph, rho, tot);
+}
+
+// The tension tensor of Eq. 11 (6 components) and the recolouring normals at
+// a node, from its own (phi, rho) and its neighbours' fractions phi_at(i, v);
+// each pair's normal is handed to nrm_out(q, nx, ny, nz) as soon as it is
+// formed
+template <int N, typename PhiAt, typename NrmOut>
+__device__ __forceinline__ void tension_node(PhiAt phi_at, const DArgs& a, const float (&ph)[N], float rho,
+                                             float4& t4, float2& t2, NrmOut nrm_out) {
+  float g[N][3];
 #pragma unroll
   for (int k = 0; k < N; ++k) g[k][0] = g[k][1] = g[k][2] = 0.0f;
-  // Eq. fd1: (1/cs2) sum_i w_i phi(x + e_i) e_i, all colours from one vector
-  // load per neighbour
+  // Eq. fd1: (1/cs2) sum_i w_i phi(x + e_i) e_i
 #pragma unroll
   for (int i = 1; i < Q3; ++i) {
     float v[N];
-    pr_phi<N>(pr, at(a, p, cx(i), cy(i), cz(i)), v);
+    phi_at(i, v);
     const float w3 = 3.0f * w3f(i);
 #pragma unroll
     for (int k = 0; k < N; ++k) {
@@ -205,7 +316,6 @@ __global__ void __launch_bounds__(kBX) d_tension_kernel(const float4* __restrict
       g[k][2] += w3 * cz(i) * v[k];
     }
   }
-  const float rho = pr_rho<N>(pr, p.n);
   float txx = 0.0f, txy = 0.0f, txz = 0.0f, tyy = 0.0f, tyz = 0.0f, tzz = 0.0f;
   int q = 0;
 #pragma unroll
@@ -235,35 +345,42 @@ __global__ void __launch_bounds__(kBX) d_tension_kernel(const float4* __restrict
         nv[1] = Gy / den;
         nv[2] = Gz / den;
       }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) nrm[(static_cast<size_t>(q) * 3 + c) * NN + p.n] = nv[c];
+      nrm_out(q, nv[0], nv[1], nv[2]);
     }
-  T4[p.n] = make_float4(txx, txy, txz, tyy);
-  T2[p.n] = make_float2(tyz, tzz);
+  t4 = make_float4(txx, txy, txz, tyy);
+  t2 = make_float2(tyz, tzz);
 }
 
-// F_s = div T (Eq. 11): F_a = (1/cs2) sum_i w_i sum_b e_ib T_ab(x + e_i)
-__device__ __forceinline__ void divergence(const float4* __restrict__ T4, const float2* __restrict__ T2,
-                                           const DArgs& a, const Node& p, float (&F)[3]) {
+// F_s = div T (Eq. 11): F_a = (1/cs2) sum_i w_i sum_b e_ib T_ab(x + e_i), the
+// neighbours' tensors from t_at(i, ta, tb)
+template <typename TAt>
+__device__ __forceinline__ void divergence_at(TAt t_at, float (&F)[3]) {
   F[0] = F[1] = F[2] = 0.0f;
 #pragma unroll
   for (int i = 1; i < Q3; ++i) {
-    const size_t m = at(a, p, cx(i), cy(i), cz(i));
     const float w3 = 3.0f * w3f(i);
-    const float4 ta = T4[m];
-    const float2 tb = T2[m];
+    float4 ta;
+    float2 tb;
+    t_at(i, ta, tb);
     const float txx = ta.x, txy = ta.y, txz = ta.z, tyy = ta.w, tyz = tb.x, tzz = tb.y;
     F[0] += w3 * (cx(i) * txx + cy(i) * txy + cz(i) * txz);
     F[1] += w3 * (cx(i) * txy + cy(i) * tyy + cz(i) * tyz);
     F[2] += w3 * (cx(i) * txz + cy(i) * tyz + cz(i) * tzz);
   }
 }
+__device__ __forceinline__ void divergence(const float4* __restrict__ T4, const float2* __restrict__ T2,
+                                           const DArgs& a, const Node& p, float (&F)[3]) {
+  divergence_at(
+      [&](int i, float4& ta, float2& tb) {
+        const size_t m = at(a, p, cx(i), cy(i), cz(i));
+        ta = T4[m];
+        tb = T2[m];
+      },
+      F);
+}
 
 // momentum sum_i f_i e_i of the total distribution
-__device__ __forceinline__ void momentum(const float* __restrict__ fi, size_t n, size_t NN, float (&f)[Q3],
-                                         float (&m)[3]) {
-#pragma unroll
-  for (int i = 0; i < Q3; ++i) f[i] = fi[static_cast<size_t>(i) * NN + n];
+__device__ __forceinline__ void momentum_of(const float (&f)[Q3], float (&m)[3]) {
   m[0] = m[1] = m[2] = 0.0f;
 #pragma unroll
   for (int i = 1; i < Q3; ++i) {
@@ -272,22 +389,23 @@ __device__ __forceinline__ void momentum(const float* __restrict__ fi, size_t n,
     m[2] += cz(i) * f[i];
   }
 }
+__device__ __forceinline__ void momentum(const float* __restrict__ fi, size_t n, size_t NN, float (&f)[Q3],
+                                         float (&m)[3]) {
+#pragma unroll
+  for (int i = 0; i < Q3; ++i) f[i] = fi[static_cast<size_t>(i) * NN + n];
+  momentum_of(f, m);
+}
 
-template <int N>
-__global__ void __launch_bounds__(kBX) d_collide_kernel(const float4* __restrict__ pr, const float* __restrict__ fi,
-                                                        const float4* __restrict__ T4, const float2* __restrict__ T2,
-                                                        const float* __restrict__ nrm, float* __restrict__ fout,
-                                                        DArgs a) {
-  Node p;
-  if (!node_of(a, &p)) return;
-  const size_t NN = p.NN;
-  float F[3];
-  divergence(T4, T2, a, p, F);
-  const float rho = pr_rho<N>(pr, p.n);
-  float ph[N];
-  pr_phi<N>(pr, p.n, ph);
-  float f[Q3], m[3];
-  momentum(fi, p.n, NN, f, m);
+// Collision (BGK with Guo's forcing, Eqs. 1-3, 5; tau_f of Eqs. vis_1, tau),
+// the segregation parameters and the recolouring of Eq. 6, stored at node n
+// (the next step's pull streams it, Eq. 30) as 19 N populations or, RED, as
+// the reduced state; normals from nrm_at(q, c)
+template <int N, bool RED, typename NrmAt>
+__device__ __forceinline__ void collide_store(const DArgs& a, const float (&F)[3], const float (&ph)[N], float rho,
+                                              const float (&f)[Q3], NrmAt nrm_at, float* __restrict__ fout, size_t n,
+                                              size_t NN) {
+  float m[3];
+  momentum_of(f, m);
   const float irho = 1.0f / rho;
   float u[3];
 #pragma unroll
@@ -327,18 +445,98 @@ __global__ void __launch_bounds__(kBX) d_collide_kernel(const float4* __restrict
       const float amp = a.beta0 * b * ph[k] * ph[l] * rho;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float nc = nrm[(static_cast<size_t>(q) * 3 + c) * NN + p.n];
+        const float nc = nrm_at(q, c);
         V[k][c] += amp * nc;
         V[l][c] -= amp * nc;
       }
     }
-  // Eq. 6, stored at the node (the next step's pull streams it, Eq. 30)
+  if constexpr (RED) {
+    rec_store<N>(reinterpret_cast<float4*>(fout), n, NN, ph, V);
+    float* __restrict__ fdo = fout + static_cast<size_t>(4 * N) * NN;
 #pragma unroll
-  for (int k = 0; k < N; ++k)
+    for (int i = 0; i < Q3; ++i) fdo[static_cast<size_t>(i) * NN + n] = fd[i];
+  } else {
 #pragma unroll
-    for (int i = 0; i < Q3; ++i)
-      fout[(static_cast<size_t>(k) * Q3 + i) * NN + p.n] =
-          ph[k] * fd[i] + a.wrec[i] * (cx(i) * V[k][0] + cy(i) * V[k][1] + cz(i) * V[k][2]);
+    for (int k = 0; k < N; ++k)
+#pragma unroll
+      for (int i = 0; i < Q3; ++i)
+        fout[(static_cast<size_t>(k) * Q3 + i) * NN + n] =
+            recolour(ph[k], fd[i], a.wrec[i], edot(i, V[k][0], V[k][1], V[k][2]));
+  }
+}
+
+// ------------------------------------------------------- three-kernel path
+
+template <int N, bool RED>
+__global__ void __launch_bounds__(kBX) d_density_kernel(const float* __restrict__ f, float4* __restrict__ pr,
+                                                        float* __restrict__ fi, DArgs a) {
+  Node p;
+  if (!node_of(a, &p)) return;
+  float ph[N], rho, tot[Q3];
+  density_any<N, RED>(f, a, p, ph, rho, tot);
+  pr_store<N>(pr, p.n, ph, rho);
+#pragma unroll
+  for (int i = 0; i < Q3; ++i) fi[static_cast<size_t>(i) * p.NN + p.n] = tot[i];
+}
+
+template <int N>
+__global__ void __launch_bounds__(kBX) d_tension_kernel(const float4* __restrict__ pr, float4* __restrict__ T4,
+                                                        float2* __restrict__ T2, float* __restrict__ nrm, DArgs a) {
+  Node p;
+  if (!node_of(a, &p)) return;
+  const size_t NN = p.NN;
+  float ph[N];
+  pr_phi<N>(pr, p.n, ph);
+  const float rho = pr_rho<N>(pr, p.n);
+  float4 t4;
+  float2 t2;
+  tension_node<N>([&](int i, float (&v)[N]) { pr_phi<N>(pr, at(a, p, cx(i), cy(i), cz(i)), v); }, a, ph, rho, t4,
+                  t2, [&](int q, float nx, float ny, float nz) {
+                    nrm[(static_cast<size_t>(q) * 3) * NN + p.n] = nx;
+                    nrm[(static_cast<size_t>(q) * 3 + 1) * NN + p.n] = ny;
+                    nrm[(static_cast<size_t>(q) * 3 + 2) * NN + p.n] = nz;
+                  });
+  T4[p.n] = t4;
+  T2[p.n] = t2;
+}
+
+template <int N, bool RED>
+__global__ void __launch_bounds__(kBX) d_collide_kernel(const float4* __restrict__ pr, const float* __restrict__ fi,
+                                                        const float4* __restrict__ T4, const float2* __restrict__ T2,
+                                                        const float* __restrict__ nrm, float* __restrict__ fout,
+                                                        DArgs a) {
+  Node p;
+  if (!node_of(a, &p)) return;
+  const size_t NN = p.NN;
+  float F[3];
+  divergence(T4, T2, a, p, F);
+  const float rho = pr_rho<N>(pr, p.n);
+  float ph[N];
+  pr_phi<N>(pr, p.n, ph);
+  float f[Q3];
+#pragma unroll
+  for (int i = 0; i < Q3; ++i) f[i] = fi[static_cast<size_t>(i) * NN + p.n];
+  collide_store<N, RED>(a, F, ph, rho, f, [&](int q, int c) { return nrm[(static_cast<size_t>(q) * 3 + c) * NN + p.n]; },
+                        fout, p.n, NN);
+}
+
+// the reduced state g expanded into the populations it stands for, stored at
+// the producing node (the form the population buffers hold between steps)
+template <int N>
+__global__ void __launch_bounds__(kBX) d_expand_kernel(const float* __restrict__ g, float* __restrict__ f, DArgs a) {
+  Node p;
+  if (!node_of(a, &p)) return;
+  const size_t NN = p.NN;
+  float ph[N], V[N][3];
+  rec_load<N>(reinterpret_cast<const float4*>(g), p.n, NN, ph, V);
+  const float* __restrict__ fd = g + static_cast<size_t>(4 * N) * NN;
+#pragma unroll
+  for (int i = 0; i < Q3; ++i) {
+    const float fdi = fd[static_cast<size_t>(i) * NN + p.n];
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      f[(static_cast<size_t>(k) * Q3 + i) * NN + p.n] = recolour(ph[k], fdi, a.wrec[i], edot(i, V[k][0], V[k][1], V[k][2]));
+  }
 }
 
 // Observables of the state the density and tension kernels have just
@@ -390,46 +588,69 @@ struct Work {
   }
 };
 
-template <int N>
+template <int N, bool RED>
 cudaError_t d_fields(const float* fin, float* work, double* rho, double* u, double* pr_out, const DArgs& a,
                      cudaStream_t s) {
   const size_t NN = static_cast<size_t>(a.nx) * a.ny * a.nz;
   const Work<N> w(work, NN);
   const dim3 g = grid3(a);
-  d_density_kernel<N><<<g, kBX, 0, s>>>(fin, w.pr, w.fi, a);
+  d_density_kernel<N, RED><<<g, kBX, 0, s>>>(fin, w.pr, w.fi, a);
   d_tension_kernel<N><<<g, kBX, 0, s>>>(w.pr, w.T4, w.T2, w.nrm, a);
   d_fields_kernel<N><<<g, kBX, 0, s>>>(w.pr, w.fi, w.T4, w.T2, rho, u, pr_out, a);
   return cudaGetLastError();
 }
 
-cudaError_t d_fields_any(int N, const float* fin, float* work, double* rho, double* u, double* p, const DArgs& a,
-                         cudaStream_t s) {
-  switch (N) {
-    case 2: return d_fields<2>(fin, work, rho, u, p, a, s);
-    case 3: return d_fields<3>(fin, work, rho, u, p, a, s);
-    case 4: return d_fields<4>(fin, work, rho, u, p, a, s);
+cudaError_t d_fields_any(int N, bool red, const float* fin, float* work, double* rho, double* u, double* p,
+                         const DArgs& a, cudaStream_t s) {
+  switch (N * 2 + (red ? 1 : 0)) {
+    case 4: return d_fields<2, false>(fin, work, rho, u, p, a, s);
+    case 5: return d_fields<2, true>(fin, work, rho, u, p, a, s);
+    case 6: return d_fields<3, false>(fin, work, rho, u, p, a, s);
+    case 7: return d_fields<3, true>(fin, work, rho, u, p, a, s);
+    case 8: return d_fields<4, false>(fin, work, rho, u, p, a, s);
+    case 9: return d_fields<4, true>(fin, work, rho, u, p, a, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
+// one step from the state fin (populations, or the reduced state with
+// in_red) to fout (the reduced state with out_red)
 template <int N>
-cudaError_t d_step(const float* fin, float* fout, float* work, const DArgs& a, cudaStream_t s) {
+cudaError_t d_step(const float* fin, float* fout, float* work, const DArgs& a, cudaStream_t s, bool in_red,
+                   bool out_red) {
   const size_t NN = static_cast<size_t>(a.nx) * a.ny * a.nz;
   const Work<N> w(work, NN);
   const dim3 g = grid3(a);
-  d_density_kernel<N><<<g, kBX, 0, s>>>(fin, w.pr, w.fi, a);
+  if (in_red)
+    d_density_kernel<N, true><<<g, kBX, 0, s>>>(fin, w.pr, w.fi, a);
+  else
+    d_density_kernel<N, false><<<g, kBX, 0, s>>>(fin, w.pr, w.fi, a);
   d_tension_kernel<N><<<g, kBX, 0, s>>>(w.pr, w.T4, w.T2, w.nrm, a);
-  d_collide_kernel<N><<<g, kBX, 0, s>>>(w.pr, w.fi, w.T4, w.T2, w.nrm, fout, a);
+  if (out_red)
+    d_collide_kernel<N, true><<<g, kBX, 0, s>>>(w.pr, w.fi, w.T4, w.T2, w.nrm, fout, a);
+  else
+    d_collide_kernel<N, false><<<g, kBX, 0, s>>>(w.pr, w.fi, w.T4, w.T2, w.nrm, fout, a);
   return cudaGetLastError();
 }
 
-cudaError_t d_step_any(int N, const float* fin, float* fout, float* work, const DArgs& a, cudaStream_t s) {
+cudaError_t d_step_any(int N, const float* fin, float* fout, float* work, const DArgs& a, cudaStream_t s,
+                       bool in_red, bool out_red) {
   switch (N) {
-    case 2: return d_step<2>(fin, fout, work, a, s);
-    case 3: return d_step<3>(fin, fout, work, a, s);
-    case 4: return d_step<4>(fin, fout, work, a, s);
+    case 2: return d_step<2>(fin, fout, work, a, s, in_red, out_red);
+    case 3: return d_step<3>(fin, fout, work, a, s, in_red, out_red);
+    case 4: return d_step<4>(fin, fout, work, a, s, in_red, out_red);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t d_expand_any(int N, const float* g, float* f, const DArgs& a, cudaStream_t s) {
+  switch (N) {
+    case 2: d_expand_kernel<2><<<grid3(a), kBX, 0, s>>>(g, f, a); break;
+    case 3: d_expand_kernel<3><<<grid3(a), kBX, 0, s>>>(g, f, a); break;
+    case 4: d_expand_kernel<4><<<grid3(a), kBX, 0, s>>>(g, f, a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 // intermediates (4 or 8 floats of (phi_k, rho), 6 of T, 19 f_i and 3P normal
@@ -517,6 +738,8 @@ struct lbm3d_ctx {
   double* sums = nullptr;
   int cur = 0;
   bool state_set = false;
+  bool reduced = false;  // the storage form of the steps (LBM3_REDUCED)
+  bool red = false;      // buf[cur] holds the reduced state (else populations)
   lbm3::DArgs args{};
   std::string msg;
 };
@@ -534,6 +757,15 @@ lbm3_status dcuda(lbm3d_ctx* c, cudaError_t e, const char* where) {
 
 size_t nodes(const lbm3d_ctx* c) { return static_cast<size_t>(c->nx) * c->ny * c->nz; }
 
+// the current state as stored populations: buf[cur] itself, or the reduced
+// state expanded into the idle buffer
+const float* stored_populations(lbm3d_ctx* c, cudaError_t* e) {
+  *e = cudaSuccess;
+  if (!c->red) return c->buf[c->cur];
+  *e = lbm3::d_expand_any(c->N, c->buf[c->cur], c->buf[c->cur ^ 1], c->args, c->stream);
+  return c->buf[c->cur ^ 1];
+}
+
 }  // namespace
 
 extern "C" {
@@ -547,7 +779,8 @@ lbm3_status lbm3d_create(const lbm3d_params* p, void* cuda_stream, lbm3d_ctx** o
     return LBM3_EINVAL;
   if (static_cast<double>(p->nx) * p->ny * p->nz * lbm3::Q3 * N >= 4294967296.0) return LBM3_EINVAL;
   if (!(p->beta0 > 0.0 && p->beta0 <= 1.0) || p->beta_form < 0 || p->beta_form > 1 || p->recolor_form < 0 ||
-      p->recolor_form > 1 || !(p->normal_delta >= 0.0 && p->normal_delta <= 1.0))
+      p->recolor_form > 1 || !(p->normal_delta >= 0.0 && p->normal_delta <= 1.0) ||
+      (p->storage != LBM3_FP32 && p->storage != LBM3_REDUCED))
     return LBM3_EINVAL;
   for (int k = 0; k < N; ++k) {
     if (!(p->tau[k] > 0.5) || !(p->rho0[k] > 0.0)) return LBM3_EINVAL;
@@ -563,6 +796,7 @@ lbm3_status lbm3d_create(const lbm3d_params* p, void* cuda_stream, lbm3d_ctx** o
   c->ny = p->ny;
   c->nz = p->nz;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->reduced = p->storage == LBM3_REDUCED;
   lbm3::DArgs& a = c->args;
   a.nx = p->nx;
   a.ny = p->ny;
@@ -629,6 +863,7 @@ lbm3_status lbm3d_set_populations(lbm3d_ctx* c, const double* f, int on_device) 
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return dcuda(c, e, "lbm3d_set_populations");
   c->state_set = true;
+  c->red = false;
   return LBM3_OK;
 }
 
@@ -649,6 +884,7 @@ lbm3_status lbm3d_init(lbm3d_ctx* c, const double* rho, int on_device) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return dcuda(c, e, "lbm3d_init");
   c->state_set = true;
+  c->red = false;
   return LBM3_OK;
 }
 
@@ -657,9 +893,11 @@ lbm3_status lbm3d_step(lbm3d_ctx* c, int64_t n) {
   if (n < 0) return dfail(c, LBM3_EINVAL, "lbm3d_step: n < 0");
   if (!c->state_set) return dfail(c, LBM3_ESTATE, "lbm3d_step: state not set");
   for (int64_t s = 0; s < n; ++s) {
-    const cudaError_t e = lbm3::d_step_any(c->N, c->buf[c->cur], c->buf[c->cur ^ 1], c->work, c->args, c->stream);
+    const cudaError_t e = lbm3::d_step_any(c->N, c->buf[c->cur], c->buf[c->cur ^ 1], c->work, c->args, c->stream,
+                                           c->red, c->reduced);
     if (e != cudaSuccess) return dcuda(c, e, "lbm3d_step");
     c->cur ^= 1;
+    c->red = c->reduced;
   }
   return LBM3_OK;
 }
@@ -671,8 +909,12 @@ lbm3_status lbm3d_populations(lbm3d_ctx* c, double* f, int on_device) {
   const size_t NN = nodes(c);
   const int planes = lbm3::Q3 * c->N;
   double* dst = on_device ? f : reinterpret_cast<double*>(c->work + lbm3::work_floats3(c->N, NN));
-  lbm3::d_get_kernel<<<lbm3::grid3(c->args), lbm3::kBX, 0, c->stream>>>(c->buf[c->cur], dst, c->args, planes);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  const float* src = stored_populations(c, &e);
+  if (e == cudaSuccess) {
+    lbm3::d_get_kernel<<<lbm3::grid3(c->args), lbm3::kBX, 0, c->stream>>>(src, dst, c->args, planes);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess && !on_device)
     e = cudaMemcpyAsync(f, dst, planes * NN * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -689,7 +931,7 @@ lbm3_status lbm3d_fields(lbm3d_ctx* c, double* rho, double* u, double* p, int on
   double* d_rho = rho ? (on_device ? rho : staging) : nullptr;
   double* d_u = u ? (on_device ? u : staging + static_cast<size_t>(c->N) * NN) : nullptr;
   double* d_p = p ? (on_device ? p : staging + static_cast<size_t>(c->N + 3) * NN) : nullptr;
-  cudaError_t e = lbm3::d_fields_any(c->N, c->buf[c->cur], c->work, d_rho, d_u, d_p, c->args, c->stream);
+  cudaError_t e = lbm3::d_fields_any(c->N, c->red, c->buf[c->cur], c->work, d_rho, d_u, d_p, c->args, c->stream);
   if (e == cudaSuccess && !on_device) {
     if (rho)
       e = cudaMemcpyAsync(rho, d_rho, static_cast<size_t>(c->N) * NN * sizeof(double), cudaMemcpyDeviceToHost,
@@ -707,10 +949,14 @@ lbm3_status lbm3d_mass(lbm3d_ctx* c, double* mass, double* mom) {
   if (!c) return LBM3_EINVAL;
   if (!c->state_set) return dfail(c, LBM3_ESTATE, "lbm3d_mass: state not set");
   const int planes = lbm3::Q3 * c->N;
-  lbm3::d_plane_sum_kernel<<<dim3(lbm3::kSumBlocks, planes), lbm3::kSumThreads, 0, c->stream>>>(
-      c->buf[c->cur], nodes(c), c->sums);
+  cudaError_t e;
+  const float* src = stored_populations(c, &e);
+  if (e == cudaSuccess) {
+    lbm3::d_plane_sum_kernel<<<dim3(lbm3::kSumBlocks, planes), lbm3::kSumThreads, 0, c->stream>>>(src, nodes(c),
+                                                                                                   c->sums);
+    e = cudaGetLastError();
+  }
   std::vector<double> h(static_cast<size_t>(planes) * lbm3::kSumBlocks);
-  cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h.data(), c->sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

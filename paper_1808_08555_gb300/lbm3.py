@@ -693,7 +693,7 @@ class lbm3d_params(ctypes.Structure):
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("nfluids", ctypes.c_int32),
         ("tau", ctypes.c_void_p), ("rho0", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
         ("beta0", ctypes.c_double), ("beta_form", ctypes.c_int32), ("recolor_form", ctypes.c_int32),
-        ("normal_delta", ctypes.c_double),
+        ("normal_delta", ctypes.c_double), ("storage", ctypes.c_int32),
     ]
 
 
@@ -723,10 +723,12 @@ class D3Q19Simulation:
     """N-fluid simulation on the D3Q19 lattice (include/lbm3.h, lbm3d_*) on
     the current device and torch's current stream.  sigma: (N, N) symmetric
     tension matrix with a zero diagonal; tau, rho0: length N.  Densities are
-    (N, nz, ny, nx), populations (N, 19, nz, ny, nx), post-streaming."""
+    (N, nz, ny, nx), populations (N, 19, nz, ny, nx), post-streaming.
+    storage: FP32 (populations) or REDUCED (phi_k, f^dagger_i, V_k per node;
+    the same results, bit for bit)."""
 
     def __init__(self, nx: int, ny: int, nz: int, sigma, tau, rho0=None, beta0: float = 0.7, beta_form: int = 0,
-                 recolor_form: int = RECOLOR_COSINE, normal_delta: float = 0.1):
+                 recolor_form: int = RECOLOR_COSINE, normal_delta: float = 0.1, storage: int = FP32):
         import torch
 
         self.sigma = np.ascontiguousarray(sigma, dtype=np.float64)
@@ -739,6 +741,7 @@ class D3Q19Simulation:
         p.tau, p.rho0, p.sigma = self.tau.ctypes.data, self.rho0.ctypes.data, self.sigma.ctypes.data
         p.beta0, p.beta_form, p.recolor_form, p.normal_delta = float(beta0), int(beta_form), int(recolor_form), \
             float(normal_delta)
+        p.storage = int(storage)
         self.ctx = ctypes.c_void_p()
         self.stream = torch.cuda.current_stream()
         s = _load_d().lbm3d_create(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.ctx))

@@ -46,9 +46,10 @@ def test_params_struct_layout_matches_header():
     # lbm3n_params: 3 int32, 3 pointers, beta0, 2 int32, normal_delta
     assert ctypes.sizeof(L.lbm3n_params) == 64 and L.lbm3n_params.tau.offset == 16
     assert L.lbm3n_params.normal_delta.offset == 56
-    # lbm3d_params: 4 int32, 3 pointers, beta0, 2 int32, normal_delta
-    assert ctypes.sizeof(L.lbm3d_params) == 64 and L.lbm3d_params.tau.offset == 16
+    # lbm3d_params: 4 int32, 3 pointers, beta0, 2 int32, normal_delta, storage
+    assert ctypes.sizeof(L.lbm3d_params) == 72 and L.lbm3d_params.tau.offset == 16
     assert L.lbm3d_params.beta0.offset == 40 and L.lbm3d_params.normal_delta.offset == 56
+    assert L.lbm3d_params.storage.offset == 64
 
 
 @pytest.mark.parametrize("kw", [
@@ -129,7 +130,8 @@ def _params_nd(cls, dims, n=3, **kw):
 
 @pytest.mark.parametrize("kw", [dict(nfluids=1), dict(nfluids=5), dict(nz=0), dict(ny=70000), dict(nz=70000),
                                 dict(asym=True), dict(tau0=0.5), dict(beta0=0.0), dict(beta_form=2),
-                                dict(recolor_form=-1), dict(normal_delta=2.0)])
+                                dict(recolor_form=-1), dict(normal_delta=2.0), dict(storage=1), dict(storage=2),
+                                dict(storage=4)])
 def test_d3q19_create_validates_on_the_host(lib, kw):
     """lbm3d_create rejects invalid parameters before any CUDA call."""
     n = 3 if kw.get("nfluids", 3) in (1, 5) else kw.get("nfluids", 3)
