@@ -469,13 +469,15 @@ def run_janus(args):
 
 
 def run_nphase(args):
-    """N fluids (the first N-fluid path, three kernels per step): four fluids
-    in a nested droplet on an n x n grid (default 2048^2; radii 3n/8, n/4,
-    n/8), tensions 0.01 / 0.008 / 0.006 between neighbouring layers and 0.012
-    otherwise, tau = (1.0, 0.8, 0.9, 1.2).  Algorithmic bytes per node update
-    are the state's, 2 x 9N x 4 (288 B at N = 4); the three kernels also move
-    their intermediates through HBM (written once, read by the next kernel;
-    the stencil reads from L2)."""
+    """N fluids (three kernels per step): four fluids in a nested droplet on
+    an n x n grid (default 2048^2; radii 3n/8, n/4, n/8), tensions 0.01 /
+    0.008 / 0.006 between neighbouring layers and 0.012 otherwise, tau =
+    (1.0, 0.8, 0.9, 1.2), in the reduced state (the headline) and with FP32
+    populations (bit-identical trajectories); --storage restricts the run to
+    one form.  Algorithmic bytes per node update are the state's: 2 x 9N x 4 =
+    288 B for the populations, 2 x (3N + 9) x 4 = 168 B for the reduced state
+    at N = 4; the three kernels also move their intermediates through HBM
+    (written once, read by the next kernel; the stencil reads from L2)."""
     import torch
 
     from paper_1808_08555_gb300 import build as B
@@ -493,30 +495,42 @@ def run_nphase(args):
     np.fill_diagonal(sig, 0.0)
     for (k, l, v) in ((0, 1, 0.01), (1, 2, 0.008), (2, 3, 0.006)):
         sig[k, l] = sig[l, k] = v
-    sim = L.NSimulation(n, n, sig, tau=(1.0, 0.8, 0.9, 1.2))
-    sim.init(rho)
-    sim.step(args.warmup)
-    s = sim.stream
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(s)
-    sim.step(args.steps)
-    e1.record(s)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    m, _ = sim.mass()
-    sim.close()
-    mlups = n * n / ms / 1e3
+    storage = getattr(args, "storage", "both")
+    order = ["reduced", "fp32"] if storage == "both" else [storage]
     peak, peak_kind = hbm_peak()
-    bpn = 2 * 9 * 4 * 4
-    return {"metric": "D2Q9 MLUPS, four fluids (N-fluid path)", "value": round(mlups, 1), "unit": "MLUPS",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
+    forms, masses = {}, {}
+    for name in order:
+        sim = L.NSimulation(n, n, sig, tau=(1.0, 0.8, 0.9, 1.2), storage=L.REDUCED if name == "reduced" else L.FP32)
+        sim.init(rho)
+        sim.step(args.warmup)
+        s = sim.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        sim.step(args.steps)
+        e1.record(s)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        masses[name] = [float(v) for v in sim.mass()[0]]
+        sim.close()
+        mlups = n * n / ms / 1e3
+        bpn = 2 * (3 * 4 + 9) * 4 if name == "reduced" else 2 * 9 * 4 * 4
+        forms[name] = {"MLUPS": round(mlups, 1), "ms_per_step": round(ms, 5), "bytes_per_node": bpn,
+                       "achieved_GBs": round(bpn * mlups / 1e3, 1),
+                       "frac": round(bpn * mlups * 1e6 / (peak * 1e9), 4)}
+    head = forms[order[0]]
+    checks = {"mass": masses[order[0]]}
+    if len(masses) == 2:
+        checks["same_masses_both_forms"] = masses["reduced"] == masses["fp32"]
+    return {"metric": "D2Q9 MLUPS, four fluids (N-fluid path)", "value": head["MLUPS"], "unit": "MLUPS",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"four-fluid nested droplet {n}x{n}, radii {3 * n // 8}/{n // 4}/{n // 8}"},
-            "roofline": {"bound": "hbm", "achieved": round(bpn * mlups / 1e3, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(bpn * mlups * 1e6 / (peak * 1e9), 4), "traffic": None, "bytes_per_node": bpn,
+            "config": {"workload": f"four-fluid nested droplet {n}x{n}, radii {3 * n // 8}/{n // 4}/{n // 8}",
+                       "form": order[0] + (" (headline); fp32 populations in 'forms'" if len(order) == 2 else "")},
+            "roofline": {"bound": "hbm", "achieved": head["achieved_GBs"], "peak": peak, "unit": "GB/s",
+                         "frac": head["frac"], "traffic": None, "bytes_per_node": head["bytes_per_node"],
                          "kernel": "n_density + n_tension + n_collide kernels (N = 4)", "peak_source": peak_kind},
-            "checks": {"mass": [float(v) for v in m]}, "gpu_launches": 3 * args.steps}
+            "forms": forms, "checks": checks, "gpu_launches": 3 * args.steps * len(order)}
 
 
 def run_d3q19(args):
@@ -798,7 +812,7 @@ def main():
     ap.add_argument("--horizon", type=int, default=2000,
                     help="adjoint workload: steps of the differentiated run (2000 is the workload; fewer for profiling)")
     ap.add_argument("--storage", default="both", choices=["both", "fp32", "reduced"],
-                    help="compound, sweep and d3q19 workloads: state storage (both: the reduced form as the headline and the "
+                    help="compound, sweep, nphase and d3q19 workloads: state storage (both: the reduced form as the headline and the "
                          "plain FP32 form beside it; fp32: 27 populations only; reduced: phi_k, f^dagger_i, V_k only)")
     ap.add_argument("--size", type=int, default=None,
                     help="grid edge (default: 2048 compound, 4096 janus, 256 adjoint); other edges scale the "

@@ -380,7 +380,14 @@ lbm3_status lbm3_mass_noalloc(const float* dev_f, int32_t nx, int32_t ny, void* 
  * post-streaming) as for the three-fluid calls; the state is FP32.  Any
  * invalid parameter gives LBM3_EINVAL from lbm3n_create.  The context
  * allocates its two population buffers, the intermediates
- * ((N + 13 + N (N - 1)) nx ny floats) and an FP64 staging area. */
+ * ((N + 13 + N (N - 1)) nx ny floats) and an FP64 staging area.
+ * storage LBM3_REDUCED keeps, per node, the colour fractions phi_k, the
+ * recolouring vectors V_k and the post-collision total distribution
+ * f^dagger_i (3 N + 9 values instead of 9 N, in the same buffers), as
+ * LBM3_REDUCED does for lbm3_ctx: results are bit-identical to LBM3_FP32; a
+ * state set from populations is held as populations until the next step, and
+ * lbm3n_populations / lbm3n_mass expand the reduced state into the idle
+ * buffer first. */
 typedef struct lbm3n_ctx lbm3n_ctx;
 typedef struct {
   int32_t nx, ny, nfluids;
@@ -391,6 +398,7 @@ typedef struct {
   int32_t beta_form;    /* 0: the N-fluid form above; 1: Eq. fu */
   int32_t recolor_form; /* as lbm3_recolor_form */
   double normal_delta;  /* as lbm3_params.normal_delta */
+  int32_t storage;      /* LBM3_FP32 or LBM3_REDUCED (below) */
 } lbm3n_params;
 lbm3_status lbm3n_create(const lbm3n_params* p, void* cuda_stream, lbm3n_ctx** out);
 /* rest equilibrium per colour from host densities (rho_k >= 0) */

@@ -18,8 +18,9 @@
 // per-node array stays in registers.
 //
 // Layout: populations [N][9][ny][nx] FP32, unpadded, periodic by index
-// arithmetic; intermediates phi [N][ny][nx], rho [ny][nx], f_i [9][ny][nx],
-// T [3][ny][nx], normals [P][2][ny][nx] with P = N(N-1)/2.
+// arithmetic, or the reduced state below; intermediates phi [N][ny][nx], rho
+// [ny][nx], f_i [9][ny][nx], T [3][ny][nx], normals [P][2][ny][nx] with
+// P = N(N-1)/2.
 
 #include <cmath>
 #include <cstdio>
@@ -55,7 +56,80 @@ __host__ __device__ constexpr int pair_index(int k, int l, int n) {  // k < l
 
 __device__ __forceinline__ int wrapn(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
+// ---------------------------------------------------------- reduced state
+// Collision (Eqs. 1-3, 5) uses only the total distribution and the colour
+// densities, and the recolouring of Eq. 6 writes
+//   f^ddagger_{i,k} = phi_k f^dagger_i + w'_i e_i . V_k,
+//   V_k = sum_{l != k} beta_kl (rho_k rho_l / rho) n_kl,
+// so a node's 9 N outputs are fixed by phi_k, V_k and f^dagger_i: 3 N + 9
+// values.  Layout inside a population buffer, by component: the fractions
+// phi_1..N, then the x components V_1x..V_Nx, then the y components, each as
+// kCK vector planes [ny][nx] of kCW floats (float2 for N = 2, float4 above,
+// unused slots zero), then 9 float planes f^dagger_i.  A pull from direction
+// i loads the fractions and only the components e_i has.  All N vectors V_k
+// are kept although they sum to zero, so that every population is rebuilt
+// from exactly the values the collision used.
 template <int N>
+constexpr int kCW = N <= 2 ? 2 : 4;  // floats per stored vector
+template <int N>
+constexpr int kCK = (N + kCW<N> - 1) / kCW<N>;  // vectors per component
+template <int N>
+constexpr size_t kRedVec = static_cast<size_t>(3) * kCK<N> * kCW<N>;  // floats per node before the f^dagger planes
+
+template <int N>
+__device__ __forceinline__ void comp_store(float* __restrict__ g, size_t NN, size_t n, int c, const float (&v)[N]) {
+#pragma unroll
+  for (int j = 0; j < kCK<N>; ++j) {
+    const size_t m = (static_cast<size_t>(c) * kCK<N> + j) * NN + n;
+    float e[kCW<N>];
+#pragma unroll
+    for (int q = 0; q < kCW<N>; ++q) e[q] = kCW<N> * j + q < N ? v[(kCW<N> * j + q) % N] : 0.0f;
+    if constexpr (kCW<N> == 2)
+      reinterpret_cast<float2*>(g)[m] = make_float2(e[0], e[1]);
+    else
+      reinterpret_cast<float4*>(g)[m] = make_float4(e[0], e[1], e[2], e[3]);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void comp_load(const float* __restrict__ g, size_t NN, size_t n, int c, float (&v)[N]) {
+#pragma unroll
+  for (int j = 0; j < kCK<N>; ++j) {
+    const size_t m = (static_cast<size_t>(c) * kCK<N> + j) * NN + n;
+    float e[4];
+    if constexpr (kCW<N> == 2) {
+      const float2 w = reinterpret_cast<const float2*>(g)[m];
+      e[0] = w.x;
+      e[1] = w.y;
+    } else {
+      const float4 w = reinterpret_cast<const float4*>(g)[m];
+      e[0] = w.x;
+      e[1] = w.y;
+      e[2] = w.z;
+      e[3] = w.w;
+    }
+#pragma unroll
+    for (int q = 0; q < kCW<N>; ++q)
+      if (kCW<N> * j + q < N) v[(kCW<N> * j + q) % N] = e[q];
+  }
+}
+
+// e_i . V over the nonzero components of e_i
+__device__ __forceinline__ float edot2(int i, float vx, float vy) {
+  const float a = ex(i) > 0 ? vx : -vx;
+  const float b = ey(i) > 0 ? vy : -vy;
+  if (ex(i) != 0) return ey(i) != 0 ? __fadd_rn(a, b) : a;
+  return ey(i) != 0 ? b : 0.0f;
+}
+
+// Eq. 6 for one population, f^ddagger = phi_k f^dagger_i + w'_i (e_i . V_k),
+// in explicitly rounded operations: the collision's store and the reduced
+// state's rebuild give the same bits
+__device__ __forceinline__ float recolour2(float phk, float fdi, float wr, float ev) {
+  return __fmaf_rn(wr, ev, __fmul_rn(phk, fdi));
+}
+
+template <int N, bool RED>
 __global__ void __launch_bounds__(kNThreads) n_density_kernel(const float* __restrict__ f, float* __restrict__ phi,
                                                               float* __restrict__ rho_out, float* __restrict__ fi,
                                                               NArgs a) {
@@ -69,19 +143,49 @@ __global__ void __launch_bounds__(kNThreads) n_density_kernel(const float* __res
     const size_t n = static_cast<size_t>(y) * nx + x;
     float r[N];
     float tot[9];
+    if constexpr (RED) {
+      // each pulled population rebuilt from its source node, then the sums of
+      // the population form in the same order (the same bits)
+      const float* __restrict__ fd = f + kRedVec<N> * NN;
+      float fdv[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) tot[i] = 0.0f;
+      for (int i = 0; i < 9; ++i)
+        fdv[i] = fd[static_cast<size_t>(i) * NN + static_cast<size_t>(wrapn(y - ey(i), ny)) * nx + wrapn(x - ex(i), nx)];
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      float s = 0.0f;
+      for (int k = 0; k < N; ++k) r[k] = 0.0f;
 #pragma unroll
       for (int i = 0; i < 9; ++i) {
         const size_t src = static_cast<size_t>(wrapn(y - ey(i), ny)) * nx + wrapn(x - ex(i), nx);
-        const float v = f[(static_cast<size_t>(k) * 9 + i) * NN + src];  // Eq. 30 as a pull
-        s += v;
-        tot[i] += v;
+        float sp[N], svx[N], svy[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) svx[k] = svy[k] = 0.0f;
+        comp_load<N>(f, NN, src, 0, sp);
+        if (ex(i) != 0) comp_load<N>(f, NN, src, 1, svx);
+        if (ey(i) != 0) comp_load<N>(f, NN, src, 2, svy);
+        float t = 0.0f;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          const float v = recolour2(sp[k], fdv[i], a.wrec[i], edot2(i, svx[k], svy[k]));
+          r[k] += v;
+          t += v;
+        }
+        tot[i] = t;
       }
-      r[k] = s;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) tot[i] = 0.0f;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        float s = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          const size_t src = static_cast<size_t>(wrapn(y - ey(i), ny)) * nx + wrapn(x - ex(i), nx);
+          const float v = f[(static_cast<size_t>(k) * 9 + i) * NN + src];  // Eq. 30 as a pull
+          s += v;
+          tot[i] += v;
+        }
+        r[k] = s;
+      }
     }
     float rho = 0.0f, rmax = -1.0f;
     int kmax = 0;
@@ -169,7 +273,7 @@ __global__ void __launch_bounds__(kNThreads) n_tension_kernel(const float* __res
   }
 }
 
-template <int N>
+template <int N, bool RED>
 __global__ void __launch_bounds__(kNThreads) n_collide_kernel(const float* __restrict__ phi,
                                                               const float* __restrict__ rho_in,
                                                               const float* __restrict__ fi,
@@ -249,13 +353,47 @@ __global__ void __launch_bounds__(kNThreads) n_collide_kernel(const float* __res
         Vx[l] -= amp * nxv;
         Vy[l] -= amp * nyv;
       }
-    // Eq. 6, stored at the node (the next step's pull streams it, Eq. 30)
+    // Eq. 6, stored at the node (the next step's pull streams it, Eq. 30), as
+    // 9 N populations or as the reduced state
+    if constexpr (RED) {
+      comp_store<N>(fout, NN, n, 0, ph);
+      comp_store<N>(fout, NN, n, 1, Vx);
+      comp_store<N>(fout, NN, n, 2, Vy);
+      float* __restrict__ fdo = fout + kRedVec<N> * NN;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) fdo[static_cast<size_t>(i) * NN + n] = fd[i];
+    } else {
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+          fout[(static_cast<size_t>(k) * 9 + i) * NN + n] = recolour2(ph[k], fd[i], a.wrec[i], edot2(i, Vx[k], Vy[k]));
+    }
+  }
+}
+
+// the reduced state g expanded into the populations it stands for, stored at
+// the producing node
+template <int N>
+__global__ void __launch_bounds__(kNThreads) n_expand_kernel(const float* __restrict__ g, float* __restrict__ f,
+                                                             NArgs a) {
+  const int nx = a.nx, ny = a.ny;
+  const size_t NN = static_cast<size_t>(nx) * ny;
+  const int y = static_cast<int>(blockIdx.x);
+  const int x = static_cast<int>(blockIdx.y) * kNThreads + static_cast<int>(threadIdx.x);
+  if (x >= nx) return;
+  const size_t n = static_cast<size_t>(y) * nx + x;
+  float ph[N], Vx[N], Vy[N];
+  comp_load<N>(g, NN, n, 0, ph);
+  comp_load<N>(g, NN, n, 1, Vx);
+  comp_load<N>(g, NN, n, 2, Vy);
+  const float* __restrict__ fd = g + kRedVec<N> * NN;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const float fdi = fd[static_cast<size_t>(i) * NN + n];
 #pragma unroll
     for (int k = 0; k < N; ++k)
-#pragma unroll
-      for (int i = 0; i < 9; ++i)
-        fout[(static_cast<size_t>(k) * 9 + i) * NN + n] =
-            ph[k] * fd[i] + a.wrec[i] * (ex(i) * Vx[k] + ey(i) * Vy[k]);
+      f[(static_cast<size_t>(k) * 9 + i) * NN + n] = recolour2(ph[k], fdi, a.wrec[i], edot2(i, Vx[k], Vy[k]));
   }
 }
 
@@ -310,8 +448,11 @@ int grid_of(size_t NN) {
   return static_cast<int>(g > 4096 ? 4096 : (g < 1 ? 1 : g));
 }
 
+// one step from the state fin (populations, or the reduced state with
+// in_red) to fout (the reduced state with out_red)
 template <int N>
-cudaError_t n_step(const float* fin, float* fout, float* work, const NArgs& a, cudaStream_t s) {
+cudaError_t n_step(const float* fin, float* fout, float* work, const NArgs& a, cudaStream_t s, bool in_red,
+                   bool out_red) {
   const size_t NN = static_cast<size_t>(a.nx) * a.ny;
   float* phi = work;
   float* rho = phi + N * NN;
@@ -319,13 +460,19 @@ cudaError_t n_step(const float* fin, float* fout, float* work, const NArgs& a, c
   float* T = fi + 9 * NN;
   float* nrm = T + 3 * NN;
   const dim3 g(static_cast<unsigned>(a.ny), static_cast<unsigned>((a.nx + kNThreads - 1) / kNThreads));
-  n_density_kernel<N><<<g, kNThreads, 0, s>>>(fin, phi, rho, fi, a);
+  if (in_red)
+    n_density_kernel<N, true><<<g, kNThreads, 0, s>>>(fin, phi, rho, fi, a);
+  else
+    n_density_kernel<N, false><<<g, kNThreads, 0, s>>>(fin, phi, rho, fi, a);
   n_tension_kernel<N><<<g, kNThreads, 0, s>>>(phi, rho, T, nrm, a);
-  n_collide_kernel<N><<<g, kNThreads, 0, s>>>(phi, rho, fi, T, nrm, fout, a);
+  if (out_red)
+    n_collide_kernel<N, true><<<g, kNThreads, 0, s>>>(phi, rho, fi, T, nrm, fout, a);
+  else
+    n_collide_kernel<N, false><<<g, kNThreads, 0, s>>>(phi, rho, fi, T, nrm, fout, a);
   return cudaGetLastError();
 }
 
-template <int N>
+template <int N, bool RED>
 cudaError_t n_fields(const float* fin, float* work, double* rho, double* ux, double* uy, double* p, const NArgs& a,
                      cudaStream_t s) {
   const size_t NN = static_cast<size_t>(a.nx) * a.ny;
@@ -335,33 +482,53 @@ cudaError_t n_fields(const float* fin, float* work, double* rho, double* ux, dou
   float* T = fi + 9 * NN;
   float* nrm = T + 3 * NN;
   const dim3 g(static_cast<unsigned>(a.ny), static_cast<unsigned>((a.nx + kNThreads - 1) / kNThreads));
-  n_density_kernel<N><<<g, kNThreads, 0, s>>>(fin, phi, rh, fi, a);
+  n_density_kernel<N, RED><<<g, kNThreads, 0, s>>>(fin, phi, rh, fi, a);
   n_tension_kernel<N><<<g, kNThreads, 0, s>>>(phi, rh, T, nrm, a);
   n_fields_kernel<N><<<g, kNThreads, 0, s>>>(phi, rh, fi, T, rho, ux, uy, p, a);
   return cudaGetLastError();
 }
 
-cudaError_t n_fields_any(int N, const float* fin, float* work, double* rho, double* ux, double* uy, double* p,
+template <int N>
+cudaError_t n_fields_red(bool red, const float* fin, float* work, double* rho, double* ux, double* uy, double* p,
                          const NArgs& a, cudaStream_t s) {
+  return red ? n_fields<N, true>(fin, work, rho, ux, uy, p, a, s) : n_fields<N, false>(fin, work, rho, ux, uy, p, a, s);
+}
+
+cudaError_t n_fields_any(int N, bool red, const float* fin, float* work, double* rho, double* ux, double* uy,
+                         double* p, const NArgs& a, cudaStream_t s) {
   switch (N) {
-    case 2: return n_fields<2>(fin, work, rho, ux, uy, p, a, s);
-    case 3: return n_fields<3>(fin, work, rho, ux, uy, p, a, s);
-    case 4: return n_fields<4>(fin, work, rho, ux, uy, p, a, s);
-    case 5: return n_fields<5>(fin, work, rho, ux, uy, p, a, s);
-    case 6: return n_fields<6>(fin, work, rho, ux, uy, p, a, s);
+    case 2: return n_fields_red<2>(red, fin, work, rho, ux, uy, p, a, s);
+    case 3: return n_fields_red<3>(red, fin, work, rho, ux, uy, p, a, s);
+    case 4: return n_fields_red<4>(red, fin, work, rho, ux, uy, p, a, s);
+    case 5: return n_fields_red<5>(red, fin, work, rho, ux, uy, p, a, s);
+    case 6: return n_fields_red<6>(red, fin, work, rho, ux, uy, p, a, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t n_step_any(int N, const float* fin, float* fout, float* work, const NArgs& a, cudaStream_t s) {
+cudaError_t n_step_any(int N, const float* fin, float* fout, float* work, const NArgs& a, cudaStream_t s, bool in_red,
+                       bool out_red) {
   switch (N) {
-    case 2: return n_step<2>(fin, fout, work, a, s);
-    case 3: return n_step<3>(fin, fout, work, a, s);
-    case 4: return n_step<4>(fin, fout, work, a, s);
-    case 5: return n_step<5>(fin, fout, work, a, s);
-    case 6: return n_step<6>(fin, fout, work, a, s);
+    case 2: return n_step<2>(fin, fout, work, a, s, in_red, out_red);
+    case 3: return n_step<3>(fin, fout, work, a, s, in_red, out_red);
+    case 4: return n_step<4>(fin, fout, work, a, s, in_red, out_red);
+    case 5: return n_step<5>(fin, fout, work, a, s, in_red, out_red);
+    case 6: return n_step<6>(fin, fout, work, a, s, in_red, out_red);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t n_expand_any(int N, const float* g, float* f, const NArgs& a, cudaStream_t s) {
+  const dim3 grid(static_cast<unsigned>(a.ny), static_cast<unsigned>((a.nx + kNThreads - 1) / kNThreads));
+  switch (N) {
+    case 2: n_expand_kernel<2><<<grid, kNThreads, 0, s>>>(g, f, a); break;
+    case 3: n_expand_kernel<3><<<grid, kNThreads, 0, s>>>(g, f, a); break;
+    case 4: n_expand_kernel<4><<<grid, kNThreads, 0, s>>>(g, f, a); break;
+    case 5: n_expand_kernel<5><<<grid, kNThreads, 0, s>>>(g, f, a); break;
+    case 6: n_expand_kernel<6><<<grid, kNThreads, 0, s>>>(g, f, a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 // intermediates, rounded up to 64 floats so that the FP64 staging behind them
@@ -449,6 +616,8 @@ struct lbm3n_ctx {
   double* sums = nullptr;
   int cur = 0;
   bool state_set = false;
+  bool reduced = false;  // the storage form of the steps (LBM3_REDUCED)
+  bool red = false;      // buf[cur] holds the reduced state (else populations)
   int64_t t = 0;
   lbm3::NArgs args{};
   std::string msg;
@@ -465,6 +634,15 @@ lbm3_status ncuda(lbm3n_ctx* c, cudaError_t e, const char* where) {
   return nfail(c, LBM3_ECUDA, std::string("lbm3n: ") + where + ": " + cudaGetErrorString(e));
 }
 
+// the current state as stored populations: buf[cur] itself, or the reduced
+// state expanded into the idle buffer
+const float* stored_populations(lbm3n_ctx* c, cudaError_t* e) {
+  *e = cudaSuccess;
+  if (!c->red) return c->buf[c->cur];
+  *e = lbm3::n_expand_any(c->N, c->buf[c->cur], c->buf[c->cur ^ 1], c->args, c->stream);
+  return c->buf[c->cur ^ 1];
+}
+
 }  // namespace
 
 extern "C" {
@@ -477,7 +655,8 @@ lbm3_status lbm3n_create(const lbm3n_params* p, void* cuda_stream, lbm3n_ctx** o
   if (N < 2 || N > lbm3::kMaxFluids || p->nx < 1 || p->ny < 1) return LBM3_EINVAL;
   if (static_cast<double>(p->nx) * p->ny * 9 * N >= 2147483648.0) return LBM3_EINVAL;
   if (!(p->beta0 > 0.0 && p->beta0 <= 1.0) || p->beta_form < 0 || p->beta_form > 1 || p->recolor_form < 0 ||
-      p->recolor_form > 1 || !(p->normal_delta >= 0.0 && p->normal_delta <= 1.0))
+      p->recolor_form > 1 || !(p->normal_delta >= 0.0 && p->normal_delta <= 1.0) ||
+      (p->storage != LBM3_FP32 && p->storage != LBM3_REDUCED))
     return LBM3_EINVAL;
   for (int k = 0; k < N; ++k) {
     if (!(p->tau[k] > 0.5) || !(p->rho0[k] > 0.0)) return LBM3_EINVAL;
@@ -492,6 +671,7 @@ lbm3_status lbm3n_create(const lbm3n_params* p, void* cuda_stream, lbm3n_ctx** o
   c->nx = p->nx;
   c->ny = p->ny;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->reduced = p->storage == LBM3_REDUCED;
   cudaGetDevice(&c->device);
   lbm3::NArgs& a = c->args;
   a.nx = p->nx;
@@ -559,6 +739,7 @@ lbm3_status lbm3n_set_populations(lbm3n_ctx* c, const double* f, int on_device) 
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return ncuda(c, e, "lbm3n_set_populations");
   c->state_set = true;
+  c->red = false;
   c->t = 0;
   return LBM3_OK;
 }
@@ -581,6 +762,7 @@ lbm3_status lbm3n_init(lbm3n_ctx* c, const double* rho, int on_device) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return ncuda(c, e, "lbm3n_init");
   c->state_set = true;
+  c->red = false;
   c->t = 0;
   return LBM3_OK;
 }
@@ -590,9 +772,11 @@ lbm3_status lbm3n_step(lbm3n_ctx* c, int64_t n) {
   if (n < 0) return nfail(c, LBM3_EINVAL, "lbm3n_step: n < 0");
   if (!c->state_set) return nfail(c, LBM3_ESTATE, "lbm3n_step: state not set");
   for (int64_t s = 0; s < n; ++s) {
-    const cudaError_t e = lbm3::n_step_any(c->N, c->buf[c->cur], c->buf[c->cur ^ 1], c->work, c->args, c->stream);
+    const cudaError_t e = lbm3::n_step_any(c->N, c->buf[c->cur], c->buf[c->cur ^ 1], c->work, c->args, c->stream,
+                                           c->red, c->reduced);
     if (e != cudaSuccess) return ncuda(c, e, "lbm3n_step");
     c->cur ^= 1;
+    c->red = c->reduced;
     c->t += 1;
   }
   return LBM3_OK;
@@ -605,8 +789,12 @@ lbm3_status lbm3n_populations(lbm3n_ctx* c, double* f, int on_device) {
   const size_t NN = static_cast<size_t>(c->nx) * c->ny;
   double* dst = on_device ? f : reinterpret_cast<double*>(c->work + lbm3::work_floats(c->N, NN));
   dim3 grid(lbm3::grid_of(NN), 9 * c->N);
-  lbm3::n_get_kernel<<<grid, lbm3::kNThreads, 0, c->stream>>>(c->buf[c->cur], dst, c->nx, c->ny);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  const float* src = stored_populations(c, &e);
+  if (e == cudaSuccess) {
+    lbm3::n_get_kernel<<<grid, lbm3::kNThreads, 0, c->stream>>>(src, dst, c->nx, c->ny);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess && !on_device)
     e = cudaMemcpyAsync(f, dst, static_cast<size_t>(9) * c->N * NN * sizeof(double), cudaMemcpyDeviceToHost,
                         c->stream);
@@ -625,7 +813,8 @@ lbm3_status lbm3n_fields(lbm3n_ctx* c, double* rho, double* ux, double* uy, doub
   double* d_ux = ux ? (on_device ? ux : staging + static_cast<size_t>(c->N) * NN) : nullptr;
   double* d_uy = uy ? (on_device ? uy : staging + static_cast<size_t>(c->N + 1) * NN) : nullptr;
   double* d_p = p ? (on_device ? p : staging + static_cast<size_t>(c->N + 2) * NN) : nullptr;
-  cudaError_t e = lbm3::n_fields_any(c->N, c->buf[c->cur], c->work, d_rho, d_ux, d_uy, d_p, c->args, c->stream);
+  cudaError_t e =
+      lbm3::n_fields_any(c->N, c->red, c->buf[c->cur], c->work, d_rho, d_ux, d_uy, d_p, c->args, c->stream);
   if (e == cudaSuccess && !on_device) {
     if (rho)
       e = cudaMemcpyAsync(rho, d_rho, static_cast<size_t>(c->N) * NN * sizeof(double), cudaMemcpyDeviceToHost,
@@ -643,10 +832,13 @@ lbm3_status lbm3n_mass(lbm3n_ctx* c, double* mass, double* mom) {
   if (!c) return LBM3_EINVAL;
   if (!c->state_set) return nfail(c, LBM3_ESTATE, "lbm3n_mass: state not set");
   const size_t NN = static_cast<size_t>(c->nx) * c->ny;
-  lbm3::n_plane_sum_kernel<<<9 * c->N, lbm3::kNThreads, 0, c->stream>>>(c->buf[c->cur], static_cast<int>(NN),
-                                                                          c->sums);
+  cudaError_t e;
+  const float* src = stored_populations(c, &e);
+  if (e == cudaSuccess) {
+    lbm3::n_plane_sum_kernel<<<9 * c->N, lbm3::kNThreads, 0, c->stream>>>(src, static_cast<int>(NN), c->sums);
+    e = cudaGetLastError();
+  }
   std::vector<double> h(static_cast<size_t>(9) * c->N);
-  cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h.data(), c->sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

@@ -586,7 +586,7 @@ class lbm3n_params(ctypes.Structure):
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nfluids", ctypes.c_int32),
         ("tau", ctypes.c_void_p), ("rho0", ctypes.c_void_p), ("sigma", ctypes.c_void_p),
         ("beta0", ctypes.c_double), ("beta_form", ctypes.c_int32), ("recolor_form", ctypes.c_int32),
-        ("normal_delta", ctypes.c_double),
+        ("normal_delta", ctypes.c_double), ("storage", ctypes.c_int32),
     ]
 
 
@@ -615,10 +615,12 @@ def _load_n():
 class NSimulation:
     """N-fluid simulation (include/lbm3.h, lbm3n_*) on the current device and
     torch's current stream.  sigma: (N, N) symmetric tension matrix with a
-    zero diagonal; tau, rho0: length N."""
+    zero diagonal; tau, rho0: length N.  storage: FP32 (populations) or
+    REDUCED (phi_k, V_k, f^dagger_i per node; the same results, bit for
+    bit)."""
 
     def __init__(self, nx: int, ny: int, sigma, tau, rho0=None, beta0: float = 0.7, beta_form: int = 0,
-                 recolor_form: int = RECOLOR_COSINE, normal_delta: float = 0.1):
+                 recolor_form: int = RECOLOR_COSINE, normal_delta: float = 0.1, storage: int = FP32):
         import torch
 
         self.sigma = np.ascontiguousarray(sigma, dtype=np.float64)
@@ -631,6 +633,7 @@ class NSimulation:
         p.tau, p.rho0, p.sigma = self.tau.ctypes.data, self.rho0.ctypes.data, self.sigma.ctypes.data
         p.beta0, p.beta_form, p.recolor_form, p.normal_delta = float(beta0), int(beta_form), int(recolor_form), \
             float(normal_delta)
+        p.storage = int(storage)
         self.ctx = ctypes.c_void_p()
         self.stream = torch.cuda.current_stream()
         s = _load_n().lbm3n_create(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.ctx))

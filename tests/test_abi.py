@@ -43,9 +43,9 @@ def test_params_struct_layout_matches_header():
     assert L.lbm3_params.normal_delta.offset == 104
     # lbm3_interfaces: 31 doubles and an int32 flag word, padded to 8 bytes
     assert ctypes.sizeof(L.lbm3_interfaces) == 256 and L.lbm3_interfaces.flags.offset == 248
-    # lbm3n_params: 3 int32, 3 pointers, beta0, 2 int32, normal_delta
-    assert ctypes.sizeof(L.lbm3n_params) == 64 and L.lbm3n_params.tau.offset == 16
-    assert L.lbm3n_params.normal_delta.offset == 56
+    # lbm3n_params: 3 int32, 3 pointers, beta0, 2 int32, normal_delta, storage
+    assert ctypes.sizeof(L.lbm3n_params) == 72 and L.lbm3n_params.tau.offset == 16
+    assert L.lbm3n_params.normal_delta.offset == 56 and L.lbm3n_params.storage.offset == 64
     # lbm3d_params: 4 int32, 3 pointers, beta0, 2 int32, normal_delta, storage
     assert ctypes.sizeof(L.lbm3d_params) == 72 and L.lbm3d_params.tau.offset == 16
     assert L.lbm3d_params.beta0.offset == 40 and L.lbm3d_params.normal_delta.offset == 56
@@ -142,7 +142,8 @@ def test_d3q19_create_validates_on_the_host(lib, kw):
 
 
 @pytest.mark.parametrize("kw", [dict(nfluids=1), dict(nfluids=7), dict(ny=0), dict(asym=True), dict(tau0=0.5),
-                                dict(beta_form=2), dict(normal_delta=-0.1)])
+                                dict(beta_form=2), dict(normal_delta=-0.1), dict(storage=1), dict(storage=2),
+                                dict(storage=4)])
 def test_nfluid_create_validates_on_the_host(lib, kw):
     """lbm3n_create rejects invalid parameters before any CUDA call."""
     p, keep = _params_nd(L.lbm3n_params, {"nx": 8, "ny": 8}, n=3, **kw)

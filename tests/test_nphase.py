@@ -40,14 +40,23 @@ def sigma_of(n):
     return N.sigma_matrix(pairs, n)
 
 
-def run_both(L, p: N.NParams, f0, steps):
-    sim = L.NSimulation(p.nx, p.ny, p.sigma, p.tau, p.rho0, beta0=p.beta0, beta_form=p.beta_form,
-                        recolor_form=p.recolor_form, normal_delta=p.normal_delta)
+def sim_of(L, p: N.NParams, storage=0):
+    return L.NSimulation(p.nx, p.ny, p.sigma, p.tau, p.rho0, beta0=p.beta0, beta_form=p.beta_form,
+                         recolor_form=p.recolor_form, normal_delta=p.normal_delta, storage=storage)
+
+
+def run_gpu(L, p: N.NParams, f0, steps, storage=0):
+    sim = sim_of(L, p, storage)
     sim.set_populations(f0)
     sim.step(steps)
     fg = sim.populations()
     m, _ = sim.mass()
     sim.close()
+    return fg, m
+
+
+def run_both(L, p: N.NParams, f0, steps):
+    fg, m = run_gpu(L, p, f0, steps)
     return fg, N.run(p, f0.copy(), steps), m
 
 
@@ -117,6 +126,44 @@ def test_four_fluids_three_droplets_1000_steps(L):
     assert relerr(fg, fo) <= 1e-4
     m0 = f0.reshape(4, 9, -1).sum(axis=(1, 2))
     assert np.abs(m / m0 - 1).max() <= 1e-5
+    # the reduced state runs the same trajectory
+    fr, mr = run_gpu(L, p, f0, 1000, storage=L.REDUCED)
+    assert np.array_equal(fr, fg) and np.array_equal(mr, m)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
+@pytest.mark.parametrize("beta_form,recolor_form,delta", [(0, 0, 0.1), (1, 1, 0.0)])
+def test_reduced_state_is_bit_identical(L, n, beta_form, recolor_form, delta):
+    """The reduced state (phi_k, V_k, f^dagger_i per node, by component)
+    rebuilds every population from its source node with the operations the
+    population form stores it with, so both forms give the same bits:
+    populations, masses and fields after 1, 7 and 12 steps of random states
+    on a 300 x 6 grid (a ragged second block per row), readouts in between
+    (which expand the state into the idle buffer) leaving the trajectory
+    unchanged.  (Parity of the reduced form with the oracle: the 1000-step
+    case above.)"""
+    nx, ny = 300, 6
+    p = N.NParams(nx, ny, sigma=sigma_of(n), tau=tuple(0.6 + 0.15 * k for k in range(n)), rho0=(1.0,) * n,
+                  beta_form=beta_form, recolor_form=recolor_form, normal_delta=delta)
+    f0 = random_state(n, nx, ny, seed=40 + n)
+    a, b = sim_of(L, p), sim_of(L, p, storage=L.REDUCED)
+    for sim in (a, b):
+        sim.set_populations(f0)
+    for steps in (1, 6, 5):
+        for sim in (a, b):
+            sim.step(steps)
+        assert np.array_equal(a.populations(), b.populations())
+        ma, moa = a.mass()
+        mb, mob = b.mass()
+        assert np.array_equal(ma, mb) and np.array_equal(moa, mob)
+        fa, fb = a.fields(), b.fields()
+        for key in ("rho", "ux", "uy", "p"):
+            assert np.array_equal(fa[key], fb[key])
+    f1 = b.populations()
+    b.set_populations(f1)
+    assert np.array_equal(b.populations(), f1)
+    a.close()
+    b.close()
 
 
 def test_absent_fluid_gives_the_three_fluid_result(L):
