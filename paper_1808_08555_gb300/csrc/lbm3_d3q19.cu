@@ -195,10 +195,15 @@ __device__ __forceinline__ void density_node(const float* __restrict__ f, const 
 //   V_k = sum_{l != k} beta_kl (rho_k rho_l / rho) n_kl,
 // so a node's 19 N outputs are fixed by phi_k, f^dagger_i and V_k: 19 + 4 N
 // values (31 instead of 57 for three fluids).  Layout inside a population
-// buffer: N float4 planes [nz][ny][nx] holding (phi_1 .. phi_N, V_1x, V_1y,
-// V_1z, .., V_Nz) in that order, then 19 float planes f^dagger_i.  All N
-// vectors V_k are kept although they sum to zero, so that every population is
-// rebuilt from exactly the values the collision used.
+// buffer, by component: four vector planes [nz][ny][nx] of kCW3 floats
+// (float2 for N = 2, float4 above) holding the fractions phi_1..N, the x
+// components V_1x..V_Nx, the y and the z components, then the float planes
+// f^dagger_i.  A pull from direction i loads the source's fractions and only
+// the components that e_i has.  For N = 3 the fourth slot of the four vector
+// planes holds f^dagger of directions 0, 1, 3 and 5 (whose pulls load that
+// plane anyway), and 15 float planes the others.  All N vectors V_k are kept
+// although they sum to zero, so that every population is rebuilt from exactly
+// the values the collision used.
 
 // e_i . V over the nonzero components of e_i (at most two on D3Q19)
 __device__ __forceinline__ float edot(int i, float vx, float vy, float vz) {
@@ -218,36 +223,53 @@ __device__ __forceinline__ float recolour(float phk, float fdi, float wr, float 
 }
 
 template <int N>
-__device__ __forceinline__ void rec_store(float4* __restrict__ R, size_t n, size_t NN, const float (&ph)[N],
-                                          const float (&V)[N][3]) {
-  float r[4 * N];
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    r[k] = ph[k];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) r[N + 3 * k + c] = V[k][c];
-  }
-#pragma unroll
-  for (int j = 0; j < N; ++j) R[static_cast<size_t>(j) * NN + n] = make_float4(r[4 * j], r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+constexpr int kCW3 = N <= 2 ? 2 : 4;  // floats per vector plane
+template <int N>
+constexpr bool kSlot3 = N == 3;  // f^dagger of four directions in the spare slots
+// the vector plane whose spare slot holds f^dagger_i (N = 3), else -1
+__host__ __device__ constexpr int slot3(int i) { return i == 0 ? 0 : (i == 1 ? 1 : (i == 3 ? 2 : (i == 5 ? 3 : -1))); }
+template <int N>
+__host__ __device__ constexpr bool in_slot3(int i) { return kSlot3<N> && slot3(i) >= 0; }
+// the float plane of f^dagger_i (not in a slot)
+template <int N>
+__host__ __device__ constexpr int fd_plane3(int i) {
+  return kSlot3<N> ? i - (i > 0) - (i > 1) - (i > 3) - (i > 5) : i;
+}
+template <int N>
+__device__ __forceinline__ const float* fd_base3(const float* g, size_t NN) {
+  return g + static_cast<size_t>(4 * kCW3<N>) * NN;
 }
 
+// vector plane c (0: phi, 1..3: V_x, V_y, V_z) of node n: the N values and the
+// spare slot
 template <int N>
-__device__ __forceinline__ void rec_load(const float4* __restrict__ R, size_t n, size_t NN, float (&ph)[N],
-                                         float (&V)[N][3]) {
-  float r[4 * N];
+__device__ __forceinline__ void cstore3(float* __restrict__ g, size_t NN, size_t n, int c, const float (&v)[N],
+                                        float spare) {
+  const size_t m = static_cast<size_t>(c) * NN + n;
+  if constexpr (N == 2) {
+    reinterpret_cast<float2*>(g)[m] = make_float2(v[0], v[1]);
+  } else {
+    float e[4];
 #pragma unroll
-  for (int j = 0; j < N; ++j) {
-    const float4 v = R[static_cast<size_t>(j) * NN + n];
-    r[4 * j] = v.x;
-    r[4 * j + 1] = v.y;
-    r[4 * j + 2] = v.z;
-    r[4 * j + 3] = v.w;
+    for (int q = 0; q < 4; ++q) e[q] = q < N ? v[q % N] : spare;
+    reinterpret_cast<float4*>(g)[m] = make_float4(e[0], e[1], e[2], e[3]);
   }
+}
+template <int N>
+__device__ __forceinline__ void cload3(const float* __restrict__ g, size_t NN, size_t n, int c, float (&v)[N],
+                                       float& spare) {
+  const size_t m = static_cast<size_t>(c) * NN + n;
+  if constexpr (N == 2) {
+    const float2 w = reinterpret_cast<const float2*>(g)[m];
+    v[0] = w.x;
+    v[1] = w.y;
+    spare = 0.0f;
+  } else {
+    const float4 w = reinterpret_cast<const float4*>(g)[m];
+    const float e[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    ph[k] = r[k];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) V[k][c] = r[N + 3 * k + c];
+    for (int q = 0; q < N; ++q) v[q] = e[q];
+    spare = e[3];
   }
 }
 
@@ -258,24 +280,33 @@ template <int N>
 __device__ __forceinline__ void density_node_red(const float* __restrict__ g, const DArgs& a, const Node& p,
                                                  float (&ph)[N], float& rho, float (&tot)[Q3]) {
   const size_t NN = p.NN;
-  const float4* __restrict__ R = reinterpret_cast<const float4*>(g);
-  const float* __restrict__ fd = g + static_cast<size_t>(4 * N) * NN;
+  const float* __restrict__ fd = fd_base3<N>(g, NN);
   float r[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) r[k] = 0.0f;
-  // the 19 pulled f^dagger_i loaded together first, then one source record
-  // per direction (loading several directions' records together was slower)
+  // the pulled f^dagger_i of the float planes loaded together first, then per
+  // direction the source's vector planes (loading several directions' vectors
+  // together was slower)
   float fdv[Q3];
 #pragma unroll
-  for (int i = 0; i < Q3; ++i) fdv[i] = fd[static_cast<size_t>(i) * NN + at(a, p, -cx(i), -cy(i), -cz(i))];
+  for (int i = 0; i < Q3; ++i)
+    if (!in_slot3<N>(i))
+      fdv[i] = fd[static_cast<size_t>(fd_plane3<N>(i)) * NN + at(a, p, -cx(i), -cy(i), -cz(i))];
 #pragma unroll
   for (int i = 0; i < Q3; ++i) {
-    float sp[N], sv[N][3];
-    rec_load<N>(R, at(a, p, -cx(i), -cy(i), -cz(i)), NN, sp, sv);
+    const size_t src = at(a, p, -cx(i), -cy(i), -cz(i));
+    float sp[N], vx[N], vy[N], vz[N], e[4];
+#pragma unroll
+    for (int k = 0; k < N; ++k) vx[k] = vy[k] = vz[k] = 0.0f;
+    cload3<N>(g, NN, src, 0, sp, e[0]);
+    if (cx(i) != 0) cload3<N>(g, NN, src, 1, vx, e[1]);
+    if (cy(i) != 0) cload3<N>(g, NN, src, 2, vy, e[2]);
+    if (cz(i) != 0) cload3<N>(g, NN, src, 3, vz, e[3]);
+    const float fdi = in_slot3<N>(i) ? e[slot3(i) < 0 ? 0 : slot3(i)] : fdv[i];
     float t = 0.0f;
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      const float v = recolour(sp[k], fdv[i], a.wrec[i], edot(i, sv[k][0], sv[k][1], sv[k][2]));
+      const float v = recolour(sp[k], fdi, a.wrec[i], edot(i, vx[k], vy[k], vz[k]));
       r[k] += v;
       t += v;
     }
@@ -451,10 +482,21 @@ __device__ __forceinline__ void collide_store(const DArgs& a, const float (&F)[3
       }
     }
   if constexpr (RED) {
-    rec_store<N>(reinterpret_cast<float4*>(fout), n, NN, ph, V);
-    float* __restrict__ fdo = fout + static_cast<size_t>(4 * N) * NN;
+    float vx[N], vy[N], vz[N];
 #pragma unroll
-    for (int i = 0; i < Q3; ++i) fdo[static_cast<size_t>(i) * NN + n] = fd[i];
+    for (int k = 0; k < N; ++k) {
+      vx[k] = V[k][0];
+      vy[k] = V[k][1];
+      vz[k] = V[k][2];
+    }
+    cstore3<N>(fout, NN, n, 0, ph, fd[0]);
+    cstore3<N>(fout, NN, n, 1, vx, fd[1]);
+    cstore3<N>(fout, NN, n, 2, vy, fd[3]);
+    cstore3<N>(fout, NN, n, 3, vz, fd[5]);
+    float* __restrict__ fdo = fout + static_cast<size_t>(4 * kCW3<N>) * NN;
+#pragma unroll
+    for (int i = 0; i < Q3; ++i)
+      if (!in_slot3<N>(i)) fdo[static_cast<size_t>(fd_plane3<N>(i)) * NN + n] = fd[i];
   } else {
 #pragma unroll
     for (int k = 0; k < N; ++k)
@@ -527,15 +569,19 @@ __global__ void __launch_bounds__(kBX) d_expand_kernel(const float* __restrict__
   Node p;
   if (!node_of(a, &p)) return;
   const size_t NN = p.NN;
-  float ph[N], V[N][3];
-  rec_load<N>(reinterpret_cast<const float4*>(g), p.n, NN, ph, V);
-  const float* __restrict__ fd = g + static_cast<size_t>(4 * N) * NN;
+  float ph[N], vx[N], vy[N], vz[N], e[4];
+  cload3<N>(g, NN, p.n, 0, ph, e[0]);
+  cload3<N>(g, NN, p.n, 1, vx, e[1]);
+  cload3<N>(g, NN, p.n, 2, vy, e[2]);
+  cload3<N>(g, NN, p.n, 3, vz, e[3]);
+  const float* __restrict__ fd = fd_base3<N>(g, NN);
 #pragma unroll
   for (int i = 0; i < Q3; ++i) {
-    const float fdi = fd[static_cast<size_t>(i) * NN + p.n];
+    const float fdi =
+        in_slot3<N>(i) ? e[slot3(i) < 0 ? 0 : slot3(i)] : fd[static_cast<size_t>(fd_plane3<N>(i)) * NN + p.n];
 #pragma unroll
     for (int k = 0; k < N; ++k)
-      f[(static_cast<size_t>(k) * Q3 + i) * NN + p.n] = recolour(ph[k], fdi, a.wrec[i], edot(i, V[k][0], V[k][1], V[k][2]));
+      f[(static_cast<size_t>(k) * Q3 + i) * NN + p.n] = recolour(ph[k], fdi, a.wrec[i], edot(i, vx[k], vy[k], vz[k]));
   }
 }
 
