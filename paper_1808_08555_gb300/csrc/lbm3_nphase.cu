@@ -7,10 +7,13 @@
 //               sum to 1 exactly), the total distribution f_i
 //   tension:    grad phi_k (Eq. fd1), G_kl and C_kl (Eq. 15) for the
 //               N(N-1)/2 pairs, the tension tensor of Eq. 11 summed over the
-//               pairs, the recolouring normals n_kl = G / max(|G|, delta phi_k phi_l)
+//               pairs, the recolouring normals n_kl = G / max(|G|, delta phi_k phi_l),
+//               beta_kl and the recolouring vectors V_k = sum_{l != k} beta_kl
+//               (rho_k rho_l / rho) n_kl (2N values instead of N(N-1) normal
+//               components)
 //   collide:    F_s = div T (Eq. fd1), u (Eq. uk1), tau_f (Eqs. vis_1, tau),
-//               BGK with Guo's forcing (Eqs. 1-3, 5), beta_kl, recolouring
-//               (Eq. 6); f^ddagger stored at the node that produced it
+//               BGK with Guo's forcing (Eqs. 1-3, 5), recolouring (Eq. 6);
+//               f^ddagger stored at the node that produced it
 // beta_kl for N fluids (the paper gives Eqs. 18-20 for three):
 //   beta_kl = beta^0 [1 + sum_{m != k,l} min(35 rho_k rho_l rho_m / rho^3, 1) g(X_kl^m)],
 // with g(X_kl^m) of Eqs. 18 and 20 precomputed on the host; it is Eq. 19
@@ -19,8 +22,8 @@
 //
 // Layout: populations [N][9][ny][nx] FP32, unpadded, periodic by index
 // arithmetic, or the reduced state below; intermediates phi [N][ny][nx], rho
-// [ny][nx], f_i [9][ny][nx], T [3][ny][nx], normals [P][2][ny][nx] with
-// P = N(N-1)/2.
+// [ny][nx], f_i [9][ny][nx], T [3][ny][nx], V [2][N][ny][nx] (x components,
+// then y).
 
 #include <cmath>
 #include <cstdio>
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(kNThreads) n_density_kernel(const float* __res
 template <int N>
 __global__ void __launch_bounds__(kNThreads) n_tension_kernel(const float* __restrict__ phi,
                                                               const float* __restrict__ rho_in, float* __restrict__ T,
-                                                              float* __restrict__ nrm, NArgs a) {
+                                                              float* __restrict__ Vout, NArgs a) {
   const int nx = a.nx, ny = a.ny;
   const size_t NN = static_cast<size_t>(nx) * ny;
   {
@@ -243,6 +246,10 @@ __global__ void __launch_bounds__(kNThreads) n_tension_kernel(const float* __res
     }
     const float rho = rho_in[n];
     float txx = 0.0f, txy = 0.0f, tyy = 0.0f;
+    // V_k = sum_{l != k} beta_kl (rho_k rho_l / rho) n_kl, n_lk = -n_kl
+    float Vx[N], Vy[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) Vx[k] = Vy[k] = 0.0f;
     int q = 0;
 #pragma unroll
     for (int k = 0; k < N; ++k)
@@ -264,12 +271,27 @@ __global__ void __launch_bounds__(kNThreads) n_tension_kernel(const float* __res
           nxv = Gx / den;
           nyv = Gy / den;
         }
-        nrm[(static_cast<size_t>(q) * 2) * NN + n] = nxv;
-        nrm[(static_cast<size_t>(q) * 2 + 1) * NN + n] = nyv;
+        // the segregation parameter of the pair (beta_kl above)
+        float b = 1.0f;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+          if (m == k || m == l) continue;
+          b += fminf(a.beta_A * ph[k] * ph[l] * ph[m], 1.0f) * a.gjunc[q][m];
+        }
+        const float amp = a.beta0 * b * ph[k] * ph[l] * rho;
+        Vx[k] += amp * nxv;
+        Vy[k] += amp * nyv;
+        Vx[l] -= amp * nxv;
+        Vy[l] -= amp * nyv;
       }
     T[n] = txx;
     T[NN + n] = txy;
     T[2 * NN + n] = tyy;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      Vout[static_cast<size_t>(k) * NN + n] = Vx[k];
+      Vout[static_cast<size_t>(N + k) * NN + n] = Vy[k];
+    }
   }
 }
 
@@ -278,7 +300,7 @@ __global__ void __launch_bounds__(kNThreads) n_collide_kernel(const float* __res
                                                               const float* __restrict__ rho_in,
                                                               const float* __restrict__ fi,
                                                               const float* __restrict__ T,
-                                                              const float* __restrict__ nrm, float* __restrict__ fout,
+                                                              const float* __restrict__ Vin, float* __restrict__ fout,
                                                               NArgs a) {
   const int nx = a.nx, ny = a.ny;
   const size_t NN = static_cast<size_t>(nx) * ny;
@@ -329,30 +351,13 @@ __global__ void __launch_bounds__(kNThreads) n_collide_kernel(const float* __res
       const float Phi = wt(i) * g * (cx * Fx + cy * Fy);                               // Eq. 5
       fd[i] = f[i] + om * (feq - f[i]) + Phi;                                          // Eqs. 1, 2
     }
-    // segregation parameters and the recolouring vectors
-    // V_k = sum_{l != k} beta_kl (rho_k rho_l / rho) n_kl, n_lk = -n_kl
+    // the recolouring vectors V_k of the tension kernel
     float Vx[N], Vy[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) Vx[k] = Vy[k] = 0.0f;
-    int q = 0;
-#pragma unroll
-    for (int k = 0; k < N; ++k)
-#pragma unroll
-      for (int l = k + 1; l < N; ++l, ++q) {
-        float b = 1.0f;
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-          if (m == k || m == l) continue;
-          b += fminf(a.beta_A * ph[k] * ph[l] * ph[m], 1.0f) * a.gjunc[q][m];
-        }
-        const float amp = a.beta0 * b * ph[k] * ph[l] * rho;
-        const float nxv = nrm[(static_cast<size_t>(q) * 2) * NN + n];
-        const float nyv = nrm[(static_cast<size_t>(q) * 2 + 1) * NN + n];
-        Vx[k] += amp * nxv;
-        Vy[k] += amp * nyv;
-        Vx[l] -= amp * nxv;
-        Vy[l] -= amp * nyv;
-      }
+    for (int k = 0; k < N; ++k) {
+      Vx[k] = Vin[static_cast<size_t>(k) * NN + n];
+      Vy[k] = Vin[static_cast<size_t>(N + k) * NN + n];
+    }
     // Eq. 6, stored at the node (the next step's pull streams it, Eq. 30), as
     // 9 N populations or as the reduced state
     if constexpr (RED) {
@@ -458,17 +463,17 @@ cudaError_t n_step(const float* fin, float* fout, float* work, const NArgs& a, c
   float* rho = phi + N * NN;
   float* fi = rho + NN;
   float* T = fi + 9 * NN;
-  float* nrm = T + 3 * NN;
+  float* V = T + 3 * NN;
   const dim3 g(static_cast<unsigned>(a.ny), static_cast<unsigned>((a.nx + kNThreads - 1) / kNThreads));
   if (in_red)
     n_density_kernel<N, true><<<g, kNThreads, 0, s>>>(fin, phi, rho, fi, a);
   else
     n_density_kernel<N, false><<<g, kNThreads, 0, s>>>(fin, phi, rho, fi, a);
-  n_tension_kernel<N><<<g, kNThreads, 0, s>>>(phi, rho, T, nrm, a);
+  n_tension_kernel<N><<<g, kNThreads, 0, s>>>(phi, rho, T, V, a);
   if (out_red)
-    n_collide_kernel<N, true><<<g, kNThreads, 0, s>>>(phi, rho, fi, T, nrm, fout, a);
+    n_collide_kernel<N, true><<<g, kNThreads, 0, s>>>(phi, rho, fi, T, V, fout, a);
   else
-    n_collide_kernel<N, false><<<g, kNThreads, 0, s>>>(phi, rho, fi, T, nrm, fout, a);
+    n_collide_kernel<N, false><<<g, kNThreads, 0, s>>>(phi, rho, fi, T, V, fout, a);
   return cudaGetLastError();
 }
 
@@ -480,10 +485,10 @@ cudaError_t n_fields(const float* fin, float* work, double* rho, double* ux, dou
   float* rh = phi + N * NN;
   float* fi = rh + NN;
   float* T = fi + 9 * NN;
-  float* nrm = T + 3 * NN;
+  float* V = T + 3 * NN;
   const dim3 g(static_cast<unsigned>(a.ny), static_cast<unsigned>((a.nx + kNThreads - 1) / kNThreads));
   n_density_kernel<N, RED><<<g, kNThreads, 0, s>>>(fin, phi, rh, fi, a);
-  n_tension_kernel<N><<<g, kNThreads, 0, s>>>(phi, rh, T, nrm, a);
+  n_tension_kernel<N><<<g, kNThreads, 0, s>>>(phi, rh, T, V, a);
   n_fields_kernel<N><<<g, kNThreads, 0, s>>>(phi, rh, fi, T, rho, ux, uy, p, a);
   return cudaGetLastError();
 }
@@ -534,7 +539,7 @@ cudaError_t n_expand_any(int N, const float* g, float* f, const NArgs& a, cudaSt
 // intermediates, rounded up to 64 floats so that the FP64 staging behind them
 // is aligned
 size_t work_floats(int N, size_t NN) {
-  return ((N + 1 + 9 + 3 + static_cast<size_t>(N) * (N - 1)) * NN + 63) / 64 * 64;
+  return ((N + 1 + 9 + 3 + static_cast<size_t>(2) * N) * NN + 63) / 64 * 64;
 }
 
 // stored (post-collision, at the producing node) <-> post-streaming populations
