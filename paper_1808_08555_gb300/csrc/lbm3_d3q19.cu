@@ -82,6 +82,32 @@ __host__ __device__ constexpr int pair3(int k, int l, int n) {  // k < l
 
 __device__ __forceinline__ int wrap3(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
+// Programmatic dependent launch: the step's kernels are launched with
+// programmatic stream serialisation, so a kernel's launch overlaps the tail of
+// the one before it.  Each waits here until its predecessor grid has completed
+// and its writes are visible, then lets its own successor launch.  The wait
+// always ends: the predecessor does not wait on this grid, and a successor
+// starts only once every block of this grid is resident.
+__device__ __forceinline__ void pdl_wait_then_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... K, typename... A>
+cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, dim3 block, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<K>(args)...);
+}
+
 // the node of this thread and the strides of the [nz][ny][nx] planes
 struct Node {
   int x, y, z;
@@ -512,6 +538,7 @@ __device__ __forceinline__ void collide_store(const DArgs& a, const float (&F)[3
 template <int N, bool RED>
 __global__ void __launch_bounds__(kBX) d_density_kernel(const float* __restrict__ f, float4* __restrict__ pr,
                                                         float* __restrict__ fi, DArgs a) {
+  pdl_wait_then_release();
   Node p;
   if (!node_of(a, &p)) return;
   float ph[N], rho, tot[Q3];
@@ -524,6 +551,7 @@ __global__ void __launch_bounds__(kBX) d_density_kernel(const float* __restrict_
 template <int N>
 __global__ void __launch_bounds__(kBX) d_tension_kernel(const float4* __restrict__ pr, float4* __restrict__ T4,
                                                         float2* __restrict__ T2, float* __restrict__ nrm, DArgs a) {
+  pdl_wait_then_release();
   Node p;
   if (!node_of(a, &p)) return;
   const size_t NN = p.NN;
@@ -547,6 +575,7 @@ __global__ void __launch_bounds__(kBX) d_collide_kernel(const float4* __restrict
                                                         const float4* __restrict__ T4, const float2* __restrict__ T2,
                                                         const float* __restrict__ nrm, float* __restrict__ fout,
                                                         DArgs a) {
+  pdl_wait_then_release();
   Node p;
   if (!node_of(a, &p)) return;
   const size_t NN = p.NN;
@@ -667,16 +696,14 @@ cudaError_t d_step(const float* fin, float* fout, float* work, const DArgs& a, c
   const size_t NN = static_cast<size_t>(a.nx) * a.ny * a.nz;
   const Work<N> w(work, NN);
   const dim3 g = grid3(a);
-  if (in_red)
-    d_density_kernel<N, true><<<g, kBX, 0, s>>>(fin, w.pr, w.fi, a);
-  else
-    d_density_kernel<N, false><<<g, kBX, 0, s>>>(fin, w.pr, w.fi, a);
-  d_tension_kernel<N><<<g, kBX, 0, s>>>(w.pr, w.T4, w.T2, w.nrm, a);
-  if (out_red)
-    d_collide_kernel<N, true><<<g, kBX, 0, s>>>(w.pr, w.fi, w.T4, w.T2, w.nrm, fout, a);
-  else
-    d_collide_kernel<N, false><<<g, kBX, 0, s>>>(w.pr, w.fi, w.T4, w.T2, w.nrm, fout, a);
-  return cudaGetLastError();
+  const dim3 b(kBX);
+  cudaError_t e = in_red ? launch_pdl(d_density_kernel<N, true>, g, b, s, fin, w.pr, w.fi, a)
+                         : launch_pdl(d_density_kernel<N, false>, g, b, s, fin, w.pr, w.fi, a);
+  if (e == cudaSuccess) e = launch_pdl(d_tension_kernel<N>, g, b, s, w.pr, w.T4, w.T2, w.nrm, a);
+  if (e == cudaSuccess)
+    e = out_red ? launch_pdl(d_collide_kernel<N, true>, g, b, s, w.pr, w.fi, w.T4, w.T2, w.nrm, fout, a)
+                : launch_pdl(d_collide_kernel<N, false>, g, b, s, w.pr, w.fi, w.T4, w.T2, w.nrm, fout, a);
+  return e;
 }
 
 cudaError_t d_step_any(int N, const float* fin, float* fout, float* work, const DArgs& a, cudaStream_t s,

@@ -59,6 +59,32 @@ __host__ __device__ constexpr int pair_index(int k, int l, int n) {  // k < l
 
 __device__ __forceinline__ int wrapn(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
+// Programmatic dependent launch: the step's kernels are launched with
+// programmatic stream serialisation, so a kernel's launch overlaps the tail of
+// the one before it.  Each waits here until its predecessor grid has completed
+// and its writes are visible, then lets its own successor launch.  The wait
+// always ends: the predecessor does not wait on this grid, and a successor
+// starts only once every block of this grid is resident.
+__device__ __forceinline__ void pdl_wait_then_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... K, typename... A>
+cudaError_t launch_pdl(void (*kernel)(K...), dim3 grid, dim3 block, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<K>(args)...);
+}
+
 // ---------------------------------------------------------- reduced state
 // Collision (Eqs. 1-3, 5) uses only the total distribution and the colour
 // densities, and the recolouring of Eq. 6 writes
@@ -136,6 +162,7 @@ template <int N, bool RED>
 __global__ void __launch_bounds__(kNThreads) n_density_kernel(const float* __restrict__ f, float* __restrict__ phi,
                                                               float* __restrict__ rho_out, float* __restrict__ fi,
                                                               NArgs a) {
+  pdl_wait_then_release();
   const int nx = a.nx, ny = a.ny;
   const size_t NN = static_cast<size_t>(nx) * ny;
   {
@@ -220,6 +247,7 @@ template <int N>
 __global__ void __launch_bounds__(kNThreads) n_tension_kernel(const float* __restrict__ phi,
                                                               const float* __restrict__ rho_in, float* __restrict__ T,
                                                               float* __restrict__ Vout, NArgs a) {
+  pdl_wait_then_release();
   const int nx = a.nx, ny = a.ny;
   const size_t NN = static_cast<size_t>(nx) * ny;
   {
@@ -302,6 +330,7 @@ __global__ void __launch_bounds__(kNThreads) n_collide_kernel(const float* __res
                                                               const float* __restrict__ T,
                                                               const float* __restrict__ Vin, float* __restrict__ fout,
                                                               NArgs a) {
+  pdl_wait_then_release();
   const int nx = a.nx, ny = a.ny;
   const size_t NN = static_cast<size_t>(nx) * ny;
   {
@@ -465,16 +494,14 @@ cudaError_t n_step(const float* fin, float* fout, float* work, const NArgs& a, c
   float* T = fi + 9 * NN;
   float* V = T + 3 * NN;
   const dim3 g(static_cast<unsigned>(a.ny), static_cast<unsigned>((a.nx + kNThreads - 1) / kNThreads));
-  if (in_red)
-    n_density_kernel<N, true><<<g, kNThreads, 0, s>>>(fin, phi, rho, fi, a);
-  else
-    n_density_kernel<N, false><<<g, kNThreads, 0, s>>>(fin, phi, rho, fi, a);
-  n_tension_kernel<N><<<g, kNThreads, 0, s>>>(phi, rho, T, V, a);
-  if (out_red)
-    n_collide_kernel<N, true><<<g, kNThreads, 0, s>>>(phi, rho, fi, T, V, fout, a);
-  else
-    n_collide_kernel<N, false><<<g, kNThreads, 0, s>>>(phi, rho, fi, T, V, fout, a);
-  return cudaGetLastError();
+  const dim3 b(kNThreads);
+  cudaError_t e = in_red ? launch_pdl(n_density_kernel<N, true>, g, b, s, fin, phi, rho, fi, a)
+                         : launch_pdl(n_density_kernel<N, false>, g, b, s, fin, phi, rho, fi, a);
+  if (e == cudaSuccess) e = launch_pdl(n_tension_kernel<N>, g, b, s, phi, rho, T, V, a);
+  if (e == cudaSuccess)
+    e = out_red ? launch_pdl(n_collide_kernel<N, true>, g, b, s, phi, rho, fi, T, V, fout, a)
+                : launch_pdl(n_collide_kernel<N, false>, g, b, s, phi, rho, fi, T, V, fout, a);
+  return e;
 }
 
 template <int N, bool RED>
