@@ -21,9 +21,10 @@
 // per-node array stays in registers.
 //
 // Layout: populations [N][9][ny][nx] FP32, unpadded, periodic by index
-// arithmetic, or the reduced state below; intermediates phi [N][ny][nx], rho
-// [ny][nx], f_i [9][ny][nx], T [3][ny][nx], V [2][N][ny][nx] (x components,
-// then y).
+// arithmetic, or the reduced state below; intermediates: the fractions phi
+// as vector planes (kCK planes [ny][nx] of kCW floats, as a component of the
+// reduced state), rho [ny][nx], f_i [9][ny][nx], T [3][ny][nx], V [2][N][ny][nx]
+// (x components, then y).
 
 #include <cmath>
 #include <cstdio>
@@ -228,15 +229,17 @@ __global__ void __launch_bounds__(kNThreads) n_density_kernel(const float* __res
       }
     }
     const float ir = 1.0f / rho;
-    float rest = 1.0f;
+    float rest = 1.0f, ph[N];
 #pragma unroll
     for (int k = 0; k < N; ++k)
       if (k != kmax) {
-        const float p = r[k] * ir;
-        phi[static_cast<size_t>(k) * NN + n] = p;
-        rest -= p;
+        ph[k] = r[k] * ir;
+        rest -= ph[k];
       }
-    phi[static_cast<size_t>(kmax) * NN + n] = rest;  // the fractions sum to 1 exactly
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      if (k == kmax) ph[k] = rest;  // the fractions sum to 1 exactly
+    comp_store<N>(phi, NN, n, 0, ph);
     rho_out[n] = rho;
 #pragma unroll
     for (int i = 0; i < 9; ++i) fi[static_cast<size_t>(i) * NN + n] = tot[i];
@@ -257,20 +260,21 @@ __global__ void __launch_bounds__(kNThreads) n_tension_kernel(const float* __res
     if (x >= nx) return;
     const size_t n = static_cast<size_t>(y) * nx + x;
     float ph[N], gx[N], gy[N];
+    comp_load<N>(phi, NN, n, 0, ph);
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      ph[k] = phi[static_cast<size_t>(k) * NN + n];
-      float sx = 0.0f, sy = 0.0f;  // Eq. fd1: (1/cs2) sum_i w_i phi(x + e_i) e_i
+    for (int k = 0; k < N; ++k) gx[k] = gy[k] = 0.0f;
+    // Eq. fd1: (1/cs2) sum_i w_i phi(x + e_i) e_i, all colours of a neighbour
+    // from its vectors
 #pragma unroll
-      for (int i = 1; i < 9; ++i) {
-        const float v = phi[static_cast<size_t>(k) * NN + static_cast<size_t>(wrapn(y + ey(i), ny)) * nx +
-                            wrapn(x + ex(i), nx)];
-        const float w3 = 3.0f * (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
-        sx += w3 * ex(i) * v;
-        sy += w3 * ey(i) * v;
+    for (int i = 1; i < 9; ++i) {
+      float v[N];
+      comp_load<N>(phi, NN, static_cast<size_t>(wrapn(y + ey(i), ny)) * nx + wrapn(x + ex(i), nx), 0, v);
+      const float w3 = 3.0f * (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        gx[k] += w3 * ex(i) * v[k];
+        gy[k] += w3 * ey(i) * v[k];
       }
-      gx[k] = sx;
-      gy[k] = sy;
     }
     const float rho = rho_in[n];
     float txx = 0.0f, txy = 0.0f, tyy = 0.0f;
@@ -352,7 +356,7 @@ __global__ void __launch_bounds__(kNThreads) n_collide_kernel(const float* __res
     const float rho = rho_in[n];
     float ph[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) ph[k] = phi[static_cast<size_t>(k) * NN + n];
+    comp_load<N>(phi, NN, n, 0, ph);
     float f[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = fi[static_cast<size_t>(i) * NN + n];
@@ -449,9 +453,10 @@ __global__ void __launch_bounds__(kNThreads) n_fields_kernel(const float* __rest
   const size_t n = static_cast<size_t>(y) * nx + x;
   const float rho = rho_in[n];
   if (rho_out) {
+    float ph[N];
+    comp_load<N>(phi, NN, n, 0, ph);
 #pragma unroll
-    for (int k = 0; k < N; ++k)
-      rho_out[static_cast<size_t>(k) * NN + n] = static_cast<double>(phi[static_cast<size_t>(k) * NN + n] * rho);
+    for (int k = 0; k < N; ++k) rho_out[static_cast<size_t>(k) * NN + n] = static_cast<double>(ph[k] * rho);
   }
   if (ux_out || uy_out) {
     float Fx = 0.0f, Fy = 0.0f;
@@ -488,8 +493,8 @@ template <int N>
 cudaError_t n_step(const float* fin, float* fout, float* work, const NArgs& a, cudaStream_t s, bool in_red,
                    bool out_red) {
   const size_t NN = static_cast<size_t>(a.nx) * a.ny;
-  float* phi = work;
-  float* rho = phi + N * NN;
+  float* phi = work;  // kCK vector planes of kCW floats
+  float* rho = phi + kRedVec<N> / 3 * NN;
   float* fi = rho + NN;
   float* T = fi + 9 * NN;
   float* V = T + 3 * NN;
@@ -509,7 +514,7 @@ cudaError_t n_fields(const float* fin, float* work, double* rho, double* ux, dou
                      cudaStream_t s) {
   const size_t NN = static_cast<size_t>(a.nx) * a.ny;
   float* phi = work;
-  float* rh = phi + N * NN;
+  float* rh = phi + kRedVec<N> / 3 * NN;
   float* fi = rh + NN;
   float* T = fi + 9 * NN;
   float* V = T + 3 * NN;
@@ -566,7 +571,8 @@ cudaError_t n_expand_any(int N, const float* g, float* f, const NArgs& a, cudaSt
 // intermediates, rounded up to 64 floats so that the FP64 staging behind them
 // is aligned
 size_t work_floats(int N, size_t NN) {
-  return ((N + 1 + 9 + 3 + static_cast<size_t>(2) * N) * NN + 63) / 64 * 64;
+  const size_t phiv = N <= 2 ? 2 : (N <= 4 ? 4 : 8);  // the fractions as vectors of 2 or 4 floats
+  return ((phiv + 1 + 9 + 3 + static_cast<size_t>(2) * N) * NN + 63) / 64 * 64;
 }
 
 // stored (post-collision, at the producing node) <-> post-streaming populations
