@@ -21,10 +21,10 @@
 // per-node array stays in registers.
 //
 // Layout: populations [N][9][ny][nx] FP32, unpadded, periodic by index
-// arithmetic, or the reduced state below; intermediates: the fractions phi
-// as vector planes (kCK planes [ny][nx] of kCW floats, as a component of the
-// reduced state), rho [ny][nx], f_i [9][ny][nx], T [3][ny][nx], V [2][N][ny][nx]
-// (x components, then y).
+// arithmetic, or the reduced state below; intermediates: the tension tensor
+// as one float4 (xx, xy, yy, 0) per node, the fractions phi as vector planes
+// (kCK planes [ny][nx] of kCW floats, as a component of the reduced state),
+// rho [ny][nx], f_i [9][ny][nx], V [2][N][ny][nx] (x components, then y).
 
 #include <cmath>
 #include <cstdio>
@@ -248,7 +248,7 @@ __global__ void __launch_bounds__(kNThreads) n_density_kernel(const float* __res
 
 template <int N>
 __global__ void __launch_bounds__(kNThreads) n_tension_kernel(const float* __restrict__ phi,
-                                                              const float* __restrict__ rho_in, float* __restrict__ T,
+                                                              const float* __restrict__ rho_in, float4* __restrict__ T,
                                                               float* __restrict__ Vout, NArgs a) {
   pdl_wait_then_release();
   const int nx = a.nx, ny = a.ny;
@@ -316,9 +316,7 @@ __global__ void __launch_bounds__(kNThreads) n_tension_kernel(const float* __res
         Vx[l] -= amp * nxv;
         Vy[l] -= amp * nyv;
       }
-    T[n] = txx;
-    T[NN + n] = txy;
-    T[2 * NN + n] = tyy;
+    T[n] = make_float4(txx, txy, tyy, 0.0f);
 #pragma unroll
     for (int k = 0; k < N; ++k) {
       Vout[static_cast<size_t>(k) * NN + n] = Vx[k];
@@ -331,7 +329,7 @@ template <int N, bool RED>
 __global__ void __launch_bounds__(kNThreads) n_collide_kernel(const float* __restrict__ phi,
                                                               const float* __restrict__ rho_in,
                                                               const float* __restrict__ fi,
-                                                              const float* __restrict__ T,
+                                                              const float4* __restrict__ T,
                                                               const float* __restrict__ Vin, float* __restrict__ fout,
                                                               NArgs a) {
   pdl_wait_then_release();
@@ -349,13 +347,13 @@ __global__ void __launch_bounds__(kNThreads) n_collide_kernel(const float* __res
     for (int i = 1; i < 9; ++i) {
       const size_t m = static_cast<size_t>(wrapn(y + ey(i), ny)) * nx + wrapn(x + ex(i), nx);
       const float w3 = 3.0f * (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
-      const float txx = T[m], txy = T[NN + m], tyy = T[2 * NN + m];
+      const float4 t = T[m];
+      const float txx = t.x, txy = t.y, tyy = t.z;
       Fx += w3 * (ex(i) * txx + ey(i) * txy);
       Fy += w3 * (ex(i) * txy + ey(i) * tyy);
     }
     const float rho = rho_in[n];
     float ph[N];
-#pragma unroll
     comp_load<N>(phi, NN, n, 0, ph);
     float f[9];
 #pragma unroll
@@ -442,7 +440,7 @@ template <int N>
 __global__ void __launch_bounds__(kNThreads) n_fields_kernel(const float* __restrict__ phi,
                                                              const float* __restrict__ rho_in,
                                                              const float* __restrict__ fi,
-                                                             const float* __restrict__ T, double* __restrict__ rho_out,
+                                                             const float4* __restrict__ T, double* __restrict__ rho_out,
                                                              double* __restrict__ ux_out, double* __restrict__ uy_out,
                                                              double* __restrict__ p_out, NArgs a) {
   const int nx = a.nx, ny = a.ny;
@@ -464,7 +462,8 @@ __global__ void __launch_bounds__(kNThreads) n_fields_kernel(const float* __rest
     for (int i = 1; i < 9; ++i) {
       const size_t m = static_cast<size_t>(wrapn(y + ey(i), ny)) * nx + wrapn(x + ex(i), nx);
       const float w3 = 3.0f * (i < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
-      const float txx = T[m], txy = T[NN + m], tyy = T[2 * NN + m];
+      const float4 t = T[m];
+      const float txx = t.x, txy = t.y, tyy = t.z;
       Fx += w3 * (ex(i) * txx + ey(i) * txy);
       Fy += w3 * (ex(i) * txy + ey(i) * tyy);
     }
@@ -493,11 +492,13 @@ template <int N>
 cudaError_t n_step(const float* fin, float* fout, float* work, const NArgs& a, cudaStream_t s, bool in_red,
                    bool out_red) {
   const size_t NN = static_cast<size_t>(a.nx) * a.ny;
-  float* phi = work;  // kCK vector planes of kCW floats
+  // the tension tensor first (one float4 per node), then the fractions (kCK
+  // vector planes of kCW floats), so that both are aligned for vector access
+  float4* T = reinterpret_cast<float4*>(work);
+  float* phi = work + 4 * NN;
   float* rho = phi + kRedVec<N> / 3 * NN;
   float* fi = rho + NN;
-  float* T = fi + 9 * NN;
-  float* V = T + 3 * NN;
+  float* V = fi + 9 * NN;
   const dim3 g(static_cast<unsigned>(a.ny), static_cast<unsigned>((a.nx + kNThreads - 1) / kNThreads));
   const dim3 b(kNThreads);
   cudaError_t e = in_red ? launch_pdl(n_density_kernel<N, true>, g, b, s, fin, phi, rho, fi, a)
@@ -513,11 +514,11 @@ template <int N, bool RED>
 cudaError_t n_fields(const float* fin, float* work, double* rho, double* ux, double* uy, double* p, const NArgs& a,
                      cudaStream_t s) {
   const size_t NN = static_cast<size_t>(a.nx) * a.ny;
-  float* phi = work;
+  float4* T = reinterpret_cast<float4*>(work);
+  float* phi = work + 4 * NN;
   float* rh = phi + kRedVec<N> / 3 * NN;
   float* fi = rh + NN;
-  float* T = fi + 9 * NN;
-  float* V = T + 3 * NN;
+  float* V = fi + 9 * NN;
   const dim3 g(static_cast<unsigned>(a.ny), static_cast<unsigned>((a.nx + kNThreads - 1) / kNThreads));
   n_density_kernel<N, RED><<<g, kNThreads, 0, s>>>(fin, phi, rh, fi, a);
   n_tension_kernel<N><<<g, kNThreads, 0, s>>>(phi, rh, T, V, a);
@@ -572,7 +573,7 @@ cudaError_t n_expand_any(int N, const float* g, float* f, const NArgs& a, cudaSt
 // is aligned
 size_t work_floats(int N, size_t NN) {
   const size_t phiv = N <= 2 ? 2 : (N <= 4 ? 4 : 8);  // the fractions as vectors of 2 or 4 floats
-  return ((phiv + 1 + 9 + 3 + static_cast<size_t>(2) * N) * NN + 63) / 64 * 64;
+  return ((4 + phiv + 1 + 9 + static_cast<size_t>(2) * N) * NN + 63) / 64 * 64;
 }
 
 // stored (post-collision, at the producing node) <-> post-streaming populations
