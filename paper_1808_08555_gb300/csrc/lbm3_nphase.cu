@@ -41,7 +41,7 @@ namespace {
 
 constexpr int kMaxFluids = 6;
 constexpr int kMaxPairs = kMaxFluids * (kMaxFluids - 1) / 2;
-constexpr int kNThreads = 256;
+constexpr int kNThreads = 128;
 
 struct NArgs {
   int nx, ny;
@@ -207,13 +207,17 @@ __global__ void __launch_bounds__(kNThreads) n_density_kernel(const float* __res
       for (int i = 0; i < 9; ++i) tot[i] = 0.0f;
 #pragma unroll
       for (int k = 0; k < N; ++k) {
+        // a colour's 9 pulled values (Eq. 30) loaded together, then summed
+        float v[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+          v[i] = f[(static_cast<size_t>(k) * 9 + i) * NN + static_cast<size_t>(wrapn(y - ey(i), ny)) * nx +
+                   wrapn(x - ex(i), nx)];
         float s = 0.0f;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-          const size_t src = static_cast<size_t>(wrapn(y - ey(i), ny)) * nx + wrapn(x - ex(i), nx);
-          const float v = f[(static_cast<size_t>(k) * 9 + i) * NN + src];  // Eq. 30 as a pull
-          s += v;
-          tot[i] += v;
+          s += v[i];
+          tot[i] += v[i];
         }
         r[k] = s;
       }
