@@ -380,7 +380,8 @@ lbm3_status lbm3_mass_noalloc(const float* dev_f, int32_t nx, int32_t ny, void* 
  * post-streaming) as for the three-fluid calls; the state is FP32.  Any
  * invalid parameter gives LBM3_EINVAL from lbm3n_create.  The context
  * allocates its two population buffers, the intermediates
- * ((3 N + 13) nx ny floats) and an FP64 staging area.
+ * ((14 + v + 2 N) nx ny floats, v = 2 for N = 2, 4 for N = 3, 4 and 8
+ * for N = 5, 6) and an FP64 staging area.
  * storage LBM3_REDUCED keeps, per node, the colour fractions phi_k, the
  * recolouring vectors V_k and the post-collision total distribution
  * f^dagger_i (3 N + 9 values instead of 9 N, in the same buffers), as
