@@ -85,15 +85,17 @@ def test_random_state_one_step(L, n, beta_form, recolor_form, delta):
 
 
 @pytest.mark.parametrize("n", [2, 3, 4])
-@pytest.mark.parametrize("beta_form,recolor_form,delta", [(0, 0, 0.1), (1, 1, 0.0)])
-def test_reduced_state_is_bit_identical(L, n, beta_form, recolor_form, delta):
+@pytest.mark.parametrize("beta_form,recolor_form,delta,dims", [(0, 0, 0.1, (150, 6, 5)), (1, 1, 0.0, (150, 6, 5)),
+                                                                (0, 0, 0.1, (131, 5, 3))])
+def test_reduced_state_is_bit_identical(L, n, beta_form, recolor_form, delta, dims):
     """The reduced state (phi_k, f^dagger_i, V_k per node) rebuilds every
     population from its source node with the operations the population form
     stores it with, so both forms give the same bits: populations, masses and
-    fields after 1, 7 and 12 steps of random states on a grid with a ragged
-    128-thread block (150 x 6 x 5), readouts in between (which expand the
-    state into the idle buffer) leaving the trajectory unchanged."""
-    nx, ny, nz = 150, 6, 5
+    fields after 1, 7 and 12 steps of random states on grids with a ragged
+    128-thread block (150 x 6 x 5, and 131 x 5 x 3 with an odd node count, so
+    that planes start at odd node offsets), readouts in between (which expand
+    the state into the idle buffer) leaving the trajectory unchanged."""
+    nx, ny, nz = dims
     p = D.Params3D(nx, ny, nz, sigma=sigma_of(n), tau=tuple(0.6 + 0.15 * k for k in range(n)), rho0=(1.0,) * n,
                    beta_form=beta_form, recolor_form=recolor_form, normal_delta=delta)
     f0 = f32(W.random_populations_3d(nx, ny, nz, seed=70 + n, n_fluids=n))

@@ -132,17 +132,18 @@ def test_four_fluids_three_droplets_1000_steps(L):
 
 
 @pytest.mark.parametrize("n", [2, 3, 4, 5, 6])
-@pytest.mark.parametrize("beta_form,recolor_form,delta", [(0, 0, 0.1), (1, 1, 0.0)])
-def test_reduced_state_is_bit_identical(L, n, beta_form, recolor_form, delta):
+@pytest.mark.parametrize("beta_form,recolor_form,delta,nx,ny", [(0, 0, 0.1, 300, 6), (1, 1, 0.0, 300, 6),
+                                                                 (0, 0, 0.1, 301, 5)])
+def test_reduced_state_is_bit_identical(L, n, beta_form, recolor_form, delta, nx, ny):
     """The reduced state (phi_k, V_k, f^dagger_i per node, by component)
     rebuilds every population from its source node with the operations the
     population form stores it with, so both forms give the same bits:
     populations, masses and fields after 1, 7 and 12 steps of random states
-    on a 300 x 6 grid (a ragged second block per row), readouts in between
-    (which expand the state into the idle buffer) leaving the trajectory
-    unchanged.  (Parity of the reduced form with the oracle: the 1000-step
-    case above.)"""
-    nx, ny = 300, 6
+    on a 300 x 6 grid (a ragged last block per row) and a 301 x 5 one (an
+    odd node count, so that planes start at odd node offsets), readouts in
+    between (which expand the state into the idle buffer) leaving the
+    trajectory unchanged.  (Parity of the reduced form with the oracle: the
+    1000-step case above.)"""
     p = N.NParams(nx, ny, sigma=sigma_of(n), tau=tuple(0.6 + 0.15 * k for k in range(n)), rho0=(1.0,) * n,
                   beta_form=beta_form, recolor_form=recolor_form, normal_delta=delta)
     f0 = random_state(n, nx, ny, seed=40 + n)
