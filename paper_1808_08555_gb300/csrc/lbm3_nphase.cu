@@ -296,16 +296,17 @@ __global__ void __launch_bounds__(kNThreads) n_tension_kernel(const float* __res
         const float g2 = Gx * Gx + Gy * Gy;
         float nxv = 0.0f, nyv = 0.0f;
         if (g2 > 1e-30f) {
-          const float mag = sqrtf(g2);
+          const float rm = rsqrtf(g2);  // 1/|G|
+          const float mag = g2 * rm;
           const float pp = ph[k] * ph[l];
           const float ck = fminf(a.cpair[q] * pp * rho * rho, 1.0f);  // Eq. 15
-          const float sc = a.sigma[q] * ck / mag;                     // sigma C |G| (I - n n) = sigma C (|G|^2 I - G G)/|G|
+          const float sc = a.sigma[q] * ck * rm;                      // sigma C |G| (I - n n) = sigma C (|G|^2 I - G G)/|G|
           txx += sc * Gy * Gy;
           txy -= sc * Gx * Gy;
           tyy += sc * Gx * Gx;
-          const float den = fmaxf(mag, a.ndelta * pp);
-          nxv = Gx / den;
-          nyv = Gy / den;
+          const float inv = 1.0f / fmaxf(mag, a.ndelta * pp);
+          nxv = Gx * inv;
+          nyv = Gy * inv;
         }
         // the segregation parameter of the pair (beta_kl above)
         float b = 1.0f;
