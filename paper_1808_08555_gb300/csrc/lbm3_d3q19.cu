@@ -386,21 +386,22 @@ __device__ __forceinline__ void tension_node(PhiAt phi_at, const DArgs& a, const
       const float g2 = Gx * Gx + Gy * Gy + Gz * Gz;
       float nv[3] = {0.0f, 0.0f, 0.0f};
       if (g2 > 1e-30f) {
-        const float mag = sqrtf(g2);
+        const float rm = rsqrtf(g2);  // 1/|G|
+        const float mag = g2 * rm;
         const float pp = ph[k] * ph[l];
         const float ck = fminf(a.cpair[q] * pp * rho * rho, 1.0f);  // Eq. 15
         // sigma C |G| (I - n n) = sigma C (|G|^2 I - G G) / |G|
-        const float sc = a.sigma[q] * ck / mag;
+        const float sc = a.sigma[q] * ck * rm;
         txx += sc * (Gy * Gy + Gz * Gz);
         tyy += sc * (Gx * Gx + Gz * Gz);
         tzz += sc * (Gx * Gx + Gy * Gy);
         txy -= sc * Gx * Gy;
         txz -= sc * Gx * Gz;
         tyz -= sc * Gy * Gz;
-        const float den = fmaxf(mag, a.ndelta * pp);
-        nv[0] = Gx / den;
-        nv[1] = Gy / den;
-        nv[2] = Gz / den;
+        const float inv = 1.0f / fmaxf(mag, a.ndelta * pp);
+        nv[0] = Gx * inv;
+        nv[1] = Gy * inv;
+        nv[2] = Gz * inv;
       }
       nrm_out(q, nv[0], nv[1], nv[2]);
     }
